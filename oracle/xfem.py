@@ -1,0 +1,699 @@
+"""FP64 CPU oracle of the X-FFT solver for periodic 3D linear-elastic homogenization.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Every routine restates the method of
+arXiv 2601.02172 in plain NumPy/SciPy, following the paper's order and notation:
+
+* the X-FEM space with modified abs enrichment (Sec. 2.1, eqs. X-FEM_space, enrichedN,
+  levelset, modifiedabsEnrichment) on voxels split into six P1 tetrahedra (Sec. 3, Fig. P16);
+* the internal scaling of the enriched functions (Sec. 2.2, eqs. scaledEnrichedFunction,
+  XFFT_diagonal, L2X), read per degree of freedom;
+* the element matrices and vectors by sub-tetrahedron quadrature with the 4-point degree-2
+  rule (Sec. 3, eqs. Kapp, b, Kapp_q, b_q, Sapp_q) after splitting each cut P1 element along
+  the linearised interface (snap threshold for nodal level-set values, Sec. 3);
+* global assembly (eq. linearSystem_element), the X-FFT block preconditioner
+  ``P = diag(A0_11, I)`` (eqs. scaledPreconditioner, constantCoefficientPreconditioner), the
+  Fourier symbol of ``A0_11`` built from the voxel matrix (eqs. A0Voxel, GreenHermitian), the
+  linear CG of Algorithm 1 with the stopping rule of eqs. stoppingCriterion/convergence;
+* average stress, effective stiffness (stress form and energy form, App. A identity) and the
+  derivative of the effective stiffness with respect to the phase Lame constants and a
+  per-voxel modulus scale (envelope identity of App. A; not in the paper's experiments).
+
+Readings of silent or garbled passages (Kuhn split, sign of the residual, per-DOF scaling,
+snap units, cell-volume normalisation of the stopping rule, ...) are stated where they are used.
+
+Parity pins (tests/test_oracle_*.py): homogeneous cells, the tilted laminate's closed form,
+Voigt/Reuss bounds, symmetry, axis-permutation invariance, PCG = direct solve, dense
+brute-force eigen-analysis on tiny grids, FFT symbol = assembled operator, quadrature
+exactness, sub-tetrahedron volumes, the DOF overhead printed for Hashin's inclusion, finite
+differences and Euler homogeneity of the gradient.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+SQ2 = math.sqrt(2.0)
+# Voigt-Mandel component order (11, 22, 33, 23, 13, 12), shear entries carry sqrt(2).
+MANDEL_PAIRS = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+# Six P1 tetrahedra per voxel: one per permutation (p, q, r) of the axes, with vertices
+# o, o+e_p, o+e_p+e_q, o+(1,1,1) (the split around the main voxel diagonal).
+KUHN_PERMS = tuple(itertools.permutations(range(3)))
+# Node numbering of the voxel corners, matrix Y of Sec. 3 (before eq. GreenHermitian).
+VOXEL_CORNERS = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0],
+                          [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]], dtype=np.int64)
+
+
+def mandel_extraction():
+    """Matrix M (6x9) that maps a displacement gradient H (row-major, H[i,j] = du_i/dx_j) to
+    the Mandel vector of its symmetric part (eq. shapeFunctionGradient)."""
+    M = np.zeros((6, 9))
+    for r, (i, j) in enumerate(MANDEL_PAIRS):
+        if i == j:
+            M[r, 3 * i + j] = 1.0
+        else:
+            M[r, 3 * i + j] = SQ2 / 2.0
+            M[r, 3 * j + i] = SQ2 / 2.0
+    return M
+
+
+_M = mandel_extraction()
+
+
+def iso_stiffness(lam, mu):
+    """Isotropic stiffness lam I(x)I + 2 mu I_sym as a 6x6 Mandel matrix."""
+    m = np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
+    return lam * np.outer(m, m) + 2.0 * mu * np.eye(6)
+
+
+def symgrad_operator(grads):
+    """Symmetric-gradient operator B = M (grad N (x) I_3) of eq. shapeFunctionGradient.
+
+    ``grads`` has shape (..., nf, 3) (scalar gradients of nf shape functions).  Returns
+    (..., 6, 3 nf) with column ``3 a + c`` the Mandel strain of ``N_a e_c``.
+    """
+    grads = np.asarray(grads, dtype=float)
+    nf = grads.shape[-2]
+    lead = grads.shape[:-2]
+    H = np.zeros(lead + (nf, 3, 3, 3))  # [a, c, i, j]: du_i/dx_j for N_a e_c
+    for c in range(3):
+        H[..., :, c, c, :] = grads
+    Hf = H.reshape(lead + (nf, 3, 9))
+    B = np.einsum("rk,...ack->...rac", _M, Hf)
+    return B.reshape(lead + (6, 3 * nf))
+
+
+def quad4():
+    """Symmetric 4-point rule on the reference tetrahedron, exact for quadratics.
+
+    Barycentric points are the permutations of (a, b, b, b) with a = (5 + 3 sqrt5)/20 and
+    b = (5 - sqrt5)/20, equal weights 1/4 (times the volume); the paper's 4-point rule of
+    Shunn and Ham integrates the same quadratic integrands exactly (Sec. 3).
+    """
+    a = (5.0 + 3.0 * math.sqrt(5.0)) / 20.0
+    b = (5.0 - math.sqrt(5.0)) / 20.0
+    bary = np.full((4, 4), b)
+    np.fill_diagonal(bary, a)
+    return bary, np.full(4, 0.25)
+
+
+_QB, _QW = quad4()
+
+
+def tet_volume(P):
+    P = np.asarray(P, dtype=float)
+    return abs(float(np.linalg.det(np.stack([P[1] - P[0], P[2] - P[0], P[3] - P[0]])))) / 6.0
+
+
+def clip_tet(X, L, s):
+    """Sub-tetrahedra covering {x in T : s * L_h(x) >= 0} for the P1 interpolant L_h.
+
+    Generic convex clip (independent of any case table): each face of T is clipped against the
+    half-space, the interface polygon {L_h = 0} is added as one more face, and every boundary
+    triangle is joined to an interior apex.  Returns a list of 4x3 vertex arrays.  This is
+    the subdivision of Sec. 3 (Fig. subdivision) up to how the convex pieces are cut into
+    tetrahedra, which does not change any integral.
+    """
+    X = np.asarray(X, dtype=float)
+    L = np.asarray(L, dtype=float)
+    inside = s * L >= 0.0
+
+    def cross(i, j):
+        t = L[i] / (L[i] - L[j])
+        return X[i] + t * (X[j] - X[i])
+
+    faces = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
+    polys = []
+    for f in faces:
+        poly = []
+        for m in range(3):
+            i, j = f[m], f[(m + 1) % 3]
+            if inside[i]:
+                poly.append(X[i])
+            if L[i] * L[j] < 0.0:
+                poly.append(cross(i, j))
+        if len(poly) >= 3:
+            polys.append(poly)
+    cut = [X[i] for i in range(4) if L[i] == 0.0]
+    for i in range(4):
+        for j in range(i + 1, 4):
+            if L[i] * L[j] < 0.0:
+                cut.append(cross(i, j))
+    if len(cut) >= 3:
+        C = np.array(cut)
+        ctr = C.mean(axis=0)
+        # plane normal: gradient of L_h
+        J = np.stack([X[1] - X[0], X[2] - X[0], X[3] - X[0]])
+        g = np.linalg.solve(J, L[1:] - L[0])
+        nrm = g / np.linalg.norm(g)
+        u = C[0] - ctr
+        u = u - nrm * (u @ nrm)
+        if np.linalg.norm(u) == 0.0:
+            u = C[1] - ctr
+            u = u - nrm * (u @ nrm)
+        u /= np.linalg.norm(u)
+        v = np.cross(nrm, u)
+        ang = np.arctan2((C - ctr) @ v, (C - ctr) @ u)
+        polys.append([C[k] for k in np.argsort(ang)])
+    verts = [X[i] for i in range(4) if inside[i]]
+    for i in range(4):
+        for j in range(i + 1, 4):
+            if L[i] * L[j] < 0.0:
+                verts.append(cross(i, j))
+    apex = np.mean(np.array(verts), axis=0)
+    out = []
+    for poly in polys:
+        for m in range(1, len(poly) - 1):
+            out.append(np.array([apex, poly[0], poly[m], poly[m + 1]]))
+    return out
+
+
+def classify(L, n, tau):
+    """Cut flags (nvox, 6) and enriched node set of a nodal level set (Sec. 2.1 and Sec. 3):
+    after snapping |L| < tau to 0, a tet is cut iff its vertex values take both signs, and
+    the enriched nodes are all nodes of cut tets."""
+    n = tuple(int(v) for v in n)
+    Ls = np.where(np.abs(L) < tau, 0.0, np.asarray(L, float)).ravel()
+    i, j, k = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij")
+    ijk = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+    cut = np.zeros((ijk.shape[0], 6), bool)
+    nodes_all = []
+    for t, (p, q, r) in enumerate(KUHN_PERMS):
+        off = np.zeros((4, 3), dtype=np.int64)
+        off[1, p] = 1
+        off[2, p] = 1
+        off[2, q] = 1
+        off[3, :] = 1
+        idx = np.stack([((ijk + off[a]) % n) @ np.array([n[1] * n[2], n[2], 1]) for a in range(4)], 1)
+        Lt = Ls[idx]
+        cut[:, t] = (Lt.min(1) < 0) & (Lt.max(1) > 0)
+        nodes_all.append(idx[cut[:, t]])
+    return cut, np.unique(np.concatenate(nodes_all).ravel())
+
+
+class XFEM:
+    """The discrete X-FFT cell problem of one microstructure.
+
+    Parameters
+    ----------
+    L : nodal level set, shape ``n`` (C order), ``L < 0`` = phase "minus".
+    n : voxels per axis (N1, N2, N3); length: cell edge lengths.
+    lame_minus, lame_plus : (lambda, mu) of the ``L < 0`` and ``L > 0`` phases.
+    scale : optional per-voxel modulus scale s_v (shape ``n``); C = s_v C_phase.
+    tau : snap threshold; nodal values with |L| < tau become 0 (Sec. 3: "below 1e-6").
+          Default ``1e-6 * min(h)`` (the paper's absolute 1e-6 at its N = 16, h ~ 1 um scale).
+
+    DOF numbering (shared with nothing; chosen to make comparisons easy): standard DOF
+    (node n, component c) -> ``c * nFE + n``; scaled enriched DOF (enriched id j, component
+    c) -> ``3 nFE + c * nX + j``; enriched ids follow increasing node index.
+    """
+
+    def __init__(self, L, n, length=(1.0, 1.0, 1.0), lame_minus=(1.0, 1.0),
+                 lame_plus=(1.0, 1.0), scale=None, tau=None):
+        self.n = tuple(int(v) for v in n)
+        self.length = tuple(float(v) for v in length)
+        self.h = np.array([self.length[a] / self.n[a] for a in range(3)])
+        self.nFE = int(np.prod(self.n))
+        self.nvox = self.nFE
+        self.volY = float(np.prod(self.length))
+        self.tau = 1e-6 * float(np.min(self.h)) if tau is None else float(tau)
+        L = np.asarray(L, dtype=float).reshape(self.n)
+        self.L = np.where(np.abs(L) < self.tau, 0.0, L).ravel()
+        self.lame = {-1: tuple(map(float, lame_minus)), +1: tuple(map(float, lame_plus))}
+        self.scale = (np.ones(self.nvox) if scale is None
+                      else np.asarray(scale, dtype=np.float64).ravel().copy())
+        self._geometry()
+        self._classify()
+        self._cut_quadrature()
+        self.ndof = 3 * (self.nFE + self.nX)
+
+    # ------------------------------------------------------------------ geometry
+    def node_index(self, ijk):
+        ijk = np.asarray(ijk) % np.asarray(self.n)
+        return (ijk[..., 0] * self.n[1] + ijk[..., 1]) * self.n[2] + ijk[..., 2]
+
+    def _geometry(self):
+        n = self.n
+        i, j, k = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij")
+        self.vox_ijk = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+        self.tet_offsets = []
+        self.tet_grads = []
+        self.tet_vol = []
+        nodes = np.zeros((self.nvox, 6, 4), dtype=np.int64)
+        for t, (p, q, r) in enumerate(KUHN_PERMS):
+            off = np.zeros((4, 3), dtype=np.int64)
+            off[1, p] = 1
+            off[2, p] = 1
+            off[2, q] = 1
+            off[3, :] = 1
+            self.tet_offsets.append(off)
+            X = off * self.h
+            J = np.stack([X[1] - X[0], X[2] - X[0], X[3] - X[0]])  # rows: edge vectors
+            Jinv = np.linalg.inv(J)
+            # barycentric N_b (b = 1..3) = (Jinv^T (x - X0))_b ; grad N_b = column b of Jinv
+            G = np.zeros((4, 3))
+            G[1:] = Jinv.T
+            G[0] = -G[1:].sum(axis=0)
+            self.tet_grads.append(G)
+            self.tet_vol.append(abs(np.linalg.det(J)) / 6.0)
+            for a in range(4):
+                nodes[:, t, a] = self.node_index(self.vox_ijk + off[a])
+        self.tet_nodes = nodes
+        self.B_std = [symgrad_operator(G) for G in self.tet_grads]  # 6 x 12 per tet type
+
+    def _classify(self):
+        Lt = self.L[self.tet_nodes]  # (nvox, 6, 4)
+        self.cut = (Lt.min(axis=2) < 0.0) & (Lt.max(axis=2) > 0.0)
+        # phase of an uncut tet: minus if some vertex is negative, else plus (a tet whose
+        # vertices are all 0 lies on the interface; it gets the plus phase)
+        self.tet_phase = np.where((Lt < 0.0).any(axis=2), -1, 1)
+        J = np.unique(self.tet_nodes[self.cut])
+        self.enr_nodes = J
+        self.nX = int(J.size)
+        self.enr_id = -np.ones(self.nFE, dtype=np.int64)
+        self.enr_id[J] = np.arange(self.nX)
+        cv, ct = np.nonzero(self.cut)
+        self.cut_list = np.stack([cv, ct], axis=1) if cv.size else np.zeros((0, 2), np.int64)
+
+    # ------------------------------------------------------------------ cut elements
+    def _cut_tet_points(self, v, t):
+        """Quadrature data of cut tet (v, t): per side, points' barycentric coordinates and
+        weights, for the sub-tetrahedra of the linearised interface (Sec. 3)."""
+        off = self.tet_offsets[t]
+        X = off * self.h
+        Lv = self.L[self.tet_nodes[v, t]]
+        J = np.stack([X[1] - X[0], X[2] - X[0], X[3] - X[0]])
+        Jinv = np.linalg.inv(J)
+        sides = {}
+        for s in (+1, -1):
+            bary, wts = [], []
+            for P in clip_tet(X, Lv, s):
+                vol = tet_volume(P)
+                pts = _QB @ P  # (4, 3)
+                lam = (pts - X[0]) @ Jinv  # barycentric 1..3
+                b = np.concatenate([1.0 - lam.sum(axis=1, keepdims=True), lam], axis=1)
+                bary.append(b)
+                wts.append(_QW * vol)
+            sides[s] = (np.concatenate(bary), np.concatenate(wts))
+        return Lv, sides
+
+    def _enriched_B(self, G, Lv, s, bary):
+        """Unscaled symmetric gradients of the 4 enriched functions N_a rho^m on side s.
+
+        On side s the modified abs enrichment is rho = sum_b N_b (|L_b| - s L_b)
+        (eq. modifiedabsEnrichment with |L_h| = s L_h), so grad(N_a rho) =
+        rho grad N_a + N_a grad rho (eq. enrichedN).  Returns (nq, 6, 12).
+        """
+        coef = np.abs(Lv) - s * Lv
+        rho = bary @ coef  # (nq,)
+        grho = G.T @ coef  # (3,)
+        gX = rho[:, None, None] * G[None, :, :] + bary[:, :, None] * grho[None, None, :]
+        return symgrad_operator(gX)
+
+    def _cut_quadrature(self):
+        """Scaling factors D0 per enriched DOF (eq. XFFT_diagonal, per-DOF reading) and the
+        quadrature data of every cut tet."""
+        self.D = np.zeros((self.nX, 3))
+        self.cut_data = []
+        for v, t in self.cut_list:
+            Lv, sides = self._cut_tet_points(v, t)
+            G = self.tet_grads[t]
+            eids = self.enr_id[self.tet_nodes[v, t]]
+            for s in (+1, -1):
+                bary, w = sides[s]
+                BX = self._enriched_B(G, Lv, s, bary)  # (nq, 6, 12)
+                sq = np.einsum("q,qrk->k", w, BX * BX).reshape(4, 3)
+                for a in range(4):
+                    self.D[eids[a]] += sq[a]
+            self.cut_data.append((Lv, sides))
+        if self.nX and np.any(self.D <= 0.0):
+            raise ValueError("non-positive enrichment scaling factor")
+        self.Dinvsqrt = 1.0 / np.sqrt(self.D) if self.nX else np.zeros((0, 3))
+
+    def _C(self, s, v):
+        lam, mu = self.lame[s]
+        return self.scale[v] * iso_stiffness(lam, mu)
+
+    def cut_element(self, idx):
+        """Scaled element matrix (24x24), stress matrix (6x24, eq. Sapp_q) and DOF indices of
+        the idx-th cut tet; local DOF order: std (3a+c), then enriched (12 + 3a + c)."""
+        v, t = self.cut_list[idx]
+        Lv, sides = self.cut_data[idx]
+        G = self.tet_grads[t]
+        nodes = self.tet_nodes[v, t]
+        eids = self.enr_id[nodes]
+        scale = np.concatenate([np.ones(12), self.Dinvsqrt[eids].ravel()])
+        K = np.zeros((24, 24))
+        S = np.zeros((6, 24))
+        Bs = self.B_std[t]
+        for s in (+1, -1):
+            bary, w = sides[s]
+            BX = self._enriched_B(G, Lv, s, bary)
+            Bf = np.concatenate([np.broadcast_to(Bs, BX.shape), BX], axis=2) * scale
+            C = self._C(s, v)
+            CB = np.matmul(C, Bf)  # (nq, 6, 24)
+            K += np.tensordot(Bf * w[:, None, None], CB, axes=([0, 1], [0, 1]))
+            S += np.tensordot(w, CB, axes=(0, 0))
+        dofs = np.concatenate([
+            (np.arange(3)[None, :] * self.nFE + nodes[:, None]).ravel(),
+            (3 * self.nFE + np.arange(3)[None, :] * self.nX + eids[:, None]).ravel()])
+        return dofs, K, S
+
+    # ------------------------------------------------------------------ assembly
+    def _uncut_blocks(self, ref=False):
+        """Yield (dofs (m,12), K (m,12,12), S (m,6,12), vox (m,)) per tet type for uncut tets
+        (all tets and C = identity when ``ref``: the operator A0_11 of eq.
+        constantCoefficientPreconditioner)."""
+        for t in range(6):
+            mask = np.ones(self.nvox, bool) if ref else ~self.cut[:, t]
+            vox = np.flatnonzero(mask)
+            if vox.size == 0:
+                continue
+            nodes = self.tet_nodes[vox, t]
+            dofs = (np.arange(3)[None, None, :] * self.nFE + nodes[:, :, None]).reshape(-1, 12)
+            B = self.B_std[t]
+            vol = self.tet_vol[t]
+            if ref:
+                K = np.broadcast_to(vol * B.T @ B, (vox.size, 12, 12))
+                S = np.broadcast_to(vol * B, (vox.size, 6, 12))
+            else:
+                ph = self.tet_phase[vox, t]
+                lam = np.where(ph < 0, self.lame[-1][0], self.lame[1][0]) * self.scale[vox]
+                mu = np.where(ph < 0, self.lame[-1][1], self.lame[1][1]) * self.scale[vox]
+                Cl = iso_stiffness(1.0, 0.0)
+                Cm = iso_stiffness(0.0, 1.0)
+                Kl = vol * B.T @ Cl @ B
+                Km = vol * B.T @ Cm @ B
+                K = lam[:, None, None] * Kl + mu[:, None, None] * Km
+                S = vol * (lam[:, None, None] * (Cl @ B) + mu[:, None, None] * (Cm @ B))
+            yield dofs, K, S, vox
+
+    def assemble(self):
+        """Scaled system matrix A (eq. linearSystem via eq. linearSystem_element), the stress
+        operator S (6 x ndof) with sum_e int C B u_e = S u (eq. Sapp_q) and
+        Cbar = sum_e int C (6x6)."""
+        rows, cols, vals = [], [], []
+        Srows, Scols, Svals = [], [], []
+        Cbar = np.zeros((6, 6))
+        for dofs, K, S, vox in self._uncut_blocks():
+            m = dofs.shape[0]
+            rows.append(np.repeat(dofs, 12, axis=1).ravel())
+            cols.append(np.tile(dofs, (1, 12)).ravel())
+            vals.append(K.ravel())
+            Srows.append(np.broadcast_to(np.arange(6)[None, :, None], (m, 6, 12)).ravel())
+            Scols.append(np.broadcast_to(dofs[:, None, :], (m, 6, 12)).ravel())
+            Svals.append(np.ascontiguousarray(S).ravel())
+        for t in range(6):
+            vox = np.flatnonzero(~self.cut[:, t])
+            ph = self.tet_phase[vox, t]
+            for s in (-1, 1):
+                sel = vox[ph == s]
+                Cbar += self.tet_vol[t] * float(self.scale[sel].sum()) * iso_stiffness(*self.lame[s])
+        for idx in range(len(self.cut_list)):
+            dofs, K, S = self.cut_element(idx)
+            rows.append(np.repeat(dofs, 24))
+            cols.append(np.tile(dofs, 24))
+            vals.append(K.ravel())
+            Srows.append(np.repeat(np.arange(6), 24))
+            Scols.append(np.tile(dofs, 6))
+            Svals.append(S.ravel())
+            v, t = self.cut_list[idx]
+            _, sides = self.cut_data[idx]
+            for s in (+1, -1):
+                Cbar += float(sides[s][1].sum()) * self._C(s, v)
+        A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(self.ndof, self.ndof)).tocsr()
+        Sm = sp.coo_matrix((np.concatenate(Svals), (np.concatenate(Srows), np.concatenate(Scols))),
+                           shape=(6, self.ndof)).tocsr()
+        self.A, self.Sm, self.Cbar = A, Sm, Cbar
+        return A, Sm, Cbar
+
+    def assemble_reference(self):
+        """A0_11 = int grad^s N_FE : grad^s N_FE (std DOFs only; eq. constantCoefficientPreconditioner)."""
+        rows, cols, vals = [], [], []
+        for dofs, K, S, vox in self._uncut_blocks(ref=True):
+            rows.append(np.repeat(dofs, 12, axis=1).ravel())
+            cols.append(np.tile(dofs, (1, 12)).ravel())
+            vals.append(np.ascontiguousarray(K).ravel())
+        n3 = 3 * self.nFE
+        A0 = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                           shape=(n3, n3)).tocsr()
+        self.A0 = A0
+        return A0
+
+    def rhs(self, eps):
+        """b = sum_e Lambda_e^T int B^T C eps_bar (eq. b); the same element integral as the
+        stress matrix of eq. Sapp_q, transposed: b = S^T eps_bar."""
+        if not hasattr(self, "Sm"):
+            self.assemble()
+        return np.asarray(self.Sm.T @ np.asarray(eps, dtype=float)).ravel()
+
+    # ------------------------------------------------------------------ solvers
+    def _pinned_lu(self, A, nstd):
+        """Sparse LU of A with the three std DOFs of node 0 removed.  The kernel of A is the
+        translations of the standard part, so a pinned solution shifted to a zero std mean is
+        the solution under the constraint sum_i u_FE^i = 0 (eq. X-FEM_space)."""
+        keep = np.setdiff1d(np.arange(A.shape[0]), np.arange(3) * nstd)
+        lu = spla.splu(A[keep][:, keep].tocsc(), permc_spec="MMD_AT_PLUS_A",
+                       options={"SymmetricMode": True})
+
+        def solve(rhs):
+            x = np.zeros(A.shape[0])
+            x[keep] = lu.solve(rhs[keep])
+            for c in range(3):
+                x[c * nstd:(c + 1) * nstd] -= x[c * nstd:(c + 1) * nstd].mean()
+            return x
+        return solve
+
+    def solve_direct(self, eps):
+        """Solve A u = -b with sum_i u_FE^i = 0 (eqs. discreteFormConti, X-FEM_space) by a
+        sparse direct solve."""
+        if not hasattr(self, "A"):
+            self.assemble()
+        if not hasattr(self, "_Alu"):
+            self._Alu = self._pinned_lu(self.A, self.nFE)
+        return self._Alu(-self.rhs(eps))
+
+    def _green_sparse(self):
+        if not hasattr(self, "_A0lu"):
+            self._A0lu = self._pinned_lu(self.assemble_reference(), self.nFE)
+        return self._A0lu
+
+    def voxel_reference_matrix(self):
+        """A0_11,v (24x24): the six tets' int grad^s N : grad^s N placed on the voxel's corner
+        DOFs (eq. A0Voxel), with corners numbered as in the node table Y (Sec. 3) and DOFs
+        node-major (3 * corner + component).  Uses the true tet volume h1 h2 h3 / 6."""
+        Av = np.zeros((24, 24))
+        corner_of = {tuple(c): k for k, c in enumerate(VOXEL_CORNERS)}
+        for t in range(6):
+            B = self.B_std[t]
+            K = self.tet_vol[t] * B.T @ B
+            idx = []
+            for a in range(4):
+                k = corner_of[tuple(self.tet_offsets[t][a])]
+                idx.extend([3 * k, 3 * k + 1, 3 * k + 2])
+            Av[np.ix_(idx, idx)] += K
+        return Av
+
+    def green_symbol(self):
+        """Hermitian 3x3 matrices Z(xi)^H A0_v Z(xi) for every frequency (eq. GreenHermitian),
+        Z = c(xi) (x) I_3 with c_j = exp(2 pi i sum_k Y_jk xi_k / N_k).  Shape (N1,N2,N3,3,3)."""
+        Av = self.voxel_reference_matrix()
+        n = self.n
+        xi = np.meshgrid(*[np.fft.fftfreq(n[a]) for a in range(3)], indexing="ij")
+        phase = sum(np.multiply.outer(xi[a], VOXEL_CORNERS[:, a]) for a in range(3))
+        c = np.exp(2j * np.pi * phase)  # (N1,N2,N3,8)
+        Z = np.einsum("...j,kl->...jkl", c, np.eye(3)).reshape(n + (24, 3))
+        return np.einsum("...ai,ab,...bj->...ij", Z.conj(), Av, Z)
+
+    def _green_fft(self):
+        Mx = self.green_symbol()
+        Mx[0, 0, 0] = np.eye(3)
+        Minv = np.linalg.inv(Mx)
+        Minv[0, 0, 0] = 0.0
+        n = self.n
+
+        def apply(f):
+            F = np.fft.fftn(f.reshape((3,) + n), axes=(1, 2, 3))
+            G = np.einsum("...ij,j...->i...", Minv, F)
+            return np.real(np.fft.ifftn(G, axes=(1, 2, 3))).ravel()
+        return apply
+
+    def precondition(self, f, green="sparse"):
+        """z = P^{-1} f with P = diag(A0_11, I) (eq. scaledPreconditioner)."""
+        n3 = 3 * self.nFE
+        g = self._green_sparse() if green == "sparse" else self._green_fft()
+        z = np.empty_like(f)
+        z[:n3] = g(f[:n3])
+        z[n3:] = f[n3:]
+        return z
+
+    def mean_stress(self, u, eps):
+        """<sigma>_Y = (1/|Y|) sum_e int C (eps_bar + grad^s u) (reading of eq. Sapp_q)."""
+        if not hasattr(self, "Sm"):
+            self.assemble()
+        return (np.asarray(self.Sm @ u).ravel() + self.Cbar @ np.asarray(eps, float)) / self.volY
+
+    def pcg(self, eps, tol=1e-10, maxit=10000, green="sparse", u0=None):
+        """Linear CG of Algorithm 1 on A u = -b with the X-FFT preconditioner.
+
+        Reading of Algorithm 1: f is the negative residual -b - A u, z = A d is the linear part
+        of the residual map, alpha = res_old^2 / <z, d>, u += alpha d, f -= alpha z, and the
+        loop stops once sqrt(f^T P^{-1} f / |Y|) <= tol ||<sigma(u)>_Y|| (eqs.
+        stoppingCriterion, convergence; the 1/|Y| makes both sides stresses) or after maxit
+        iterations.  Returns (u, info) with iteration count and residual history.
+        """
+        if not hasattr(self, "A"):
+            self.assemble()
+        gfun = self._green_sparse() if green == "sparse" else self._green_fft()
+        n3 = 3 * self.nFE
+
+        def P(f):
+            z = np.empty_like(f)
+            z[:n3] = gfun(f[:n3])
+            z[n3:] = f[n3:]
+            return z
+
+        b = self.rhs(eps)
+        u = np.zeros(self.ndof) if u0 is None else np.array(u0, dtype=float)
+        f = -b - self.A @ u
+        d = P(f)
+        rr = float(f @ d)
+        hist = []
+        k = 0
+        converged = False
+        while True:
+            res = math.sqrt(max(rr, 0.0) / self.volY)
+            sig = np.linalg.norm(self.mean_stress(u, eps))
+            hist.append(res / sig if sig > 0 else res)
+            if res <= tol * sig:
+                converged = True
+                break
+            if k >= maxit:
+                break
+            z = self.A @ d
+            alpha = rr / float(z @ d)
+            u += alpha * d
+            f -= alpha * z
+            zz = P(f)
+            rr_new = float(f @ zz)
+            beta = rr_new / rr
+            d = zz + beta * d
+            rr = rr_new
+            k += 1
+        return u, {"iters": k, "converged": converged, "history": hist}
+
+    # ------------------------------------------------------------------ post-processing
+    def effective_stiffness(self, solver="direct", tol=1e-12, green="sparse"):
+        """C_eff column k = <sigma> for eps_bar = E_k (Mandel basis) and the energy form
+        C_kl = (1/|Y|) int eps_k : C : eps_l.  Returns (C_stress, C_energy, U) with U the
+        6 solution vectors."""
+        if not hasattr(self, "A"):
+            self.assemble()
+        U = []
+        Cs = np.zeros((6, 6))
+        for k in range(6):
+            e = np.eye(6)[k]
+            u = self.solve_direct(e) if solver == "direct" else self.pcg(e, tol=tol, green=green)[0]
+            U.append(u)
+            Cs[:, k] = self.mean_stress(u, e)
+        U = np.array(U)
+        SU = np.asarray(self.Sm @ U.T)  # (6, 6): column l = S u_l
+        AU = np.asarray(self.A @ U.T)
+        Ce = (self.Cbar + SU + SU.T + U @ AU) / self.volY
+        return Cs, Ce, U
+
+    def voxel_stress(self, u, eps):
+        """Per-voxel average stress (1/|v|) int_v C (eps_bar + grad^s u), shape (nvox, 6)."""
+        eps = np.asarray(eps, float)
+        out = np.zeros((self.nvox, 6))
+        for dofs, K, S, vox in self._uncut_blocks():
+            out[vox] += np.einsum("mrk,mk->mr", S, u[dofs])
+        for t in range(6):
+            vox = np.flatnonzero(~self.cut[:, t])
+            ph = self.tet_phase[vox, t]
+            for s in (-1, 1):
+                sel = vox[ph == s]
+                out[sel] += (self.tet_vol[t] * self.scale[sel])[:, None] * (iso_stiffness(*self.lame[s]) @ eps)[None, :]
+        for idx in range(len(self.cut_list)):
+            dofs, K, S = self.cut_element(idx)
+            v, t = self.cut_list[idx]
+            _, sides = self.cut_data[idx]
+            out[v] += S @ u[dofs]
+            for s in (+1, -1):
+                out[v] += float(sides[s][1].sum()) * (self._C(s, v) @ eps)
+        return out / float(np.prod(self.h))
+
+    # ------------------------------------------------------------------ gradient
+    def _strains_uncut(self, U, t, vox):
+        """Mandel strains (nrhs, m, 6) of tet type t in voxels vox for solution vectors U
+        (without the macroscopic part)."""
+        nodes = self.tet_nodes[vox, t]
+        dofs = (np.arange(3)[None, None, :] * self.nFE + nodes[:, :, None]).reshape(-1, 12)
+        return np.einsum("rk,nmk->nmr", self.B_std[t], U[:, dofs])
+
+    def stiffness_gradient(self, U, E=None):
+        """Derivatives of the energy-form C_eff with respect to the phase Lame constants and
+        the per-voxel scale: dC_kl/dtheta = (1/|Y|) int eps_k : dC/dtheta : eps_l with
+        eps_k = E_k + grad^s u_k (envelope identity; the basis does not depend on C).
+
+        Returns (dC_dlame (4,6,6) in order lam_minus, mu_minus, lam_plus, mu_plus;
+        dC_ds (nvox,6,6)).
+        """
+        E = np.eye(6) if E is None else np.asarray(E, float)
+        nr = U.shape[0]
+        Al = {s: np.zeros((self.nvox, nr, nr)) for s in (-1, 1)}  # int tr eps_k tr eps_l
+        Am = {s: np.zeros((self.nvox, nr, nr)) for s in (-1, 1)}  # int 2 eps_k : eps_l
+        m = np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
+        for t in range(6):
+            vox = np.flatnonzero(~self.cut[:, t])
+            if vox.size == 0:
+                continue
+            eps = self._strains_uncut(U, t, vox) + E[:, None, :]  # (nr, m, 6)
+            tr = eps @ m
+            ph = self.tet_phase[vox, t]
+            vol = self.tet_vol[t]
+            al = vol * np.einsum("km,lm->mkl", tr, tr)
+            am = 2.0 * vol * np.einsum("kmr,lmr->mkl", eps, eps)
+            for s in (-1, 1):
+                sel = ph == s
+                np.add.at(Al[s], vox[sel], al[sel])
+                np.add.at(Am[s], vox[sel], am[sel])
+        for idx in range(len(self.cut_list)):
+            v, t = self.cut_list[idx]
+            Lv, sides = self.cut_data[idx]
+            G = self.tet_grads[t]
+            nodes = self.tet_nodes[v, t]
+            eids = self.enr_id[nodes]
+            dofs = np.concatenate([
+                (np.arange(3)[None, :] * self.nFE + nodes[:, None]).ravel(),
+                (3 * self.nFE + np.arange(3)[None, :] * self.nX + eids[:, None]).ravel()])
+            scale = np.concatenate([np.ones(12), self.Dinvsqrt[eids].ravel()])
+            ue = U[:, dofs] * scale  # (nr, 24)
+            for s in (+1, -1):
+                bary, w = sides[s]
+                BX = self._enriched_B(G, Lv, s, bary)
+                Bf = np.concatenate([np.broadcast_to(self.B_std[t], BX.shape), BX], axis=2)
+                eps = np.einsum("qrj,nj->nqr", Bf, ue) + E[:, None, :]
+                tr = eps @ m
+                Al[s][v] += np.einsum("q,kq,lq->kl", w, tr, tr)
+                Am[s][v] += 2.0 * np.einsum("q,kqr,lqr->kl", w, eps, eps)
+        sc = self.scale[:, None, None]
+        dl = np.stack([(sc * Al[-1]).sum(0), (sc * Am[-1]).sum(0) / 1.0,
+                       (sc * Al[1]).sum(0), (sc * Am[1]).sum(0)]) / self.volY
+        ds = (self.lame[-1][0] * Al[-1] + self.lame[-1][1] * Am[-1]
+              + self.lame[1][0] * Al[1] + self.lame[1][1] * Am[1]) / self.volY
+        return dl, ds
+
+    # ------------------------------------------------------------------ local evaluation
+    def apply(self, d, eps=None):
+        """A d (+ b if eps given): the residual map of eq. resVector up to the sign reading."""
+        if not hasattr(self, "A"):
+            self.assemble()
+        out = np.asarray(self.A @ d).ravel()
+        if eps is not None:
+            out += self.rhs(eps)
+        return out
