@@ -1,0 +1,163 @@
+/*
+ * xfft.h -- C-ABI of the GB300 (sm_103a) X-FFT solver for periodic 3D linear-elastic
+ * homogenization with an X-FEM discretization (Gehrig & Schneider, arXiv 2601.02172).
+ *
+ * Problem statement (Sec. 2.1): find the periodic displacement fluctuation u_h in the X-FEM
+ * space V_h (eq. X-FEM_space: standard P1 functions on six tetrahedra per voxel plus enriched
+ * functions N_X^j = N_FE^j rho^m with the modified abs enrichment rho^m, eq.
+ * modifiedabsEnrichment) such that  int_Y grad^s v : C : (eps_bar + grad^s u_h) dV = 0  for
+ * all v in V_h (eq. discreteFormConti), with a mean-free standard part.  The enriched
+ * functions are scaled to unit energy norm (eqs. scaledEnrichedFunction, XFFT_diagonal), and
+ * the system is solved by linear CG (Algorithm 1) preconditioned with
+ * P = diag(A0_11, I) (eq. scaledPreconditioner), A0_11 inverted by FFT (eq. GreenHermitian).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Grid: n[0] x n[1] x n[2] voxels on the cell [0,len[0]] x [0,len[1]] x [0,len[2]]; the
+ *    periodic nodes are indexed  node = (i * n[1] + j) * n[2] + k  (C order, last axis
+ *    fastest).  Voxel v has its lowest corner at node v.  Every n[a] must be even, of the form
+ *    2^a 3^b 5^c, and between 4 and 1024.
+ *  - Strains and stresses are Mandel 6-vectors, order (11, 22, 33, 23, 13, 12) with sqrt(2)
+ *    on the shear entries; a 6x6 stiffness is stored row-major.
+ *  - Phases: L < 0 is the "minus" phase, L > 0 the "plus" phase; each phase is isotropic and
+ *    given by its Lame pair (lambda, mu).  An optional per-voxel factor s_v scales C in voxel v.
+ *  - Field layouts (per right-hand side, contiguous, one RHS after the other):
+ *      standard DOFs  u_std[rhs][c][node]    c = 0..2, node = 0..N-1   (N = n0 n1 n2)
+ *      enriched DOFs  u_enr[rhs][c][j]       j = enriched id 0..nX-1 (increasing node index)
+ *    Enriched values exchanged through this API are the *unscaled* coefficients u_X of
+ *    eq. X-FEM_space (u_X = D^{-1/2} u~_X) unless a function says otherwise.
+ *  - Pointers: every pointer argument is caller-owned.  ptrs_on_device = 1 means all array
+ *    arguments of that call are device pointers (on the context's GPU); 0 means host memory
+ *    (the call copies through pinned staging buffers).  Small fixed-size arguments (Lame
+ *    pairs, eps_bar, C_eff, dL_dCeff, dL_dlame, stats) are always host memory.
+ *  - Streams: all device work is enqueued on the stream given to xfft_create (0 = legacy
+ *    default stream).  Calls that return host results synchronise that stream.
+ *  - Errors: no function aborts, traps or exits; each returns an xfft_status and stores a
+ *    message retrievable with xfft_last_error() (thread-local).  On XFFT_ENOTCONV the outputs
+ *    hold the last iterate.
+ *  - The library allocates its own device workspace with cudaMalloc and frees it in
+ *    xfft_destroy.
+ */
+#ifndef XFFT_H
+#define XFFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xfft_ctx xfft_ctx; /* opaque, library-owned */
+
+typedef enum {
+  XFFT_OK = 0,
+  XFFT_EINVAL = 1,       /* invalid argument (sizes, NULL pointers, unsupported grid) */
+  XFFT_ENOMEM = 2,       /* device or pinned allocation failed */
+  XFFT_ECUDA = 3,        /* a CUDA runtime call failed; see xfft_last_error() */
+  XFFT_ENOTCONV = 4,     /* maxit reached before the stopping rule held */
+  XFFT_EBREAKDOWN = 5,   /* CG breakdown: <A d, d> <= 0 or a NaN/Inf scalar */
+  XFFT_ETIMEOUT = 6,     /* reserved: a bounded device wait gave up */
+  XFFT_EUNSUPPORTED = 7, /* valid request that this build does not implement */
+  XFFT_ESTATE = 8        /* call order violated (e.g. solve before set_microstructure) */
+} xfft_status;
+
+enum { XFFT_FP64 = 0, XFFT_FP32_REFINED = 1 };
+enum { XFFT_ENR_IDENTITY = 0, XFFT_ENR_BLOCK3 = 1 };
+
+typedef struct {
+  int n[3];       /* voxels per axis */
+  double len[3];  /* cell edge lengths */
+} xfft_grid;
+
+typedef struct {
+  int precision;       /* XFFT_FP64 (all FP64) or XFFT_FP32_REFINED (FP32 CG, FP64 residuals) */
+  double tol;          /* stopping rule sqrt(r^T P^-1 r / |Y|) <= tol * ||<sigma>_Y|| (eqs.
+                          stoppingCriterion, convergence) */
+  int maxit;           /* CG iteration cap (FP64) or inner cap per refinement step */
+  double snap_tau;     /* |L| < snap_tau counts as on the interface (Sec. 3); <= 0: 1e-6 * min h */
+  int enr_precond;     /* XFFT_ENR_IDENTITY (the paper's choice) */
+  double inner_tol;    /* FP32_REFINED: relative residual reduction per inner solve */
+  int max_refine;      /* FP32_REFINED: cap on FP64 refinement steps */
+  int poll_every;      /* iterations between host checks of the device convergence flags */
+} xfft_options;
+
+typedef struct {
+  int n_rhs;
+  int iters[64];        /* CG iterations per RHS (sum over refinement steps) */
+  double final_res[64]; /* sqrt(r^T P^-1 r / |Y|) / ||<sigma>|| at exit, per RHS */
+  int refine_steps;     /* FP64 residual evaluations after the first (FP32_REFINED) */
+  int n_fe, n_x, n_cut_tets;
+  double ms_setup, ms_solve;
+} xfft_stats;
+
+/* Fill *opt with the defaults: FP64, tol 1e-10, maxit 10000, snap_tau 0 (=> 1e-6 min h),
+ * identity enriched block, inner_tol 1e-4, max_refine 20, poll_every 8. */
+xfft_status xfft_default_options(xfft_options* opt);
+
+/* Create a context for one grid.  stream: a cudaStream_t (or NULL for the legacy stream).
+ * Uses the current CUDA device.  Errors: EINVAL for an unsupported grid or options. */
+xfft_status xfft_create(xfft_ctx** ctx, const xfft_grid* grid, const xfft_options* opt,
+                        void* stream);
+
+/* Load a microstructure (Sec. 2.1 level set, eq. levelset): nodal level set L (N doubles,
+ * node order), phase Lame pairs, optional per-voxel scale (N floats, voxel order, or NULL).
+ * Runs the setup on the GPU: snapping (Sec. 3), cut-tet classification and enriched-node
+ * numbering (eq. X-FEM_space), per-side sub-tetrahedron moments of every cut tet (Sec. 3,
+ * Fig. subdivision), the scaling factors D0 (eq. XFFT_diagonal, per DOF).
+ * Errors: EINVAL (NULL L, non-positive mu), ECUDA, ENOMEM. */
+xfft_status xfft_set_microstructure(xfft_ctx* ctx, const double* L, const double lame_minus[2],
+                                    const double lame_plus[2], const float* voxel_scale,
+                                    int ptrs_on_device);
+
+/* Solve the cell problem for n_rhs (1..64) macroscopic strains eps_bar (n_rhs x 6 Mandel,
+ * host).  Outputs (each may be NULL): u_std (n_rhs x 3 x N), u_enr (n_rhs x 3 x nX, unscaled
+ * u_X), voxel_stress (n_rhs x 6 x N: per-voxel average stress, voxel order),
+ * mean_stress (n_rhs x 6, host: <sigma>_Y).  The solution is kept in the context (for
+ * xfft_grad).  Returns ENOTCONV if some RHS hit maxit (outputs hold the last iterate). */
+xfft_status xfft_solve(xfft_ctx* ctx, int n_rhs, const double* eps_bar, double* u_std,
+                       double* u_enr, double* voxel_stress, double* mean_stress,
+                       xfft_stats* stats, int ptrs_on_device);
+
+/* Solve the six unit Mandel load cases and return the 6x6 effective stiffness (row-major,
+ * C_eff[i*6+k] = <sigma_i> for eps_bar = E_k; Sec. 4.1 relation of <sigma> and C_eff).
+ * The six converged fields stay in the context as the checkpoint for xfft_grad. */
+xfft_status xfft_effective_stiffness(xfft_ctx* ctx, double C_eff[36], xfft_stats* stats);
+
+/* Gradient of a scalar loss through C_eff: given G = dLoss/dC_eff (6x6 row-major, host),
+ * return dLoss/d(lambda_minus, mu_minus, lambda_plus, mu_plus) in dL_dlame[4] (host) and,
+ * if dL_dscale != NULL, dLoss/ds_v (N floats, voxel order).  Uses the envelope identity
+ * dC_kl/dtheta = (1/|Y|) int eps_k : dC/dtheta : eps_l on the six checkpointed load cases
+ * of the last xfft_effective_stiffness call (not in the paper; App. A gives the identity's
+ * ingredients).  C_energy (36, host, may be NULL) receives the energy-form C_eff.
+ * Errors: ESTATE if no six-case solve is stored. */
+xfft_status xfft_grad(xfft_ctx* ctx, const double dL_dCeff[36], double dL_dlame[4],
+                      float* dL_dscale, double C_energy[36], int ptrs_on_device);
+
+/* Step-level entry points (each is one piece of Algorithm 1 and is what the parity tests
+ * call).  Vectors here use the *scaled* enriched coefficients u~_X of eq. scaledEnrichedU and
+ * the full DOF layout [std (3N) | enr (3 nX)] per RHS.
+ *   xfft_apply:        q = A d  (+ b(eps_bar) when eps_bar != NULL), i.e. the residual map of
+ *                      eq. resVector with the sign of eq. linearSystem; also returns, per RHS,
+ *                      int_Y C (eps_bar + grad^s d) in sigma_int (n_rhs x 6, host, may be NULL).
+ *   xfft_precondition: z = P^{-1} f with P = diag(A0_11, I) (eqs. scaledPreconditioner,
+ *                      GreenHermitian); the standard part of f must have zero mean per
+ *                      component.  rr (n_rhs, host, may be NULL) receives f^T z.
+ * precision: XFFT_FP64 or 1 for the FP32 kernels (inputs and outputs stay double). */
+xfft_status xfft_apply(xfft_ctx* ctx, int n_rhs, const double* d, const double* eps_bar,
+                       double* q, double* sigma_int, int precision, int ptrs_on_device);
+xfft_status xfft_precondition(xfft_ctx* ctx, int n_rhs, const double* f, double* z,
+                              double* rr, int precision, int ptrs_on_device);
+
+/* Setup results for inspection: enr_nodes (nX ints), D0 (nX x 3 doubles, eq. XFFT_diagonal
+ * per DOF), tet_code (N uint16: 2 bits per Kuhn tet t = 0..5 in itertools.permutations order
+ * of the axes: 0 = minus phase, 1 = plus phase, 2 = cut).  Host pointers; each may be NULL. */
+xfft_status xfft_get_setup(xfft_ctx* ctx, int* enr_nodes, double* D0, unsigned short* tet_code);
+
+int xfft_num_enriched(const xfft_ctx* ctx);   /* nX, or -1 before set_microstructure */
+int xfft_num_cut_tets(const xfft_ctx* ctx);   /* number of cut tetrahedra, or -1 */
+const char* xfft_status_string(xfft_status s);
+const char* xfft_last_error(void);
+void xfft_destroy(xfft_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XFFT_H */

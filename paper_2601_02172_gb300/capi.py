@@ -1,0 +1,268 @@
+"""ctypes binding of libxfft (include/xfft.h): argument marshalling only.
+
+Every computation runs in the CUDA library; if ``libxfft.so`` cannot be loaded the import of
+:func:`lib` raises, there is no fallback.  Arrays may be NumPy arrays (host memory) or torch
+CUDA tensors (device memory); one call uses one kind for all of its arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libxfft.so")
+
+XFFT_OK, XFFT_EINVAL, XFFT_ENOMEM, XFFT_ECUDA, XFFT_ENOTCONV, XFFT_EBREAKDOWN, XFFT_ETIMEOUT, \
+    XFFT_EUNSUPPORTED, XFFT_ESTATE = range(9)
+XFFT_FP64, XFFT_FP32_REFINED = 0, 1
+
+EXPORTED = (
+    "xfft_default_options", "xfft_create", "xfft_set_microstructure", "xfft_solve",
+    "xfft_effective_stiffness", "xfft_grad", "xfft_apply", "xfft_precondition", "xfft_get_setup",
+    "xfft_num_enriched", "xfft_num_cut_tets", "xfft_status_string", "xfft_last_error",
+    "xfft_destroy",
+)
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("len", C.c_double * 3)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
+                ("snap_tau", C.c_double), ("enr_precond", C.c_int), ("inner_tol", C.c_double),
+                ("max_refine", C.c_int), ("poll_every", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_rhs", C.c_int), ("iters", C.c_int * 64), ("final_res", C.c_double * 64),
+                ("refine_steps", C.c_int), ("n_fe", C.c_int), ("n_x", C.c_int),
+                ("n_cut_tets", C.c_int), ("ms_setup", C.c_double), ("ms_solve", C.c_double)]
+
+    def to_dict(self):
+        k = self.n_rhs
+        return {"iters": list(self.iters[:k]), "final_res": list(self.final_res[:k]),
+                "refine_steps": self.refine_steps, "n_fe": self.n_fe, "n_x": self.n_x,
+                "n_cut_tets": self.n_cut_tets, "ms_setup": self.ms_setup, "ms_solve": self.ms_solve}
+
+
+_lib = None
+
+
+def lib():
+    """Load libxfft.so (raises OSError/RuntimeError when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libxfft.so is not built; run paper_2601_02172_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    L.xfft_default_options.argtypes = [C.POINTER(Options)]
+    L.xfft_create.argtypes = [C.POINTER(vp), C.POINTER(Grid), C.POINTER(Options), vp]
+    L.xfft_set_microstructure.argtypes = [vp, vp, C.POINTER(d), C.POINTER(d), vp, i]
+    L.xfft_solve.argtypes = [vp, i, C.POINTER(d), vp, vp, vp, C.POINTER(d), C.POINTER(Stats), i]
+    L.xfft_effective_stiffness.argtypes = [vp, C.POINTER(d), C.POINTER(Stats)]
+    L.xfft_grad.argtypes = [vp, C.POINTER(d), C.POINTER(d), vp, C.POINTER(d), i]
+    L.xfft_apply.argtypes = [vp, i, vp, C.POINTER(d), vp, C.POINTER(d), i, i]
+    L.xfft_precondition.argtypes = [vp, i, vp, vp, C.POINTER(d), i, i]
+    L.xfft_get_setup.argtypes = [vp, vp, vp, vp]
+    L.xfft_num_enriched.argtypes = [vp]
+    L.xfft_num_cut_tets.argtypes = [vp]
+    L.xfft_status_string.argtypes = [i]
+    L.xfft_status_string.restype = C.c_char_p
+    L.xfft_last_error.restype = C.c_char_p
+    L.xfft_destroy.argtypes = [vp]
+    L.xfft_destroy.restype = None
+    for name in ("xfft_default_options", "xfft_create", "xfft_set_microstructure", "xfft_solve",
+                 "xfft_effective_stiffness", "xfft_grad", "xfft_apply", "xfft_precondition",
+                 "xfft_get_setup", "xfft_num_enriched", "xfft_num_cut_tets"):
+        getattr(L, name).restype = i
+    _lib = L
+    return L
+
+
+class XfftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (lib().xfft_status_string(status).decode(), msg))
+        self.status = status
+
+
+def check(status, allow=()):
+    if status != XFFT_OK and status not in allow:
+        raise XfftError(status, lib().xfft_last_error().decode())
+    return status
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """Pointer of a contiguous array of the given NumPy dtype (host) or torch CUDA tensor."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        want = {np.float64: torch.float64, np.float32: torch.float32}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError("tensor must be contiguous %s" % want)
+        return C.c_void_p(x.data_ptr()), bool(x.is_cuda)
+    if not (isinstance(x, np.ndarray) and x.dtype == dtype and x.flags.c_contiguous):
+        raise TypeError("array must be a C-contiguous %s ndarray" % np.dtype(dtype).name)
+    return C.c_void_p(x.ctypes.data), False
+
+
+def _dvec(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Solver:
+    """One grid on the current CUDA device (thin wrapper of ``xfft_ctx``)."""
+
+    def __init__(self, n, length=(1.0, 1.0, 1.0), precision="fp64", tol=1e-10, maxit=10000,
+                 snap_tau=0.0, inner_tol=1e-4, max_refine=20, poll_every=8, stream=None):
+        L = lib()
+        self.n = tuple(int(v) for v in n)
+        self.length = tuple(float(v) for v in length)
+        self.N = int(np.prod(self.n))
+        g = Grid()
+        for a in range(3):
+            g.n[a] = self.n[a]
+            g.len[a] = self.length[a]
+        o = Options()
+        L.xfft_default_options(C.byref(o))
+        o.precision = XFFT_FP64 if precision == "fp64" else XFFT_FP32_REFINED
+        o.tol = tol
+        o.maxit = maxit
+        o.snap_tau = snap_tau
+        o.inner_tol = inner_tol
+        o.max_refine = max_refine
+        o.poll_every = poll_every
+        self.precision = precision
+        self._ctx = C.c_void_p()
+        check(L.xfft_create(C.byref(self._ctx), C.byref(g), C.byref(o),
+                            C.c_void_p(stream) if stream else None))
+
+    def close(self):
+        if self._ctx:
+            lib().xfft_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    __del__ = close
+
+    @property
+    def num_enriched(self):
+        return lib().xfft_num_enriched(self._ctx)
+
+    @property
+    def num_cut_tets(self):
+        return lib().xfft_num_cut_tets(self._ctx)
+
+    @property
+    def stride(self):
+        return 3 * (self.N + self.num_enriched)
+
+    def set_microstructure(self, L, lame_minus, lame_plus, scale=None):
+        Lp, dev = _ptr(L, np.float64)
+        sp_, sdev = _ptr(scale, np.float32)
+        if scale is not None and sdev != dev:
+            raise TypeError("L and scale must both be host or both be device arrays")
+        lm, lmp = _dvec(lame_minus)
+        lp, lpp = _dvec(lame_plus)
+        check(lib().xfft_set_microstructure(self._ctx, Lp, lmp, lpp, sp_, int(dev)))
+
+    def solve(self, eps, u=True, voxel_stress=False, device=None):
+        """Solve for the Mandel strains ``eps`` (k x 6).  Host (NumPy) outputs unless
+        ``device`` is a torch device, in which case outputs are CUDA tensors."""
+        e, ep = _dvec(np.atleast_2d(eps))
+        k = e.shape[0]
+        nX = self.num_enriched
+        out = {}
+        if device is not None:
+            import torch
+            us = torch.empty((k, 3, self.N), dtype=torch.float64, device=device) if u else None
+            ue = torch.empty((k, 3, max(nX, 1)), dtype=torch.float64, device=device) if u else None
+            vs = torch.empty((k, 6, self.N), dtype=torch.float64, device=device) if voxel_stress else None
+            dev = 1
+        else:
+            us = np.empty((k, 3, self.N)) if u else None
+            ue = np.empty((k, 3, max(nX, 1))) if u else None
+            vs = np.empty((k, 6, self.N)) if voxel_stress else None
+            dev = 0
+        ms = np.empty((k, 6))
+        st = Stats()
+        status = check(lib().xfft_solve(self._ctx, k, ep, _ptr(us, np.float64)[0],
+                                        _ptr(ue, np.float64)[0], _ptr(vs, np.float64)[0],
+                                        ms.ctypes.data_as(C.POINTER(C.c_double)), C.byref(st), dev),
+                       allow=(XFFT_ENOTCONV,))
+        out["u_std"] = us
+        out["u_enr"] = ue[:, :, :nX] if ue is not None else None
+        out["voxel_stress"] = vs
+        out["mean_stress"] = ms
+        out["stats"] = st.to_dict()
+        out["converged"] = status == XFFT_OK
+        return out
+
+    def effective_stiffness(self):
+        Cm = np.empty(36)
+        st = Stats()
+        status = check(lib().xfft_effective_stiffness(self._ctx, Cm.ctypes.data_as(C.POINTER(C.c_double)),
+                                                      C.byref(st)), allow=(XFFT_ENOTCONV,))
+        return Cm.reshape(6, 6), dict(st.to_dict(), converged=status == XFFT_OK)
+
+    def grad(self, G, scale_grad=True, device=None):
+        """dLoss/d(lam-, mu-, lam+, mu+), dLoss/ds_v (float32) and the energy-form C_eff for
+        G = dLoss/dC_eff of the last effective_stiffness call."""
+        g, gp = _dvec(np.asarray(G, dtype=np.float64).reshape(36))
+        dl = np.empty(4)
+        ce = np.empty(36)
+        if scale_grad:
+            if device is not None:
+                import torch
+                ds = torch.empty(self.N, dtype=torch.float32, device=device)
+            else:
+                ds = np.empty(self.N, dtype=np.float32)
+        else:
+            ds = None
+        dsp, dev = _ptr(ds, np.float32)
+        check(lib().xfft_grad(self._ctx, gp, dl.ctypes.data_as(C.POINTER(C.c_double)), dsp,
+                              ce.ctypes.data_as(C.POINTER(C.c_double)), int(bool(dev))))
+        return dl, ds, ce.reshape(6, 6)
+
+    def apply(self, d, eps=None, precision="fp64"):
+        """q = A d (+ b(eps)) on full DOF vectors (k x stride, scaled enriched part)."""
+        d = np.ascontiguousarray(np.atleast_2d(d), dtype=np.float64)
+        k = d.shape[0]
+        q = np.empty_like(d)
+        sig = np.empty((k, 6))
+        if eps is not None:
+            e, ep = _dvec(np.atleast_2d(eps))
+        else:
+            ep = None
+        check(lib().xfft_apply(self._ctx, k, C.c_void_p(d.ctypes.data), ep, C.c_void_p(q.ctypes.data),
+                               sig.ctypes.data_as(C.POINTER(C.c_double)),
+                               0 if precision == "fp64" else 1, 0))
+        return q, sig
+
+    def precondition(self, f, precision="fp64"):
+        f = np.ascontiguousarray(np.atleast_2d(f), dtype=np.float64)
+        k = f.shape[0]
+        z = np.empty_like(f)
+        rr = np.empty(k)
+        check(lib().xfft_precondition(self._ctx, k, C.c_void_p(f.ctypes.data), C.c_void_p(z.ctypes.data),
+                                      rr.ctypes.data_as(C.POINTER(C.c_double)),
+                                      0 if precision == "fp64" else 1, 0))
+        return z, rr
+
+    def setup_info(self):
+        nX = self.num_enriched
+        en = np.empty(max(nX, 1), dtype=np.int32)
+        D0 = np.empty((max(nX, 1), 3))
+        code = np.empty(self.N, dtype=np.uint16)
+        check(lib().xfft_get_setup(self._ctx, C.c_void_p(en.ctypes.data), C.c_void_p(D0.ctypes.data),
+                                   C.c_void_p(code.ctypes.data)))
+        return en[:nX], D0[:nX], code

@@ -1,0 +1,635 @@
+// Matrix-free stiffness apply of the scaled X-FEM system (eqs. Kapp, b, resVector):
+//   q = sum_e Lambda_e^T int_e B~^T C (eps_bar + B~ d_e)        (eps_bar only in TOTAL mode)
+// with fused reductions <d, A d> = sum_e int eps(d) : C : eps(d) and int_Y C (eps_bar + grad^s d).
+//
+// Uncut tets (constant strain, one phase): a 2.5-D marching kernel.  A block of 32 x 8 threads
+// owns one voxel column each (y, z) and walks along x; node planes of d are staged in shared
+// memory, each voxel's six Kuhn tets are evaluated once, the 8 corner forces are combined
+// along z by warp shuffles and along y through shared memory, and the x direction is carried
+// in registers, so every node force is written exactly once with a plain store.
+//
+// Cut tets: one thread per cut tet.  On each side s the strain is linear in the parent P1
+// functions, eps(x) = sum_b N_b E_b with E_b = eps_std + c_b sym(W) + sym(w_b (x) gamma),
+// where c_b = |L_b| - s L_b, gamma = sum_b c_b grad N_b (modified abs enrichment restricted to
+// the side), w the unscaled enriched coefficients and W = sum_a w_a (x) grad N_a.  With the
+// side moments m_b = int N_b and M_bc = int N_b N_c every integral is exact:
+//   std force  q_a   = (sum_b m_b S_b) g_a
+//   enr force  q~_a  = D_a^{-1/2} [ (sum_b (sum_c M_bc c_c) S_b) g_a + (sum_b M_ab S_b) gamma ]
+// with S_b = C_s E_b.  Contributions are scatter-added with atomics after the uncut kernel.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xfft_kernels.h"
+
+namespace xfft {
+
+constexpr int kTZ = 32;  // threads along z (one warp)
+constexpr int kTY = 8;   // threads along y
+constexpr int kCX = 16;  // output planes per block along x
+
+template <typename T>
+__device__ __forceinline__ T cut_real(const CutData& cd, int f, int e);
+template <>
+__device__ __forceinline__ double cut_real<double>(const CutData& cd, int f, int e) {
+  return cd.dp[(long long)f * cd.ncut + e];
+}
+template <>
+__device__ __forceinline__ float cut_real<float>(const CutData& cd, int f, int e) {
+  return cd.fp[(long long)f * cd.ncut + e];
+}
+
+// symmetric tensor stored as (00, 11, 22, 12, 02, 01)
+template <typename T>
+__device__ __forceinline__ T sym_at(const T (&s)[6], int i, int j) {
+  if (i == j) return s[i];
+  const int k = i + j;  // 1 -> (0,1), 2 -> (0,2), 3 -> (1,2)
+  return k == 1 ? s[5] : (k == 2 ? s[4] : s[3]);
+}
+
+template <typename T>
+__device__ __forceinline__ void mandel_to_tensor(const double* e, T (&E)[6]) {
+  const double r = 0.70710678118654752440;
+  E[0] = (T)e[0];
+  E[1] = (T)e[1];
+  E[2] = (T)e[2];
+  E[3] = (T)(e[3] * r);
+  E[4] = (T)(e[4] * r);
+  E[5] = (T)(e[5] * r);
+}
+
+template <typename T>
+__device__ __forceinline__ void iso_stress(const T (&e)[6], T lam, T mu, T (&s)[6]) {
+  const T tr = e[0] + e[1] + e[2];
+  const T m2 = mu + mu;
+  s[0] = lam * tr + m2 * e[0];
+  s[1] = lam * tr + m2 * e[1];
+  s[2] = lam * tr + m2 * e[2];
+  s[3] = m2 * e[3];
+  s[4] = m2 * e[4];
+  s[5] = m2 * e[5];
+}
+
+template <typename T>
+__device__ __forceinline__ T ddot(const T (&s)[6], const T (&e)[6]) {
+  return s[0] * e[0] + s[1] * e[1] + s[2] * e[2] + T(2) * (s[3] * e[3] + s[4] * e[4] + s[5] * e[5]);
+}
+
+// One uncut Kuhn tet t of a voxel with corner displacements u: adds its corner forces to F and
+// its energy/stress integrals to the accumulators.
+template <typename T, int t, bool TOTAL>
+__device__ __forceinline__ void tet_uncut(const T (&u)[8][3], T (&F)[8][3], unsigned code,
+                                          const T (&lm)[2], const T (&mu2)[2], const T (&ih)[3],
+                                          const T (&w)[3], T vol, const T (&E)[6], T& en,
+                                          T (&sg)[6]) {
+  constexpr int p = perm_p(t), q = perm_q(t), r = perm_r(t);
+  constexpr int c1 = tet_c1(t), c2 = tet_c2(t);
+  const unsigned cd = (code >> (2 * t)) & 3u;
+  if (cd == 2u) return;
+  const T lam = lm[cd], mu = mu2[cd];
+  T H[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    H[i][p] = (u[c1][i] - u[0][i]) * ih[p];
+    H[i][q] = (u[c2][i] - u[c1][i]) * ih[q];
+    H[i][r] = (u[7][i] - u[c2][i]) * ih[r];
+  }
+  T e[6];
+  e[0] = H[0][0];
+  e[1] = H[1][1];
+  e[2] = H[2][2];
+  e[3] = T(0.5) * (H[1][2] + H[2][1]);
+  e[4] = T(0.5) * (H[0][2] + H[2][0]);
+  e[5] = T(0.5) * (H[0][1] + H[1][0]);
+  if (TOTAL) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) e[k] += E[k];
+  }
+  T s[6];
+  iso_stress(e, lam, mu, s);
+  en += vol * ddot(s, e);
+  sg[0] += vol * s[0];
+  sg[1] += vol * s[1];
+  sg[2] += vol * s[2];
+  sg[3] += vol * s[3];
+  sg[4] += vol * s[4];
+  sg[5] += vol * s[5];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T tp = w[p] * sym_at(s, i, p);
+    const T tq = w[q] * sym_at(s, i, q);
+    const T tr = w[r] * sym_at(s, i, r);
+    F[0][i] -= tp;
+    F[c1][i] += tp - tq;
+    F[c2][i] += tq - tr;
+    F[7][i] += tr;
+  }
+}
+
+template <typename T, bool TOTAL>
+__global__ void __launch_bounds__(kTZ* kTY)
+    k_apply_uncut(const T* __restrict__ d, T* __restrict__ q, const ApplyArgs a, int nxchunks) {
+  const int tz = threadIdx.x, ty = threadIdx.y;
+  const int tid = tz + kTZ * ty;
+  const int rhs = blockIdx.z / nxchunks;
+  const int xc = blockIdx.z - rhs * nxchunks;
+  if (a.active && !a.active[rhs]) return;
+  const GridDev& g = a.g;
+  const int n0 = g.n0, n1 = g.n1, n2 = g.n2;
+  const long long N = g.N;
+  const long long plane = (long long)n1 * n2;
+  const int z0 = blockIdx.x * (kTZ - 1), y0 = blockIdx.y * (kTY - 1), x0 = xc * kCX;
+  const int x1 = min(x0 + kCX, n0);
+  const T* dr = d + rhs * a.stride;
+  T* qr = q + rhs * a.stride;
+
+  __shared__ T P[2][3][kTY + 1][kTZ + 1];
+  __shared__ T Ys[2][3][kTY][kTZ];
+  __shared__ double red[7 * 32];
+
+  // the (up to two) plane nodes this thread loads
+  constexpr int kPlaneNodes = (kTY + 1) * (kTZ + 1);
+  int ld_slot[2];
+  long long ld_off[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int lin = tid + k * kTZ * kTY;
+    ld_slot[k] = lin < kPlaneNodes ? lin : -1;
+    const int iy = lin / (kTZ + 1), iz = lin - iy * (kTZ + 1);
+    const int yy = ((y0 - 1 + iy) % n1 + n1) % n1;
+    const int zz = ((z0 - 1 + iz) % n2 + n2) % n2;
+    ld_off[k] = (long long)yy * n2 + zz;
+  }
+  const int yg = y0 - 1 + ty, zg = z0 - 1 + tz;  // unwrapped voxel column
+  const int yv = (yg % n1 + n1) % n1, zv = (zg % n2 + n2) % n2;
+  const bool own = ty >= 1 && tz >= 1 && yg < n1 && zg < n2;
+
+  T lm[2], mu2[2], ih[3], w[3];
+  lm[0] = (T)a.ph.lam[0];
+  lm[1] = (T)a.ph.lam[1];
+  mu2[0] = (T)a.ph.mu[0];
+  mu2[1] = (T)a.ph.mu[1];
+  const T vol = (T)g.vol_tet;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    ih[k] = (T)(1.0 / g.h[k]);
+    w[k] = (T)(g.vol_tet / g.h[k]);
+  }
+  T E[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  if (TOTAL) mandel_to_tensor(a.eps + 6 * rhs, E);
+
+  auto load_plane = [&](int xp, int buf) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (ld_slot[k] >= 0) {
+        const int iy = ld_slot[k] / (kTZ + 1), iz = ld_slot[k] - iy * (kTZ + 1);
+        const long long nd = (long long)xp * plane + ld_off[k];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) P[buf][c][iy][iz] = dr[c * N + nd];
+      }
+    }
+  };
+
+  T pend[3] = {T(0), T(0), T(0)};
+  T en = T(0);
+  T sg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  load_plane(((x0 - 1) % n0 + n0) % n0, 0);
+  for (int s = 0; s <= x1 - x0; ++s) {
+    const int xv = x0 - 1 + s;
+    const int xw = (xv % n0 + n0) % n0;
+    load_plane(xw + 1 == n0 ? 0 : xw + 1, (s + 1) & 1);
+    __syncthreads();
+    T u[8][3];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[c][i] = P[(s + dx) & 1][i][ty + dy][tz + dz];
+    }
+    const long long vox = (long long)xw * plane + (long long)yv * n2 + zv;
+    const unsigned code = a.code[vox];
+    T lms[2] = {lm[0], lm[1]}, mus[2] = {mu2[0], mu2[1]};
+    if (a.scale) {
+      const T sv = (T)a.scale[vox];
+      lms[0] *= sv;
+      lms[1] *= sv;
+      mus[0] *= sv;
+      mus[1] *= sv;
+    }
+    T F[8][3];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) F[c][0] = F[c][1] = F[c][2] = T(0);
+    T ven = T(0);
+    T vsg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    tet_uncut<T, 0, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
+    tet_uncut<T, 1, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
+    tet_uncut<T, 2, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
+    tet_uncut<T, 3, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
+    tet_uncut<T, 4, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
+    tet_uncut<T, 5, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
+    if (own && s >= 1) {
+      en += ven;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sg[k] += vsg[k];
+    }
+    // combine along z (lane tz receives the dz = 1 corners of voxel tz - 1)
+    T G[2][2][3];
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const T up = __shfl_up_sync(0xffffffffu, F[dx + 2 * dy + 4][i], 1);
+          G[dx][dy][i] = F[dx + 2 * dy][i] + up;
+        }
+    // combine along y through shared memory
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Ys[dx][i][ty][tz] = G[dx][1][i];
+    __syncthreads();
+    if (own) {
+      T H0[3], H1[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        H0[i] = G[0][0][i] + Ys[0][i][ty - 1][tz];
+        H1[i] = G[1][0][i] + Ys[1][i][ty - 1][tz];
+      }
+      if (s >= 1) {
+        const long long nd = (long long)xw * plane + (long long)yv * n2 + zv;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) qr[i * N + nd] = pend[i] + H0[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) pend[i] = H1[i];
+    }
+  }
+  // block reduction of the energy and stress integrals
+  double v[7] = {(double)en, (double)sg[0], (double)sg[1], (double)sg[2],
+                 (double)(sg[3] * T(1.41421356237309504880)),
+                 (double)(sg[4] * T(1.41421356237309504880)),
+                 (double)(sg[5] * T(1.41421356237309504880))};
+  double tot[7];
+  block_sum<7>(v, red, tot);
+  if (tid == 0) {
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * xc);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) a.partials[((long long)rhs * 7 + k) * a.nparts + bid] = tot[k];
+  }
+}
+
+template <typename T, bool TOTAL>
+__global__ void __launch_bounds__(128)
+    k_apply_cut(const T* __restrict__ d, T* __restrict__ q, const T* __restrict__ isD,
+                const CutData cd, const ApplyArgs a) {
+  const int rhs = blockIdx.y;
+  if (a.active && !a.active[rhs]) return;
+  __shared__ double red[7 * 32];
+  const GridDev& g = a.g;
+  const long long N = g.N;
+  const int nX = a.nX;
+  const int ncut = cd.ncut;
+  const T* dr = d + rhs * a.stride;
+  T* qr = q + rhs * a.stride;
+  T ih[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ih[k] = (T)(1.0 / g.h[k]);
+  T E[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  if (TOTAL) mandel_to_tensor(a.eps + 6 * rhs, E);
+  T en = T(0);
+  T sg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
+    int nd[4], ei[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      nd[k] = cd.ip[k * ncut + e];
+      ei[k] = cd.ip[(4 + k) * ncut + e];
+    }
+    const int vox = cd.ip[8 * ncut + e];
+    const int t = cd.ip[9 * ncut + e];
+    T gr[4][3];
+    tet_grads<T>(t, ih, gr);
+    T us[4][3], ws[4][3], sc[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        us[k][c] = dr[c * N + nd[k]];
+        sc[k][c] = isD[(long long)c * nX + ei[k]];
+        ws[k][c] = dr[3 * N + (long long)c * nX + ei[k]] * sc[k][c];
+      }
+    T L[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) L[b] = cut_real<T>(cd, cut_f_L(b), e);
+    const T sv = a.scale ? (T)a.scale[vox] : T(1);
+    // standard and enriched displacement gradients
+    T Hs[3][3], Hw[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Hs[i][j] = us[0][i] * gr[0][j] + us[1][i] * gr[1][j] + us[2][i] * gr[2][j] + us[3][i] * gr[3][j];
+        Hw[i][j] = ws[0][i] * gr[0][j] + ws[1][i] * gr[1][j] + ws[2][i] * gr[2][j] + ws[3][i] * gr[3][j];
+      }
+    T es[6] = {Hs[0][0], Hs[1][1], Hs[2][2], T(0.5) * (Hs[1][2] + Hs[2][1]),
+               T(0.5) * (Hs[0][2] + Hs[2][0]), T(0.5) * (Hs[0][1] + Hs[1][0])};
+    if (TOTAL) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) es[k] += E[k];
+    }
+    const T ew[6] = {Hw[0][0], Hw[1][1], Hw[2][2], T(0.5) * (Hw[1][2] + Hw[2][1]),
+                     T(0.5) * (Hw[0][2] + Hw[2][0]), T(0.5) * (Hw[0][1] + Hw[1][0])};
+    T qs[4][3], qe[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) qs[k][c] = qe[k][c] = T(0);
+#pragma unroll
+    for (int si = 0; si < 2; ++si) {
+      const T s = si == 0 ? T(1) : T(-1);
+      const int ph = si == 0 ? 1 : 0;
+      const T lam = (T)a.ph.lam[ph] * sv, mu = (T)a.ph.mu[ph] * sv;
+      T c[4], gam[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        c[b] = fabs(L[b]) - s * L[b];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
+      }
+      T mm[4], MM[10];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) mm[b] = cut_real<T>(cd, cut_f_m(si, b), e);
+#pragma unroll
+      for (int k = 0; k < 10; ++k) MM[k] = cut_real<T>(cd, cut_f_M(si, k), e);
+      T Eb[4][6], Sb[4][6];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const T* wb = ws[b];
+        const T sw[6] = {wb[0] * gam[0], wb[1] * gam[1], wb[2] * gam[2],
+                         T(0.5) * (wb[1] * gam[2] + wb[2] * gam[1]),
+                         T(0.5) * (wb[0] * gam[2] + wb[2] * gam[0]),
+                         T(0.5) * (wb[0] * gam[1] + wb[1] * gam[0])};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Eb[b][k] = es[k] + c[b] * ew[k] + sw[k];
+        T ebk[6] = {Eb[b][0], Eb[b][1], Eb[b][2], Eb[b][3], Eb[b][4], Eb[b][5]};
+        T sbk[6];
+        iso_stress(ebk, lam, mu, sbk);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Sb[b][k] = sbk[k];
+      }
+      T sbar[6], Tt[6];
+      T Pb[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        Pb[b] = T(0);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) Pb[b] += MM[midx(b, cc)] * c[cc];
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        sbar[k] = mm[0] * Sb[0][k] + mm[1] * Sb[1][k] + mm[2] * Sb[2][k] + mm[3] * Sb[3][k];
+        Tt[k] = Pb[0] * Sb[0][k] + Pb[1] * Sb[1][k] + Pb[2] * Sb[2][k] + Pb[3] * Sb[3][k];
+      }
+      // energy int sigma : eps = sum_bc M_bc S_b : E_c
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const T* sb = Sb[b];
+          const T* ec = Eb[cc];
+          const T dd = sb[0] * ec[0] + sb[1] * ec[1] + sb[2] * ec[2] +
+                       T(2) * (sb[3] * ec[3] + sb[4] * ec[4] + sb[5] * ec[5]);
+          en += MM[midx(b, cc)] * dd;
+        }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sg[k] += sbar[k];
+#pragma unroll
+      for (int aa = 0; aa < 4; ++aa) {
+        T Ra[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          Ra[k] = MM[midx(aa, 0)] * Sb[0][k] + MM[midx(aa, 1)] * Sb[1][k] +
+                  MM[midx(aa, 2)] * Sb[2][k] + MM[midx(aa, 3)] * Sb[3][k];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          T a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            a1 += sym_at(sbar, i, j) * gr[aa][j];
+            a2 += sym_at(Tt, i, j) * gr[aa][j];
+            a3 += sym_at(Ra, i, j) * gam[j];
+          }
+          qs[aa][i] += a1;
+          qe[aa][i] += a2 + a3;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        atomicAdd(&qr[c * N + nd[k]], qs[k][c]);
+        atomicAdd(&qr[3 * N + (long long)c * nX + ei[k]], qe[k][c] * sc[k][c]);
+      }
+  }
+  double v[7] = {(double)en, (double)sg[0], (double)sg[1], (double)sg[2],
+                 (double)sg[3] * 1.41421356237309504880, (double)sg[4] * 1.41421356237309504880,
+                 (double)sg[5] * 1.41421356237309504880};
+  double tot[7];
+  block_sum<7>(v, red, tot);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+      a.partials[((long long)rhs * 7 + k) * a.nparts + a.part_offset_cut + blockIdx.x] = tot[k];
+  }
+}
+
+int apply_uncut_blocks(const GridDev& g) {
+  const int gz = (g.n2 + kTZ - 2) / (kTZ - 1);
+  const int gy = (g.n1 + kTY - 2) / (kTY - 1);
+  const int gx = (g.n0 + kCX - 1) / kCX;
+  return gz * gy * gx;
+}
+
+constexpr int kCutBlocksMax = 1024;
+int apply_cut_blocks(int ncut) {
+  const int nb = (ncut + 127) / 128;
+  return nb < 1 ? 1 : (nb > kCutBlocksMax ? kCutBlocksMax : nb);
+}
+
+template <typename T>
+cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
+                         int n_rhs, cudaStream_t s) {
+  const GridDev& g = a.g;
+  // enriched part of q only receives atomic contributions: clear it first
+  if (a.nX > 0) {
+    for (int r = 0; r < n_rhs; ++r) {
+      cudaError_t e = cudaMemsetAsync(q + r * a.stride + 3 * g.N, 0, sizeof(T) * 3 * (size_t)a.nX, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  const int gz = (g.n2 + kTZ - 2) / (kTZ - 1);
+  const int gy = (g.n1 + kTY - 2) / (kTY - 1);
+  const int gx = (g.n0 + kCX - 1) / kCX;
+  dim3 block(kTZ, kTY, 1);
+  dim3 grid(gz, gy, gx * n_rhs);
+  if (a.eps)
+    k_apply_uncut<T, true><<<grid, block, 0, s>>>(d, q, a, gx);
+  else
+    k_apply_uncut<T, false><<<grid, block, 0, s>>>(d, q, a, gx);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 cgrid(apply_cut_blocks(cd.ncut), n_rhs, 1);
+  if (a.eps)
+    k_apply_cut<T, true><<<cgrid, 128, 0, s>>>(d, q, isD, cd, a);
+  else
+    k_apply_cut<T, false><<<cgrid, 128, 0, s>>>(d, q, isD, cd, a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_apply<float>(const float*, float*, const float*, CutData,
+                                         const ApplyArgs&, int, cudaStream_t);
+template cudaError_t launch_apply<double>(const double*, double*, const double*, CutData,
+                                          const ApplyArgs&, int, cudaStream_t);
+
+// ---------------------------------------------------------------- per-voxel average stress
+__global__ void k_voxel_stress_uncut(const double* __restrict__ u, const ApplyArgs a,
+                                     double* __restrict__ out) {
+  const int rhs = blockIdx.y;
+  const GridDev& g = a.g;
+  const double* ur = u + rhs * a.stride;
+  double E[6];
+  mandel_to_tensor(a.eps + 6 * rhs, E);
+  double ih[3], w[3];
+  for (int k = 0; k < 3; ++k) {
+    ih[k] = 1.0 / g.h[k];
+    w[k] = g.vol_tet / g.h[k];
+  }
+  const double lm[2] = {a.ph.lam[0], a.ph.lam[1]};
+  const double mu2[2] = {a.ph.mu[0], a.ph.mu[1]};
+  const double ivox = 1.0 / (6.0 * g.vol_tet);
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.N;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(v % g.n2);
+    const int j = (int)((v / g.n2) % g.n1);
+    const int i = (int)(v / ((long long)g.n1 * g.n2));
+    double uu[8][3];
+    for (int c = 0; c < 8; ++c) {
+      const long long nd = corner_node(g, i, j, k, c);
+      for (int x = 0; x < 3; ++x) uu[c][x] = ur[x * g.N + nd];
+    }
+    const double sv = a.scale ? (double)a.scale[v] : 1.0;
+    double lms[2] = {lm[0] * sv, lm[1] * sv}, mus[2] = {mu2[0] * sv, mu2[1] * sv};
+    double F[8][3] = {};
+    double en = 0.0, sg[6] = {0, 0, 0, 0, 0, 0};
+    const unsigned code = a.code[v];
+    tet_uncut<double, 0, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
+    tet_uncut<double, 1, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
+    tet_uncut<double, 2, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
+    tet_uncut<double, 3, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
+    tet_uncut<double, 4, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
+    tet_uncut<double, 5, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
+    const double r2 = 1.41421356237309504880;
+    double* o = out + (long long)rhs * 6 * g.N;
+    o[0 * g.N + v] = sg[0] * ivox;
+    o[1 * g.N + v] = sg[1] * ivox;
+    o[2 * g.N + v] = sg[2] * ivox;
+    o[3 * g.N + v] = sg[3] * r2 * ivox;
+    o[4 * g.N + v] = sg[4] * r2 * ivox;
+    o[5 * g.N + v] = sg[5] * r2 * ivox;
+  }
+}
+
+__global__ void k_voxel_stress_cut(const double* __restrict__ u, const double* __restrict__ isD,
+                                   const CutData cd, const ApplyArgs a, double* __restrict__ out) {
+  const int rhs = blockIdx.y;
+  const GridDev& g = a.g;
+  const long long N = g.N;
+  const int nX = a.nX, ncut = cd.ncut;
+  const double* ur = u + rhs * a.stride;
+  double E[6];
+  mandel_to_tensor(a.eps + 6 * rhs, E);
+  double ih[3];
+  for (int k = 0; k < 3; ++k) ih[k] = 1.0 / g.h[k];
+  const double ivox = 1.0 / (6.0 * g.vol_tet);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
+    int nd[4], ei[4];
+    for (int k = 0; k < 4; ++k) {
+      nd[k] = cd.ip[k * ncut + e];
+      ei[k] = cd.ip[(4 + k) * ncut + e];
+    }
+    const int vox = cd.ip[8 * ncut + e];
+    const int t = cd.ip[9 * ncut + e];
+    double gr[4][3];
+    tet_grads<double>(t, ih, gr);
+    double us[4][3], ws[4][3];
+    for (int k = 0; k < 4; ++k)
+      for (int c = 0; c < 3; ++c) {
+        us[k][c] = ur[c * N + nd[k]];
+        ws[k][c] = ur[3 * N + (long long)c * nX + ei[k]] * isD[(long long)c * nX + ei[k]];
+      }
+    double L[4];
+    for (int b = 0; b < 4; ++b) L[b] = cd.dp[(long long)cut_f_L(b) * ncut + e];
+    const double sv = a.scale ? (double)a.scale[vox] : 1.0;
+    double es[6] = {0, 0, 0, 0, 0, 0}, ew[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 4; ++k) {
+      es[0] += us[k][0] * gr[k][0];
+      es[1] += us[k][1] * gr[k][1];
+      es[2] += us[k][2] * gr[k][2];
+      es[3] += 0.5 * (us[k][1] * gr[k][2] + us[k][2] * gr[k][1]);
+      es[4] += 0.5 * (us[k][0] * gr[k][2] + us[k][2] * gr[k][0]);
+      es[5] += 0.5 * (us[k][0] * gr[k][1] + us[k][1] * gr[k][0]);
+      ew[0] += ws[k][0] * gr[k][0];
+      ew[1] += ws[k][1] * gr[k][1];
+      ew[2] += ws[k][2] * gr[k][2];
+      ew[3] += 0.5 * (ws[k][1] * gr[k][2] + ws[k][2] * gr[k][1]);
+      ew[4] += 0.5 * (ws[k][0] * gr[k][2] + ws[k][2] * gr[k][0]);
+      ew[5] += 0.5 * (ws[k][0] * gr[k][1] + ws[k][1] * gr[k][0]);
+    }
+    for (int k = 0; k < 6; ++k) es[k] += E[k];
+    double tot[6] = {0, 0, 0, 0, 0, 0};
+    for (int si = 0; si < 2; ++si) {
+      const double s = si == 0 ? 1.0 : -1.0;
+      const int ph = si == 0 ? 1 : 0;
+      const double lam = a.ph.lam[ph] * sv, mu = a.ph.mu[ph] * sv;
+      double c[4], gam[3] = {0, 0, 0};
+      for (int b = 0; b < 4; ++b) {
+        c[b] = fabs(L[b]) - s * L[b];
+        for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
+      }
+      for (int b = 0; b < 4; ++b) {
+        const double mb = cd.dp[(long long)cut_f_m(si, b) * ncut + e];
+        const double* wb = ws[b];
+        double eb[6] = {es[0] + c[b] * ew[0] + wb[0] * gam[0], es[1] + c[b] * ew[1] + wb[1] * gam[1],
+                        es[2] + c[b] * ew[2] + wb[2] * gam[2],
+                        es[3] + c[b] * ew[3] + 0.5 * (wb[1] * gam[2] + wb[2] * gam[1]),
+                        es[4] + c[b] * ew[4] + 0.5 * (wb[0] * gam[2] + wb[2] * gam[0]),
+                        es[5] + c[b] * ew[5] + 0.5 * (wb[0] * gam[1] + wb[1] * gam[0])};
+        double sb[6];
+        iso_stress(eb, lam, mu, sb);
+        for (int k = 0; k < 6; ++k) tot[k] += mb * sb[k];
+      }
+    }
+    const double r2 = 1.41421356237309504880;
+    double* o = out + (long long)rhs * 6 * N;
+    atomicAdd(&o[0 * N + vox], tot[0] * ivox);
+    atomicAdd(&o[1 * N + vox], tot[1] * ivox);
+    atomicAdd(&o[2 * N + vox], tot[2] * ivox);
+    atomicAdd(&o[3 * N + vox], tot[3] * r2 * ivox);
+    atomicAdd(&o[4 * N + vox], tot[4] * r2 * ivox);
+    atomicAdd(&o[5 * N + vox], tot[5] * r2 * ivox);
+  }
+}
+
+cudaError_t launch_voxel_stress(const double* u, const double* isD, CutData cd,
+                                const ApplyArgs& a, double* out, int n_rhs, cudaStream_t s) {
+  long long nb = (a.g.N + 255) / 256;
+  if (nb > 65535) nb = 65535;
+  k_voxel_stress_uncut<<<dim3((unsigned)nb, n_rhs), 256, 0, s>>>(u, a, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || cd.ncut == 0) return e;
+  k_voxel_stress_cut<<<dim3(apply_cut_blocks(cd.ncut), n_rhs), 128, 0, s>>>(u, isD, cd, a, out);
+  return cudaGetLastError();
+}
+
+}  // namespace xfft

@@ -1,0 +1,918 @@
+// C-ABI of libxfft: context, setup pipeline and solver orchestration (see include/xfft.h).
+//
+// Solver loop (Algorithm 1, read as standard preconditioned CG on A u = -b):
+//   f = -(b + A u0); z = P^-1 f; rr = f^T z; d = z
+//   repeat: q = A d; alpha = rr / <q, d>; u += alpha d; f -= alpha q;
+//           z = P^-1 f; rr' = f^T z; beta = rr'/rr; d = z + beta d
+// until sqrt(rr / |Y|) <= tol ||<sigma(u)>_Y|| (eq. stoppingCriterion).
+// Every scalar stays on the device; the host only polls the per-RHS activity flags.
+//
+// FP32_REFINED: iterative refinement.  The residual r = -(b + A u) of the FP64 iterate u is
+// evaluated with the FP64 kernels and tested against the stopping rule; otherwise an FP32
+// PCG solves A delta = r to a relative reduction inner_tol and u += delta.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/xfft.h"
+#include "xfft_kernels.h"
+
+using namespace xfft;
+
+static thread_local std::string g_err;
+
+static xfft_status fail(xfft_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CU(...)                                                                             \
+  do {                                                                                      \
+    cudaError_t e_ = (__VA_ARGS__);                                                         \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? XFFT_ENOMEM : XFFT_ECUDA,              \
+                  std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+template <typename T>
+static void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+struct xfft_ctx {
+  GridDev g;
+  xfft_options opt;
+  cudaStream_t stream;
+  // microstructure
+  bool have_micro = false;
+  PhaseDev ph;
+  double tau = 0.0;
+  double* Ls = nullptr;
+  double* Lin = nullptr;  // device copy of a host level set
+  uint16_t* code = nullptr;
+  int* cutcount = nullptr;
+  int* enr_flag = nullptr;
+  int* enr_id = nullptr;
+  int* enr_nodes = nullptr;
+  int* scan_tmp = nullptr;
+  int* d_tot = nullptr;
+  float* scale = nullptr;
+  bool has_scale = false;
+  int nX = -1, ncut = -1;
+  int* cut_ip = nullptr;
+  double* cut_dp = nullptr;
+  float* cut_fp = nullptr;
+  double* D = nullptr;
+  double* isD = nullptr;
+  float* isF = nullptr;
+  FftPlan* fft = nullptr;
+  // solver workspace
+  int cap_rhs = 0;
+  long long cap_stride = 0;
+  int cap_prec = -1;
+  double* v64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // u f d z q (FP64)
+  float* v32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // u f d z q (FP32)
+  void* spec = nullptr;
+  size_t spec_bytes = 0;
+  RhsState* st = nullptr;
+  int* act = nullptr;
+  int* outer_mask = nullptr;
+  double* eps_d = nullptr;
+  double* partials = nullptr;
+  size_t partials_count = 0;
+  double* red_out = nullptr;
+  int* h_act = nullptr;          // pinned
+  RhsState* h_st = nullptr;      // pinned
+  // checkpoint of the six unit load cases (scaled DOFs, FP64)
+  double* U6 = nullptr;
+  bool have6 = false;
+  double C6[36];
+  double* dscale = nullptr;
+  float* dscale_f = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+static CutData cutdata(const xfft_ctx* c) {
+  CutData cd;
+  cd.ip = c->cut_ip;
+  cd.dp = c->cut_dp;
+  cd.fp = c->cut_fp;
+  cd.ncut = c->ncut;
+  return cd;
+}
+
+static long long stride_of(const xfft_ctx* c) { return 3LL * (c->g.N + c->nX); }
+
+static bool good_len(int n) {
+  if (n < 4 || n > 1024 || (n & 1)) return false;
+  int m = n;
+  for (int p : {2, 3, 5})
+    while (m % p == 0) m /= p;
+  return m == 1;
+}
+
+extern "C" const char* xfft_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* xfft_status_string(xfft_status s) {
+  switch (s) {
+    case XFFT_OK: return "ok";
+    case XFFT_EINVAL: return "invalid argument";
+    case XFFT_ENOMEM: return "out of memory";
+    case XFFT_ECUDA: return "CUDA error";
+    case XFFT_ENOTCONV: return "not converged";
+    case XFFT_EBREAKDOWN: return "CG breakdown";
+    case XFFT_ETIMEOUT: return "device wait timed out";
+    case XFFT_EUNSUPPORTED: return "unsupported";
+    case XFFT_ESTATE: return "invalid call order";
+  }
+  return "unknown status";
+}
+
+extern "C" xfft_status xfft_default_options(xfft_options* opt) {
+  if (!opt) return fail(XFFT_EINVAL, "opt is NULL");
+  opt->precision = XFFT_FP64;
+  opt->tol = 1e-10;
+  opt->maxit = 10000;
+  opt->snap_tau = 0.0;
+  opt->enr_precond = XFFT_ENR_IDENTITY;
+  opt->inner_tol = 1e-4;
+  opt->max_refine = 20;
+  opt->poll_every = 8;
+  return XFFT_OK;
+}
+
+extern "C" xfft_status xfft_create(xfft_ctx** out, const xfft_grid* grid, const xfft_options* opt,
+                                   void* stream) {
+  if (!out || !grid) return fail(XFFT_EINVAL, "NULL argument");
+  *out = nullptr;
+  for (int a = 0; a < 3; ++a) {
+    if (!good_len(grid->n[a]))
+      return fail(XFFT_EINVAL, "grid size must be even, 2^a 3^b 5^c and in [4, 1024]");
+    if (!(grid->len[a] > 0.0)) return fail(XFFT_EINVAL, "cell lengths must be positive");
+  }
+  const long long N = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+  if (N > (1LL << 28)) return fail(XFFT_EUNSUPPORTED, "more than 2^28 voxels");
+  xfft_options o;
+  xfft_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != XFFT_FP64 && o.precision != XFFT_FP32_REFINED)
+    return fail(XFFT_EINVAL, "unknown precision");
+  if (o.enr_precond != XFFT_ENR_IDENTITY)
+    return fail(XFFT_EUNSUPPORTED, "only the identity enriched preconditioner is built");
+  if (!(o.tol > 0.0) || o.maxit < 1 || o.poll_every < 1 || o.max_refine < 1 || !(o.inner_tol > 0.0))
+    return fail(XFFT_EINVAL, "invalid options");
+  xfft_ctx* c = new xfft_ctx();
+  c->opt = o;
+  c->stream = (cudaStream_t)stream;
+  GridDev& g = c->g;
+  g.n0 = grid->n[0];
+  g.n1 = grid->n[1];
+  g.n2 = grid->n[2];
+  g.N = N;
+  for (int a = 0; a < 3; ++a) g.h[a] = grid->len[a] / grid->n[a];
+  g.vol_tet = g.h[0] * g.h[1] * g.h[2] / 6.0;
+  g.volY = grid->len[0] * grid->len[1] * grid->len[2];
+  cudaError_t e = cudaSuccess;
+  c->fft = fft_plan_create(g, &e);
+  if (!c->fft || e != cudaSuccess) {
+    delete c;
+    return fail(XFFT_ECUDA, std::string("FFT plan: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaEventCreate(&c->ev0)) != cudaSuccess || (e = cudaEventCreate(&c->ev1)) != cudaSuccess ||
+      (e = cudaMallocHost((void**)&c->h_act, 64 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMallocHost((void**)&c->h_st, 64 * sizeof(RhsState))) != cudaSuccess) {
+    xfft_destroy(c);
+    return fail(XFFT_ECUDA, cudaGetErrorString(e));
+  }
+  *out = c;
+  return XFFT_OK;
+}
+
+static void free_micro(xfft_ctx* c) {
+  dfree(c->Ls);
+  dfree(c->Lin);
+  dfree(c->code);
+  dfree(c->cutcount);
+  dfree(c->enr_flag);
+  dfree(c->enr_id);
+  dfree(c->enr_nodes);
+  dfree(c->scan_tmp);
+  dfree(c->d_tot);
+  dfree(c->scale);
+  dfree(c->cut_ip);
+  dfree(c->cut_dp);
+  dfree(c->cut_fp);
+  dfree(c->D);
+  dfree(c->isD);
+  dfree(c->isF);
+  dfree(c->U6);
+  dfree(c->dscale);
+  dfree(c->dscale_f);
+  c->have_micro = false;
+  c->have6 = false;
+  c->nX = c->ncut = -1;
+}
+
+static void free_work(xfft_ctx* c) {
+  for (int k = 0; k < 5; ++k) {
+    dfree(c->v64[k]);
+    dfree(c->v32[k]);
+  }
+  if (c->spec) cudaFree(c->spec);
+  c->spec = nullptr;
+  dfree(c->st);
+  dfree(c->act);
+  dfree(c->outer_mask);
+  dfree(c->eps_d);
+  dfree(c->partials);
+  dfree(c->red_out);
+  c->cap_rhs = 0;
+  c->cap_stride = 0;
+  c->cap_prec = -1;
+}
+
+extern "C" void xfft_destroy(xfft_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_micro(c);
+  free_work(c);
+  fft_plan_destroy(c->fft);
+  if (c->h_act) cudaFreeHost(c->h_act);
+  if (c->h_st) cudaFreeHost(c->h_st);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+extern "C" int xfft_num_enriched(const xfft_ctx* c) { return c && c->have_micro ? c->nX : -1; }
+extern "C" int xfft_num_cut_tets(const xfft_ctx* c) { return c && c->have_micro ? c->ncut : -1; }
+
+// ---------------------------------------------------------------- microstructure setup
+extern "C" xfft_status xfft_set_microstructure(xfft_ctx* c, const double* L, const double lame_minus[2],
+                                               const double lame_plus[2], const float* voxel_scale,
+                                               int ptrs_on_device) {
+  if (!c || !L || !lame_minus || !lame_plus) return fail(XFFT_EINVAL, "NULL argument");
+  if (!(lame_minus[1] > 0.0) || !(lame_plus[1] > 0.0) ||
+      !(3.0 * lame_minus[0] + 2.0 * lame_minus[1] > 0.0) || !(3.0 * lame_plus[0] + 2.0 * lame_plus[1] > 0.0))
+    return fail(XFFT_EINVAL, "Lame constants must give a positive definite stiffness");
+  free_micro(c);
+  const GridDev& g = c->g;
+  const long long N = g.N;
+  cudaStream_t s = c->stream;
+  CU(cudaEventRecord(c->ev0, s));
+  c->ph.lam[0] = lame_minus[0];
+  c->ph.mu[0] = lame_minus[1];
+  c->ph.lam[1] = lame_plus[0];
+  c->ph.mu[1] = lame_plus[1];
+  c->tau = c->opt.snap_tau > 0.0 ? c->opt.snap_tau : 1e-6 * std::min(g.h[0], std::min(g.h[1], g.h[2]));
+  CU(dalloc(&c->Ls, N));
+  CU(dalloc(&c->code, N));
+  CU(dalloc(&c->cutcount, N));
+  CU(dalloc(&c->enr_flag, N));
+  CU(dalloc(&c->enr_id, N));
+  CU(dalloc(&c->scan_tmp, scan_tmp_ints(N)));
+  CU(dalloc(&c->d_tot, 4));
+  const double* Ldev = L;
+  if (!ptrs_on_device) {
+    CU(dalloc(&c->Lin, N));
+    CU(cudaMemcpyAsync(c->Lin, L, N * sizeof(double), cudaMemcpyHostToDevice, s));
+    Ldev = c->Lin;
+  }
+  if (voxel_scale) {
+    CU(dalloc(&c->scale, N));
+    CU(cudaMemcpyAsync(c->scale, voxel_scale, N * sizeof(float),
+                       ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    c->has_scale = true;
+  } else {
+    c->has_scale = false;
+  }
+  CU(launch_snap_classify(Ldev, c->Ls, c->code, c->cutcount, c->enr_flag, g, c->tau, s));
+  // enriched ids (scan of node flags) and cut-tet offsets (scan of per-voxel counts)
+  CU(launch_scan(c->enr_flag, c->enr_id, N, c->d_tot + 0, c->scan_tmp, s));
+  CU(launch_scan(c->cutcount, c->cutcount, N, c->d_tot + 1, c->scan_tmp, s));
+  int tot[2];
+  CU(cudaMemcpyAsync(tot, c->d_tot, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  c->nX = tot[0];
+  c->ncut = tot[1];
+  CU(dalloc(&c->enr_nodes, c->nX));
+  CU(dalloc(&c->cut_ip, (size_t)kCutInts * c->ncut));
+  CU(dalloc(&c->cut_dp, (size_t)kCutReals * c->ncut));
+  CU(dalloc(&c->cut_fp, (size_t)kCutReals * c->ncut));
+  CU(launch_build_lists(c->code, c->cutcount, c->enr_flag, c->enr_id, c->enr_nodes, c->cut_ip,
+                        c->ncut, g, s));
+  CutData cd = cutdata(c);
+  CU(launch_cut_geometry(c->Ls, cd, c->cut_dp, c->cut_ip, g, s));
+  CU(launch_cut_eids(c->cut_ip, c->enr_id, c->ncut, s));
+  CU(dalloc(&c->D, 3 * (size_t)c->nX));
+  CU(dalloc(&c->isD, 3 * (size_t)c->nX));
+  CU(dalloc(&c->isF, 3 * (size_t)c->nX));
+  CU(launch_cut_scaling(cd, c->D, c->nX, g, s));
+  CU(launch_finish_scaling(c->D, c->isD, c->isF, c->nX, s));
+  CU(launch_cut_to_float(c->cut_dp, c->cut_fp, (long long)kCutReals * c->ncut, s));
+  CU(cudaEventRecord(c->ev1, s));
+  CU(cudaStreamSynchronize(s));
+  c->have_micro = true;
+  c->have6 = false;
+  return XFFT_OK;
+}
+
+// ---------------------------------------------------------------- workspace
+static xfft_status ensure_work(xfft_ctx* c, int n_rhs, int prec) {
+  const long long stride = stride_of(c);
+  if (c->cap_rhs >= n_rhs && c->cap_stride == stride && c->cap_prec == prec) return XFFT_OK;
+  free_work(c);
+  const size_t tot = (size_t)n_rhs * stride;
+  if (prec == XFFT_FP64) {
+    for (int k = 0; k < 5; ++k) CU(dalloc(&c->v64[k], tot));
+  } else {
+    CU(dalloc(&c->v64[0], tot));  // u (FP64 iterate)
+    CU(dalloc(&c->v64[4], tot));  // FP64 residual
+    for (int k = 0; k < 5; ++k) CU(dalloc(&c->v32[k], tot));
+  }
+  c->spec_bytes = (size_t)n_rhs * fft_spectrum_elems(c->fft) * (prec == XFFT_FP64 ? 16 : 8);
+  CU(cudaMalloc(&c->spec, c->spec_bytes));
+  CU(dalloc(&c->st, 64));
+  CU(dalloc(&c->act, 64));
+  CU(dalloc(&c->outer_mask, 64));
+  CU(dalloc(&c->eps_d, 6 * 64));
+  const int na = apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut);
+  const int np = precondition_blocks(c->fft, c->nX);
+  const int ng = grad_blocks_uncut(c->g) + grad_blocks_cut(c->ncut);
+  const int nparts = std::max(na, np);
+  c->partials_count = std::max((size_t)n_rhs * 7 * nparts, (size_t)25 * ng);
+  CU(dalloc(&c->partials, c->partials_count));
+  CU(dalloc(&c->red_out, 64));
+  c->cap_rhs = n_rhs;
+  c->cap_stride = stride;
+  c->cap_prec = prec;
+  return XFFT_OK;
+}
+
+static int nparts_of(const xfft_ctx* c) {
+  return std::max(apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut),
+                  precondition_blocks(c->fft, c->nX));
+}
+
+static ApplyArgs apply_args(const xfft_ctx* c, const double* eps, const int* active) {
+  ApplyArgs a;
+  a.g = c->g;
+  a.ph = c->ph;
+  a.code = c->code;
+  a.scale = c->has_scale ? c->scale : nullptr;
+  a.eps = eps;
+  a.active = active;
+  a.stride = stride_of(c);
+  a.nX = c->nX;
+  a.partials = c->partials;
+  a.nparts = nparts_of(c);
+  a.part_offset_cut = apply_uncut_blocks(c->g);
+  return a;
+}
+
+template <typename T>
+static const T* isd_of(const xfft_ctx* c);
+template <>
+const double* isd_of<double>(const xfft_ctx* c) {
+  return c->isD;
+}
+template <>
+const float* isd_of<float>(const xfft_ctx* c) {
+  return c->isF;
+}
+
+// q = A d (+ b(eps)); finalisation `mode` (0 or 1) on the apply partials
+template <typename T>
+static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev, int n_rhs,
+                            const int* active, int fin_mode, double tol, int crit, int maxit) {
+  ApplyArgs a = apply_args(c, eps_dev, active);
+  CU(launch_apply<T>(d, q, isd_of<T>(c), cutdata(c), a, n_rhs, c->stream));
+  if (fin_mode >= 0) {
+    FinArgs fa;
+    fa.mode = fin_mode;
+    fa.crit = crit;
+    fa.tol = tol;
+    fa.volY = c->g.volY;
+    fa.maxit = maxit;
+    fa.nparts = a.nparts;
+    fa.nparts_used = apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut);
+    CU(launch_finalize(c->st, c->partials, fa, n_rhs, c->act, c->stream));
+  }
+  return XFFT_OK;
+}
+
+template <typename T>
+static xfft_status do_prec(xfft_ctx* c, const T* f, T* z, int n_rhs, const int* active, int fin_mode,
+                           double tol, int crit, int maxit) {
+  const int nparts = nparts_of(c);
+  CU(launch_precondition<T>(c->fft, f, z, c->spec, stride_of(c), c->nX, active, c->partials, nparts,
+                            n_rhs, c->stream));
+  if (fin_mode >= 0) {
+    FinArgs fa;
+    fa.mode = fin_mode;
+    fa.crit = crit;
+    fa.tol = tol;
+    fa.volY = c->g.volY;
+    fa.maxit = maxit;
+    fa.nparts = nparts;
+    fa.nparts_used = precondition_blocks(c->fft, c->nX);
+    CU(launch_finalize(c->st, c->partials, fa, n_rhs, c->act, c->stream));
+  }
+  return XFFT_OK;
+}
+
+static xfft_status poll_active(xfft_ctx* c, int n_rhs, int* nactive) {
+  CU(cudaMemcpyAsync(c->h_act, c->act, n_rhs * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  int k = 0;
+  for (int r = 0; r < n_rhs; ++r) k += c->h_act[r] != 0;
+  *nactive = k;
+  return XFFT_OK;
+}
+
+static xfft_status read_states(xfft_ctx* c, int n_rhs) {
+  CU(cudaMemcpyAsync(c->h_st, c->st, n_rhs * sizeof(RhsState), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return XFFT_OK;
+}
+
+#define TRY(...)                      \
+  do {                                \
+    xfft_status s_ = (__VA_ARGS__);   \
+    if (s_ != XFFT_OK) return s_;     \
+  } while (0)
+
+// CG iterations on vectors (u, f, d, z, q) of type T, starting from an initialised state
+// (f, z = P^-1 f, rr set by a mode-3 finalisation, d = z).
+template <typename T>
+static xfft_status cg_loop(xfft_ctx* c, T* u, T* f, T* d, T* z, T* q, int n_rhs, double tol, int crit,
+                           int maxit) {
+  const long long stride = stride_of(c);
+  for (int it = 0; it <= maxit; ++it) {
+    if (it % c->opt.poll_every == 0) {
+      int na = 0;
+      TRY(poll_active(c, n_rhs, &na));
+      if (na == 0) break;
+    }
+    TRY(do_apply<T>(c, d, q, nullptr, n_rhs, c->act, 1, tol, crit, maxit));
+    CU(launch_axpy_cg<T>(u, f, d, q, c->st, stride, n_rhs, c->stream));
+    TRY(do_prec<T>(c, f, z, n_rhs, c->act, 2, tol, crit, maxit));
+    CU(launch_xpby<T>(d, z, c->st, stride, n_rhs, c->stream));
+  }
+  return XFFT_OK;
+}
+
+__global__ void k_copy_act_to_mask(const int* act, int* mask, int n) {
+  const int r = threadIdx.x;
+  if (r < n) mask[r] = act[r];
+}
+
+struct SolveResult {
+  int iters[64];
+  double res[64];
+  double sig[64][6];
+  int status[64];
+  int refine_steps;
+};
+
+// Solve for n_rhs strains (device eps_d already filled); the FP64 solution (scaled enriched
+// DOFs) ends in c->v64[0].
+static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
+  const long long stride = stride_of(c);
+  const size_t tot = (size_t)n_rhs * stride;
+  const double tol = c->opt.tol;
+  cudaStream_t s = c->stream;
+  for (int r = 0; r < n_rhs; ++r) {
+    R->iters[r] = 0;
+    R->res[r] = 0.0;
+    R->status[r] = 0;
+    for (int k = 0; k < 6; ++k) R->sig[r][k] = 0.0;
+  }
+  R->refine_steps = 0;
+  if (c->opt.precision == XFFT_FP64) {
+    double *u = c->v64[0], *f = c->v64[1], *d = c->v64[2], *z = c->v64[3], *q = c->v64[4];
+    CU(cudaMemsetAsync(u, 0, tot * sizeof(double), s));
+    CU(launch_init_state(c->st, c->act, n_rhs, nullptr, s));
+    TRY(do_apply<double>(c, u, q, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit));
+    CU(launch_scale_copy<double, double>(q, f, -1.0, stride, n_rhs, c->act, s));
+    TRY(do_prec<double>(c, f, z, n_rhs, c->act, 3, tol, 0, c->opt.maxit));
+    CU(launch_scale_copy<double, double>(z, d, 1.0, stride, n_rhs, nullptr, s));
+    TRY(cg_loop<double>(c, u, f, d, z, q, n_rhs, tol, 0, c->opt.maxit));
+    TRY(read_states(c, n_rhs));
+    for (int r = 0; r < n_rhs; ++r) {
+      const RhsState& st = c->h_st[r];
+      R->iters[r] = st.iters;
+      double sn = 0.0;
+      for (int k = 0; k < 6; ++k) {
+        R->sig[r][k] = st.sig[k];
+        sn += st.sig[k] * st.sig[k];
+      }
+      R->res[r] = sn > 0 ? sqrt(std::max(st.rr, 0.0) / c->g.volY) / (sqrt(sn) / c->g.volY) : 0.0;
+      R->status[r] = st.converged ? 0 : (st.status ? st.status : 4);
+    }
+    return XFFT_OK;
+  }
+  // FP32 inner solves with FP64 residual refinement
+  double* u = c->v64[0];
+  double* r64 = c->v64[4];
+  float *du = c->v32[0], *f = c->v32[1], *d = c->v32[2], *z = c->v32[3], *q = c->v32[4];
+  CU(cudaMemsetAsync(u, 0, tot * sizeof(double), s));
+  std::vector<int> pending(n_rhs, 1);
+  std::vector<int> hmask(64, 0);
+  for (int ref = 0; ref <= c->opt.max_refine; ++ref) {
+    for (int r = 0; r < n_rhs; ++r) hmask[r] = pending[r];
+    CU(cudaMemcpyAsync(c->outer_mask, hmask.data(), 64 * sizeof(int), cudaMemcpyHostToDevice, s));
+    CU(launch_init_state(c->st, c->act, n_rhs, c->outer_mask, s));
+    // FP64 residual of the current iterate and the stopping rule
+    TRY(do_apply<double>(c, u, r64, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit));
+    CU(launch_scale_copy<double, float>(r64, f, -1.0, stride, n_rhs, c->act, s));
+    TRY(do_prec<float>(c, f, z, n_rhs, c->act, 3, tol, 0, c->opt.maxit));
+    TRY(read_states(c, n_rhs));
+    int still = 0;
+    for (int r = 0; r < n_rhs; ++r) {
+      if (!pending[r]) continue;
+      const RhsState& st = c->h_st[r];
+      double sn = 0.0;
+      for (int k = 0; k < 6; ++k) {
+        R->sig[r][k] = st.sig[k];
+        sn += st.sig[k] * st.sig[k];
+      }
+      R->res[r] = sn > 0 ? sqrt(std::max(st.rr, 0.0) / c->g.volY) / (sqrt(sn) / c->g.volY) : 0.0;
+      if (st.converged) {
+        pending[r] = 0;
+        R->status[r] = 0;
+      } else if (st.status == 5) {
+        pending[r] = 0;
+        R->status[r] = 5;
+      } else {
+        ++still;
+      }
+    }
+    if (still == 0) break;
+    if (ref == c->opt.max_refine) {
+      for (int r = 0; r < n_rhs; ++r)
+        if (pending[r]) R->status[r] = 4;
+      break;
+    }
+    if (ref > 0) R->refine_steps++;
+    // inner FP32 PCG on A delta = r (relative reduction inner_tol); the act flags of the
+    // refining RHS were set by the mode-3 finalisation
+    k_copy_act_to_mask<<<1, 64, 0, s>>>(c->act, c->outer_mask, n_rhs);
+    CU(cudaGetLastError());
+    CU(cudaMemsetAsync(du, 0, tot * sizeof(float), s));
+    CU(launch_scale_copy<float, float>(z, d, 1.0, stride, n_rhs, nullptr, s));
+    TRY(cg_loop<float>(c, du, f, d, z, q, n_rhs, c->opt.inner_tol, 1, c->opt.maxit));
+    TRY(read_states(c, n_rhs));
+    for (int r = 0; r < n_rhs; ++r)
+      if (hmask[r]) R->iters[r] += c->h_st[r].iters;
+    CU(launch_add_to_double<float>(u, du, stride, n_rhs, c->outer_mask, s));
+  }
+  return XFFT_OK;
+}
+
+__global__ void k_unscale_enr(const double* __restrict__ u, const double* __restrict__ isD,
+                              double* __restrict__ out, long long stride, long long N, int nX) {
+  const int rhs = blockIdx.y;
+  const long long n = 3LL * nX;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[rhs * n + i] = u[rhs * stride + 3 * N + i] * isD[i];
+}
+
+static xfft_status upload_eps(xfft_ctx* c, int n_rhs, const double* eps_host) {
+  CU(cudaMemcpyAsync(c->eps_d, eps_host, 6 * n_rhs * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  return XFFT_OK;
+}
+
+static xfft_status finish_stats(xfft_ctx* c, const SolveResult& R, int n_rhs, float ms_solve,
+                                xfft_stats* stats) {
+  if (!stats) return XFFT_OK;
+  memset(stats, 0, sizeof(*stats));
+  stats->n_rhs = n_rhs;
+  for (int r = 0; r < n_rhs; ++r) {
+    stats->iters[r] = R.iters[r];
+    stats->final_res[r] = R.res[r];
+  }
+  stats->refine_steps = R.refine_steps;
+  stats->n_fe = (int)c->g.N;
+  stats->n_x = c->nX;
+  stats->n_cut_tets = c->ncut;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  stats->ms_setup = ms;
+  stats->ms_solve = ms_solve;
+  return XFFT_OK;
+}
+
+static xfft_status status_of(const SolveResult& R, int n_rhs) {
+  xfft_status st = XFFT_OK;
+  for (int r = 0; r < n_rhs; ++r) {
+    if (R.status[r] == 5) return fail(XFFT_EBREAKDOWN, "CG breakdown");
+    if (R.status[r] == 4) st = XFFT_ENOTCONV;
+  }
+  if (st == XFFT_ENOTCONV) g_err = "maximum number of iterations reached";
+  return st;
+}
+
+extern "C" xfft_status xfft_solve(xfft_ctx* c, int n_rhs, const double* eps_bar, double* u_std,
+                                  double* u_enr, double* voxel_stress, double* mean_stress,
+                                  xfft_stats* stats, int ptrs_on_device) {
+  if (!c || !eps_bar) return fail(XFFT_EINVAL, "NULL argument");
+  if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
+  if (n_rhs < 1 || n_rhs > 64) return fail(XFFT_EINVAL, "n_rhs must be in [1, 64]");
+  TRY(ensure_work(c, n_rhs, c->opt.precision));
+  cudaStream_t s = c->stream;
+  TRY(upload_eps(c, n_rhs, eps_bar));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, s));
+  SolveResult R;
+  xfft_status rs = solve_core(c, n_rhs, &R);
+  if (rs != XFFT_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rs;
+  }
+  CU(cudaEventRecord(e1, s));
+  const GridDev& g = c->g;
+  const long long stride = stride_of(c);
+  const double* u = c->v64[0];
+  const cudaMemcpyKind kind = ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (u_std) {
+    for (int r = 0; r < n_rhs; ++r)
+      CU(cudaMemcpyAsync(u_std + (size_t)r * 3 * g.N, u + r * stride, 3 * g.N * sizeof(double), kind, s));
+  }
+  if (u_enr && c->nX > 0) {
+    double* tmp = c->v64[4];  // free after the solve (residual / q buffer)
+    long long nb = (3LL * c->nX + 255) / 256;
+    if (nb > 4096) nb = 4096;
+    k_unscale_enr<<<dim3((unsigned)nb, n_rhs), 256, 0, s>>>(u, c->isD, tmp, stride, g.N, c->nX);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(u_enr, tmp, (size_t)n_rhs * 3 * c->nX * sizeof(double), kind, s));
+  }
+  if (voxel_stress) {
+    double* out = voxel_stress;
+    double* tmp = nullptr;
+    if (!ptrs_on_device) {
+      CU(dalloc(&tmp, (size_t)n_rhs * 6 * g.N));
+      out = tmp;
+    }
+    ApplyArgs a = apply_args(c, c->eps_d, nullptr);
+    CU(launch_voxel_stress(u, c->isD, cutdata(c), a, out, n_rhs, s));
+    if (tmp) {
+      CU(cudaMemcpyAsync(voxel_stress, tmp, (size_t)n_rhs * 6 * g.N * sizeof(double),
+                         cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      cudaFree(tmp);
+    }
+  }
+  CU(cudaStreamSynchronize(s));
+  if (mean_stress)
+    for (int r = 0; r < n_rhs; ++r)
+      for (int k = 0; k < 6; ++k) mean_stress[6 * r + k] = R.sig[r][k] / g.volY;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  finish_stats(c, R, n_rhs, ms, stats);
+  return status_of(R, n_rhs);
+}
+
+extern "C" xfft_status xfft_effective_stiffness(xfft_ctx* c, double C_eff[36], xfft_stats* stats) {
+  if (!c || !C_eff) return fail(XFFT_EINVAL, "NULL argument");
+  if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
+  double eps[36];
+  for (int k = 0; k < 36; ++k) eps[k] = (k % 7 == 0) ? 1.0 : 0.0;
+  double ms[36];
+  c->have6 = false;
+  TRY(ensure_work(c, 6, c->opt.precision));
+  TRY(upload_eps(c, 6, eps));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, c->stream));
+  SolveResult R;
+  xfft_status rs = solve_core(c, 6, &R);
+  CU(cudaEventRecord(e1, c->stream));
+  if (rs != XFFT_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rs;
+  }
+  const long long stride = stride_of(c);
+  if (!c->U6) CU(dalloc(&c->U6, 6 * (size_t)stride));
+  CU(cudaMemcpyAsync(c->U6, c->v64[0], 6 * (size_t)stride * sizeof(double), cudaMemcpyDeviceToDevice,
+                     c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int r = 0; r < 6; ++r)
+    for (int k = 0; k < 6; ++k) ms[6 * r + k] = R.sig[r][k] / c->g.volY;
+  // C_eff[i][k] = <sigma_i>(E_k)
+  for (int i = 0; i < 6; ++i)
+    for (int k = 0; k < 6; ++k) C_eff[i * 6 + k] = ms[6 * k + i];
+  memcpy(c->C6, C_eff, sizeof(c->C6));
+  float msolve = 0.f;
+  cudaEventElapsedTime(&msolve, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  finish_stats(c, R, 6, msolve, stats);
+  xfft_status st = status_of(R, 6);
+  if (st == XFFT_OK) c->have6 = true;
+  return st;
+}
+
+extern "C" xfft_status xfft_grad(xfft_ctx* c, const double dL_dCeff[36], double dL_dlame[4],
+                                 float* dL_dscale, double C_energy[36], int ptrs_on_device) {
+  if (!c || !dL_dCeff || !dL_dlame) return fail(XFFT_EINVAL, "NULL argument");
+  if (!c->have_micro || !c->have6) return fail(XFFT_ESTATE, "xfft_effective_stiffness first");
+  TRY(ensure_work(c, 6, c->cap_prec >= 0 ? c->cap_prec : c->opt.precision));
+  const GridDev& g = c->g;
+  cudaStream_t s = c->stream;
+  GradArgs a;
+  a.g = g;
+  a.ph = c->ph;
+  a.code = c->code;
+  a.scale = c->has_scale ? c->scale : nullptr;
+  a.stride = stride_of(c);
+  a.nX = c->nX;
+  for (int k = 0; k < 36; ++k) a.G[k] = dL_dCeff[k];
+  a.partials = c->partials;
+  a.nparts = grad_blocks_uncut(g) + grad_blocks_cut(c->ncut);
+  a.part_offset_cut = grad_blocks_uncut(g);
+  if (!c->dscale) CU(dalloc(&c->dscale, g.N));
+  CU(launch_grad(c->U6, c->isD, cutdata(c), a, c->dscale, s));
+  CU(launch_reduce_partials(c->partials, 25, a.nparts, a.nparts, c->red_out, s));
+  double red[25];
+  CU(cudaMemcpyAsync(red, c->red_out, sizeof(red), cudaMemcpyDeviceToHost, s));
+  if (dL_dscale) {
+    if (ptrs_on_device) {
+      CU(launch_scale_copy<double, float>(c->dscale, dL_dscale, 1.0, g.N, 1, nullptr, s));
+    } else {
+      if (!c->dscale_f) CU(dalloc(&c->dscale_f, g.N));
+      CU(launch_scale_copy<double, float>(c->dscale, c->dscale_f, 1.0, g.N, 1, nullptr, s));
+      CU(cudaMemcpyAsync(dL_dscale, c->dscale_f, g.N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+  }
+  CU(cudaStreamSynchronize(s));
+  dL_dlame[0] = red[0];  // lambda_minus
+  dL_dlame[1] = red[2];  // mu_minus
+  dL_dlame[2] = red[1];  // lambda_plus
+  dL_dlame[3] = red[3];  // mu_plus
+  if (C_energy) {
+    int idx = 0;
+    for (int k = 0; k < 6; ++k)
+      for (int l = k; l < 6; ++l, ++idx) {
+        C_energy[k * 6 + l] = red[4 + idx];
+        C_energy[l * 6 + k] = red[4 + idx];
+      }
+  }
+  return XFFT_OK;
+}
+
+// ---------------------------------------------------------------- step-level entry points
+template <typename T>
+static xfft_status stage_in(xfft_ctx* c, const double* src, T* dst, size_t count, int on_dev,
+                            double* scratch64) {
+  // dst (device, type T) <- src (double, host or device)
+  const double* dsrc = src;
+  if (!on_dev) {
+    CU(cudaMemcpyAsync(scratch64, src, count * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    dsrc = scratch64;
+  }
+  CU(launch_scale_copy<double, T>(dsrc, dst, 1.0, (long long)count, 1, nullptr, c->stream));
+  return XFFT_OK;
+}
+
+template <typename T>
+static xfft_status stage_out(xfft_ctx* c, const T* src, double* dst, size_t count, int on_dev,
+                             double* scratch64) {
+  double* ddst = on_dev ? dst : scratch64;
+  CU(launch_scale_copy<T, double>(src, ddst, 1.0, (long long)count, 1, nullptr, c->stream));
+  if (!on_dev)
+    CU(cudaMemcpyAsync(dst, scratch64, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return XFFT_OK;
+}
+
+template <typename T>
+static xfft_status apply_entry(xfft_ctx* c, int n_rhs, const double* d, const double* eps_bar, double* q,
+                               double* sigma_int, int on_dev) {
+  const long long stride = stride_of(c);
+  const size_t tot = (size_t)n_rhs * stride;
+  double* scratch = nullptr;
+  T* dd = nullptr;
+  T* qq = nullptr;
+  CU(dalloc(&scratch, tot));
+  CU(dalloc(&dd, tot));
+  CU(dalloc(&qq, tot));
+  xfft_status st = stage_in<T>(c, d, dd, tot, on_dev, scratch);
+  if (st == XFFT_OK && eps_bar) st = upload_eps(c, n_rhs, eps_bar);
+  if (st == XFFT_OK) st = do_apply<T>(c, dd, qq, eps_bar ? c->eps_d : nullptr, n_rhs, nullptr, -1, 0, 0, 0);
+  if (st == XFFT_OK) st = stage_out<T>(c, qq, q, tot, on_dev, scratch);
+  if (st == XFFT_OK && sigma_int) {
+    const int nparts = nparts_of(c);
+    const int used = apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut);
+    cudaError_t e = launch_reduce_partials(c->partials, 7 * n_rhs, nparts, used, c->red_out, c->stream);
+    double red[7 * 64];
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(red, c->red_out, 7 * n_rhs * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = fail(XFFT_ECUDA, cudaGetErrorString(e));
+    for (int r = 0; r < n_rhs && st == XFFT_OK; ++r)
+      for (int k = 0; k < 6; ++k) sigma_int[6 * r + k] = red[7 * r + 1 + k];
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  cudaFree(scratch);
+  cudaFree(dd);
+  cudaFree(qq);
+  if (st == XFFT_OK && e != cudaSuccess) st = fail(XFFT_ECUDA, cudaGetErrorString(e));
+  return st;
+}
+
+extern "C" xfft_status xfft_apply(xfft_ctx* c, int n_rhs, const double* d, const double* eps_bar,
+                                  double* q, double* sigma_int, int precision, int ptrs_on_device) {
+  if (!c || !d || !q) return fail(XFFT_EINVAL, "NULL argument");
+  if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
+  if (n_rhs < 1 || n_rhs > 64) return fail(XFFT_EINVAL, "n_rhs must be in [1, 64]");
+  TRY(ensure_work(c, std::max(n_rhs, c->cap_rhs), c->cap_prec >= 0 ? c->cap_prec : c->opt.precision));
+  return precision == XFFT_FP64 ? apply_entry<double>(c, n_rhs, d, eps_bar, q, sigma_int, ptrs_on_device)
+                                : apply_entry<float>(c, n_rhs, d, eps_bar, q, sigma_int, ptrs_on_device);
+}
+
+template <typename T>
+static xfft_status prec_entry(xfft_ctx* c, int n_rhs, const double* f, double* z, double* rr, int on_dev) {
+  const long long stride = stride_of(c);
+  const size_t tot = (size_t)n_rhs * stride;
+  double* scratch = nullptr;
+  T* ff = nullptr;
+  T* zz = nullptr;
+  void* spec_save = c->spec;
+  void* spec = nullptr;
+  CU(dalloc(&scratch, tot));
+  CU(dalloc(&ff, tot));
+  CU(dalloc(&zz, tot));
+  CU(cudaMalloc(&spec, (size_t)n_rhs * fft_spectrum_elems(c->fft) * sizeof(T) * 2));
+  c->spec = spec;
+  xfft_status st = stage_in<T>(c, f, ff, tot, on_dev, scratch);
+  if (st == XFFT_OK) st = do_prec<T>(c, ff, zz, n_rhs, nullptr, -1, 0, 0, 0);
+  if (st == XFFT_OK) st = stage_out<T>(c, zz, z, tot, on_dev, scratch);
+  if (st == XFFT_OK && rr) {
+    const int nparts = nparts_of(c);
+    cudaError_t e = launch_reduce_partials(c->partials, n_rhs, nparts, precondition_blocks(c->fft, c->nX),
+                                           c->red_out, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rr, c->red_out, n_rhs * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = fail(XFFT_ECUDA, cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  c->spec = spec_save;
+  cudaFree(spec);
+  cudaFree(scratch);
+  cudaFree(ff);
+  cudaFree(zz);
+  if (st == XFFT_OK && e != cudaSuccess) st = fail(XFFT_ECUDA, cudaGetErrorString(e));
+  return st;
+}
+
+extern "C" xfft_status xfft_precondition(xfft_ctx* c, int n_rhs, const double* f, double* z, double* rr,
+                                         int precision, int ptrs_on_device) {
+  if (!c || !f || !z) return fail(XFFT_EINVAL, "NULL argument");
+  if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
+  if (n_rhs < 1 || n_rhs > 64) return fail(XFFT_EINVAL, "n_rhs must be in [1, 64]");
+  TRY(ensure_work(c, std::max(n_rhs, c->cap_rhs), c->cap_prec >= 0 ? c->cap_prec : c->opt.precision));
+  return precision == XFFT_FP64 ? prec_entry<double>(c, n_rhs, f, z, rr, ptrs_on_device)
+                                : prec_entry<float>(c, n_rhs, f, z, rr, ptrs_on_device);
+}
+
+extern "C" xfft_status xfft_get_setup(xfft_ctx* c, int* enr_nodes, double* D0, unsigned short* tet_code) {
+  if (!c) return fail(XFFT_EINVAL, "NULL argument");
+  if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
+  cudaStream_t s = c->stream;
+  if (enr_nodes && c->nX > 0)
+    CU(cudaMemcpyAsync(enr_nodes, c->enr_nodes, c->nX * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (D0 && c->nX > 0) {
+    // device layout [component][j]; API layout [j][component]
+    std::vector<double> tmp(3 * (size_t)c->nX);
+    CU(cudaMemcpyAsync(tmp.data(), c->D, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int j = 0; j < c->nX; ++j)
+      for (int k = 0; k < 3; ++k) D0[3 * (size_t)j + k] = tmp[(size_t)k * c->nX + j];
+  }
+  if (tet_code)
+    CU(cudaMemcpyAsync(tet_code, c->code, c->g.N * sizeof(uint16_t), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return XFFT_OK;
+}

@@ -1,0 +1,218 @@
+// Vector updates and FP64 scalar finalisation of the linear CG of Algorithm 1.
+//
+// Reading of Algorithm 1 (the printed sign of f - alpha z does not match r(u) = A u - b):
+// f is the negative residual -b - A u, z = A d is the linear part of the residual map,
+//   alpha = res^2 / <A d, d>,  u += alpha d,  f -= alpha A d,  z = P^{-1} f,
+//   res_new^2 = f^T z,  beta = res_new^2 / res^2,  d = z + beta d,
+// and the loop stops once sqrt(res^2 / |Y|) <= tol ||<sigma(u)>_Y|| (eqs. stoppingCriterion,
+// convergence; dividing by |Y| makes both sides stresses).  <sigma(u)>_Y is tracked as
+// sigma_int(u + alpha d) = sigma_int(u) + alpha int C grad^s d with the integral fused into the
+// stiffness apply.  All scalars are FP64 and live on the device: one finalisation block per
+// right-hand side reduces the per-block partial sums in a fixed order (deterministic).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "xfft_kernels.h"
+
+namespace xfft {
+
+template <typename T>
+__global__ void k_axpy_cg(T* __restrict__ u, T* __restrict__ f, const T* __restrict__ d,
+                          const T* __restrict__ q, const RhsState* __restrict__ st, long long stride) {
+  const int rhs = blockIdx.y;
+  if (!st[rhs].active) return;
+  const T a = (T)st[rhs].alpha;
+  T* ur = u + rhs * stride;
+  T* fr = f + rhs * stride;
+  const T* dr = d + rhs * stride;
+  const T* qr = q + rhs * stride;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < stride;
+       i += (long long)gridDim.x * blockDim.x) {
+    ur[i] += a * dr[i];
+    fr[i] -= a * qr[i];
+  }
+}
+
+template <typename T>
+__global__ void k_xpby(T* __restrict__ d, const T* __restrict__ z, const RhsState* __restrict__ st,
+                       long long stride) {
+  const int rhs = blockIdx.y;
+  if (!st[rhs].active) return;
+  const T b = (T)st[rhs].beta;
+  T* dr = d + rhs * stride;
+  const T* zr = z + rhs * stride;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < stride;
+       i += (long long)gridDim.x * blockDim.x)
+    dr[i] = zr[i] + b * dr[i];
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_scale_copy(const Tin* __restrict__ x, Tout* __restrict__ y, double a,
+                             long long stride, const int* __restrict__ active) {
+  const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
+  const Tin* xr = x + rhs * stride;
+  Tout* yr = y + rhs * stride;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < stride;
+       i += (long long)gridDim.x * blockDim.x)
+    yr[i] = (Tout)(a * (double)xr[i]);
+}
+
+template <typename T>
+__global__ void k_add_to_double(double* __restrict__ u, const T* __restrict__ dlt, long long stride,
+                                const int* __restrict__ active) {
+  const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
+  double* ur = u + rhs * stride;
+  const T* dr = dlt + rhs * stride;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < stride;
+       i += (long long)gridDim.x * blockDim.x)
+    ur[i] += (double)dr[i];
+}
+
+static unsigned vec_blocks(long long stride) {
+  long long nb = (stride + 255) / 256;
+  if (nb > 2048) nb = 2048;
+  return (unsigned)(nb < 1 ? 1 : nb);
+}
+
+template <typename T>
+cudaError_t launch_axpy_cg(T* u, T* f, const T* d, const T* q, const RhsState* st, long long stride,
+                           int n_rhs, cudaStream_t s) {
+  k_axpy_cg<T><<<dim3(vec_blocks(stride), n_rhs), 256, 0, s>>>(u, f, d, q, st, stride);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_xpby(T* d, const T* z, const RhsState* st, long long stride, int n_rhs,
+                        cudaStream_t s) {
+  k_xpby<T><<<dim3(vec_blocks(stride), n_rhs), 256, 0, s>>>(d, z, st, stride);
+  return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_scale_copy(const Tin* x, Tout* y, double a, long long stride, int n_rhs,
+                              const int* active, cudaStream_t s) {
+  k_scale_copy<Tin, Tout><<<dim3(vec_blocks(stride), n_rhs), 256, 0, s>>>(x, y, a, stride, active);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_add_to_double(double* u, const T* dlt, long long stride, int n_rhs,
+                                 const int* active, cudaStream_t s) {
+  k_add_to_double<T><<<dim3(vec_blocks(stride), n_rhs), 256, 0, s>>>(u, dlt, stride, active);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_axpy_cg<float>(float*, float*, const float*, const float*,
+                                           const RhsState*, long long, int, cudaStream_t);
+template cudaError_t launch_axpy_cg<double>(double*, double*, const double*, const double*,
+                                            const RhsState*, long long, int, cudaStream_t);
+template cudaError_t launch_xpby<float>(float*, const float*, const RhsState*, long long, int,
+                                        cudaStream_t);
+template cudaError_t launch_xpby<double>(double*, const double*, const RhsState*, long long, int,
+                                         cudaStream_t);
+template cudaError_t launch_scale_copy<double, double>(const double*, double*, double, long long,
+                                                       int, const int*, cudaStream_t);
+template cudaError_t launch_scale_copy<double, float>(const double*, float*, double, long long,
+                                                      int, const int*, cudaStream_t);
+template cudaError_t launch_scale_copy<float, double>(const float*, double*, double, long long,
+                                                      int, const int*, cudaStream_t);
+template cudaError_t launch_scale_copy<float, float>(const float*, float*, double, long long, int,
+                                                     const int*, cudaStream_t);
+template cudaError_t launch_add_to_double<float>(double*, const float*, long long, int,
+                                                 const int*, cudaStream_t);
+template cudaError_t launch_add_to_double<double>(double*, const double*, long long, int,
+                                                  const int*, cudaStream_t);
+
+// ---------------------------------------------------------------- finalisation
+__device__ inline bool stop_rule(const RhsState& s, const FinArgs& fa) {
+  if (!(s.rr > 0.0)) return true;
+  if (fa.crit == 1) return s.rr <= fa.tol * fa.tol * s.rr0;
+  double sn = 0.0;
+  for (int k = 0; k < 6; ++k) sn += s.sig[k] * s.sig[k];
+  return sqrt(s.rr / fa.volY) <= fa.tol * sqrt(sn) / fa.volY;
+}
+
+__global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
+                           const double* __restrict__ partials, FinArgs fa, int ncount) {
+  __shared__ double red[7 * 32];
+  const int rhs = blockIdx.x;
+  RhsState& s = st[rhs];
+  if (!s.active) return;  // uniform per block
+  const int nv = (fa.mode <= 1) ? 7 : 1;
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < ncount; i += blockDim.x)
+    for (int k = 0; k < nv; ++k) v[k] += partials[((long long)rhs * nv + k) * fa.nparts + i];
+  double tot[7];
+  block_sum<7>(v, red, tot);
+  if (threadIdx.x != 0) return;
+  if (fa.mode == 0) {
+    for (int k = 0; k < 6; ++k) s.sig[k] = tot[1 + k];
+  } else if (fa.mode == 1) {
+    s.dq = tot[0];
+    for (int k = 0; k < 6; ++k) s.sd[k] = tot[1 + k];
+    const double a = s.rr / s.dq;
+    if (!(s.dq > 0.0) || !isfinite(a)) {
+      s.status = 5;
+      s.active = 0;
+      s.alpha = 0.0;
+    } else {
+      s.alpha = a;
+      for (int k = 0; k < 6; ++k) s.sig[k] += a * s.sd[k];
+    }
+  } else {
+    const double rr = tot[0];
+    if (!isfinite(rr)) {
+      s.status = 5;
+      s.active = 0;
+    } else if (fa.mode == 3) {
+      s.rr = rr;
+      s.rr0 = rr;
+      s.beta = 0.0;
+      if (stop_rule(s, fa)) {
+        s.converged = 1;
+        s.active = 0;
+      }
+    } else {
+      s.beta = s.rr > 0.0 ? rr / s.rr : 0.0;
+      s.rr = rr;
+      s.iters += 1;
+      if (stop_rule(s, fa)) {
+        s.converged = 1;
+        s.active = 0;
+      } else if (s.iters >= fa.maxit) {
+        s.status = 4;
+        s.active = 0;
+      }
+    }
+  }
+  act[rhs] = s.active;
+}
+
+cudaError_t launch_finalize(RhsState* st, const double* partials, FinArgs fa, int n_rhs, int* act,
+                            cudaStream_t s) {
+  k_finalize<<<n_rhs, 256, 0, s>>>(st, act, partials, fa, fa.nparts_used);
+  return cudaGetLastError();
+}
+
+__global__ void k_init_state(RhsState* st, int* act, int n_rhs, const int* mask) {
+  const int r = threadIdx.x;
+  if (r >= n_rhs) return;
+  RhsState s;
+  s.rr = s.rr0 = s.dq = s.alpha = s.beta = 0.0;
+  for (int k = 0; k < 6; ++k) s.sig[k] = s.sd[k] = 0.0;
+  s.active = mask ? mask[r] : 1;
+  s.iters = 0;
+  s.status = 0;
+  s.converged = 0;
+  st[r] = s;
+  act[r] = s.active;
+}
+
+cudaError_t launch_init_state(RhsState* st, int* act, int n_rhs, const int* mask, cudaStream_t s) {
+  k_init_state<<<1, 64, 0, s>>>(st, act, n_rhs, mask);
+  return cudaGetLastError();
+}
+
+}  // namespace xfft

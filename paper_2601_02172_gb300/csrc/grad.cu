@@ -1,0 +1,256 @@
+// Gradient of a scalar loss through the effective stiffness (not in the paper).
+//
+// The six converged load cases u_k (eps_bar = E_k, Mandel basis) are stationary points of the
+// cell energy, and the X-FEM basis (including the scaling D0, built from grad^s only, eq.
+// XFFT_diagonal) does not depend on C, so for any parameter theta of C
+//   dC_kl / dtheta = (1/|Y|) int_Y eps_k : (dC/dtheta) : eps_l,   eps_k = E_k + grad^s u_k
+// (the energy identity used in App. A).  With C = s_v (lambda_p I(x)I + 2 mu_p I_sym) and
+// G = dLoss/dC_eff this gives, per tet or cut-tet side,
+//   dL/dlambda_p += s_v sum_kl G_kl int tr eps_k tr eps_l / |Y|
+//   dL/dmu_p     += s_v sum_kl G_kl int 2 eps_k : eps_l / |Y|
+//   dL/ds_v      += sum_kl G_kl int eps_k : C_p : eps_l / |Y|
+// and the energy form C_kl = int eps_k : C : eps_l / |Y| as a by-product.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "xfft_kernels.h"
+
+namespace xfft {
+
+constexpr int kNG = 25;  // partial values: dl[2], dm[2], C_energy (21 upper entries)
+
+__device__ __forceinline__ int upper_idx(int k, int l) {
+  // k <= l, row-major upper triangle of 6x6
+  return k * 6 - (k * (k - 1)) / 2 + (l - k);
+}
+
+__device__ __forceinline__ void unit_strain(int k, double (&e)[6]) {
+  const double r = 0.70710678118654752440;
+  for (int i = 0; i < 6; ++i) e[i] = 0.0;
+  e[k] = k < 3 ? 1.0 : r;
+}
+
+__device__ __forceinline__ double dd6(const double* a, const double* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + 2.0 * (a[3] * b[3] + a[4] * b[4] + a[5] * b[5]);
+}
+
+// block: 32 voxels (x) by 6 tets (y)
+__global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U, const GradArgs a,
+                                                     double* __restrict__ dscale) {
+  __shared__ double sds[6][32];
+  __shared__ double red[kNG * 32];
+  __shared__ double Gs[36];
+  const int lane = threadIdx.x, t = threadIdx.y;
+  const int tid = lane + 32 * t;
+  if (tid < 36) Gs[tid] = a.G[tid];
+  __syncthreads();
+  const GridDev& g = a.g;
+  const double inv = 1.0 / g.volY;
+  double ih[3];
+  for (int k = 0; k < 3; ++k) ih[k] = 1.0 / g.h[k];
+  double acc[kNG];
+  for (int i = 0; i < kNG; ++i) acc[i] = 0.0;
+  const long long ngroups = (g.N + 31) / 32;
+  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const long long v = grp * 32 + lane;
+    double contrib = 0.0;
+    if (v < g.N) {
+      const unsigned cd = (a.code[v] >> (2 * t)) & 3u;
+      if (cd != 2u) {
+        const int k3 = (int)(v % g.n2);
+        const int j3 = (int)((v / g.n2) % g.n1);
+        const int i3 = (int)(v / ((long long)g.n1 * g.n2));
+        long long nd[4];
+        for (int c = 0; c < 4; ++c) nd[c] = corner_node(g, i3, j3, k3, tet_corner(t, c));
+        const int p = perm_p(t), q = perm_q(t), r = perm_r(t);
+        double eps[6][6], tr[6];
+        for (int k = 0; k < 6; ++k) {
+          const double* uk = U + k * a.stride;
+          double H[3][3];
+          for (int i = 0; i < 3; ++i) {
+            const double u0 = uk[i * g.N + nd[0]], u1 = uk[i * g.N + nd[1]];
+            const double u2 = uk[i * g.N + nd[2]], u3 = uk[i * g.N + nd[3]];
+            H[i][p] = (u1 - u0) * ih[p];
+            H[i][q] = (u2 - u1) * ih[q];
+            H[i][r] = (u3 - u2) * ih[r];
+          }
+          double E[6];
+          unit_strain(k, E);
+          eps[k][0] = H[0][0] + E[0];
+          eps[k][1] = H[1][1] + E[1];
+          eps[k][2] = H[2][2] + E[2];
+          eps[k][3] = 0.5 * (H[1][2] + H[2][1]) + E[3];
+          eps[k][4] = 0.5 * (H[0][2] + H[2][0]) + E[4];
+          eps[k][5] = 0.5 * (H[0][1] + H[1][0]) + E[5];
+          tr[k] = eps[k][0] + eps[k][1] + eps[k][2];
+        }
+        const int ph = (int)cd;
+        const double lam = a.ph.lam[ph], mu = a.ph.mu[ph];
+        const double sv = a.scale ? (double)a.scale[v] : 1.0;
+        const double w = g.vol_tet * inv;
+        double ql = 0.0, qm = 0.0;
+        for (int k = 0; k < 6; ++k)
+          for (int l = k; l < 6; ++l) {
+            const double tt = tr[k] * tr[l];
+            const double ee = 2.0 * dd6(eps[k], eps[l]);
+            const double gk = (k == l) ? Gs[k * 6 + l] : Gs[k * 6 + l] + Gs[l * 6 + k];
+            ql += gk * tt;
+            qm += gk * ee;
+            acc[4 + upper_idx(k, l)] += w * sv * (lam * tt + mu * ee);
+          }
+        acc[ph] += w * sv * ql;
+        acc[2 + ph] += w * sv * qm;
+        contrib = w * (lam * ql + mu * qm);
+      }
+    }
+    sds[t][lane] = contrib;
+    __syncthreads();
+    if (t == 0 && v < g.N)
+      dscale[v] = sds[0][lane] + sds[1][lane] + sds[2][lane] + sds[3][lane] + sds[4][lane] + sds[5][lane];
+    __syncthreads();
+  }
+  double tot[kNG];
+  block_sum<kNG>(acc, red, tot);
+  if (tid == 0)
+    for (int i = 0; i < kNG; ++i) a.partials[(long long)i * a.nparts + blockIdx.x] = tot[i];
+}
+
+__global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
+                                                  const double* __restrict__ isD, const CutData cd,
+                                                  const GradArgs a, double* __restrict__ dscale) {
+  __shared__ double red[kNG * 32];
+  const GridDev& g = a.g;
+  const long long N = g.N;
+  const int nX = a.nX, ncut = cd.ncut;
+  const double inv = 1.0 / g.volY;
+  double ih[3];
+  for (int k = 0; k < 3; ++k) ih[k] = 1.0 / g.h[k];
+  double acc[kNG];
+  for (int i = 0; i < kNG; ++i) acc[i] = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
+    int nd[4], ei[4];
+    for (int k = 0; k < 4; ++k) {
+      nd[k] = cd.ip[k * ncut + e];
+      ei[k] = cd.ip[(4 + k) * ncut + e];
+    }
+    const int vox = cd.ip[8 * ncut + e];
+    const int t = cd.ip[9 * ncut + e];
+    double gr[4][3];
+    tet_grads<double>(t, ih, gr);
+    double L[4];
+    for (int b = 0; b < 4; ++b) L[b] = cd.dp[(long long)cut_f_L(b) * ncut + e];
+    const double sv = a.scale ? (double)a.scale[vox] : 1.0;
+    double contrib = 0.0;
+    for (int si = 0; si < 2; ++si) {
+      const double s = si == 0 ? 1.0 : -1.0;
+      const int ph = si == 0 ? 1 : 0;
+      const double lam = a.ph.lam[ph], mu = a.ph.mu[ph];
+      double c[4], gam[3] = {0, 0, 0};
+      for (int b = 0; b < 4; ++b) {
+        c[b] = fabs(L[b]) - s * L[b];
+        for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
+      }
+      double M[10];
+      for (int k = 0; k < 10; ++k) M[k] = cd.dp[(long long)cut_f_M(si, k) * ncut + e];
+      double Eb[6][4][6];  // [load case][b][component]
+      double trb[6][4];
+      for (int k = 0; k < 6; ++k) {
+        const double* uk = U + k * a.stride;
+        double us[4][3], ws[4][3];
+        for (int aa = 0; aa < 4; ++aa)
+          for (int x = 0; x < 3; ++x) {
+            us[aa][x] = uk[x * N + nd[aa]];
+            ws[aa][x] = uk[3 * N + (long long)x * nX + ei[aa]] * isD[(long long)x * nX + ei[aa]];
+          }
+        double Hs[3][3], Hw[3][3];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) {
+            Hs[i][j] = 0.0;
+            Hw[i][j] = 0.0;
+            for (int aa = 0; aa < 4; ++aa) {
+              Hs[i][j] += us[aa][i] * gr[aa][j];
+              Hw[i][j] += ws[aa][i] * gr[aa][j];
+            }
+          }
+        double E[6];
+        unit_strain(k, E);
+        const double es[6] = {Hs[0][0] + E[0], Hs[1][1] + E[1], Hs[2][2] + E[2],
+                              0.5 * (Hs[1][2] + Hs[2][1]) + E[3], 0.5 * (Hs[0][2] + Hs[2][0]) + E[4],
+                              0.5 * (Hs[0][1] + Hs[1][0]) + E[5]};
+        const double ew[6] = {Hw[0][0], Hw[1][1], Hw[2][2], 0.5 * (Hw[1][2] + Hw[2][1]),
+                              0.5 * (Hw[0][2] + Hw[2][0]), 0.5 * (Hw[0][1] + Hw[1][0])};
+        for (int b = 0; b < 4; ++b) {
+          const double* wb = ws[b];
+          const double sw[6] = {wb[0] * gam[0], wb[1] * gam[1], wb[2] * gam[2],
+                                0.5 * (wb[1] * gam[2] + wb[2] * gam[1]),
+                                0.5 * (wb[0] * gam[2] + wb[2] * gam[0]),
+                                0.5 * (wb[0] * gam[1] + wb[1] * gam[0])};
+          for (int x = 0; x < 6; ++x) Eb[k][b][x] = es[x] + c[b] * ew[x] + sw[x];
+          trb[k][b] = Eb[k][b][0] + Eb[k][b][1] + Eb[k][b][2];
+        }
+      }
+      double ql = 0.0, qm = 0.0;
+      for (int k = 0; k < 6; ++k)
+        for (int l = k; l < 6; ++l) {
+          double tt = 0.0, ee = 0.0;
+          for (int b = 0; b < 4; ++b)
+            for (int cc = 0; cc < 4; ++cc) {
+              const double m = M[midx(b, cc)];
+              tt += m * trb[k][b] * trb[l][cc];
+              ee += m * 2.0 * dd6(Eb[k][b], Eb[l][cc]);
+            }
+          const double gk = (k == l) ? a.G[k * 6 + l] : a.G[k * 6 + l] + a.G[l * 6 + k];
+          ql += gk * tt;
+          qm += gk * ee;
+          acc[4 + upper_idx(k, l)] += inv * sv * (lam * tt + mu * ee);
+        }
+      acc[ph] += inv * sv * ql;
+      acc[2 + ph] += inv * sv * qm;
+      contrib += inv * (lam * ql + mu * qm);
+    }
+    atomicAdd(&dscale[vox], contrib);
+  }
+  double tot[kNG];
+  block_sum<kNG>(acc, red, tot);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kNG; ++i)
+      a.partials[(long long)i * a.nparts + a.part_offset_cut + blockIdx.x] = tot[i];
+}
+
+int grad_blocks_uncut(const GridDev& g) {
+  const long long ngroups = (g.N + 31) / 32;
+  return (int)(ngroups < 4096 ? ngroups : 4096);
+}
+int grad_blocks_cut(int ncut) {
+  const int nb = (ncut + 63) / 64;
+  return nb < 1 ? 1 : (nb > 1024 ? 1024 : nb);
+}
+
+cudaError_t launch_grad(const double* U, const double* isD, CutData cd, const GradArgs& a,
+                        double* dscale, cudaStream_t s) {
+  k_grad_uncut<<<grad_blocks_uncut(a.g), dim3(32, 6), 0, s>>>(U, a, dscale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_grad_cut<<<grad_blocks_cut(cd.ncut), 64, 0, s>>>(U, isD, cd, a, dscale);
+  return cudaGetLastError();
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nparts, int ncount,
+                                  double* __restrict__ out) {
+  __shared__ double red[32];
+  const int k = blockIdx.x;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < ncount; i += blockDim.x) v += partials[(long long)k * nparts + i];
+  double vv[1] = {v}, tot[1];
+  block_sum<1>(vv, red, tot);
+  if (threadIdx.x == 0) out[k] = tot[0];
+}
+
+// out[k] = sum_{i < ncount} partials[k * nparts + i] for k < nvals
+cudaError_t launch_reduce_partials(const double* partials, int nvals, int nparts, int ncount,
+                                   double* out, cudaStream_t s) {
+  k_reduce_partials<<<nvals, 256, 0, s>>>(partials, nparts, ncount, out);
+  return cudaGetLastError();
+}
+
+}  // namespace xfft

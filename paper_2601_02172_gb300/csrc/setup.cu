@@ -1,0 +1,460 @@
+// Setup kernels of the X-FFT solver: snapping, cut-tet classification, enriched-node
+// numbering, per-side sub-tetrahedron moments and the scaling factors D0.
+//
+//  * Snap (Sec. 3): |L_i| < tau counts as on the interface, L_i <- 0.
+//  * A P1 tet is cut iff its nodal level-set values take both signs (the modified abs
+//    enrichment, eq. modifiedabsEnrichment, vanishes identically otherwise); the enriched
+//    nodes J are all nodes of cut tets (eq. X-FEM_space).  Enriched ids follow the node order.
+//  * Each side s of a cut tet (s = +: L_h > 0, s = -: L_h < 0) is a tetrahedron or a
+//    triangular prism bounded by the linearised interface L_h = 0 (Sec. 3, Fig. subdivision).
+//    Instead of quadrature points we store its exact moments int N_b and int N_b N_c of the
+//    parent P1 functions; every integrand of the method is a quadratic in the N_b on a side,
+//    so these moments reproduce the paper's exact sub-tetrahedron quadrature.
+//  * D0 per enriched DOF (node j, component k): int |sym(grad N_X^j (x) e_k)|^2
+//    (eq. XFFT_diagonal with the symmetrised gradient of the vector shape function).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xfft_kernels.h"
+
+namespace xfft {
+
+// ---------------------------------------------------------------- snap + classify
+__global__ void k_snap(const double* __restrict__ L, double* __restrict__ Ls, long long N,
+                       double tau) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = L[i];
+    Ls[i] = fabs(v) < tau ? 0.0 : v;
+  }
+}
+
+__global__ void k_classify(const double* __restrict__ Ls, GridDev g, uint16_t* __restrict__ code,
+                           int* __restrict__ cutcount, int* __restrict__ enr_flag) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.N;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(v % g.n2);
+    const int j = (int)((v / g.n2) % g.n1);
+    const int i = (int)(v / ((long long)g.n1 * g.n2));
+    double Lc[8];
+    long long nd[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      nd[c] = corner_node(g, i, j, k, c);
+      Lc[c] = Ls[nd[c]];
+    }
+    unsigned cd = 0;
+    int cnt = 0;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      const double a = Lc[0], b = Lc[tet_c1(t)], c = Lc[tet_c2(t)], d = Lc[7];
+      const double mn = fmin(fmin(a, b), fmin(c, d));
+      const double mx = fmax(fmax(a, b), fmax(c, d));
+      unsigned bits;
+      if (mn < 0.0 && mx > 0.0) {
+        bits = 2u;
+        ++cnt;
+        enr_flag[nd[0]] = 1;
+        enr_flag[nd[tet_c1(t)]] = 1;
+        enr_flag[nd[tet_c2(t)]] = 1;
+        enr_flag[nd[7]] = 1;
+      } else {
+        bits = mn < 0.0 ? 0u : 1u;  // minus phase if any vertex is negative
+      }
+      cd |= bits << (2 * t);
+    }
+    code[v] = (uint16_t)cd;
+    cutcount[v] = cnt;
+  }
+}
+
+cudaError_t launch_snap_classify(const double* L, double* Ls, uint16_t* code, int* cutcount,
+                                 int* enr_flag, GridDev g, double tau, cudaStream_t s) {
+  const int nb = (int)((g.N + kThreads - 1) / kThreads);
+  const int grid = nb < 65535 * 16 ? nb : 65535 * 16;
+  cudaError_t e = cudaMemsetAsync(enr_flag, 0, sizeof(int) * g.N, s);
+  if (e != cudaSuccess) return e;
+  k_snap<<<grid, kThreads, 0, s>>>(L, Ls, g.N, tau);
+  k_classify<<<grid, kThreads, 0, s>>>(Ls, g, code, cutcount, enr_flag);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- exclusive scan (int32)
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kThreads * kScanItems;
+
+__device__ inline int block_exclusive_scan(int v, int* smem, int* total) {
+  // returns the exclusive prefix of v over the block; *total receives the block sum
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    int w = lane < nw ? smem[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) smem[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  const int before = wid > 0 ? smem[wid - 1] : 0;
+  *total = smem[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+// Phase 1/3: each block scans one tile in place (exclusive) and records its total.
+// in and out may alias (in-place scan): no __restrict__ on them
+__global__ void k_scan_tiles(const int* in, int* out, long long n, int* __restrict__ tile_sums) {
+  __shared__ int smem[32];
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  int vals[kScanItems];
+  int sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long idx = base + k;
+    vals[k] = idx < n ? in[idx] : 0;
+    sum += vals[k];
+  }
+  int total;
+  int run = block_exclusive_scan(sum, smem, &total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const long long idx = base + k;
+    if (idx < n) out[idx] = run;
+    run += vals[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// Phase 2: one block scans the tile sums (exclusive) and writes the grand total.
+__global__ void k_scan_sums(int* __restrict__ sums, int nt, int* __restrict__ total_out) {
+  __shared__ int smem[32];
+  const int per = (nt + blockDim.x - 1) / blockDim.x;
+  const int beg = threadIdx.x * per;
+  int local = 0;
+  for (int k = 0; k < per; ++k)
+    if (beg + k < nt) local += sums[beg + k];
+  int total;
+  int run = block_exclusive_scan(local, smem, &total);
+  for (int k = 0; k < per; ++k) {
+    if (beg + k < nt) {
+      const int v = sums[beg + k];
+      sums[beg + k] = run;
+      run += v;
+    }
+  }
+  if (threadIdx.x == 0) *total_out = total;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, long long n, const int* __restrict__ sums) {
+  const int add = sums[blockIdx.x];
+  const long long base = (long long)blockIdx.x * kScanTile;
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+    const long long idx = base + k;
+    if (idx < n) out[idx] += add;
+  }
+}
+
+size_t scan_tmp_ints(long long n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 32; }
+
+cudaError_t launch_scan(const int* in, int* out, long long n, int* d_total, int* d_tmp,
+                        cudaStream_t s) {
+  const long long nt = (n + kScanTile - 1) / kScanTile;
+  if (nt > (1LL << 30)) return cudaErrorInvalidValue;
+  k_scan_tiles<<<(unsigned)nt, kThreads, 0, s>>>(in, out, n, d_tmp);
+  k_scan_sums<<<1, 1024, 0, s>>>(d_tmp, (int)nt, d_total);
+  k_scan_add<<<(unsigned)nt, kThreads, 0, s>>>(out, n, d_tmp);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- lists
+__global__ void k_build_lists(const uint16_t* __restrict__ code, const int* __restrict__ cutoff,
+                              const int* __restrict__ enr_flag, int* __restrict__ enr_id,
+                              int* __restrict__ enr_nodes, int* __restrict__ cut_ints, int ncut,
+                              GridDev g) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.N;
+       v += (long long)gridDim.x * blockDim.x) {
+    // enr_id holds the exclusive scan of enr_flag on entry
+    if (enr_flag[v]) {
+      enr_nodes[enr_id[v]] = (int)v;
+    } else {
+      enr_id[v] = -1;
+    }
+    const unsigned cd = code[v];
+    int off = cutoff[v];
+    for (int t = 0; t < 6; ++t) {
+      if (((cd >> (2 * t)) & 3u) == 2u) {
+        cut_ints[8 * ncut + off] = (int)v;  // voxel
+        cut_ints[9 * ncut + off] = t;       // tet
+        ++off;
+      }
+    }
+  }
+}
+
+cudaError_t launch_build_lists(const uint16_t* code, const int* cutoff, const int* enr_flag,
+                               int* enr_id, int* enr_nodes, int* cut_ints, int ncut, GridDev g,
+                               cudaStream_t s) {
+  const int nb = (int)((g.N + kThreads - 1) / kThreads);
+  const int grid = nb < 65535 * 16 ? nb : 65535 * 16;
+  k_build_lists<<<grid, kThreads, 0, s>>>(code, cutoff, enr_flag, enr_id, enr_nodes, cut_ints,
+                                           ncut, g);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- side moments
+struct Moments {
+  double m[4];
+  double M[10];
+};
+
+__device__ inline double det4(const double b[4][4]) {
+  // Laplace expansion along the first row
+  double d = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int cols[3];
+    int q = 0;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+      if (cc != c) cols[q++] = cc;
+    const double m3 = b[1][cols[0]] * (b[2][cols[1]] * b[3][cols[2]] - b[2][cols[2]] * b[3][cols[1]])
+                    - b[1][cols[1]] * (b[2][cols[0]] * b[3][cols[2]] - b[2][cols[2]] * b[3][cols[0]])
+                    + b[1][cols[2]] * (b[2][cols[0]] * b[3][cols[1]] - b[2][cols[1]] * b[3][cols[0]]);
+    d += ((c & 1) ? -1.0 : 1.0) * b[0][c] * m3;
+  }
+  return d;
+}
+
+// Add the moments of the sub-tetrahedron whose vertices have parent barycentric coordinates
+// beta[v][.]: its volume is |det beta| |T|, int N_b = vol/4 sum_v beta_vb and
+// int N_b N_c = vol/20 (sum_v beta_vb beta_vc + (sum_v beta_vb)(sum_v beta_vc)).
+__device__ inline void add_subtet(Moments& acc, const double b0[4], const double b1[4],
+                                  const double b2[4], const double b3[4], double vol) {
+  const double B[4][4] = {{b0[0], b0[1], b0[2], b0[3]},
+                          {b1[0], b1[1], b1[2], b1[3]},
+                          {b2[0], b2[1], b2[2], b2[3]},
+                          {b3[0], b3[1], b3[2], b3[3]}};
+  const double vs = fabs(det4(B)) * vol;
+  double S[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) S[c] = B[0][c] + B[1][c] + B[2][c] + B[3][c];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc.m[c] += 0.25 * vs * S[c];
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int c = b; c < 4; ++c) {
+      const double pp = B[0][b] * B[0][c] + B[1][b] * B[1][c] + B[2][b] * B[2][c] + B[3][b] * B[3][c];
+      acc.M[midx(b, c)] += vs / 20.0 * (pp + S[b] * S[c]);
+    }
+}
+
+__device__ inline void unit_bary(int a, double out[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out[c] = (c == a) ? 1.0 : 0.0;
+}
+
+// barycentric point where L_h = 0 on the edge (a, b) (L_a L_b < 0), or vertex a if L_a = 0
+__device__ inline void edge_point(const double L[4], int a, int b, double out[4]) {
+  if (L[a] == 0.0) {
+    unit_bary(a, out);
+    return;
+  }
+  const double t = L[a] / (L[a] - L[b]);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out[c] = 0.0;
+  out[a] = 1.0 - t;
+  out[b] = t;
+}
+
+// Moments of side s (+1: s L_h >= 0) of a cut tet with nodal values L.
+//   one strictly positive vertex a:   tet (a, edge points to the others)
+//   one strictly negative vertex q:   prism (other three) -> (their edge points to q)
+//   two and two:                       prism (a1, x11, x12) -> (a2, x21, x22)
+__device__ void side_moments(const double L[4], int s, double vol, Moments& out) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out.m[c] = 0.0;
+#pragma unroll
+  for (int c = 0; c < 10; ++c) out.M[c] = 0.0;
+  int P[4], Q[4], Z[4];
+  int np = 0, nq = 0, nz = 0;
+  for (int a = 0; a < 4; ++a) {
+    const double x = s * L[a];
+    if (x > 0.0)
+      P[np++] = a;
+    else if (x < 0.0)
+      Q[nq++] = a;
+    else
+      Z[nz++] = a;
+  }
+  double v[6][4];
+  if (np == 1) {
+    const int a = P[0];
+    unit_bary(a, v[0]);
+    int k = 1;
+    for (int i = 0; i < nq; ++i) edge_point(L, a, Q[i], v[k++]);
+    for (int i = 0; i < nz; ++i) unit_bary(Z[i], v[k++]);
+    add_subtet(out, v[0], v[1], v[2], v[3], vol);
+  } else if (nq == 1) {
+    const int q = Q[0];
+    int k = 0;
+    for (int a = 0; a < 4; ++a) {
+      if (a == q) continue;
+      unit_bary(a, v[k]);
+      edge_point(L, a, q, v[3 + k]);
+      ++k;
+    }
+    add_subtet(out, v[0], v[1], v[2], v[3], vol);
+    add_subtet(out, v[1], v[2], v[3], v[4], vol);
+    add_subtet(out, v[2], v[3], v[4], v[5], vol);
+  } else {
+    const int a1 = P[0], a2 = P[1], b1 = Q[0], b2 = Q[1];
+    unit_bary(a1, v[0]);
+    edge_point(L, a1, b1, v[1]);
+    edge_point(L, a1, b2, v[2]);
+    unit_bary(a2, v[3]);
+    edge_point(L, a2, b1, v[4]);
+    edge_point(L, a2, b2, v[5]);
+    add_subtet(out, v[0], v[1], v[2], v[3], vol);
+    add_subtet(out, v[1], v[2], v[3], v[4], vol);
+    add_subtet(out, v[2], v[3], v[4], v[5], vol);
+  }
+}
+
+__global__ void k_cut_geometry(const double* __restrict__ Ls, int* __restrict__ ip,
+                               double* __restrict__ dp, int ncut, GridDev g) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
+    const long long v = ip[8 * ncut + e];
+    const int t = ip[9 * ncut + e];
+    const int k = (int)(v % g.n2);
+    const int j = (int)((v / g.n2) % g.n1);
+    const int i = (int)(v / ((long long)g.n1 * g.n2));
+    double L[4];
+    for (int a = 0; a < 4; ++a) {
+      const long long nd = corner_node(g, i, j, k, tet_corner(t, a));
+      ip[a * ncut + e] = (int)nd;
+      L[a] = Ls[nd];
+      dp[cut_f_L(a) * (long long)ncut + e] = L[a];
+    }
+    for (int si = 0; si < 2; ++si) {
+      Moments mo;
+      side_moments(L, si == 0 ? +1 : -1, g.vol_tet, mo);
+      for (int b = 0; b < 4; ++b) dp[cut_f_m(si, b) * (long long)ncut + e] = mo.m[b];
+      for (int c = 0; c < 10; ++c) dp[cut_f_M(si, c) * (long long)ncut + e] = mo.M[c];
+    }
+  }
+}
+
+__global__ void k_cut_eids(int* __restrict__ ip, const int* __restrict__ enr_id, int ncut) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
+    for (int a = 0; a < 4; ++a) ip[(4 + a) * ncut + e] = enr_id[ip[a * ncut + e]];
+  }
+}
+
+cudaError_t launch_cut_geometry(const double* Ls, CutData cd, double* dp_mut, int* ip_mut,
+                                GridDev g, cudaStream_t s) {
+  if (cd.ncut == 0) return cudaSuccess;
+  const int nb = (cd.ncut + 127) / 128;
+  k_cut_geometry<<<nb, 128, 0, s>>>(Ls, ip_mut, dp_mut, cd.ncut, g);
+  return cudaGetLastError();
+}
+
+// enr ids of the cut-tet nodes (needs enr_id); called after launch_cut_geometry
+cudaError_t launch_cut_eids(int* ip_mut, const int* enr_id, int ncut, cudaStream_t s) {
+  if (ncut == 0) return cudaSuccess;
+  k_cut_eids<<<(ncut + 255) / 256, 256, 0, s>>>(ip_mut, enr_id, ncut);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- scaling factors D0
+// On side s of a cut tet, grad N_X^a(x) = sum_b N_b(x) V_ab with V_ab = c_b g_a + delta_ab gamma,
+// c_b = |L_b| - s L_b, gamma = sum_b c_b g_b.  Hence
+//   D_{a,k} += 1/2 sum_bc M_bc (V_ab . V_ac + V_ab[k] V_ac[k]).
+__global__ void k_cut_scaling(const int* __restrict__ ip, const double* __restrict__ dp, int ncut,
+                              double* __restrict__ D, int nX, GridDev g) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
+    const int t = ip[9 * ncut + e];
+    double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
+    double gr[4][3];
+    tet_grads<double>(t, ih, gr);
+    double L[4];
+    for (int b = 0; b < 4; ++b) L[b] = dp[cut_f_L(b) * (long long)ncut + e];
+    double acc[4][3] = {};
+    for (int si = 0; si < 2; ++si) {
+      const double s = si == 0 ? 1.0 : -1.0;
+      double c[4], gam[3] = {0.0, 0.0, 0.0};
+      for (int b = 0; b < 4; ++b) {
+        c[b] = fabs(L[b]) - s * L[b];
+        for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
+      }
+      double M[10];
+      for (int k = 0; k < 10; ++k) M[k] = dp[cut_f_M(si, k) * (long long)ncut + e];
+      for (int a = 0; a < 4; ++a) {
+        double V[4][3];
+        for (int b = 0; b < 4; ++b)
+          for (int x = 0; x < 3; ++x) V[b][x] = c[b] * gr[a][x] + (a == b ? gam[x] : 0.0);
+        for (int b = 0; b < 4; ++b)
+          for (int cc = 0; cc < 4; ++cc) {
+            const double w = M[midx(b, cc)];
+            const double dot = V[b][0] * V[cc][0] + V[b][1] * V[cc][1] + V[b][2] * V[cc][2];
+            for (int x = 0; x < 3; ++x) acc[a][x] += 0.5 * w * (dot + V[b][x] * V[cc][x]);
+          }
+      }
+    }
+    for (int a = 0; a < 4; ++a) {
+      const int j = ip[(4 + a) * ncut + e];
+      for (int x = 0; x < 3; ++x) atomicAdd(&D[(long long)x * nX + j], acc[a][x]);
+    }
+  }
+}
+
+cudaError_t launch_cut_scaling(CutData cd, double* D, int nX, GridDev g, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(D, 0, sizeof(double) * 3 * (size_t)nX, s);
+  if (e != cudaSuccess || cd.ncut == 0) return e;
+  k_cut_scaling<<<(cd.ncut + 127) / 128, 128, 0, s>>>(cd.ip, cd.dp, cd.ncut, D, nX, g);
+  return cudaGetLastError();
+}
+
+__global__ void k_finish_scaling(const double* __restrict__ D, double* __restrict__ isd,
+                                 float* __restrict__ isf, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = D[i] > 0.0 ? 1.0 / sqrt(D[i]) : 0.0;
+    isd[i] = v;
+    isf[i] = (float)v;
+  }
+}
+
+cudaError_t launch_finish_scaling(const double* D, double* isd, float* isf, int nX,
+                                  cudaStream_t s) {
+  if (nX == 0) return cudaSuccess;
+  const long long n = 3LL * nX;
+  k_finish_scaling<<<(int)((n + 255) / 256), 256, 0, s>>>(D, isd, isf, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+cudaError_t launch_cut_to_float(const double* dp, float* fp, long long count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  long long nb = (count + 255) / 256;
+  if (nb > 65535LL * 16) nb = 65535LL * 16;
+  k_to_float<<<(int)nb, 256, 0, s>>>(dp, fp, count);
+  return cudaGetLastError();
+}
+
+}  // namespace xfft

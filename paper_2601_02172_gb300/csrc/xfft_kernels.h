@@ -1,0 +1,137 @@
+// Host-side prototypes of the kernel launchers (internal to libxfft).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xfft_common.cuh"
+
+namespace xfft {
+
+// Per-cut-tet data, structure of arrays of length ncut.
+//   ints   (10 fields): node[a] (a<4), eid[a] (a<4), voxel, tet
+//   reals  (32 fields): L[b] (b<4), then for side s = 0 (plus) and 1 (minus):
+//                       m[s][b] = int_side N_b (b<4) and M[s][k] = int_side N_b N_c
+//                       (k<10, packed (00,01,02,03,11,12,13,22,23,33))
+struct CutData {
+  const int* ip;
+  const double* dp;
+  const float* fp;
+  int ncut;
+};
+constexpr int kCutInts = 10;
+constexpr int kCutReals = 32;
+__host__ __device__ constexpr int cut_f_L(int b) { return b; }
+__host__ __device__ constexpr int cut_f_m(int s, int b) { return 4 + 14 * s + b; }
+__host__ __device__ constexpr int cut_f_M(int s, int k) { return 8 + 14 * s + k; }
+__host__ __device__ constexpr int midx(int b, int c) {
+  // packed index of the symmetric 4x4 entry (b,c)
+  return b <= c ? (b == 0 ? c : b == 1 ? 3 + c : b == 2 ? 5 + c : 9)
+                : (c == 0 ? b : c == 1 ? 3 + b : c == 2 ? 5 + b : 9);
+}
+
+// ---- setup (setup.cu)
+cudaError_t launch_snap_classify(const double* L, double* Ls, uint16_t* code, int* cutcount,
+                                 int* enr_flag, GridDev g, double tau, cudaStream_t s);
+// exclusive scan of n ints into out (may alias in); writes the total to *d_total (device)
+cudaError_t launch_scan(const int* in, int* out, long long n, int* d_total, int* d_tmp,
+                        cudaStream_t s);
+size_t scan_tmp_ints(long long n);
+cudaError_t launch_build_lists(const uint16_t* code, const int* cutoff, const int* enr_flag,
+                               int* enr_id, int* enr_nodes, int* cut_ints, int ncut, GridDev g,
+                               cudaStream_t s);
+cudaError_t launch_cut_geometry(const double* Ls, CutData cd, double* dp_mut, int* ip_mut,
+                                GridDev g, cudaStream_t s);
+cudaError_t launch_cut_eids(int* ip_mut, const int* enr_id, int ncut, cudaStream_t s);
+cudaError_t launch_cut_scaling(CutData cd, double* D, int nX, GridDev g, cudaStream_t s);
+cudaError_t launch_finish_scaling(const double* D, double* isd, float* isf, int nX,
+                                  cudaStream_t s);
+cudaError_t launch_cut_to_float(const double* dp, float* fp, long long count, cudaStream_t s);
+
+// ---- stiffness apply (apply.cu)
+struct ApplyArgs {
+  GridDev g;
+  PhaseDev ph;
+  const uint16_t* code;
+  const float* scale;      // per-voxel modulus scale or nullptr
+  const double* eps;       // per RHS Mandel strain (n_rhs x 6) or nullptr (linear apply)
+  const int* active;       // per RHS flag or nullptr (all active)
+  long long stride;        // elements per RHS vector (3 (N + nX))
+  int nX;
+  double* partials;        // [rhs][7][nparts]: 0 = <d, A d> (energy), 1..6 = int C eps (Mandel)
+  int nparts;              // partial slots per RHS and component
+  int part_offset_cut;     // first slot of the cut-tet kernel
+};
+template <typename T>
+cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
+                         int n_rhs, cudaStream_t s);
+int apply_uncut_blocks(const GridDev& g);
+int apply_cut_blocks(int ncut);
+
+// per-voxel average stress of the (scaled) solution u, double
+cudaError_t launch_voxel_stress(const double* u, const double* isD, CutData cd,
+                                const ApplyArgs& a, double* out, int n_rhs, cudaStream_t s);
+
+// ---- preconditioner (fft.cu)
+struct FftPlan;  // opaque
+FftPlan* fft_plan_create(const GridDev& g, cudaError_t* err);
+void fft_plan_destroy(FftPlan* p);
+size_t fft_spectrum_elems(const FftPlan* p);  // complex elements per RHS
+// z = P^-1 f per RHS (std part via FFT + Green, enr part identity); f^T z partials into
+// partials[rhs][nparts] (slots 0..nb-1).  spec: workspace of n_rhs * spectrum elems complex.
+template <typename T>
+cudaError_t launch_precondition(const FftPlan* p, const T* f, T* z, void* spec, long long stride,
+                                int nX, const int* active, double* partials, int nparts,
+                                int n_rhs, cudaStream_t s);
+int precondition_blocks(const FftPlan* p, int nX);
+
+// ---- CG vector ops and scalar finalisation (cg.cu)
+template <typename T>
+cudaError_t launch_axpy_cg(T* u, T* f, const T* d, const T* q, const RhsState* st,
+                           long long stride, int n_rhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_xpby(T* d, const T* z, const RhsState* st, long long stride, int n_rhs,
+                        cudaStream_t s);
+template <typename Tin, typename Tout>
+cudaError_t launch_scale_copy(const Tin* x, Tout* y, double a, long long stride, int n_rhs,
+                              const int* active, cudaStream_t s);
+template <typename T>
+cudaError_t launch_add_to_double(double* u, const T* dlt, long long stride, int n_rhs,
+                                 const int* active, cudaStream_t s);
+// mode: 0 = after the initial total apply (sig = partials 1..6), 1 = after an apply (alpha),
+// 2 = after a preconditioner application (rr, beta, stopping rule), 3 = initial precond
+struct FinArgs {
+  int mode;
+  int crit;        // 0: absolute-stress stopping rule, 1: relative rr reduction
+  double tol;
+  double volY;
+  int maxit;
+  int nparts;      // stride of the partial-sum rows
+  int nparts_used; // valid partial sums per row
+};
+// act[rhs] mirrors st[rhs].active for the kernels' early exit
+cudaError_t launch_finalize(RhsState* st, const double* partials, FinArgs fa, int n_rhs, int* act,
+                            cudaStream_t s);
+cudaError_t launch_init_state(RhsState* st, int* act, int n_rhs, const int* mask, cudaStream_t s);
+
+// ---- gradient (grad.cu)
+struct GradArgs {
+  GridDev g;
+  PhaseDev ph;
+  const uint16_t* code;
+  const float* scale;
+  long long stride;
+  int nX;
+  double G[36];           // dLoss/dC_eff
+  double* partials;       // [25][nparts]: dlam[2], dmu[2], C_energy upper triangle (21)
+  int nparts;
+  int part_offset_cut;
+};
+cudaError_t launch_grad(const double* U, const double* isD, CutData cd, const GradArgs& a,
+                        double* dscale, cudaStream_t s);
+int grad_blocks_uncut(const GridDev& g);
+int grad_blocks_cut(int ncut);
+cudaError_t launch_reduce_partials(const double* partials, int nvals, int nparts, int ncount,
+                                   double* out, cudaStream_t s);
+
+}  // namespace xfft

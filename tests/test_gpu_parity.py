@@ -1,0 +1,243 @@
+"""GPU <-> oracle parity through the C-ABI (libxfft.so).
+
+Every comparison uses the same seeded inputs on both sides.  Tolerances: the FP64 path must
+match the oracle's effective stiffness to relative 1e-10 and fields to relative L2 1e-9; the
+FP32 kernels (single apply / preconditioner) to relative 1e-5 of the vector norm, and the
+FP32-refined solve to relative 1e-6 in C_eff.  Integer setup results (classification, enriched
+numbering) are bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import XFEM
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2601_02172_gb300 as pkg
+    return pkg
+
+
+def _case(name):
+    if name == "sphere16":
+        n = (16, 16, 16)
+        L = synth.sphere_levelset(n, (0.5, 0.5, 0.5), 0.3)
+        return n, (1.0, 1.0, 1.0), L, synth.lame_from_E_nu(10.0, 0.3), synth.lame_from_E_nu(1.0, 0.3), None
+    if name == "ragged":
+        n = (10, 12, 8)
+        L = np.minimum(synth.sphere_levelset(n, (0.3, 0.4, 0.5), 0.22),
+                       synth.sphere_levelset(n, (0.8, 0.85, 0.2), 0.15))
+        return (n, (1.0, 1.0, 1.0), L, synth.lame_from_E_nu(20.0, 0.2), synth.lame_from_E_nu(1.0, 0.3),
+                synth.voxel_scale(n, 3))
+    if name == "aniso_cell":
+        n = (12, 8, 10)
+        ell = (1.5, 0.8, 1.2)
+        L = synth.sphere_levelset(n, (0.7, 0.35, 0.6), 0.3, ell)
+        return n, ell, L, synth.lame_from_E_nu(0.1, 0.35), synth.lame_from_E_nu(1.0, 0.3), None
+    raise KeyError(name)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+@pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell"])
+def test_setup_matches_oracle(xf, name):
+    n, ell, L, lm, lp, sc = _case(name)
+    s = xf.Solver(n, ell)
+    s.set_microstructure(L, lm, lp, sc)
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    en, D0, code = s.setup_info()
+    assert s.num_enriched == o.nX
+    assert s.num_cut_tets == len(o.cut_list)
+    assert np.array_equal(en, o.enr_nodes)
+    # tet codes: 2 = cut, else 0 / 1 = minus / plus phase
+    exp = np.zeros(o.nvox, dtype=np.uint16)
+    for t in range(6):
+        bits = np.where(o.cut[:, t], 2, np.where(o.tet_phase[:, t] < 0, 0, 1)).astype(np.uint16)
+        exp |= bits << (2 * t)
+    assert np.array_equal(code, exp)
+    assert _rel(D0, o.D) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_matches_oracle(xf, name, prec):
+    n, ell, L, lm, lp, sc = _case(name)
+    s = xf.Solver(n, ell)
+    s.set_microstructure(L, lm, lp, sc)
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o.assemble()
+    rng = np.random.default_rng(5)
+    d = rng.normal(size=(2, o.ndof))
+    eps = rng.normal(size=(2, 6))
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    q, sig = s.apply(d, precision=prec)
+    for r in range(2):
+        assert _rel(q[r], o.A @ d[r]) < tol
+    q, sig = s.apply(d, eps=eps, precision=prec)
+    for r in range(2):
+        assert _rel(q[r], o.A @ d[r] + o.rhs(eps[r])) < tol
+        ref = np.asarray(o.Sm @ d[r]).ravel() + o.Cbar @ eps[r]
+        assert _rel(sig[r], ref) < tol
+
+
+@pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_precondition_matches_oracle(xf, name, prec):
+    n, ell, L, lm, lp, sc = _case(name)
+    s = xf.Solver(n, ell)
+    s.set_microstructure(L, lm, lp, sc)
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    rng = np.random.default_rng(9)
+    f = rng.normal(size=(3, o.ndof))
+    for r in range(3):  # the standard part must be mean-free per component
+        std = f[r, : 3 * o.nFE].reshape(3, -1)
+        std -= std.mean(axis=1, keepdims=True)
+    z, rr = s.precondition(f, precision=prec)
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    for r in range(3):
+        ref = o.precondition(f[r], green="sparse")
+        assert _rel(z[r], ref) < tol
+        assert abs(rr[r] - f[r] @ ref) <= tol * abs(f[r] @ ref) * 10
+
+
+@pytest.mark.parametrize("name", ["sphere16", "ragged"])
+def test_fp64_solve_matches_direct(xf, name):
+    n, ell, L, lm, lp, sc = _case(name)
+    s = xf.Solver(n, ell, tol=1e-12)
+    s.set_microstructure(L, lm, lp, sc)
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    eps = np.array([[1.0, 0, 0, 0, 0, 0], [0.2, -0.1, 0.3, 0.4, -0.2, 0.1]])
+    out = s.solve(eps, u=True, voxel_stress=True)
+    assert out["converged"], out["stats"]
+    for r in range(2):
+        u = o.solve_direct(eps[r])
+        ustd = u[: 3 * o.nFE].reshape(3, -1)
+        uenr = (u[3 * o.nFE:].reshape(3, -1) * o.Dinvsqrt.T)
+        assert _rel(out["u_std"][r], ustd) < 1e-9
+        if o.nX:
+            assert _rel(out["u_enr"][r], uenr) < 1e-9
+        ms = o.mean_stress(u, eps[r])
+        assert np.abs(out["mean_stress"][r] - ms).max() < 1e-10 * np.abs(ms).max()
+        vs = o.voxel_stress(u, eps[r])
+        assert _rel(out["voxel_stress"][r], vs.T) < 1e-9
+
+
+def test_fp64_effective_stiffness_and_gradient(xf):
+    n, ell, L, lm, lp, sc = _case("ragged")
+    s = xf.Solver(n, ell, tol=1e-12)
+    s.set_microstructure(L, lm, lp, sc)
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    C, st = s.effective_stiffness()
+    assert st["converged"]
+    Cs, Ce, U = o.effective_stiffness()
+    assert np.abs(C - Cs).max() < 1e-10 * np.abs(Cs).max()
+    rng = np.random.default_rng(2)
+    G = rng.normal(size=(6, 6))
+    dl, ds, Cenergy = s.grad(G)
+    assert np.abs(Cenergy - Ce).max() < 1e-10 * np.abs(Ce).max()
+    dlr, dsr = o.stiffness_gradient(U)
+    ref_l = np.einsum("kl,pkl->p", G, dlr)
+    ref_s = np.einsum("kl,vkl->v", G, dsr)
+    assert np.abs(dl - ref_l).max() < 1e-9 * np.abs(ref_l).max()
+    assert _rel(ds.astype(np.float64), ref_s) < 1e-6  # float32 output
+
+
+def test_fp32_refined_effective_stiffness(xf):
+    n, ell, L, lm, lp, sc = _case("ragged")
+    s = xf.Solver(n, ell, precision="fp32", tol=1e-10)
+    s.set_microstructure(L, lm, lp, sc)
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    C, st = s.effective_stiffness()
+    assert st["converged"], st
+    Cs, Ce, U = o.effective_stiffness()
+    assert np.abs(C - Cs).max() < 1e-6 * np.abs(Cs).max()
+
+
+def test_gradient_against_finite_differences(xf):
+    n = (8, 8, 8)
+    L = synth.sphere_levelset(n, (0.45, 0.5, 0.55), 0.3)
+    lm = synth.lame_from_E_nu(8.0, 0.2)
+    lp = synth.lame_from_E_nu(1.0, 0.3)
+    sc = synth.voxel_scale(n, 7)
+    rng = np.random.default_rng(4)
+    Ct = rng.normal(size=(6, 6))
+
+    def ceff(lmv, lpv, scv):
+        s = xf.Solver(n, tol=1e-13)
+        s.set_microstructure(L, lmv, lpv, scv)
+        C, st = s.effective_stiffness()
+        return s, C
+
+    s, C = ceff(lm, lp, sc)
+    G = 2.0 * (C - Ct)
+    dl, ds, _ = s.grad(G)
+    theta = [lm[0], lm[1], lp[0], lp[1]]
+    for p in range(4):
+        h = 1e-6 * theta[p]
+        tp, tm = list(theta), list(theta)
+        tp[p] += h
+        tm[p] -= h
+        _, Cp = ceff((tp[0], tp[1]), (tp[2], tp[3]), sc)
+        _, Cm = ceff((tm[0], tm[1]), (tm[2], tm[3]), sc)
+        fd = (np.sum((Cp - Ct) ** 2) - np.sum((Cm - Ct) ** 2)) / (2 * h)
+        assert abs(fd - dl[p]) < 1e-5 * max(abs(dl[p]), 1e-3 * np.abs(dl).max())
+
+
+def test_laminate_closed_form_gpu(xf):
+    from tests.test_oracle_pins import _laminate_closed_form
+    n = (32, 32, 32)
+    normal = (1, 2, 3)
+    L = synth.laminate_levelset(n, normal=normal, offset=0.1234567, fraction=0.5)
+    lm = synth.lame_from_E_nu(100.0, 0.2)
+    lp = synth.lame_from_E_nu(1.0, 0.3)
+    Cref = _laminate_closed_form(normal, 0.5, lm, lp)
+    for prec, tol in (("fp64", 1e-9), ("fp32", 1e-6)):
+        s = xf.Solver(n, precision=prec, tol=1e-11)
+        s.set_microstructure(L, lm, lp)
+        C, st = s.effective_stiffness()
+        assert st["converged"], st
+        assert np.abs(C - Cref).max() < tol * np.abs(Cref).max(), (prec, np.abs(C - Cref).max())
+
+
+def test_homogeneous_and_equal_phase_edge_cases(xf):
+    n = (4, 4, 4)
+    lp = synth.lame_from_E_nu(2.0, 0.3)
+    s = xf.Solver(n)
+    s.set_microstructure(np.ones(n), (5.0, 1.0), lp)
+    assert s.num_enriched == 0 and s.num_cut_tets == 0
+    C, st = s.effective_stiffness()
+    from oracle import iso_stiffness
+    assert np.allclose(C, iso_stiffness(*lp), atol=1e-13)
+    n = (8, 8, 8)
+    lam = synth.lame_from_E_nu(3.0, 0.25)
+    L = synth.sphere_levelset(n, (0.43, 0.51, 0.47), 0.27)
+    s = xf.Solver(n)
+    s.set_microstructure(L, lam, lam)
+    assert s.num_enriched > 0
+    out = s.solve(np.eye(6))
+    assert np.abs(out["u_std"]).max() < 1e-11
+    assert np.allclose(out["mean_stress"], iso_stiffness(*lam), atol=1e-12)
+
+
+def test_invalid_arguments_are_reported(xf):
+    with pytest.raises(xf.XfftError):
+        xf.Solver((7, 8, 8))
+    with pytest.raises(xf.XfftError):
+        xf.Solver((14, 8, 8))  # 7 is not a supported radix
+    s = xf.Solver((8, 8, 8))
+    with pytest.raises(xf.XfftError):
+        s.solve(np.eye(6)[:1])  # before set_microstructure
+    with pytest.raises(xf.XfftError):
+        s.set_microstructure(np.ones((8, 8, 8)), (1.0, -1.0), (1.0, 1.0))
