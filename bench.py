@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Benchmark of the X-FFT hot path on GB300.
+
+One step = the whole hot path for one microstructure: GPU setup of the 128^3 X-FEM
+discretization (snap, classification, enriched numbering, cut-tet moments, scaling), the six
+unit load cases solved as one batch by FP32 PCG with FP64 residual refinement, the effective
+stiffness, and the adjoint gradient of ||C_eff - C_target||_F^2 with respect to the four phase
+Lame constants and the per-voxel modulus scale.  Inputs are resident in HBM when the timed region
+starts (``value``); ``e2e`` repeats the step through the C-ABI with host buffers.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xfft|reference]
+Multi-GPU runs (torchrun) are replicas: every rank solves its own copy of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "X-FFT solves/s (6 load cases) & DOF-iters/s at 128^3, %HBM roofline, FP32 vs FP64"
+UNIT = "solves/s"
+WORKLOAD = ("ellipsoids40: 128^3 periodic grid, 40 random ellipsoids (aspect 1-3, random "
+            "orientation, vf 25%), contrast E_incl/E_matrix = 50 (nu 0.2/0.3), per-voxel modulus "
+            "scale U[0.8,1.2]; six unit Mandel load cases; loss ||C_eff - C_target||_F^2")
+
+# algorithmic bytes per processed right-hand side and launch ("Roofline")
+def algorithmic_bytes(kind, N, nX, ncut, has_scale):
+    geo = N * (2 + (4 if has_scale else 0))
+    if kind == "apply_uncut_f32":
+        return 24 * N + geo
+    if kind == "apply_uncut_f64":
+        return 48 * N + geo
+    if kind == "prec_f32":
+        return 24 * (N + nX)
+    if kind == "prec_f64":
+        return 48 * (N + nX)
+    if kind == "apply_cut_f32":
+        return 408 * ncut
+    if kind == "apply_cut_f64":
+        return 776 * ncut
+    return None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("xfft", "reference"), default="xfft")
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=16)
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _oracle_sample(n_cpu, tol):
+    """One bounded run of the CPU oracle (FP64, as it stands) on the workload's ellipsoids
+    resampled at n_cpu^3: setup + assembly, then PCG (FFT Green operator) for one load case."""
+    import synth
+    from oracle import XFEM
+    w = synth.make_workload("ellipsoids40")
+    n = (n_cpu,) * 3
+    L = synth.ellipsoids_levelset(n, w["info"]["inclusions"])
+    step = 128 // n_cpu if 128 % n_cpu == 0 else 1
+    sc = np.ascontiguousarray(w["scale"][::step, ::step, ::step][:n_cpu, :n_cpu, :n_cpu])
+    t0 = time.perf_counter()
+    o = XFEM(L, n, lame_minus=w["lame_minus"], lame_plus=w["lame_plus"], scale=sc)
+    o.assemble()
+    t1 = time.perf_counter()
+    u, info = o.pcg(np.eye(6)[0], tol=tol, green="fft")
+    t2 = time.perf_counter()
+    return {"n": n_cpu, "ncut": len(o.cut_list), "t_setup": t1 - t0, "t_pcg": t2 - t1,
+            "iters": info["iters"], "dofit": o.ndof * info["iters"] / (t2 - t1)}
+
+
+_FULL = {}
+
+
+def _full_size_counts():
+    """Cut tets and DOFs of the 128^3 workload (host classification, computed once)."""
+    if not _FULL:
+        import synth
+        from oracle import classify
+        w = synth.make_workload("ellipsoids40")
+        cut, J = classify(w["L"], (128,) * 3, 1e-6 / 128)
+        _FULL.update(ncut=int(cut.sum()), ndof=3 * (128 ** 3 + J.size))
+    return _FULL
+
+
+def _scaled(sample):
+    """Seconds for one 128^3 six-case solve: setup scales with the cut tets, each PCG with
+    DOF-iterations (iteration counts are mesh independent, Sec. 4)."""
+    full = _full_size_counts()
+    t_setup = sample["t_setup"] * full["ncut"] / max(sample["ncut"], 1)
+    t_pcg = 6.0 * sample["iters"] * full["ndof"] / sample["dofit"]
+    return t_setup + t_pcg
+
+
+def _sample_text(sample, tol):
+    full = _full_size_counts()
+    return ("ellipsoids40 resampled at %d^3 (%d cut tets), one load case, tol %g: setup %.1f s, PCG "
+            "%d it in %.2f s (%.3g DOF-it/s); scaled to 128^3 x 6 cases by cut tets (%d) and "
+            "DOF-iterations (6 x %d it x %d DOF)" % (sample["n"], sample["ncut"], tol, sample["t_setup"],
+                                                    sample["iters"], sample["t_pcg"], sample["dofit"],
+                                                    full["ncut"], sample["iters"], full["ndof"]))
+
+
+def cpu_baseline(n_cpu, tol):
+    sample = _oracle_sample(n_cpu, tol)
+    t = _scaled(sample)
+    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": _sample_text(sample, tol), "dof_iters_per_s": sample["dofit"],
+            "os_cpu_count": os.cpu_count()}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, each step a bounded sample of the workload."""
+    _full_size_counts()
+    ts, samples = [], []
+    for k in range(args.warmup + args.steps):
+        sample = _oracle_sample(args.cpu_n, args.tol)
+        if k >= args.warmup:
+            samples.append(sample)
+            ts.append(_scaled(sample))
+    t = statistics.mean(ts)
+    value = 1.0 / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tol": args.tol,
+                       "sample": "each step: the oracle on the workload resampled at %d^3, one load "
+                                 "case, scaled to the 128^3 six-case solve" % args.cpu_n},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                             "sample": _sample_text(samples[-1], args.tol),
+                             "dof_iters_per_s": statistics.mean(s["dofit"] for s in samples)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def traffic_for(kind):
+    """DRAM bytes per launch and RHS from the committed ncu summary, if the kernel source has
+    not changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get(kind)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2601_02172_gb300", "csrc", ent["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if sha != ent.get("source_sha"):
+        return None
+    return ent
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import torch
+    import synth
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_02172_gb300 import Solver
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    n = (args.n,) * 3
+    w = synth.make_workload("ellipsoids40", n=n)
+    N = int(np.prod(n))
+    lm, lp = w["lame_minus"], w["lame_plus"]
+    L_h = np.ascontiguousarray(w["L"])
+    s_h = np.ascontiguousarray(w["scale"])
+    L_d = torch.from_numpy(L_h).to(dev)
+    s_d = torch.from_numpy(s_h).to(dev)
+    L_pin = torch.from_numpy(L_h).pin_memory()  # e2e inputs come from pinned host memory
+    s_pin = torch.from_numpy(s_h).pin_memory()
+    solver = Solver(n, precision="fp32", tol=args.tol)
+
+    # C_target: a random SPD perturbation of C_eff (seeded)
+    solver.set_microstructure(L_d, lm, lp, s_d)
+    C0, _ = solver.effective_stiffness()
+    rng = np.random.default_rng(4)
+    while True:
+        G = rng.normal(size=(6, 6))
+        G = 0.5 * (G + G.T)
+        Ct = C0 + 0.05 * np.linalg.norm(C0) / np.linalg.norm(G) * G
+        if np.linalg.eigvalsh(Ct).min() > 0:
+            break
+
+    info = {"iters": 0, "dofit": 0.0, "ncut": solver.num_cut_tets, "nX": 0}
+
+    def step(device_inputs=True):
+        if device_inputs:
+            solver.set_microstructure(L_d, lm, lp, s_d)
+        else:
+            solver.set_microstructure(L_pin, lm, lp, s_pin)
+        C, st = solver.effective_stiffness()
+        dl, ds, _ = solver.grad(2.0 * (C - Ct), device=dev if device_inputs else None)
+        nX = solver.num_enriched
+        info["nX"] = nX
+        info["iters"] += sum(st["iters"])
+        info["dofit"] += 3.0 * (N + nX) * sum(st["iters"])
+        info["refine"] = st["refine_steps"]
+        return C, dl, ds
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    info.update(iters=0, dofit=0.0)
+    solver.profile(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        C, dl, ds = step()
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = solver.profile_read()
+    solver.profile(False)
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    steps_iters = info["iters"]
+    dofit_rate = info["dofit"] / (ms / 1000.0)
+    value = world * args.steps / (ms / 1000.0)
+
+    # live roofline of the dominant kernel group
+    peak, peak_kind = load_peaks()
+    kinds = ["apply_uncut_f32", "prec_f32", "apply_uncut_f64", "prec_f64", "apply_cut_f32", "apply_cut_f64"]
+    dom = max(kinds, key=lambda k: prof[k][0])
+    kms, klaunch, kunits = prof[dom]
+    nX = info["nX"]
+    bpu = algorithmic_bytes(dom, N, nX, info["ncut"], True)
+    achieved = bpu * kunits / (kms / 1000.0) / 1e9 if kms > 0 else 0.0
+    tr = traffic_for(dom)
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "bytes_per_rhs_launch": bpu,
+            "launches": klaunch, "rhs_units": kunits, "avg_launch_ms": kms / max(klaunch, 1),
+            "traffic": (tr["dram_bytes_per_rhs"] * kunits / max(klaunch, 1)) if tr else None,
+            "groups_ms": {k: round(v[0], 3) for k, v in prof.items()}}
+    gpu_launches = int(sum(v[1] for v in prof.values()))
+
+    line = None
+    if rank == 0:
+        # end to end: host buffers in, host results out, copies inside the timed region
+        torch.cuda.synchronize()
+        te = []
+        for _ in range(max(1, min(args.steps, 2))):
+            t0 = time.perf_counter()
+            C_e, dl_e, ds_e = step(device_inputs=False)
+            torch.cuda.synchronize()
+            te.append(time.perf_counter() - t0)
+        e2e = {"value": 1.0 / statistics.mean(te), "unit": UNIT,
+               "h2d_bytes_per_step": int(L_h.nbytes + s_h.nbytes + 36 * 8 * 2),
+               "d2h_bytes_per_step": int(N * 4 + 36 * 8 * 3 + 4 * 8)}
+        extra = {}
+        if not args.no_fp64:
+            # plain FP64 for comparison: six cases batched, and one case at a time
+            s64 = Solver(n, precision="fp64", tol=args.tol)
+            s64.set_microstructure(L_d, lm, lp, s_d)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            C64, st64 = s64.effective_stiffness()
+            torch.cuda.synchronize()
+            t_b = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            its1 = 0
+            for k in range(6):
+                out = s64.solve(np.eye(6)[k:k + 1], u=False)
+                its1 += out["stats"]["iters"][0]
+            torch.cuda.synchronize()
+            t_1 = time.perf_counter() - t0
+            sref = Solver(n, precision="fp64", tol=1e-10)
+            sref.set_microstructure(L_d, lm, lp, s_d)
+            Cref, _ = sref.effective_stiffness()
+            extra["fp64"] = {"solves_per_s_batched6": 1.0 / t_b, "solves_per_s_single_rhs": 1.0 / t_1,
+                             "iters_batched6": sum(st64["iters"]), "iters_single_rhs": its1,
+                             "tol": args.tol}
+            extra["accuracy"] = {
+                "ceff_rel_err_fp32_refined_vs_fp64_tol1e-10": float(np.abs(C - Cref).max() / np.abs(Cref).max()),
+                "ceff_rel_err_fp64_vs_fp64_tol1e-10": float(np.abs(C64 - Cref).max() / np.abs(Cref).max())}
+            s64.close()
+            sref.close()
+        cpu = None
+        if not args.no_cpu and world == 1:
+            try:
+                cpu = cpu_baseline(args.cpu_n, args.tol)
+            except Exception as exc:  # report, never fail the GPU line
+                cpu = {"error": repr(exc)}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": list(n), "n_rhs": 6,
+                           "precision": "FP32 PCG, FP64 residual refinement and CG scalars",
+                           "tol": args.tol, "n_enriched": nX, "n_cut_tets": info["ncut"],
+                           "l2": "inputs larger than L2 (about 1.3 GB of fields per step)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "dof_iters_per_s": dofit_rate, "cg_iters_per_step": steps_iters / args.steps,
+                "refine_steps": info.get("refine"),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "clocks": clocks}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -151,6 +151,23 @@ xfft_status xfft_precondition(xfft_ctx* ctx, int n_rhs, const double* f, double*
  * of the axes: 0 = minus phase, 1 = plus phase, 2 = cut).  Host pointers; each may be NULL. */
 xfft_status xfft_get_setup(xfft_ctx* ctx, int* enr_nodes, double* D0, unsigned short* tet_code);
 
+/* Tracing (not in the paper; per-kernel timing for roofline reports).  While enabled, every
+ * group of kernel launches is bracketed by CUDA events recorded on the context's stream.
+ * xfft_profile_read returns per group k (the XFFT_PROF_* values): the summed device time in ms,
+ * the number of kernel launches, and the number of right-hand sides processed (counted on the
+ * device by the apply and preconditioner kernels, 0 for the other groups).  Arrays have 16
+ * entries (host).  xfft_profile(ctx, 1) enables and resets; xfft_profile(ctx, 0) disables.
+ * Reading synchronises the stream.  Errors: ECUDA. */
+enum {
+  XFFT_PROF_APPLY_UNCUT_F32 = 0, XFFT_PROF_APPLY_CUT_F32 = 1, XFFT_PROF_APPLY_UNCUT_F64 = 2,
+  XFFT_PROF_APPLY_CUT_F64 = 3, XFFT_PROF_PREC_F32 = 4, XFFT_PROF_PREC_F64 = 5,
+  XFFT_PROF_VECTOR = 6, XFFT_PROF_FINALIZE = 7, XFFT_PROF_SETUP = 8, XFFT_PROF_GRAD = 9,
+  XFFT_PROF_POST = 10, XFFT_PROF_COUNT = 11
+};
+xfft_status xfft_profile(xfft_ctx* ctx, int enable);
+xfft_status xfft_profile_read(xfft_ctx* ctx, double ms[16], long long launches[16],
+                              long long units[16]);
+
 int xfft_num_enriched(const xfft_ctx* ctx);   /* nX, or -1 before set_microstructure */
 int xfft_num_cut_tets(const xfft_ctx* ctx);   /* number of cut tetrahedra, or -1 */
 const char* xfft_status_string(xfft_status s);

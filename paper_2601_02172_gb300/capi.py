@@ -22,8 +22,10 @@ EXPORTED = (
     "xfft_default_options", "xfft_create", "xfft_set_microstructure", "xfft_solve",
     "xfft_effective_stiffness", "xfft_grad", "xfft_apply", "xfft_precondition", "xfft_get_setup",
     "xfft_num_enriched", "xfft_num_cut_tets", "xfft_status_string", "xfft_last_error",
-    "xfft_destroy",
+    "xfft_destroy", "xfft_profile", "xfft_profile_read",
 )
+PROF_KINDS = ("apply_uncut_f32", "apply_cut_f32", "apply_uncut_f64", "apply_cut_f64", "prec_f32",
+              "prec_f64", "vector", "finalize", "setup", "grad", "post")
 
 
 class Grid(C.Structure):
@@ -76,9 +78,12 @@ def lib():
     L.xfft_last_error.restype = C.c_char_p
     L.xfft_destroy.argtypes = [vp]
     L.xfft_destroy.restype = None
+    L.xfft_profile.argtypes = [vp, i]
+    L.xfft_profile_read.argtypes = [vp, vp, vp, vp]
     for name in ("xfft_default_options", "xfft_create", "xfft_set_microstructure", "xfft_solve",
                  "xfft_effective_stiffness", "xfft_grad", "xfft_apply", "xfft_precondition",
-                 "xfft_get_setup", "xfft_num_enriched", "xfft_num_cut_tets"):
+                 "xfft_get_setup", "xfft_num_enriched", "xfft_num_cut_tets", "xfft_profile",
+                 "xfft_profile_read"):
         getattr(L, name).restype = i
     _lib = L
     return L
@@ -257,6 +262,19 @@ class Solver:
                                       rr.ctypes.data_as(C.POINTER(C.c_double)),
                                       0 if precision == "fp64" else 1, 0))
         return z, rr
+
+    def profile(self, enable=True):
+        """Enable (and reset) or disable the library's per-kernel-group event timing."""
+        check(lib().xfft_profile(self._ctx, int(bool(enable))))
+
+    def profile_read(self):
+        """{group: (ms, launches, rhs_units)} accumulated since profile(True)."""
+        ms = np.zeros(16)
+        la = np.zeros(16, dtype=np.int64)
+        un = np.zeros(16, dtype=np.int64)
+        check(lib().xfft_profile_read(self._ctx, C.c_void_p(ms.ctypes.data), C.c_void_p(la.ctypes.data),
+                                      C.c_void_p(un.ctypes.data)))
+        return {k: (float(ms[i]), int(la[i]), int(un[i])) for i, k in enumerate(PROF_KINDS)}
 
     def setup_info(self):
         nX = self.num_enriched

@@ -133,6 +133,8 @@ __global__ void __launch_bounds__(kTZ* kTY)
   const int rhs = blockIdx.z / nxchunks;
   const int xc = blockIdx.z - rhs * nxchunks;
   if (a.active && !a.active[rhs]) return;
+  if (a.units_uncut && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && xc == 0)
+    atomicAdd(a.units_uncut, 1ULL);
   const GridDev& g = a.g;
   const int n0 = g.n0, n1 = g.n1, n2 = g.n2;
   const long long N = g.N;
@@ -284,6 +286,7 @@ __global__ void __launch_bounds__(128)
                 const CutData cd, const ApplyArgs a) {
   const int rhs = blockIdx.y;
   if (a.active && !a.active[rhs]) return;
+  if (a.units_cut && threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(a.units_cut, 1ULL);
   __shared__ double red[7 * 32];
   const GridDev& g = a.g;
   const long long N = g.N;
@@ -458,16 +461,8 @@ int apply_cut_blocks(int ncut) {
 }
 
 template <typename T>
-cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
-                         int n_rhs, cudaStream_t s) {
+cudaError_t launch_apply_uncut(const T* d, T* q, const ApplyArgs& a, int n_rhs, cudaStream_t s) {
   const GridDev& g = a.g;
-  // enriched part of q only receives atomic contributions: clear it first
-  if (a.nX > 0) {
-    for (int r = 0; r < n_rhs; ++r) {
-      cudaError_t e = cudaMemsetAsync(q + r * a.stride + 3 * g.N, 0, sizeof(T) * 3 * (size_t)a.nX, s);
-      if (e != cudaSuccess) return e;
-    }
-  }
   const int gz = (g.n2 + kTZ - 2) / (kTZ - 1);
   const int gy = (g.n1 + kTY - 2) / (kTY - 1);
   const int gx = (g.n0 + kCX - 1) / kCX;
@@ -477,8 +472,21 @@ cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const Apply
     k_apply_uncut<T, true><<<grid, block, 0, s>>>(d, q, a, gx);
   else
     k_apply_uncut<T, false><<<grid, block, 0, s>>>(d, q, a, gx);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// The enriched part of q only receives atomic contributions from the cut-tet kernel: it is
+// cleared first; the standard part must already hold the uncut kernel's plain stores.
+template <typename T>
+cudaError_t launch_apply_cut(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
+                             int n_rhs, cudaStream_t s) {
+  const GridDev& g = a.g;
+  if (a.nX > 0) {
+    for (int r = 0; r < n_rhs; ++r) {
+      cudaError_t e = cudaMemsetAsync(q + r * a.stride + 3 * g.N, 0, sizeof(T) * 3 * (size_t)a.nX, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
   dim3 cgrid(apply_cut_blocks(cd.ncut), n_rhs, 1);
   if (a.eps)
     k_apply_cut<T, true><<<cgrid, 128, 0, s>>>(d, q, isD, cd, a);
@@ -487,10 +495,25 @@ cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const Apply
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
+                         int n_rhs, cudaStream_t s) {
+  cudaError_t e = launch_apply_uncut<T>(d, q, a, n_rhs, s);
+  if (e != cudaSuccess) return e;
+  return launch_apply_cut<T>(d, q, isD, cd, a, n_rhs, s);
+}
+
 template cudaError_t launch_apply<float>(const float*, float*, const float*, CutData,
                                          const ApplyArgs&, int, cudaStream_t);
 template cudaError_t launch_apply<double>(const double*, double*, const double*, CutData,
                                           const ApplyArgs&, int, cudaStream_t);
+template cudaError_t launch_apply_uncut<float>(const float*, float*, const ApplyArgs&, int, cudaStream_t);
+template cudaError_t launch_apply_uncut<double>(const double*, double*, const ApplyArgs&, int,
+                                                cudaStream_t);
+template cudaError_t launch_apply_cut<float>(const float*, float*, const float*, CutData,
+                                             const ApplyArgs&, int, cudaStream_t);
+template cudaError_t launch_apply_cut<double>(const double*, double*, const double*, CutData,
+                                              const ApplyArgs&, int, cudaStream_t);
 
 // ---------------------------------------------------------------- per-voxel average stress
 __global__ void k_voxel_stress_uncut(const double* __restrict__ u, const ApplyArgs a,

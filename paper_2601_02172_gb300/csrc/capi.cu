@@ -103,7 +103,68 @@ struct xfft_ctx {
   double* dscale = nullptr;
   float* dscale_f = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // tracing
+  struct PE {
+    int kind, nlaunch;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<PE> pend;
+  std::vector<cudaEvent_t> evpool;
+  double pms[16] = {};
+  long long plaunch[16] = {};
+  unsigned long long* punits = nullptr;  // device, 16 counters
 };
+
+static cudaEvent_t prof_event(xfft_ctx* c) {
+  if (!c->evpool.empty()) {
+    cudaEvent_t e = c->evpool.back();
+    c->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets a group of kernel launches with events on the context's stream (tracing only).
+struct ProfScope {
+  xfft_ctx* c;
+  int kind, n;
+  cudaEvent_t a = nullptr;
+  ProfScope(xfft_ctx* c_, int kind_, int n_) : c(c_), kind(kind_), n(n_) {
+    if (c->prof) {
+      a = prof_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (c->prof && a) {
+      cudaEvent_t b = prof_event(c);
+      cudaEventRecord(b, c->stream);
+      c->pend.push_back({kind, n, a, b});
+    }
+  }
+};
+
+// fold finished event pairs into the totals (synchronises the stream)
+static cudaError_t prof_flush(xfft_ctx* c) {
+  if (c->pend.empty()) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  for (auto& pe : c->pend) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, pe.a, pe.b);
+    c->pms[pe.kind] += ms;
+    c->plaunch[pe.kind] += pe.nlaunch;
+    c->evpool.push_back(pe.a);
+    c->evpool.push_back(pe.b);
+  }
+  c->pend.clear();
+  return cudaSuccess;
+}
+
+static unsigned long long* punit(xfft_ctx* c, int kind) { return c->prof ? c->punits + kind : nullptr; }
 
 static CutData cutdata(const xfft_ctx* c) {
   CutData cd;
@@ -193,7 +254,9 @@ extern "C" xfft_status xfft_create(xfft_ctx** out, const xfft_grid* grid, const 
   }
   if ((e = cudaEventCreate(&c->ev0)) != cudaSuccess || (e = cudaEventCreate(&c->ev1)) != cudaSuccess ||
       (e = cudaMallocHost((void**)&c->h_act, 64 * sizeof(int))) != cudaSuccess ||
-      (e = cudaMallocHost((void**)&c->h_st, 64 * sizeof(RhsState))) != cudaSuccess) {
+      (e = cudaMallocHost((void**)&c->h_st, 64 * sizeof(RhsState))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->punits, 16 * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMemset(c->punits, 0, 16 * sizeof(unsigned long long))) != cudaSuccess) {
     xfft_destroy(c);
     return fail(XFFT_ECUDA, cudaGetErrorString(e));
   }
@@ -254,6 +317,12 @@ extern "C" void xfft_destroy(xfft_ctx* c) {
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  for (auto& pe : c->pend) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
+  for (auto e : c->evpool) cudaEventDestroy(e);
+  if (c->punits) cudaFree(c->punits);
   delete c;
 }
 
@@ -299,6 +368,7 @@ extern "C" xfft_status xfft_set_microstructure(xfft_ctx* c, const double* L, con
   } else {
     c->has_scale = false;
   }
+  ProfScope ps_setup(c, XFFT_PROF_SETUP, 14);
   CU(launch_snap_classify(Ldev, c->Ls, c->code, c->cutcount, c->enr_flag, g, c->tau, s));
   // enriched ids (scan of node flags) and cut-tet offsets (scan of per-voxel counts)
   CU(launch_scan(c->enr_flag, c->enr_id, N, c->d_tot + 0, c->scan_tmp, s));
@@ -399,8 +469,21 @@ template <typename T>
 static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev, int n_rhs,
                             const int* active, int fin_mode, double tol, int crit, int maxit) {
   ApplyArgs a = apply_args(c, eps_dev, active);
-  CU(launch_apply<T>(d, q, isd_of<T>(c), cutdata(c), a, n_rhs, c->stream));
+  const bool dbl = sizeof(T) == 8;
+  const int ku = dbl ? XFFT_PROF_APPLY_UNCUT_F64 : XFFT_PROF_APPLY_UNCUT_F32;
+  const int kc = dbl ? XFFT_PROF_APPLY_CUT_F64 : XFFT_PROF_APPLY_CUT_F32;
+  a.units_uncut = punit(c, ku);
+  a.units_cut = punit(c, kc);
+  {
+    ProfScope ps(c, ku, 1);
+    CU(launch_apply_uncut<T>(d, q, a, n_rhs, c->stream));
+  }
+  {
+    ProfScope ps(c, kc, 1);
+    CU(launch_apply_cut<T>(d, q, isd_of<T>(c), cutdata(c), a, n_rhs, c->stream));
+  }
   if (fin_mode >= 0) {
+    ProfScope ps(c, XFFT_PROF_FINALIZE, 1);
     FinArgs fa;
     fa.mode = fin_mode;
     fa.crit = crit;
@@ -418,9 +501,14 @@ template <typename T>
 static xfft_status do_prec(xfft_ctx* c, const T* f, T* z, int n_rhs, const int* active, int fin_mode,
                            double tol, int crit, int maxit) {
   const int nparts = nparts_of(c);
-  CU(launch_precondition<T>(c->fft, f, z, c->spec, stride_of(c), c->nX, active, c->partials, nparts,
-                            n_rhs, c->stream));
+  {
+    const int kp = sizeof(T) == 8 ? XFFT_PROF_PREC_F64 : XFFT_PROF_PREC_F32;
+    ProfScope ps(c, kp, 6);
+    CU(launch_precondition<T>(c->fft, f, z, c->spec, stride_of(c), c->nX, active, c->partials, nparts,
+                              n_rhs, c->stream, punit(c, kp)));
+  }
   if (fin_mode >= 0) {
+    ProfScope ps(c, XFFT_PROF_FINALIZE, 1);
     FinArgs fa;
     fa.mode = fin_mode;
     fa.crit = crit;
@@ -437,6 +525,7 @@ static xfft_status do_prec(xfft_ctx* c, const T* f, T* z, int n_rhs, const int* 
 static xfft_status poll_active(xfft_ctx* c, int n_rhs, int* nactive) {
   CU(cudaMemcpyAsync(c->h_act, c->act, n_rhs * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  if (c->prof && c->pend.size() > 2048) CU(prof_flush(c));
   int k = 0;
   for (int r = 0; r < n_rhs; ++r) k += c->h_act[r] != 0;
   *nactive = k;
@@ -468,9 +557,15 @@ static xfft_status cg_loop(xfft_ctx* c, T* u, T* f, T* d, T* z, T* q, int n_rhs,
       if (na == 0) break;
     }
     TRY(do_apply<T>(c, d, q, nullptr, n_rhs, c->act, 1, tol, crit, maxit));
-    CU(launch_axpy_cg<T>(u, f, d, q, c->st, stride, n_rhs, c->stream));
+    {
+      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+      CU(launch_axpy_cg<T>(u, f, d, q, c->st, stride, n_rhs, c->stream));
+    }
     TRY(do_prec<T>(c, f, z, n_rhs, c->act, 2, tol, crit, maxit));
-    CU(launch_xpby<T>(d, z, c->st, stride, n_rhs, c->stream));
+    {
+      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+      CU(launch_xpby<T>(d, z, c->st, stride, n_rhs, c->stream));
+    }
   }
   return XFFT_OK;
 }
@@ -505,11 +600,20 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
   if (c->opt.precision == XFFT_FP64) {
     double *u = c->v64[0], *f = c->v64[1], *d = c->v64[2], *z = c->v64[3], *q = c->v64[4];
     CU(cudaMemsetAsync(u, 0, tot * sizeof(double), s));
-    CU(launch_init_state(c->st, c->act, n_rhs, nullptr, s));
+    {
+      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+      CU(launch_init_state(c->st, c->act, n_rhs, nullptr, s));
+    }
     TRY(do_apply<double>(c, u, q, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit));
-    CU(launch_scale_copy<double, double>(q, f, -1.0, stride, n_rhs, c->act, s));
+    {
+      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+      CU(launch_scale_copy<double, double>(q, f, -1.0, stride, n_rhs, c->act, s));
+    }
     TRY(do_prec<double>(c, f, z, n_rhs, c->act, 3, tol, 0, c->opt.maxit));
-    CU(launch_scale_copy<double, double>(z, d, 1.0, stride, n_rhs, nullptr, s));
+    {
+      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+      CU(launch_scale_copy<double, double>(z, d, 1.0, stride, n_rhs, nullptr, s));
+    }
     TRY(cg_loop<double>(c, u, f, d, z, q, n_rhs, tol, 0, c->opt.maxit));
     TRY(read_states(c, n_rhs));
     for (int r = 0; r < n_rhs; ++r) {
@@ -535,10 +639,16 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
   for (int ref = 0; ref <= c->opt.max_refine; ++ref) {
     for (int r = 0; r < n_rhs; ++r) hmask[r] = pending[r];
     CU(cudaMemcpyAsync(c->outer_mask, hmask.data(), 64 * sizeof(int), cudaMemcpyHostToDevice, s));
-    CU(launch_init_state(c->st, c->act, n_rhs, c->outer_mask, s));
+    {
+      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+      CU(launch_init_state(c->st, c->act, n_rhs, c->outer_mask, s));
+    }
     // FP64 residual of the current iterate and the stopping rule
     TRY(do_apply<double>(c, u, r64, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit));
-    CU(launch_scale_copy<double, float>(r64, f, -1.0, stride, n_rhs, c->act, s));
+    {
+      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+      CU(launch_scale_copy<double, float>(r64, f, -1.0, stride, n_rhs, c->act, s));
+    }
     TRY(do_prec<float>(c, f, z, n_rhs, c->act, 3, tol, 0, c->opt.maxit));
     TRY(read_states(c, n_rhs));
     int still = 0;
@@ -570,15 +680,21 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
     if (ref > 0) R->refine_steps++;
     // inner FP32 PCG on A delta = r (relative reduction inner_tol); the act flags of the
     // refining RHS were set by the mode-3 finalisation
-    k_copy_act_to_mask<<<1, 64, 0, s>>>(c->act, c->outer_mask, n_rhs);
-    CU(cudaGetLastError());
-    CU(cudaMemsetAsync(du, 0, tot * sizeof(float), s));
-    CU(launch_scale_copy<float, float>(z, d, 1.0, stride, n_rhs, nullptr, s));
+    {
+      ProfScope ps(c, XFFT_PROF_VECTOR, 2);
+      k_copy_act_to_mask<<<1, 64, 0, s>>>(c->act, c->outer_mask, n_rhs);
+      CU(cudaGetLastError());
+      CU(cudaMemsetAsync(du, 0, tot * sizeof(float), s));
+      CU(launch_scale_copy<float, float>(z, d, 1.0, stride, n_rhs, nullptr, s));
+    }
     TRY(cg_loop<float>(c, du, f, d, z, q, n_rhs, c->opt.inner_tol, 1, c->opt.maxit));
     TRY(read_states(c, n_rhs));
     for (int r = 0; r < n_rhs; ++r)
       if (hmask[r]) R->iters[r] += c->h_st[r].iters;
-    CU(launch_add_to_double<float>(u, du, stride, n_rhs, c->outer_mask, s));
+    {
+      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+      CU(launch_add_to_double<float>(u, du, stride, n_rhs, c->outer_mask, s));
+    }
   }
   return XFFT_OK;
 }
@@ -660,8 +776,11 @@ extern "C" xfft_status xfft_solve(xfft_ctx* c, int n_rhs, const double* eps_bar,
     double* tmp = c->v64[4];  // free after the solve (residual / q buffer)
     long long nb = (3LL * c->nX + 255) / 256;
     if (nb > 4096) nb = 4096;
-    k_unscale_enr<<<dim3((unsigned)nb, n_rhs), 256, 0, s>>>(u, c->isD, tmp, stride, g.N, c->nX);
-    CU(cudaGetLastError());
+    {
+      ProfScope ps(c, XFFT_PROF_POST, 1);
+      k_unscale_enr<<<dim3((unsigned)nb, n_rhs), 256, 0, s>>>(u, c->isD, tmp, stride, g.N, c->nX);
+      CU(cudaGetLastError());
+    }
     CU(cudaMemcpyAsync(u_enr, tmp, (size_t)n_rhs * 3 * c->nX * sizeof(double), kind, s));
   }
   if (voxel_stress) {
@@ -672,7 +791,10 @@ extern "C" xfft_status xfft_solve(xfft_ctx* c, int n_rhs, const double* eps_bar,
       out = tmp;
     }
     ApplyArgs a = apply_args(c, c->eps_d, nullptr);
-    CU(launch_voxel_stress(u, c->isD, cutdata(c), a, out, n_rhs, s));
+    {
+      ProfScope ps(c, XFFT_PROF_POST, 2);
+      CU(launch_voxel_stress(u, c->isD, cutdata(c), a, out, n_rhs, s));
+    }
     if (tmp) {
       CU(cudaMemcpyAsync(voxel_stress, tmp, (size_t)n_rhs * 6 * g.N * sizeof(double),
                          cudaMemcpyDeviceToHost, s));
@@ -753,11 +875,15 @@ extern "C" xfft_status xfft_grad(xfft_ctx* c, const double dL_dCeff[36], double 
   a.nparts = grad_blocks_uncut(g) + grad_blocks_cut(c->ncut);
   a.part_offset_cut = grad_blocks_uncut(g);
   if (!c->dscale) CU(dalloc(&c->dscale, g.N));
-  CU(launch_grad(c->U6, c->isD, cutdata(c), a, c->dscale, s));
-  CU(launch_reduce_partials(c->partials, 25, a.nparts, a.nparts, c->red_out, s));
+  {
+    ProfScope ps(c, XFFT_PROF_GRAD, 3);
+    CU(launch_grad(c->U6, c->isD, cutdata(c), a, c->dscale, s));
+    CU(launch_reduce_partials(c->partials, 25, a.nparts, a.nparts, c->red_out, s));
+  }
   double red[25];
   CU(cudaMemcpyAsync(red, c->red_out, sizeof(red), cudaMemcpyDeviceToHost, s));
   if (dL_dscale) {
+    ProfScope ps(c, XFFT_PROF_GRAD, 1);
     if (ptrs_on_device) {
       CU(launch_scale_copy<double, float>(c->dscale, dL_dscale, 1.0, g.N, 1, nullptr, s));
     } else {
@@ -914,5 +1040,35 @@ extern "C" xfft_status xfft_get_setup(xfft_ctx* c, int* enr_nodes, double* D0, u
   if (tet_code)
     CU(cudaMemcpyAsync(tet_code, c->code, c->g.N * sizeof(uint16_t), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
+  return XFFT_OK;
+}
+
+extern "C" xfft_status xfft_profile(xfft_ctx* c, int enable) {
+  if (!c) return fail(XFFT_EINVAL, "NULL argument");
+  CU(prof_flush(c));
+  c->prof = enable != 0;
+  if (enable) {
+    for (int k = 0; k < 16; ++k) {
+      c->pms[k] = 0.0;
+      c->plaunch[k] = 0;
+    }
+    CU(cudaMemsetAsync(c->punits, 0, 16 * sizeof(unsigned long long), c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  }
+  return XFFT_OK;
+}
+
+extern "C" xfft_status xfft_profile_read(xfft_ctx* c, double ms[16], long long launches[16],
+                                         long long units[16]) {
+  if (!c) return fail(XFFT_EINVAL, "NULL argument");
+  CU(prof_flush(c));
+  unsigned long long u[16];
+  CU(cudaMemcpyAsync(u, c->punits, sizeof(u), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 16; ++k) {
+    if (ms) ms[k] = c->pms[k];
+    if (launches) launches[k] = c->plaunch[k];
+    if (units) units[k] = (long long)u[k];
+  }
   return XFFT_OK;
 }

@@ -173,11 +173,13 @@ template <typename T>
 __global__ void k_fft_z_r2c(const T* __restrict__ f, typename Cx<T>::type* __restrict__ spec,
                             long long stride, long long sstride, AxisPlan ap, int K2, long long rows,
                             int pairs_per_block, const int* __restrict__ active,
-                            const typename Cx<T>::type* __restrict__ tw) {
+                            const typename Cx<T>::type* __restrict__ tw,
+                            unsigned long long* __restrict__ units) {
   typedef typename Cx<T>::type C;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int rhs = blockIdx.y;
   if (active && !active[rhs]) return;
+  if (units && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(units, 1ULL);
   const int n = ap.n;
   C* tws = reinterpret_cast<C*>(smraw);
   C* b0 = tws + n;
@@ -665,7 +667,7 @@ int precondition_blocks(const FftPlan* p, int nX) { return zpass_blocks(p) + enr
 template <typename T>
 cudaError_t launch_precondition(const FftPlan* p, const T* f, T* z, void* spec_v, long long stride,
                                 int nX, const int* active, double* partials, int nparts,
-                                int n_rhs, cudaStream_t s) {
+                                int n_rhs, cudaStream_t s, unsigned long long* units) {
   typedef typename Cx<T>::type C;
   const bool dbl = sizeof(T) == 8;
   const int a2 = 2;  // z axis
@@ -678,7 +680,7 @@ cudaError_t launch_precondition(const FftPlan* p, const T* f, T* z, void* spec_v
   const C* tw2 = reinterpret_cast<const C*>(dbl ? (const void*)p->twd[a2] : (const void*)p->twf[a2]);
   const int zb = zpass_blocks(p);
   k_fft_z_r2c<T><<<dim3(zb, n_rhs), kFftThreads, smem_z(p, cs), s>>>(
-      f, spec, stride, sstride, p->ax[2], p->K2, rows, p->xpairs, active, tw2);
+      f, spec, stride, sstride, p->ax[2], p->K2, rows, p->xpairs, active, tw2, units);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ytk = dbl ? p->ytk_d : p->ytk_f;
@@ -720,9 +722,9 @@ cudaError_t launch_precondition(const FftPlan* p, const T* f, T* z, void* spec_v
 
 template cudaError_t launch_precondition<float>(const FftPlan*, const float*, float*, void*,
                                                 long long, int, const int*, double*, int, int,
-                                                cudaStream_t);
+                                                cudaStream_t, unsigned long long*);
 template cudaError_t launch_precondition<double>(const FftPlan*, const double*, double*, void*,
                                                  long long, int, const int*, double*, int, int,
-                                                 cudaStream_t);
+                                                 cudaStream_t, unsigned long long*);
 
 }  // namespace xfft

@@ -61,10 +61,17 @@ struct ApplyArgs {
   double* partials;        // [rhs][7][nparts]: 0 = <d, A d> (energy), 1..6 = int C eps (Mandel)
   int nparts;              // partial slots per RHS and component
   int part_offset_cut;     // first slot of the cut-tet kernel
+  unsigned long long* units_uncut;  // optional counters of processed right-hand sides
+  unsigned long long* units_cut;
 };
 template <typename T>
 cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
                          int n_rhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply_uncut(const T* d, T* q, const ApplyArgs& a, int n_rhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply_cut(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
+                             int n_rhs, cudaStream_t s);
 int apply_uncut_blocks(const GridDev& g);
 int apply_cut_blocks(int ncut);
 
@@ -82,7 +89,7 @@ size_t fft_spectrum_elems(const FftPlan* p);  // complex elements per RHS
 template <typename T>
 cudaError_t launch_precondition(const FftPlan* p, const T* f, T* z, void* spec, long long stride,
                                 int nX, const int* active, double* partials, int nparts,
-                                int n_rhs, cudaStream_t s);
+                                int n_rhs, cudaStream_t s, unsigned long long* units = nullptr);
 int precondition_blocks(const FftPlan* p, int nX);
 
 // ---- CG vector ops and scalar finalisation (cg.cu)

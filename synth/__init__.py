@@ -11,6 +11,8 @@ from .geometry import (  # noqa: F401
     spheres_levelset,
     rsa_spheres,
     rsa_ellipsoids,
+    ellipsoids_levelset,
+    batch_uneven,
     rsa_fibers,
     laminate_levelset,
     voxel_scale,

@@ -224,6 +224,22 @@ def rsa_ellipsoids(n, count, vf, seed, aspect=(1.0, 3.0), length=(1.0, 1.0, 1.0)
     return L, {"inclusions": placed, "vf": vf_placed, "count": len(placed)}
 
 
+def ellipsoids_levelset(n, inclusions, length=(1.0, 1.0, 1.0)):
+    """Level set of already placed ellipsoids (the ``inclusions`` list returned by
+    :func:`rsa_ellipsoids`) sampled on another grid ``n``."""
+    n = tuple(int(v) for v in n)
+    L = np.full(n, np.inf)
+    for inc in inclusions:
+        semi = np.asarray(inc["semi"], dtype=float)
+        ix, iy, iz = _box_indices(n, length, inc["center"], float(semi[0]) + 4.0 * _min_gap(n, length))
+        Lc = _ellipsoid_levelset_box(n, length, inc["center"], inc["R"], semi, ix, iy, iz)
+        L[np.ix_(ix, iy, iz)] = np.minimum(L[np.ix_(ix, iy, iz)], Lc)
+    finite = np.isfinite(L)
+    if not np.all(finite):
+        L[~finite] = float(np.max(L[finite])) if np.any(finite) else 1.0
+    return L
+
+
 def rsa_fibers(n, count, radius, seed, length=(1.0, 1.0, 1.0), gap=None, max_attempts=20000):
     """Straight periodic cylinders along randomly chosen coordinate axes.
 
