@@ -168,6 +168,30 @@ xfft_status xfft_profile(xfft_ctx* ctx, int enable);
 xfft_status xfft_profile_read(xfft_ctx* ctx, double ms[16], long long launches[16],
                               long long units[16]);
 
+/* Allocation-free stiffness apply.  The paper has no counterpart: this is a service for
+ * callers that must not allocate device memory once they are running, for example an
+ * application that hands all device memory to its own pool allocator at start-up, or one
+ * whose other work cannot tolerate the device-wide synchronisation a cudaMalloc/cudaFree
+ * may cause.  It computes the same q = A d as xfft_apply in FP64 (scaled enriched DOFs,
+ * layout [std (3N) | enr (3 nX)] per RHS), all arrays on the device and caller-owned:
+ *   d        n_rhs x 3 (N + nX) doubles (input),
+ *   q        n_rhs x 3 (N + nX) doubles (output),
+ *   dAd_sig  n_rhs x 7 doubles (output, may be NULL): <d, A d> followed by
+ *            int_Y C grad^s d (Mandel 6) per RHS.
+ * Its reduction scratch is a fixed array in the library's device memory (about 1.8 MB,
+ * present on every GPU that loads the library until the process exits), so it serves at most
+ * XFFT_NOALLOC_MAX_RHS right-hand sides and grids whose apply needs at most
+ * XFFT_NOALLOC_MAX_PARTS partial sums per value (128^3 grids fit, 256^3 grids do not);
+ * larger requests return XFFT_EINVAL and touch nothing.  The first call on each device looks
+ * up the scratch address (a one-time set-up): make that first call before any stream capture.
+ * Every call shares the one scratch array: calls that overlap on the GPU (other streams,
+ * other threads, other contexts on the same device) race and must be serialised by the
+ * caller.  The context must exist with its microstructure set (those calls do allocate). */
+#define XFFT_NOALLOC_MAX_RHS 8
+#define XFFT_NOALLOC_MAX_PARTS 4096
+xfft_status xfft_apply_noalloc(xfft_ctx* ctx, int n_rhs, const double* d, double* q,
+                               double* dAd_sig);
+
 int xfft_num_enriched(const xfft_ctx* ctx);   /* nX, or -1 before set_microstructure */
 int xfft_num_cut_tets(const xfft_ctx* ctx);   /* number of cut tetrahedra, or -1 */
 const char* xfft_status_string(xfft_status s);

@@ -22,8 +22,9 @@ EXPORTED = (
     "xfft_default_options", "xfft_create", "xfft_set_microstructure", "xfft_solve",
     "xfft_effective_stiffness", "xfft_grad", "xfft_apply", "xfft_precondition", "xfft_get_setup",
     "xfft_num_enriched", "xfft_num_cut_tets", "xfft_status_string", "xfft_last_error",
-    "xfft_destroy", "xfft_profile", "xfft_profile_read",
+    "xfft_destroy", "xfft_profile", "xfft_profile_read", "xfft_apply_noalloc",
 )
+NOALLOC_MAX_RHS = 8
 PROF_KINDS = ("apply_uncut_f32", "apply_cut_f32", "apply_uncut_f64", "apply_cut_f64", "prec_f32",
               "prec_f64", "vector", "finalize", "setup", "grad", "post")
 
@@ -80,10 +81,11 @@ def lib():
     L.xfft_destroy.restype = None
     L.xfft_profile.argtypes = [vp, i]
     L.xfft_profile_read.argtypes = [vp, vp, vp, vp]
+    L.xfft_apply_noalloc.argtypes = [vp, i, vp, vp, vp]
     for name in ("xfft_default_options", "xfft_create", "xfft_set_microstructure", "xfft_solve",
                  "xfft_effective_stiffness", "xfft_grad", "xfft_apply", "xfft_precondition",
                  "xfft_get_setup", "xfft_num_enriched", "xfft_num_cut_tets", "xfft_profile",
-                 "xfft_profile_read"):
+                 "xfft_profile_read", "xfft_apply_noalloc"):
         getattr(L, name).restype = i
     _lib = L
     return L
@@ -252,6 +254,18 @@ class Solver:
                                sig.ctypes.data_as(C.POINTER(C.c_double)),
                                0 if precision == "fp64" else 1, 0))
         return q, sig
+
+    def apply_noalloc(self, d, q, dAd_sig=None):
+        """Allocation-free FP64 apply on caller-owned CUDA tensors (k x stride): q = A d; if
+        given, dAd_sig (k x 7) receives <d, A d> and int_Y C grad^s d.  The library allocates
+        nothing in this call."""
+        k = int(d.shape[0])
+        dp, dev1 = _ptr(d, np.float64)
+        qp, dev2 = _ptr(q, np.float64)
+        sp_, dev3 = _ptr(dAd_sig, np.float64)
+        if not (dev1 and dev2 and (dAd_sig is None or dev3)):
+            raise TypeError("apply_noalloc takes CUDA tensors only")
+        check(lib().xfft_apply_noalloc(self._ctx, k, dp, qp, sp_))
 
     def precondition(self, f, precision="fp64"):
         f = np.ascontiguousarray(np.atleast_2d(f), dtype=np.float64)

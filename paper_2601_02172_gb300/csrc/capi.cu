@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1070,5 +1071,58 @@ extern "C" xfft_status xfft_profile_read(xfft_ctx* c, double ms[16], long long l
     if (launches) launches[k] = c->plaunch[k];
     if (units) units[k] = (long long)u[k];
   }
+  return XFFT_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free apply
+// Reduction scratch of xfft_apply_noalloc: 7 partial-sum rows per right-hand side.  Host code
+// must not pass g_noalloc_scratch itself to a kernel (in host code the name is only a host-side
+// stand-in); its device address is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_scratch[XFFT_NOALLOC_MAX_RHS * 7 * XFFT_NOALLOC_MAX_PARTS];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[64] = {};
+
+static xfft_status noalloc_scratch(double** out) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(XFFT_EUNSUPPORTED, "device index above 63");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return XFFT_OK;
+}
+
+extern "C" xfft_status xfft_apply_noalloc(xfft_ctx* c, int n_rhs, const double* d, double* q,
+                                          double* dAd_sig) {
+  if (!c || !d || !q) return fail(XFFT_EINVAL, "NULL argument");
+  if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
+  if (n_rhs < 1 || n_rhs > XFFT_NOALLOC_MAX_RHS)
+    return fail(XFFT_EINVAL, "n_rhs must be in [1, XFFT_NOALLOC_MAX_RHS]");
+  const int nparts = apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut);
+  if (nparts > XFFT_NOALLOC_MAX_PARTS)
+    return fail(XFFT_EINVAL, "grid too large for the fixed scratch of xfft_apply_noalloc");
+  double* scratch = nullptr;
+  TRY(noalloc_scratch(&scratch));
+  ApplyArgs a;
+  a.g = c->g;
+  a.ph = c->ph;
+  a.code = c->code;
+  a.scale = c->has_scale ? c->scale : nullptr;
+  a.eps = nullptr;
+  a.active = nullptr;
+  a.stride = stride_of(c);
+  a.nX = c->nX;
+  a.partials = scratch;
+  a.nparts = nparts;
+  a.part_offset_cut = apply_uncut_blocks(c->g);
+  a.units_uncut = nullptr;
+  a.units_cut = nullptr;
+  CU(launch_apply<double>(d, q, c->isD, cutdata(c), a, n_rhs, c->stream));
+  if (dAd_sig) CU(launch_reduce_partials(scratch, 7 * n_rhs, nparts, nparts, dAd_sig, c->stream));
   return XFFT_OK;
 }
