@@ -125,8 +125,109 @@ __device__ __forceinline__ void tet_uncut(const T (&u)[8][3], T (&F)[8][3], unsi
   }
 }
 
-template <typename T, bool TOTAL>
-__global__ void __launch_bounds__(kTZ* kTY)
+// ---------------------------------------------------------------- uncut stencil
+// Node values staged in shared memory as 4-vectors (one 16- or 32-byte load per corner).
+template <typename T>
+struct Node4 {
+  T x, y, z, w;
+};
+template <typename T>
+__device__ __forceinline__ T comp(const Node4<T>& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : v.z);
+}
+
+// Per-voxel coefficients of the uncut tets, per phase ph (0 minus, 1 plus) and axis k:
+//   lw[ph][k] = lambda w_k s_v, mw[ph][k] = mu w_k s_v with w_k = |T| / h_k^2 on a uniform grid
+//   (raw node differences) or |T| / h_k otherwise (differences scaled by 1/h_k).
+template <typename T, bool UNIFORM>
+struct Coef {
+  T lw[2][UNIFORM ? 1 : 3];
+  T mw[2][UNIFORM ? 1 : 3];
+  __device__ __forceinline__ T l(int ph, int k) const { return lw[ph][UNIFORM ? 0 : k]; }
+  __device__ __forceinline__ T m(int ph, int k) const { return mw[ph][UNIFORM ? 0 : k]; }
+};
+
+// One uncut Kuhn tet: the displacement-gradient columns of the tet are the node differences
+// along its path 0 -> e_p -> e_p+e_q -> (1,1,1); the edge tensions T_k = w_k sigma e_k move
+// the corner forces: F[0] -= T_p, F[c1] += T_p - T_q, F[c2] += T_q - T_r, F[7] += T_r.
+template <typename T, int t, bool TOTAL, bool SIG, bool UNIFORM>
+__device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3], unsigned code,
+                                            const Coef<T, UNIFORM>& cf, const T (&ih)[3],
+                                            const T (&hk)[3], const T (&Eb)[3][3], T& en, T (&sg)[6]) {
+  constexpr int p = perm_p(t), q = perm_q(t), r = perm_r(t);
+  constexpr int c1 = tet_c1(t), c2 = tet_c2(t);
+  const unsigned cd = (code >> (2 * t)) & 3u;
+  if (cd == 2u) return;
+  const int ph = (int)cd;
+  T G[3][3];  // G[k][i]: column k (axis k) of the gradient, component i
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    G[p][i] = comp(u[c1], i) - comp(u[0], i);
+    G[q][i] = comp(u[c2], i) - comp(u[c1], i);
+    G[r][i] = comp(u[7], i) - comp(u[c2], i);
+  }
+  if (!UNIFORM) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      G[0][i] *= ih[0];
+      G[1][i] *= ih[1];
+      G[2][i] *= ih[2];
+    }
+  }
+  T Dr[3][3];  // unmodified columns for the energy
+  if (SIG) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Dr[k][i] = G[k][i];
+  }
+  if (TOTAL) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) G[k][i] += Eb[i][k];
+  }
+  const T tr = G[0][0] + G[1][1] + G[2][2];
+  const T s01 = G[0][1] + G[1][0], s02 = G[0][2] + G[2][0], s12 = G[1][2] + G[2][1];
+  T Tn[3][3];  // Tn[k][i] = tension on the column-k edge, component i
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T lw = cf.l(ph, k), mw = cf.m(ph, k);
+    Tn[k][k] = lw * tr + (mw + mw) * G[k][k];
+  }
+  {
+    Tn[0][1] = cf.m(ph, 0) * s01;
+    Tn[1][0] = cf.m(ph, 1) * s01;
+    Tn[0][2] = cf.m(ph, 0) * s02;
+    Tn[2][0] = cf.m(ph, 2) * s02;
+    Tn[1][2] = cf.m(ph, 1) * s12;
+    Tn[2][1] = cf.m(ph, 2) * s12;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    F[0][i] -= Tn[p][i];
+    F[c1][i] += Tn[p][i] - Tn[q][i];
+    F[c2][i] += Tn[q][i] - Tn[r][i];
+    F[7][i] += Tn[r][i];
+  }
+  if (SIG) {
+    // |T| sigma_ik = h_k Tn[k][i]; |T| sigma : eps = sum_k hk[k] Tn[k] . Dr[k]
+    sg[0] += hk[0] * Tn[0][0];
+    sg[1] += hk[1] * Tn[1][1];
+    sg[2] += hk[2] * Tn[2][2];
+    sg[3] += hk[1] * Tn[1][2];
+    sg[4] += hk[0] * Tn[0][2];
+    sg[5] += hk[0] * Tn[0][1];
+    T e = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      e += (UNIFORM ? T(1) : hk[k]) * (Tn[k][0] * Dr[k][0] + Tn[k][1] * Dr[k][1] + Tn[k][2] * Dr[k][2]);
+    en += e;
+  }
+}
+
+template <typename T, bool TOTAL, bool SIG, bool UNIFORM>
+__global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
     k_apply_uncut(const T* __restrict__ d, T* __restrict__ q, const ApplyArgs a, int nxchunks) {
   const int tz = threadIdx.x, ty = threadIdx.y;
   const int tid = tz + kTZ * ty;
@@ -144,11 +245,10 @@ __global__ void __launch_bounds__(kTZ* kTY)
   const T* dr = d + rhs * a.stride;
   T* qr = q + rhs * a.stride;
 
-  __shared__ T P[2][3][kTY + 1][kTZ + 1];
+  __shared__ Node4<T> P[2][kTY + 1][kTZ + 1];
   __shared__ T Ys[2][3][kTY][kTZ];
   __shared__ double red[7 * 32];
 
-  // the (up to two) plane nodes this thread loads
   constexpr int kPlaneNodes = (kTY + 1) * (kTZ + 1);
   int ld_slot[2];
   long long ld_off[2];
@@ -161,23 +261,39 @@ __global__ void __launch_bounds__(kTZ* kTY)
     const int zz = ((z0 - 1 + iz) % n2 + n2) % n2;
     ld_off[k] = (long long)yy * n2 + zz;
   }
-  const int yg = y0 - 1 + ty, zg = z0 - 1 + tz;  // unwrapped voxel column
+  const int yg = y0 - 1 + ty, zg = z0 - 1 + tz;
   const int yv = (yg % n1 + n1) % n1, zv = (zg % n2 + n2) % n2;
   const bool own = ty >= 1 && tz >= 1 && yg < n1 && zg < n2;
 
-  T lm[2], mu2[2], ih[3], w[3];
-  lm[0] = (T)a.ph.lam[0];
-  lm[1] = (T)a.ph.lam[1];
-  mu2[0] = (T)a.ph.mu[0];
-  mu2[1] = (T)a.ph.mu[1];
-  const T vol = (T)g.vol_tet;
+  T ih[3], hk[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     ih[k] = (T)(1.0 / g.h[k]);
-    w[k] = (T)(g.vol_tet / g.h[k]);
+    hk[k] = (T)g.h[k];
   }
-  T E[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-  if (TOTAL) mandel_to_tensor(a.eps + 6 * rhs, E);
+  // phase coefficients without the voxel scale (converted once; no FP64 work in the loop)
+  T lw0[2][3], mw0[2][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double wk = UNIFORM ? g.vol_tet / (g.h[0] * g.h[0]) : g.vol_tet / g.h[k];
+#pragma unroll
+    for (int ph = 0; ph < 2; ++ph) {
+      lw0[ph][k] = (T)(a.ph.lam[ph] * wk);
+      mw0[ph][k] = (T)(a.ph.mu[ph] * wk);
+    }
+  }
+  T Eb[3][3] = {};
+  if (TOTAL) {
+    const double* e = a.eps + 6 * rhs;
+    const double rs = 0.70710678118654752440;
+    const double sc = UNIFORM ? g.h[0] : 1.0;  // raw differences carry a factor h
+    Eb[0][0] = (T)(e[0] * sc);
+    Eb[1][1] = (T)(e[1] * sc);
+    Eb[2][2] = (T)(e[2] * sc);
+    Eb[1][2] = Eb[2][1] = (T)(e[3] * rs * sc);
+    Eb[0][2] = Eb[2][0] = (T)(e[4] * rs * sc);
+    Eb[0][1] = Eb[1][0] = (T)(e[5] * rs * sc);
+  }
 
   auto load_plane = [&](int xp, int buf) {
 #pragma unroll
@@ -185,8 +301,12 @@ __global__ void __launch_bounds__(kTZ* kTY)
       if (ld_slot[k] >= 0) {
         const int iy = ld_slot[k] / (kTZ + 1), iz = ld_slot[k] - iy * (kTZ + 1);
         const long long nd = (long long)xp * plane + ld_off[k];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) P[buf][c][iy][iz] = dr[c * N + nd];
+        Node4<T> v;
+        v.x = dr[nd];
+        v.y = dr[N + nd];
+        v.z = dr[2 * N + nd];
+        v.w = T(0);
+        P[buf][iy][iz] = v;
       }
     }
   };
@@ -200,41 +320,37 @@ __global__ void __launch_bounds__(kTZ* kTY)
     const int xw = (xv % n0 + n0) % n0;
     load_plane(xw + 1 == n0 ? 0 : xw + 1, (s + 1) & 1);
     __syncthreads();
-    T u[8][3];
+    Node4<T> u[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) u[c][i] = P[(s + dx) & 1][i][ty + dy][tz + dz];
-    }
+    for (int c = 0; c < 8; ++c) u[c] = P[(s + (c & 1)) & 1][ty + ((c >> 1) & 1)][tz + ((c >> 2) & 1)];
     const long long vox = (long long)xw * plane + (long long)yv * n2 + zv;
     const unsigned code = a.code[vox];
-    T lms[2] = {lm[0], lm[1]}, mus[2] = {mu2[0], mu2[1]};
-    if (a.scale) {
-      const T sv = (T)a.scale[vox];
-      lms[0] *= sv;
-      lms[1] *= sv;
-      mus[0] *= sv;
-      mus[1] *= sv;
-    }
+    const T sv = a.scale ? (T)a.scale[vox] : T(1);
+    Coef<T, UNIFORM> cf;
+#pragma unroll
+    for (int ph = 0; ph < 2; ++ph)
+#pragma unroll
+      for (int k = 0; k < (UNIFORM ? 1 : 3); ++k) {
+        cf.lw[ph][k] = lw0[ph][k] * sv;
+        cf.mw[ph][k] = mw0[ph][k] * sv;
+      }
     T F[8][3];
 #pragma unroll
     for (int c = 0; c < 8; ++c) F[c][0] = F[c][1] = F[c][2] = T(0);
     T ven = T(0);
     T vsg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    tet_uncut<T, 0, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
-    tet_uncut<T, 1, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
-    tet_uncut<T, 2, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
-    tet_uncut<T, 3, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
-    tet_uncut<T, 4, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
-    tet_uncut<T, 5, TOTAL>(u, F, code, lms, mus, ih, w, vol, E, ven, vsg);
-    if (own && s >= 1) {
+    tet_stencil<T, 0, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 1, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 2, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 3, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 4, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 5, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    if (SIG && own && s >= 1) {
       en += ven;
 #pragma unroll
       for (int k = 0; k < 6; ++k) sg[k] += vsg[k];
     }
-    // combine along z (lane tz receives the dz = 1 corners of voxel tz - 1)
-    T G[2][2][3];
+    T G2[2][2][3];
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx)
 #pragma unroll
@@ -242,35 +358,35 @@ __global__ void __launch_bounds__(kTZ* kTY)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
           const T up = __shfl_up_sync(0xffffffffu, F[dx + 2 * dy + 4][i], 1);
-          G[dx][dy][i] = F[dx + 2 * dy][i] + up;
+          G2[dx][dy][i] = F[dx + 2 * dy][i] + up;
         }
-    // combine along y through shared memory
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) Ys[dx][i][ty][tz] = G[dx][1][i];
+      for (int i = 0; i < 3; ++i) Ys[dx][i][ty][tz] = G2[dx][1][i];
     __syncthreads();
     if (own) {
       T H0[3], H1[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        H0[i] = G[0][0][i] + Ys[0][i][ty - 1][tz];
-        H1[i] = G[1][0][i] + Ys[1][i][ty - 1][tz];
+        H0[i] = G2[0][0][i] + Ys[0][i][ty - 1][tz];
+        H1[i] = G2[1][0][i] + Ys[1][i][ty - 1][tz];
       }
       if (s >= 1) {
         const long long nd = (long long)xw * plane + (long long)yv * n2 + zv;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) qr[i * N + nd] = pend[i] + H0[i];
+        const T q0 = pend[0] + H0[0], q1 = pend[1] + H0[1], q2 = pend[2] + H0[2];
+        qr[nd] = q0;
+        qr[N + nd] = q1;
+        qr[2 * N + nd] = q2;
+        if (!SIG) en += q0 * u[0].x + q1 * u[0].y + q2 * u[0].z;  // <d, q> of this node
       }
 #pragma unroll
       for (int i = 0; i < 3; ++i) pend[i] = H1[i];
     }
   }
-  // block reduction of the energy and stress integrals
-  double v[7] = {(double)en, (double)sg[0], (double)sg[1], (double)sg[2],
-                 (double)(sg[3] * T(1.41421356237309504880)),
-                 (double)(sg[4] * T(1.41421356237309504880)),
-                 (double)(sg[5] * T(1.41421356237309504880))};
+  const double r2 = 1.41421356237309504880;
+  double v[7] = {(double)en, (double)sg[0], (double)sg[1], (double)sg[2], (double)sg[3] * r2,
+                 (double)sg[4] * r2, (double)sg[5] * r2};
   double tot[7];
   block_sum<7>(v, red, tot);
   if (tid == 0) {
@@ -301,6 +417,8 @@ __global__ void __launch_bounds__(128)
   if (TOTAL) mandel_to_tensor(a.eps + 6 * rhs, E);
   T en = T(0);
   T sg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  const T lam_ph[2] = {(T)a.ph.lam[0], (T)a.ph.lam[1]};
+  const T mu_ph[2] = {(T)a.ph.mu[0], (T)a.ph.mu[1]};
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
     int nd[4], ei[4];
 #pragma unroll
@@ -351,7 +469,7 @@ __global__ void __launch_bounds__(128)
     for (int si = 0; si < 2; ++si) {
       const T s = si == 0 ? T(1) : T(-1);
       const int ph = si == 0 ? 1 : 0;
-      const T lam = (T)a.ph.lam[ph] * sv, mu = (T)a.ph.mu[ph] * sv;
+      const T lam = lam_ph[ph] * sv, mu = mu_ph[ph] * sv;
       T c[4], gam[3] = {T(0), T(0), T(0)};
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
@@ -393,19 +511,21 @@ __global__ void __launch_bounds__(128)
         sbar[k] = mm[0] * Sb[0][k] + mm[1] * Sb[1][k] + mm[2] * Sb[2][k] + mm[3] * Sb[3][k];
         Tt[k] = Pb[0] * Sb[0][k] + Pb[1] * Sb[1][k] + Pb[2] * Sb[2][k] + Pb[3] * Sb[3][k];
       }
-      // energy int sigma : eps = sum_bc M_bc S_b : E_c
+      if (a.want_sig) {
+        // energy int sigma : eps = sum_bc M_bc S_b : E_c
 #pragma unroll
-      for (int b = 0; b < 4; ++b)
+        for (int b = 0; b < 4; ++b)
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          const T* sb = Sb[b];
-          const T* ec = Eb[cc];
-          const T dd = sb[0] * ec[0] + sb[1] * ec[1] + sb[2] * ec[2] +
-                       T(2) * (sb[3] * ec[3] + sb[4] * ec[4] + sb[5] * ec[5]);
-          en += MM[midx(b, cc)] * dd;
-        }
+          for (int cc = 0; cc < 4; ++cc) {
+            const T* sb = Sb[b];
+            const T* ec = Eb[cc];
+            const T dd = sb[0] * ec[0] + sb[1] * ec[1] + sb[2] * ec[2] +
+                         T(2) * (sb[3] * ec[3] + sb[4] * ec[4] + sb[5] * ec[5]);
+            en += MM[midx(b, cc)] * dd;
+          }
 #pragma unroll
-      for (int k = 0; k < 6; ++k) sg[k] += sbar[k];
+        for (int k = 0; k < 6; ++k) sg[k] += sbar[k];
+      }
 #pragma unroll
       for (int aa = 0; aa < 4; ++aa) {
         T Ra[6];
@@ -426,6 +546,13 @@ __global__ void __launch_bounds__(128)
           qe[aa][i] += a2 + a3;
         }
       }
+    }
+    if (!a.want_sig) {
+      // <d, q> of this element: d~ q~ = w q_raw on the enriched DOFs
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) en += us[k][c] * qs[k][c] + ws[k][c] * qe[k][c];
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -468,10 +595,20 @@ cudaError_t launch_apply_uncut(const T* d, T* q, const ApplyArgs& a, int n_rhs, 
   const int gx = (g.n0 + kCX - 1) / kCX;
   dim3 block(kTZ, kTY, 1);
   dim3 grid(gz, gy, gx * n_rhs);
-  if (a.eps)
-    k_apply_uncut<T, true><<<grid, block, 0, s>>>(d, q, a, gx);
-  else
-    k_apply_uncut<T, false><<<grid, block, 0, s>>>(d, q, a, gx);
+  const bool uni = g.h[0] == g.h[1] && g.h[1] == g.h[2];
+  const bool sig = a.want_sig || a.eps;
+#define XFFT_LAUNCH(TOT, SG, UNI) k_apply_uncut<T, TOT, SG, UNI><<<grid, block, 0, s>>>(d, q, a, gx)
+  if (a.eps) {
+    if (uni) XFFT_LAUNCH(true, true, true);
+    else XFFT_LAUNCH(true, true, false);
+  } else if (sig) {
+    if (uni) XFFT_LAUNCH(false, true, true);
+    else XFFT_LAUNCH(false, true, false);
+  } else {
+    if (uni) XFFT_LAUNCH(false, false, true);
+    else XFFT_LAUNCH(false, false, false);
+  }
+#undef XFFT_LAUNCH
   return cudaGetLastError();
 }
 

@@ -451,6 +451,9 @@ static ApplyArgs apply_args(const xfft_ctx* c, const double* eps, const int* act
   a.partials = c->partials;
   a.nparts = nparts_of(c);
   a.part_offset_cut = apply_uncut_blocks(c->g);
+  a.units_uncut = nullptr;
+  a.units_cut = nullptr;
+  a.want_sig = 1;
   return a;
 }
 
@@ -470,6 +473,8 @@ template <typename T>
 static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev, int n_rhs,
                             const int* active, int fin_mode, double tol, int crit, int maxit) {
   ApplyArgs a = apply_args(c, eps_dev, active);
+  // the relative stopping rule of the inner FP32 solve needs no stress integrals
+  a.want_sig = (fin_mode == 1 && crit == 1) ? 0 : 1;
   const bool dbl = sizeof(T) == 8;
   const int ku = dbl ? XFFT_PROF_APPLY_UNCUT_F64 : XFFT_PROF_APPLY_UNCUT_F32;
   const int kc = dbl ? XFFT_PROF_APPLY_CUT_F64 : XFFT_PROF_APPLY_CUT_F32;
@@ -1122,6 +1127,7 @@ extern "C" xfft_status xfft_apply_noalloc(xfft_ctx* c, int n_rhs, const double* 
   a.part_offset_cut = apply_uncut_blocks(c->g);
   a.units_uncut = nullptr;
   a.units_cut = nullptr;
+  a.want_sig = 1;
   CU(launch_apply<double>(d, q, c->isD, cutdata(c), a, n_rhs, c->stream));
   if (dAd_sig) CU(launch_reduce_partials(scratch, 7 * n_rhs, nparts, nparts, dAd_sig, c->stream));
   return XFFT_OK;

@@ -51,8 +51,28 @@ struct FftPlan {
   int xpairs;       // row pairs per block in the z passes
   int ytk_d, ytiles_d, ytk_f, ytiles_f;  // k2 tile in the y passes (double / float)
   int gtk_d, gtiles_d, gtk_f, gtiles_f;  // k2 tile in the Green pass (double / float)
+  bool fast;        // every axis has a compile-time line plan (fft_fast.cu)
   void* pool;
 };
+
+// fast path (fft_fast.cu)
+bool fast_fft_supported(int n);
+int fast_z_pairs(int n2);
+template <typename T>
+cudaError_t fast_z_r2c(int n2, const T* f, void* spec, long long stride, long long sstride, long long rows,
+                       const int* active, const void* tw, unsigned long long* units, int n_rhs,
+                       cudaStream_t s);
+template <typename T>
+cudaError_t fast_z_c2r(int n2, const void* spec, const T* f, T* z, long long stride, long long sstride,
+                       long long rows, double scale, const int* active, const void* tw,
+                       double* partials, int nparts, int n_rhs, cudaStream_t s);
+template <typename T, bool INV>
+cudaError_t fast_y(int n1, int n0, void* spec, long long sstride, int K2, const int* active,
+                   const void* tw, int n_rhs, cudaStream_t s);
+template <typename T>
+cudaError_t fast_x_green(int n0, int n1, void* spec, long long sstride, int K2, const int* active,
+                         const void* tw, const void* const* ge, const void* const* gs, const double* ih,
+                         double halfvol, int n_rhs, cudaStream_t s);
 
 template <typename T>
 struct Cx;
@@ -531,6 +551,8 @@ FftPlan* fft_plan_create(const GridDev& g, cudaError_t* err) {
   p->n[1] = g.n1;
   p->n[2] = g.n2;
   p->K2 = g.n2 / 2 + 1;
+  p->fast = fast_fft_supported(g.n0) && fast_fft_supported(g.n1) && fast_fft_supported(g.n2) &&
+            true;
   for (int a = 0; a < 3; ++a) {
     factorize(p->n[a], p->ax[a]);
     if (p->ax[a].nst < 0) {
@@ -651,7 +673,8 @@ size_t fft_spectrum_elems(const FftPlan* p) { return 3ULL * p->n[0] * p->n[1] * 
 
 static int zpass_blocks(const FftPlan* p) {
   const long long rows = 3LL * p->n[0] * p->n[1];
-  return (int)((rows + 2LL * p->xpairs - 1) / (2LL * p->xpairs));
+  const long long pairs = p->fast ? fast_z_pairs(p->n[2]) : p->xpairs;
+  return (int)((rows + 2LL * pairs - 1) / (2LL * pairs));
 }
 
 static int enr_blocks(int nX) {
@@ -679,6 +702,28 @@ cudaError_t launch_precondition(const FftPlan* p, const T* f, T* z, void* spec_v
   const C* tw1 = reinterpret_cast<const C*>(dbl ? (const void*)p->twd[1] : (const void*)p->twf[1]);
   const C* tw2 = reinterpret_cast<const C*>(dbl ? (const void*)p->twd[a2] : (const void*)p->twf[a2]);
   const int zb = zpass_blocks(p);
+  if (p->fast) {
+    const void* ge[3];
+    const void* gs[3];
+    for (int a = 0; a < 3; ++a) {
+      ge[a] = dbl ? (const void*)p->ged[a] : (const void*)p->gef[a];
+      gs[a] = dbl ? (const void*)p->gsd[a] : (const void*)p->gsf[a];
+    }
+    const double ih[3] = {1.0 / p->g.h[0], 1.0 / p->g.h[1], 1.0 / p->g.h[2]};
+    cudaError_t e = fast_z_r2c<T>(p->n[2], f, spec, stride, sstride, rows, active, tw2, units, n_rhs, s);
+    if (e == cudaSuccess) e = fast_y<T, false>(p->n[1], p->n[0], spec, sstride, p->K2, active, tw1, n_rhs, s);
+    if (e == cudaSuccess)
+      e = fast_x_green<T>(p->n[0], p->n[1], spec, sstride, p->K2, active, tw0, ge, gs, ih, 0.5 * p->g.vol_tet,
+                          n_rhs, s);
+    if (e == cudaSuccess) e = fast_y<T, true>(p->n[1], p->n[0], spec, sstride, p->K2, active, tw1, n_rhs, s);
+    if (e == cudaSuccess)
+      e = fast_z_c2r<T>(p->n[2], spec, f, z, stride, sstride, rows,
+                        1.0 / ((double)p->n[0] * p->n[1] * p->n[2]), active, tw2, partials, nparts, n_rhs, s);
+    if (e != cudaSuccess) return e;
+    k_enr_identity<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, 3LL * nX,
+                                                                  active, partials, nparts, zb);
+    return cudaGetLastError();
+  }
   k_fft_z_r2c<T><<<dim3(zb, n_rhs), kFftThreads, smem_z(p, cs), s>>>(
       f, spec, stride, sstride, p->ax[2], p->K2, rows, p->xpairs, active, tw2, units);
   cudaError_t e = cudaGetLastError();

@@ -58,11 +58,13 @@ struct ApplyArgs {
   const int* active;       // per RHS flag or nullptr (all active)
   long long stride;        // elements per RHS vector (3 (N + nX))
   int nX;
-  double* partials;        // [rhs][7][nparts]: 0 = <d, A d> (energy), 1..6 = int C eps (Mandel)
+  double* partials;        // [rhs][7][nparts]: 0 = <d, A d>, 1..6 = int C eps (Mandel)
   int nparts;              // partial slots per RHS and component
   int part_offset_cut;     // first slot of the cut-tet kernel
   unsigned long long* units_uncut;  // optional counters of processed right-hand sides
   unsigned long long* units_cut;
+  int want_sig;            // 1: partials carry int_e sigma:eps and int_e sigma (always with eps);
+                           // 0: partial 0 is <d, q> and the stress integrals are 0
 };
 template <typename T>
 cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,

@@ -39,6 +39,14 @@ def _case(name):
                        synth.sphere_levelset(n, (0.8, 0.85, 0.2), 0.15))
         return (n, (1.0, 1.0, 1.0), L, synth.lame_from_E_nu(20.0, 0.2), synth.lame_from_E_nu(1.0, 0.3),
                 synth.voxel_scale(n, 3))
+    if name == "fast_mixed":  # every axis on the compile-time FFT plans, radices 2, 3, 4, 8
+        n = (16, 48, 32)
+        L = synth.sphere_levelset(n, (0.4, 0.55, 0.5), 0.28)
+        return n, (1.0, 1.2, 0.9), L, synth.lame_from_E_nu(30.0, 0.2), synth.lame_from_E_nu(1.0, 0.3), None
+    if name == "fast_radix5":
+        n = (80, 16, 16)
+        L = synth.sphere_levelset(n, (0.5, 0.5, 0.5), 0.3)
+        return n, (1.0, 1.0, 1.0), L, synth.lame_from_E_nu(5.0, 0.3), synth.lame_from_E_nu(1.0, 0.3), None
     if name == "aniso_cell":
         n = (12, 8, 10)
         ell = (1.5, 0.8, 1.2)
@@ -92,7 +100,7 @@ def test_apply_matches_oracle(xf, name, prec):
         assert _rel(sig[r], ref) < tol
 
 
-@pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell"])
+@pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell", "fast_mixed", "fast_radix5"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_precondition_matches_oracle(xf, name, prec):
     n, ell, L, lm, lp, sc = _case(name)
@@ -106,8 +114,9 @@ def test_precondition_matches_oracle(xf, name, prec):
         std -= std.mean(axis=1, keepdims=True)
     z, rr = s.precondition(f, precision=prec)
     tol = 1e-11 if prec == "fp64" else 2e-5
+    green = "fft" if name.startswith("fast") else "sparse"
     for r in range(3):
-        ref = o.precondition(f[r], green="sparse")
+        ref = o.precondition(f[r], green=green)
         assert _rel(z[r], ref) < tol
         assert abs(rr[r] - f[r] @ ref) <= tol * abs(f[r] @ ref) * 10
 
