@@ -131,7 +131,7 @@ class Solver:
     """One grid on the current CUDA device (thin wrapper of ``xfft_ctx``)."""
 
     def __init__(self, n, length=(1.0, 1.0, 1.0), precision="fp64", tol=1e-10, maxit=10000,
-                 snap_tau=0.0, inner_tol=1e-4, max_refine=20, poll_every=8, stream=None):
+                 snap_tau=0.0, inner_tol=1e-5, max_refine=20, poll_every=8, stream=None):
         L = lib()
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)

@@ -226,7 +226,7 @@ __device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3]
   }
 }
 
-template <typename T, bool TOTAL, bool SIG, bool UNIFORM>
+template <typename T, bool TOTAL, bool SIG, bool UNIFORM, bool FUSED>
 __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
     k_apply_uncut(const T* __restrict__ d, T* __restrict__ q, const ApplyArgs a, int nxchunks) {
   const int tz = threadIdx.x, ty = threadIdx.y;
@@ -295,16 +295,80 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
     Eb[0][1] = Eb[1][0] = (T)(e[5] * rs * sc);
   }
 
-  auto load_plane = [&](int xp, int buf) {
+  // fused CG update: the block owns the plane nodes with 1 <= iy <= kTY-1, 1 <= iz <= kTZ-1
+  // inside the grid; it stores d_new and updates u there (other blocks only read them as halo)
+  const T* zr = FUSED ? static_cast<const T*>(a.fz) + rhs * a.stride : nullptr;
+  T* dnr = FUSED ? static_cast<T*>(a.fdnew) + rhs * a.stride : nullptr;
+  T* ur = FUSED ? static_cast<T*>(a.fu) + rhs * a.stride : nullptr;
+  const T fa = FUSED ? (T)a.st[rhs].alpha : T(0);
+  const T fb = FUSED ? (T)a.st[rhs].beta : T(0);
+  bool slot_own[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int lin = tid + k * kTZ * kTY;
+    const int iy = lin / (kTZ + 1), iz = lin - iy * (kTZ + 1);
+    slot_own[k] = ld_slot[k] >= 0 && iy >= 1 && iy <= kTY - 1 && iz >= 1 && iz <= kTZ - 1 &&
+                  y0 - 1 + iy < n1 && z0 - 1 + iz < n2;
+  }
+
+  // Two-stage plane pipeline: fetch() issues the global loads of a node plane into registers,
+  // commit() (one step later, after the arithmetic of the current step was issued) forms the
+  // fused update, stores the block's own nodes and fills the shared-memory plane.
+  T pf[2][9];  // per load slot: z (or d) 0..2, d_old 3..5, u 6..8
+  long long pf_nd[2] = {0, 0};
+  bool pf_own[2] = {false, false};
+  auto fetch = [&](int xp, bool own_plane) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      pf_own[k] = false;
+      if (ld_slot[k] >= 0) {
+        const long long nd = (long long)xp * plane + ld_off[k];
+        pf_nd[k] = nd;
+        if (FUSED) {
+          pf[k][0] = zr[nd];
+          pf[k][1] = zr[N + nd];
+          pf[k][2] = zr[2 * N + nd];
+          pf[k][3] = dr[nd];
+          pf[k][4] = dr[N + nd];
+          pf[k][5] = dr[2 * N + nd];
+          pf_own[k] = own_plane && slot_own[k];
+          if (pf_own[k]) {
+            pf[k][6] = ur[nd];
+            pf[k][7] = ur[N + nd];
+            pf[k][8] = ur[2 * N + nd];
+          }
+        } else {
+          pf[k][0] = dr[nd];
+          pf[k][1] = dr[N + nd];
+          pf[k][2] = dr[2 * N + nd];
+        }
+      }
+    }
+  };
+  auto commit = [&](int buf) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       if (ld_slot[k] >= 0) {
         const int iy = ld_slot[k] / (kTZ + 1), iz = ld_slot[k] - iy * (kTZ + 1);
-        const long long nd = (long long)xp * plane + ld_off[k];
         Node4<T> v;
-        v.x = dr[nd];
-        v.y = dr[N + nd];
-        v.z = dr[2 * N + nd];
+        if (FUSED) {
+          v.x = pf[k][0] + fb * pf[k][3];
+          v.y = pf[k][1] + fb * pf[k][4];
+          v.z = pf[k][2] + fb * pf[k][5];
+          if (pf_own[k]) {
+            const long long nd = pf_nd[k];
+            dnr[nd] = v.x;
+            dnr[N + nd] = v.y;
+            dnr[2 * N + nd] = v.z;
+            ur[nd] = pf[k][6] + fa * pf[k][3];
+            ur[N + nd] = pf[k][7] + fa * pf[k][4];
+            ur[2 * N + nd] = pf[k][8] + fa * pf[k][5];
+          }
+        } else {
+          v.x = pf[k][0];
+          v.y = pf[k][1];
+          v.z = pf[k][2];
+        }
         v.w = T(0);
         P[buf][iy][iz] = v;
       }
@@ -314,11 +378,18 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
   T pend[3] = {T(0), T(0), T(0)};
   T en = T(0);
   T sg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-  load_plane(((x0 - 1) % n0 + n0) % n0, 0);
+  const int xfirst = ((x0 - 1) % n0 + n0) % n0;
+  fetch(xfirst, false);
+  commit(0);
+  fetch(xfirst + 1 == n0 ? 0 : xfirst + 1, x0 < x1);
   for (int s = 0; s <= x1 - x0; ++s) {
     const int xv = x0 - 1 + s;
     const int xw = (xv % n0 + n0) % n0;
-    load_plane(xw + 1 == n0 ? 0 : xw + 1, (s + 1) & 1);
+    commit((s + 1) & 1);  // plane x0 + s
+    if (s + 1 <= x1 - x0) {
+      const int xn = xw + 2 >= n0 ? xw + 2 - n0 : xw + 2;  // plane x0 + s + 1
+      fetch(xn, x0 + s + 1 < x1);
+    }
     __syncthreads();
     Node4<T> u[8];
 #pragma unroll
@@ -396,8 +467,38 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
   }
 }
 
+// Stress of the strain sum_b alpha_b E_b on one side, E_b = es + c_b ew + sym(w_b (x) gamma):
+//   sum_b alpha_b E_b = A0 es + A1 ew + sym(W (x) gamma),  A0 = sum alpha_b, A1 = sum alpha_b c_b,
+//   W = sum alpha_b w_b.
+template <typename T>
+__device__ __forceinline__ void side_stress(const T (&al)[4], const T (&c)[4], const T (&es)[6],
+                                            const T (&ew)[6], const T (&ws)[4][3], const T (&gam)[3],
+                                            T lam, T mu, T (&st)[6]) {
+  const T A0 = al[0] + al[1] + al[2] + al[3];
+  const T A1 = al[0] * c[0] + al[1] * c[1] + al[2] * c[2] + al[3] * c[3];
+  T W[3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) W[x] = al[0] * ws[0][x] + al[1] * ws[1][x] + al[2] * ws[2][x] + al[3] * ws[3][x];
+  T e[6];
+  e[0] = A0 * es[0] + A1 * ew[0] + W[0] * gam[0];
+  e[1] = A0 * es[1] + A1 * ew[1] + W[1] * gam[1];
+  e[2] = A0 * es[2] + A1 * ew[2] + W[2] * gam[2];
+  e[3] = A0 * es[3] + A1 * ew[3] + T(0.5) * (W[1] * gam[2] + W[2] * gam[1]);
+  e[4] = A0 * es[4] + A1 * ew[4] + T(0.5) * (W[0] * gam[2] + W[2] * gam[0]);
+  e[5] = A0 * es[5] + A1 * ew[5] + T(0.5) * (W[0] * gam[1] + W[1] * gam[0]);
+  iso_stress(e, lam, mu, st);
+}
+
+// (sym 3x3 stored as 00,11,22,12,02,01) times vector
+template <typename T>
+__device__ __forceinline__ void sym_mv(const T (&s)[6], const T* v, T (&out)[3]) {
+  out[0] = s[0] * v[0] + s[5] * v[1] + s[4] * v[2];
+  out[1] = s[5] * v[0] + s[1] * v[1] + s[3] * v[2];
+  out[2] = s[4] * v[0] + s[3] * v[1] + s[2] * v[2];
+}
+
 template <typename T, bool TOTAL>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4)
     k_apply_cut(const T* __restrict__ d, T* __restrict__ q, const T* __restrict__ isD,
                 const CutData cd, const ApplyArgs a) {
   const int rhs = blockIdx.y;
@@ -415,10 +516,10 @@ __global__ void __launch_bounds__(128)
   for (int k = 0; k < 3; ++k) ih[k] = (T)(1.0 / g.h[k]);
   T E[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   if (TOTAL) mandel_to_tensor(a.eps + 6 * rhs, E);
-  T en = T(0);
-  T sg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   const T lam_ph[2] = {(T)a.ph.lam[0], (T)a.ph.lam[1]};
   const T mu_ph[2] = {(T)a.ph.mu[0], (T)a.ph.mu[1]};
+  T en = T(0);
+  T sg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
     int nd[4], ei[4];
 #pragma unroll
@@ -430,36 +531,39 @@ __global__ void __launch_bounds__(128)
     const int t = cd.ip[9 * ncut + e];
     T gr[4][3];
     tet_grads<T>(t, ih, gr);
-    T us[4][3], ws[4][3], sc[4][3];
+    T us[4][3], ws[4][3];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         us[k][c] = dr[c * N + nd[k]];
-        sc[k][c] = isD[(long long)c * nX + ei[k]];
-        ws[k][c] = dr[3 * N + (long long)c * nX + ei[k]] * sc[k][c];
+        ws[k][c] = dr[3 * N + (long long)c * nX + ei[k]] * isD[(long long)c * nX + ei[k]];
       }
     T L[4];
 #pragma unroll
     for (int b = 0; b < 4; ++b) L[b] = cut_real<T>(cd, cut_f_L(b), e);
     const T sv = a.scale ? (T)a.scale[vox] : T(1);
-    // standard and enriched displacement gradients
-    T Hs[3][3], Hw[3][3];
+    // standard and enriched symmetric gradients (constant on the tet)
+    T es[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, ew[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        Hs[i][j] = us[0][i] * gr[0][j] + us[1][i] * gr[1][j] + us[2][i] * gr[2][j] + us[3][i] * gr[3][j];
-        Hw[i][j] = ws[0][i] * gr[0][j] + ws[1][i] * gr[1][j] + ws[2][i] * gr[2][j] + ws[3][i] * gr[3][j];
-      }
-    T es[6] = {Hs[0][0], Hs[1][1], Hs[2][2], T(0.5) * (Hs[1][2] + Hs[2][1]),
-               T(0.5) * (Hs[0][2] + Hs[2][0]), T(0.5) * (Hs[0][1] + Hs[1][0])};
+    for (int k = 0; k < 4; ++k) {
+      es[0] += us[k][0] * gr[k][0];
+      es[1] += us[k][1] * gr[k][1];
+      es[2] += us[k][2] * gr[k][2];
+      es[3] += T(0.5) * (us[k][1] * gr[k][2] + us[k][2] * gr[k][1]);
+      es[4] += T(0.5) * (us[k][0] * gr[k][2] + us[k][2] * gr[k][0]);
+      es[5] += T(0.5) * (us[k][0] * gr[k][1] + us[k][1] * gr[k][0]);
+      ew[0] += ws[k][0] * gr[k][0];
+      ew[1] += ws[k][1] * gr[k][1];
+      ew[2] += ws[k][2] * gr[k][2];
+      ew[3] += T(0.5) * (ws[k][1] * gr[k][2] + ws[k][2] * gr[k][1]);
+      ew[4] += T(0.5) * (ws[k][0] * gr[k][2] + ws[k][2] * gr[k][0]);
+      ew[5] += T(0.5) * (ws[k][0] * gr[k][1] + ws[k][1] * gr[k][0]);
+    }
     if (TOTAL) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) es[k] += E[k];
     }
-    const T ew[6] = {Hw[0][0], Hw[1][1], Hw[2][2], T(0.5) * (Hw[1][2] + Hw[2][1]),
-                     T(0.5) * (Hw[0][2] + Hw[2][0]), T(0.5) * (Hw[0][1] + Hw[1][0])};
     T qs[4][3], qe[4][3];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -477,89 +581,50 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
       }
-      T mm[4], MM[10];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) mm[b] = cut_real<T>(cd, cut_f_m(si, b), e);
+      T MM[10];
 #pragma unroll
       for (int k = 0; k < 10; ++k) MM[k] = cut_real<T>(cd, cut_f_M(si, k), e);
-      T Eb[4][6], Sb[4][6];
+      // weights: m_b = sum_c M_bc; P_b = sum_c M_bc c_c; rows of M
+      T mw[4], pw[4];
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const T* wb = ws[b];
-        const T sw[6] = {wb[0] * gam[0], wb[1] * gam[1], wb[2] * gam[2],
-                         T(0.5) * (wb[1] * gam[2] + wb[2] * gam[1]),
-                         T(0.5) * (wb[0] * gam[2] + wb[2] * gam[0]),
-                         T(0.5) * (wb[0] * gam[1] + wb[1] * gam[0])};
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Eb[b][k] = es[k] + c[b] * ew[k] + sw[k];
-        T ebk[6] = {Eb[b][0], Eb[b][1], Eb[b][2], Eb[b][3], Eb[b][4], Eb[b][5]};
-        T sbk[6];
-        iso_stress(ebk, lam, mu, sbk);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Sb[b][k] = sbk[k];
+        mw[b] = MM[midx(b, 0)] + MM[midx(b, 1)] + MM[midx(b, 2)] + MM[midx(b, 3)];
+        pw[b] = MM[midx(b, 0)] * c[0] + MM[midx(b, 1)] * c[1] + MM[midx(b, 2)] * c[2] + MM[midx(b, 3)] * c[3];
       }
       T sbar[6], Tt[6];
-      T Pb[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        Pb[b] = T(0);
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) Pb[b] += MM[midx(b, cc)] * c[cc];
-      }
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        sbar[k] = mm[0] * Sb[0][k] + mm[1] * Sb[1][k] + mm[2] * Sb[2][k] + mm[3] * Sb[3][k];
-        Tt[k] = Pb[0] * Sb[0][k] + Pb[1] * Sb[1][k] + Pb[2] * Sb[2][k] + Pb[3] * Sb[3][k];
-      }
+      side_stress(mw, c, es, ew, ws, gam, lam, mu, sbar);
+      side_stress(pw, c, es, ew, ws, gam, lam, mu, Tt);
       if (a.want_sig) {
-        // energy int sigma : eps = sum_bc M_bc S_b : E_c
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            const T* sb = Sb[b];
-            const T* ec = Eb[cc];
-            const T dd = sb[0] * ec[0] + sb[1] * ec[1] + sb[2] * ec[2] +
-                         T(2) * (sb[3] * ec[3] + sb[4] * ec[4] + sb[5] * ec[5]);
-            en += MM[midx(b, cc)] * dd;
-          }
 #pragma unroll
         for (int k = 0; k < 6; ++k) sg[k] += sbar[k];
       }
 #pragma unroll
       for (int aa = 0; aa < 4; ++aa) {
+        const T row[4] = {MM[midx(aa, 0)], MM[midx(aa, 1)], MM[midx(aa, 2)], MM[midx(aa, 3)]};
         T Ra[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-          Ra[k] = MM[midx(aa, 0)] * Sb[0][k] + MM[midx(aa, 1)] * Sb[1][k] +
-                  MM[midx(aa, 2)] * Sb[2][k] + MM[midx(aa, 3)] * Sb[3][k];
+        side_stress(row, c, es, ew, ws, gam, lam, mu, Ra);
+        T v1[3], v2[3], v3[3];
+        sym_mv(sbar, gr[aa], v1);
+        sym_mv(Tt, gr[aa], v2);
+        sym_mv(Ra, gam, v3);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          T a1 = T(0), a2 = T(0), a3 = T(0);
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            a1 += sym_at(sbar, i, j) * gr[aa][j];
-            a2 += sym_at(Tt, i, j) * gr[aa][j];
-            a3 += sym_at(Ra, i, j) * gam[j];
-          }
-          qs[aa][i] += a1;
-          qe[aa][i] += a2 + a3;
+          qs[aa][i] += v1[i];
+          qe[aa][i] += v2[i] + v3[i];
         }
       }
     }
-    if (!a.want_sig) {
-      // <d, q> of this element: d~ q~ = w q_raw on the enriched DOFs
+    // <d, q> of this element (d~ q~ = w q_raw on the enriched DOFs); equals int sigma : eps
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) en += us[k][c] * qs[k][c] + ws[k][c] * qe[k][c];
-    }
+      for (int c = 0; c < 3; ++c) en += us[k][c] * qs[k][c] + ws[k][c] * qe[k][c];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         atomicAdd(&qr[c * N + nd[k]], qs[k][c]);
-        atomicAdd(&qr[3 * N + (long long)c * nX + ei[k]], qe[k][c] * sc[k][c]);
+        atomicAdd(&qr[3 * N + (long long)c * nX + ei[k]], qe[k][c] * isD[(long long)c * nX + ei[k]]);
       }
   }
   double v[7] = {(double)en, (double)sg[0], (double)sg[1], (double)sg[2],
@@ -597,8 +662,17 @@ cudaError_t launch_apply_uncut(const T* d, T* q, const ApplyArgs& a, int n_rhs, 
   dim3 grid(gz, gy, gx * n_rhs);
   const bool uni = g.h[0] == g.h[1] && g.h[1] == g.h[2];
   const bool sig = a.want_sig || a.eps;
-#define XFFT_LAUNCH(TOT, SG, UNI) k_apply_uncut<T, TOT, SG, UNI><<<grid, block, 0, s>>>(d, q, a, gx)
-  if (a.eps) {
+#define XFFT_LAUNCH(TOT, SG, UNI) k_apply_uncut<T, TOT, SG, UNI, false><<<grid, block, 0, s>>>(d, q, a, gx)
+#define XFFT_LAUNCH_F(SG, UNI) k_apply_uncut<T, false, SG, UNI, true><<<grid, block, 0, s>>>(d, q, a, gx)
+  if (a.fz) {
+    if (sig) {
+      if (uni) XFFT_LAUNCH_F(true, true);
+      else XFFT_LAUNCH_F(true, false);
+    } else {
+      if (uni) XFFT_LAUNCH_F(false, true);
+      else XFFT_LAUNCH_F(false, false);
+    }
+  } else if (a.eps) {
     if (uni) XFFT_LAUNCH(true, true, true);
     else XFFT_LAUNCH(true, true, false);
   } else if (sig) {
@@ -609,6 +683,7 @@ cudaError_t launch_apply_uncut(const T* d, T* q, const ApplyArgs& a, int n_rhs, 
     else XFFT_LAUNCH(false, false, false);
   }
 #undef XFFT_LAUNCH
+#undef XFFT_LAUNCH_F
   return cudaGetLastError();
 }
 

@@ -84,8 +84,8 @@ struct xfft_ctx {
   int cap_rhs = 0;
   long long cap_stride = 0;
   int cap_prec = -1;
-  double* v64[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // u f d z q (FP64)
-  float* v32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // u f d z q (FP32)
+  double* v64[6] = {};  // u f d z q d' (FP64)
+  float* v32[6] = {};   // u f d z q d' (FP32); d and d' alternate as old / new direction
   void* spec = nullptr;
   size_t spec_bytes = 0;
   RhsState* st = nullptr;
@@ -210,7 +210,7 @@ extern "C" xfft_status xfft_default_options(xfft_options* opt) {
   opt->maxit = 10000;
   opt->snap_tau = 0.0;
   opt->enr_precond = XFFT_ENR_IDENTITY;
-  opt->inner_tol = 1e-4;
+  opt->inner_tol = 1e-5;
   opt->max_refine = 20;
   opt->poll_every = 8;
   return XFFT_OK;
@@ -291,7 +291,7 @@ static void free_micro(xfft_ctx* c) {
 }
 
 static void free_work(xfft_ctx* c) {
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     dfree(c->v64[k]);
     dfree(c->v32[k]);
   }
@@ -408,11 +408,11 @@ static xfft_status ensure_work(xfft_ctx* c, int n_rhs, int prec) {
   free_work(c);
   const size_t tot = (size_t)n_rhs * stride;
   if (prec == XFFT_FP64) {
-    for (int k = 0; k < 5; ++k) CU(dalloc(&c->v64[k], tot));
+    for (int k = 0; k < 6; ++k) CU(dalloc(&c->v64[k], tot));
   } else {
     CU(dalloc(&c->v64[0], tot));  // u (FP64 iterate)
     CU(dalloc(&c->v64[4], tot));  // FP64 residual
-    for (int k = 0; k < 5; ++k) CU(dalloc(&c->v32[k], tot));
+    for (int k = 0; k < 6; ++k) CU(dalloc(&c->v32[k], tot));
   }
   c->spec_bytes = (size_t)n_rhs * fft_spectrum_elems(c->fft) * (prec == XFFT_FP64 ? 16 : 8);
   CU(cudaMalloc(&c->spec, c->spec_bytes));
@@ -454,6 +454,10 @@ static ApplyArgs apply_args(const xfft_ctx* c, const double* eps, const int* act
   a.units_uncut = nullptr;
   a.units_cut = nullptr;
   a.want_sig = 1;
+  a.fz = nullptr;
+  a.fdnew = nullptr;
+  a.fu = nullptr;
+  a.st = nullptr;
   return a;
 }
 
@@ -471,8 +475,13 @@ const float* isd_of<float>(const xfft_ctx* c) {
 // q = A d (+ b(eps)); finalisation `mode` (0 or 1) on the apply partials
 template <typename T>
 static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev, int n_rhs,
-                            const int* active, int fin_mode, double tol, int crit, int maxit) {
+                            const int* active, int fin_mode, double tol, int crit, int maxit,
+                            const T* fz = nullptr, T* fdnew = nullptr, T* fu = nullptr, int parity = 0) {
   ApplyArgs a = apply_args(c, eps_dev, active);
+  a.fz = fz;
+  a.fdnew = fdnew;
+  a.fu = fu;
+  a.st = c->st;
   // the relative stopping rule of the inner FP32 solve needs no stress integrals
   a.want_sig = (fin_mode == 1 && crit == 1) ? 0 : 1;
   const bool dbl = sizeof(T) == 8;
@@ -486,7 +495,7 @@ static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev
   }
   {
     ProfScope ps(c, kc, 1);
-    CU(launch_apply_cut<T>(d, q, isd_of<T>(c), cutdata(c), a, n_rhs, c->stream));
+    CU(launch_apply_cut<T>(fz ? fdnew : d, q, isd_of<T>(c), cutdata(c), a, n_rhs, c->stream));
   }
   if (fin_mode >= 0) {
     ProfScope ps(c, XFFT_PROF_FINALIZE, 1);
@@ -498,20 +507,24 @@ static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev
     fa.maxit = maxit;
     fa.nparts = a.nparts;
     fa.nparts_used = apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut);
+    fa.set_rel = 0;
+    fa.inner_floor = 0.0;
+    fa.parity = parity;
     CU(launch_finalize(c->st, c->partials, fa, n_rhs, c->act, c->stream));
   }
   return XFFT_OK;
 }
 
 template <typename T>
-static xfft_status do_prec(xfft_ctx* c, const T* f, T* z, int n_rhs, const int* active, int fin_mode,
-                           double tol, int crit, int maxit) {
+static xfft_status do_prec(xfft_ctx* c, T* f, T* z, int n_rhs, const int* active, int fin_mode,
+                           double tol, int crit, int maxit, int set_rel = 0, const T* qfuse = nullptr,
+                           int parity = 0) {
   const int nparts = nparts_of(c);
   {
     const int kp = sizeof(T) == 8 ? XFFT_PROF_PREC_F64 : XFFT_PROF_PREC_F32;
     ProfScope ps(c, kp, 6);
     CU(launch_precondition<T>(c->fft, f, z, c->spec, stride_of(c), c->nX, active, c->partials, nparts,
-                              n_rhs, c->stream, punit(c, kp)));
+                              n_rhs, c->stream, punit(c, kp), qfuse, qfuse ? c->st : nullptr));
   }
   if (fin_mode >= 0) {
     ProfScope ps(c, XFFT_PROF_FINALIZE, 1);
@@ -523,6 +536,9 @@ static xfft_status do_prec(xfft_ctx* c, const T* f, T* z, int n_rhs, const int* 
     fa.maxit = maxit;
     fa.nparts = nparts;
     fa.nparts_used = precondition_blocks(c->fft, c->nX);
+    fa.set_rel = set_rel;
+    fa.inner_floor = c->opt.inner_tol;
+    fa.parity = parity;
     CU(launch_finalize(c->st, c->partials, fa, n_rhs, c->act, c->stream));
   }
   return XFFT_OK;
@@ -550,28 +566,36 @@ static xfft_status read_states(xfft_ctx* c, int n_rhs) {
     if (s_ != XFFT_OK) return s_;     \
   } while (0)
 
-// CG iterations on vectors (u, f, d, z, q) of type T, starting from an initialised state
-// (f, z = P^-1 f, rr set by a mode-3 finalisation, d = z).
+// CG iterations of type T.  On entry f is the negative residual, z = P^-1 f with the state
+// finalised in mode 3, the state's alpha = beta = 0 and dA = 0.  Each iteration:
+//   d_new = z + beta d_old, u += alpha d_old (fused into the stencil and a tail kernel),
+//   q = A d_new, alpha = rr / <q, d_new>,
+//   f -= alpha q, z = P^-1 f (fused into the first FFT pass), beta = rr'/rr.
+// The last u += alpha d of each right-hand side is applied after the loop.
 template <typename T>
-static xfft_status cg_loop(xfft_ctx* c, T* u, T* f, T* d, T* z, T* q, int n_rhs, double tol, int crit,
-                           int maxit) {
+static xfft_status cg_loop(xfft_ctx* c, T* u, T* f, T* dA, T* dB, T* z, T* q, int n_rhs, double tol,
+                           int crit, int maxit) {
   const long long stride = stride_of(c);
+  T* dbuf[2] = {dA, dB};
   for (int it = 0; it <= maxit; ++it) {
     if (it % c->opt.poll_every == 0) {
       int na = 0;
       TRY(poll_active(c, n_rhs, &na));
       if (na == 0) break;
     }
-    TRY(do_apply<T>(c, d, q, nullptr, n_rhs, c->act, 1, tol, crit, maxit));
+    T* dold = dbuf[it & 1];
+    T* dnew = dbuf[(it + 1) & 1];
+    const int par = (it + 1) & 1;
     {
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-      CU(launch_axpy_cg<T>(u, f, d, q, c->st, stride, n_rhs, c->stream));
+      CU(launch_cg_update_tail<T>(z, dold, dnew, u, c->st, 3 * c->g.N, stride, n_rhs, c->stream));
     }
-    TRY(do_prec<T>(c, f, z, n_rhs, c->act, 2, tol, crit, maxit));
-    {
-      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-      CU(launch_xpby<T>(d, z, c->st, stride, n_rhs, c->stream));
-    }
+    TRY(do_apply<T>(c, dold, q, nullptr, n_rhs, c->act, 1, tol, crit, maxit, z, dnew, u, par));
+    TRY(do_prec<T>(c, f, z, n_rhs, c->act, 2, tol, crit, maxit, 0, q, par));
+  }
+  {
+    ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+    CU(launch_cg_finish<T>(u, dA, dB, c->st, stride, n_rhs, c->stream));
   }
   return XFFT_OK;
 }
@@ -604,7 +628,8 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
   }
   R->refine_steps = 0;
   if (c->opt.precision == XFFT_FP64) {
-    double *u = c->v64[0], *f = c->v64[1], *d = c->v64[2], *z = c->v64[3], *q = c->v64[4];
+    double *u = c->v64[0], *f = c->v64[1], *d = c->v64[2], *z = c->v64[3], *q = c->v64[4],
+           *d2 = c->v64[5];
     CU(cudaMemsetAsync(u, 0, tot * sizeof(double), s));
     {
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
@@ -616,11 +641,8 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
       CU(launch_scale_copy<double, double>(q, f, -1.0, stride, n_rhs, c->act, s));
     }
     TRY(do_prec<double>(c, f, z, n_rhs, c->act, 3, tol, 0, c->opt.maxit));
-    {
-      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-      CU(launch_scale_copy<double, double>(z, d, 1.0, stride, n_rhs, nullptr, s));
-    }
-    TRY(cg_loop<double>(c, u, f, d, z, q, n_rhs, tol, 0, c->opt.maxit));
+    CU(cudaMemsetAsync(d, 0, tot * sizeof(double), s));
+    TRY(cg_loop<double>(c, u, f, d, d2, z, q, n_rhs, tol, 0, c->opt.maxit));
     TRY(read_states(c, n_rhs));
     for (int r = 0; r < n_rhs; ++r) {
       const RhsState& st = c->h_st[r];
@@ -638,7 +660,8 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
   // FP32 inner solves with FP64 residual refinement
   double* u = c->v64[0];
   double* r64 = c->v64[4];
-  float *du = c->v32[0], *f = c->v32[1], *d = c->v32[2], *z = c->v32[3], *q = c->v32[4];
+  float *du = c->v32[0], *f = c->v32[1], *d = c->v32[2], *z = c->v32[3], *q = c->v32[4],
+        *d2 = c->v32[5];
   CU(cudaMemsetAsync(u, 0, tot * sizeof(double), s));
   std::vector<int> pending(n_rhs, 1);
   std::vector<int> hmask(64, 0);
@@ -649,13 +672,20 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
       CU(launch_init_state(c->st, c->act, n_rhs, c->outer_mask, s));
     }
-    // FP64 residual of the current iterate and the stopping rule
-    TRY(do_apply<double>(c, u, r64, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit));
-    {
+    if (ref == 0) {
+      // u = 0: the residual is -b; FP32 suffices for the first inner solve because every later
+      // check recomputes the residual of the accumulated iterate in FP64
+      CU(cudaMemsetAsync(d, 0, tot * sizeof(float), s));
+      TRY(do_apply<float>(c, d, q, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit));
+      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+      CU(launch_scale_copy<float, float>(q, f, -1.0, stride, n_rhs, c->act, s));
+    } else {
+      // FP64 residual of the current iterate and the stopping rule
+      TRY(do_apply<double>(c, u, r64, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit));
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
       CU(launch_scale_copy<double, float>(r64, f, -1.0, stride, n_rhs, c->act, s));
     }
-    TRY(do_prec<float>(c, f, z, n_rhs, c->act, 3, tol, 0, c->opt.maxit));
+    TRY(do_prec<float>(c, f, z, n_rhs, c->act, 3, tol, 0, c->opt.maxit, 1));
     TRY(read_states(c, n_rhs));
     int still = 0;
     for (int r = 0; r < n_rhs; ++r) {
@@ -691,9 +721,9 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
       k_copy_act_to_mask<<<1, 64, 0, s>>>(c->act, c->outer_mask, n_rhs);
       CU(cudaGetLastError());
       CU(cudaMemsetAsync(du, 0, tot * sizeof(float), s));
-      CU(launch_scale_copy<float, float>(z, d, 1.0, stride, n_rhs, nullptr, s));
+      CU(cudaMemsetAsync(d, 0, tot * sizeof(float), s));
     }
-    TRY(cg_loop<float>(c, du, f, d, z, q, n_rhs, c->opt.inner_tol, 1, c->opt.maxit));
+    TRY(cg_loop<float>(c, du, f, d, d2, z, q, n_rhs, 0.5, 1, c->opt.maxit));
     TRY(read_states(c, n_rhs));
     for (int r = 0; r < n_rhs; ++r)
       if (hmask[r]) R->iters[r] += c->h_st[r].iters;
@@ -1128,6 +1158,10 @@ extern "C" xfft_status xfft_apply_noalloc(xfft_ctx* c, int n_rhs, const double* 
   a.units_uncut = nullptr;
   a.units_cut = nullptr;
   a.want_sig = 1;
+  a.fz = nullptr;
+  a.fdnew = nullptr;
+  a.fu = nullptr;
+  a.st = nullptr;
   CU(launch_apply<double>(d, q, c->isD, cutdata(c), a, n_rhs, c->stream));
   if (dAd_sig) CU(launch_reduce_partials(scratch, 7 * n_rhs, nparts, nparts, dAd_sig, c->stream));
   return XFFT_OK;

@@ -70,6 +70,35 @@ __global__ void k_add_to_double(double* __restrict__ u, const T* __restrict__ dl
     ur[i] += (double)dr[i];
 }
 
+template <typename T>
+__global__ void k_cg_update_tail(const T* __restrict__ z, const T* __restrict__ dold, T* __restrict__ dnew,
+                                 T* __restrict__ u, const RhsState* __restrict__ st, long long off,
+                                 long long stride) {
+  const int rhs = blockIdx.y;
+  if (!st[rhs].active) return;
+  const T a = (T)st[rhs].alpha, b = (T)st[rhs].beta;
+  const long long base = rhs * stride;
+  for (long long i = off + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < stride;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T d0 = dold[base + i];
+    dnew[base + i] = z[base + i] + b * d0;
+    u[base + i] += a * d0;
+  }
+}
+
+template <typename T>
+__global__ void k_cg_finish(T* __restrict__ u, const T* __restrict__ dA, const T* __restrict__ dB,
+                            const RhsState* __restrict__ st, long long stride) {
+  const int rhs = blockIdx.y;
+  const T a = (T)st[rhs].alpha;
+  if (a == T(0)) return;
+  T* ur = u + rhs * stride;
+  const T* dr = (st[rhs].dpar ? dB : dA) + rhs * stride;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < stride;
+       i += (long long)gridDim.x * blockDim.x)
+    ur[i] += a * dr[i];
+}
+
 static unsigned vec_blocks(long long stride) {
   long long nb = (stride + 255) / 256;
   if (nb > 2048) nb = 2048;
@@ -104,6 +133,29 @@ cudaError_t launch_add_to_double(double* u, const T* dlt, long long stride, int 
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_cg_update_tail(const T* z, const T* dold, T* dnew, T* u, const RhsState* st,
+                                  long long off, long long stride, int n_rhs, cudaStream_t s) {
+  if (stride <= off) return cudaSuccess;
+  k_cg_update_tail<T><<<dim3(vec_blocks(stride - off), n_rhs), 256, 0, s>>>(z, dold, dnew, u, st, off, stride);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_finish(T* u, const T* dA, const T* dB, const RhsState* st, long long stride,
+                             int n_rhs, cudaStream_t s) {
+  k_cg_finish<T><<<dim3(vec_blocks(stride), n_rhs), 256, 0, s>>>(u, dA, dB, st, stride);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_cg_update_tail<float>(const float*, const float*, float*, float*,
+                                                  const RhsState*, long long, long long, int, cudaStream_t);
+template cudaError_t launch_cg_update_tail<double>(const double*, const double*, double*, double*,
+                                                   const RhsState*, long long, long long, int, cudaStream_t);
+template cudaError_t launch_cg_finish<float>(float*, const float*, const float*, const RhsState*,
+                                             long long, int, cudaStream_t);
+template cudaError_t launch_cg_finish<double>(double*, const double*, const double*, const RhsState*,
+                                              long long, int, cudaStream_t);
 template cudaError_t launch_axpy_cg<float>(float*, float*, const float*, const float*,
                                            const RhsState*, long long, int, cudaStream_t);
 template cudaError_t launch_axpy_cg<double>(double*, double*, const double*, const double*,
@@ -128,7 +180,10 @@ template cudaError_t launch_add_to_double<double>(double*, const double*, long l
 // ---------------------------------------------------------------- finalisation
 __device__ inline bool stop_rule(const RhsState& s, const FinArgs& fa) {
   if (!(s.rr > 0.0)) return true;
-  if (fa.crit == 1) return s.rr <= fa.tol * fa.tol * s.rr0;
+  if (fa.crit == 1) {
+    const double rel = s.rel > 0.0 ? s.rel : fa.tol;
+    return s.rr <= rel * rel * s.rr0;
+  }
   double sn = 0.0;
   for (int k = 0; k < 6; ++k) sn += s.sig[k] * s.sig[k];
   return sqrt(s.rr / fa.volY) <= fa.tol * sqrt(sn) / fa.volY;
@@ -157,6 +212,7 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
       s.status = 5;
       s.active = 0;
       s.alpha = 0.0;
+      s.dpar = fa.parity;
     } else {
       s.alpha = a;
       for (int k = 0; k < 6; ++k) s.sig[k] += a * s.sd[k];
@@ -173,11 +229,22 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
       if (stop_rule(s, fa)) {
         s.converged = 1;
         s.active = 0;
+      } else if (fa.set_rel) {
+        // the inner solve should bring sqrt(rr/|Y|) to half the outer target
+        double sn = 0.0;
+        for (int k = 0; k < 6; ++k) sn += s.sig[k] * s.sig[k];
+        const double target = 0.5 * fa.tol * sqrt(sn) / fa.volY;
+        const double res = sqrt(rr / fa.volY);
+        double rel = res > 0.0 ? target / res : 1.0;
+        if (rel < fa.inner_floor) rel = fa.inner_floor;
+        if (rel > 0.5) rel = 0.5;
+        s.rel = rel;
       }
     } else {
       s.beta = s.rr > 0.0 ? rr / s.rr : 0.0;
       s.rr = rr;
       s.iters += 1;
+      s.dpar = fa.parity;
       if (stop_rule(s, fa)) {
         s.converged = 1;
         s.active = 0;
@@ -200,9 +267,10 @@ __global__ void k_init_state(RhsState* st, int* act, int n_rhs, const int* mask)
   const int r = threadIdx.x;
   if (r >= n_rhs) return;
   RhsState s;
-  s.rr = s.rr0 = s.dq = s.alpha = s.beta = 0.0;
+  s.rr = s.rr0 = s.dq = s.alpha = s.beta = s.rel = 0.0;
   for (int k = 0; k < 6; ++k) s.sig[k] = s.sd[k] = 0.0;
   s.active = mask ? mask[r] : 1;
+  s.dpar = 0;
   s.iters = 0;
   s.status = 0;
   s.converged = 0;

@@ -59,13 +59,14 @@ struct FftPlan {
 bool fast_fft_supported(int n);
 int fast_z_pairs(int n2);
 template <typename T>
-cudaError_t fast_z_r2c(int n2, const T* f, void* spec, long long stride, long long sstride, long long rows,
+cudaError_t fast_z_r2c(int n2, T* f, void* spec, long long stride, long long sstride, int n0, int n1,
                        const int* active, const void* tw, unsigned long long* units, int n_rhs,
-                       cudaStream_t s);
+                       cudaStream_t s, const T* q, const RhsState* st);
 template <typename T>
 cudaError_t fast_z_c2r(int n2, const void* spec, const T* f, T* z, long long stride, long long sstride,
-                       long long rows, double scale, const int* active, const void* tw,
+                       int n0, int n1, double scale, const int* active, const void* tw,
                        double* partials, int nparts, int n_rhs, cudaStream_t s);
+int fast_z_blocks(int n0, int n1, int n2);
 template <typename T, bool INV>
 cudaError_t fast_y(int n1, int n0, void* spec, long long sstride, int K2, const int* active,
                    const void* tw, int n_rhs, cudaStream_t s);
@@ -190,11 +191,12 @@ __device__ __forceinline__ void load_tw(C* tws, const C* __restrict__ tw, int n)
 
 // ---------------------------------------------------------------- pass 1: z, real -> complex
 template <typename T>
-__global__ void k_fft_z_r2c(const T* __restrict__ f, typename Cx<T>::type* __restrict__ spec,
+__global__ void k_fft_z_r2c(T* __restrict__ f, typename Cx<T>::type* __restrict__ spec,
                             long long stride, long long sstride, AxisPlan ap, int K2, long long rows,
                             int pairs_per_block, const int* __restrict__ active,
                             const typename Cx<T>::type* __restrict__ tw,
-                            unsigned long long* __restrict__ units) {
+                            unsigned long long* __restrict__ units, const T* __restrict__ q,
+                            const RhsState* __restrict__ st) {
   typedef typename Cx<T>::type C;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int rhs = blockIdx.y;
@@ -207,10 +209,20 @@ __global__ void k_fft_z_r2c(const T* __restrict__ f, typename Cx<T>::type* __res
   load_tw(tws, tw, n);
   const long long row0 = 2LL * blockIdx.x * pairs_per_block;
   const int nrows = (int)min((long long)2 * pairs_per_block, rows - row0);
-  const T* fr = f + rhs * stride + row0 * n;
+  T* fr = f + rhs * stride + row0 * n;
+  const T* qr = q ? q + rhs * stride + row0 * n : nullptr;
+  const T alpha = q ? (T)st[rhs].alpha : T(0);
   for (int idx = threadIdx.x; idx < 2 * pairs_per_block * n; idx += blockDim.x) {
     const int rl = idx / n, k = idx - rl * n;
-    const T v = rl < nrows ? fr[(long long)rl * n + k] : T(0);
+    T v = T(0);
+    if (rl < nrows) {
+      const long long o = (long long)rl * n + k;
+      v = fr[o];
+      if (q) {
+        v -= alpha * qr[o];  // fused CG update f -= alpha A d
+        fr[o] = v;
+      }
+    }
     T* dst = reinterpret_cast<T*>(&b0[(rl >> 1) * n + k]);
     dst[rl & 1] = v;
   }
@@ -492,18 +504,25 @@ __global__ void k_fft_z_c2r(const typename Cx<T>::type* __restrict__ spec, const
 
 // ---------------------------------------------------------------- enriched block: identity
 template <typename T>
-__global__ void k_enr_identity(const T* __restrict__ f, T* __restrict__ z, long long stride,
+__global__ void k_enr_identity(T* __restrict__ f, T* __restrict__ z, long long stride,
                                long long off, long long count, const int* __restrict__ active,
-                               double* __restrict__ partials, int nparts, int slot0) {
+                               double* __restrict__ partials, int nparts, int slot0,
+                               const T* __restrict__ q, const RhsState* __restrict__ st) {
   __shared__ double red[32];
   const int rhs = blockIdx.y;
   if (active && !active[rhs]) return;
-  const T* fr = f + rhs * stride + off;
+  T* fr = f + rhs * stride + off;
   T* zr = z + rhs * stride + off;
+  const T* qr = q ? q + rhs * stride + off : nullptr;
+  const T alpha = q ? (T)st[rhs].alpha : T(0);
   T acc = T(0);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {
-    const T v = fr[i];
+    T v = fr[i];
+    if (q) {
+      v -= alpha * qr[i];  // fused CG update f -= alpha A d
+      fr[i] = v;
+    }
     zr[i] = v;
     acc += v * v;
   }
@@ -672,9 +691,9 @@ void fft_plan_destroy(FftPlan* p) {
 size_t fft_spectrum_elems(const FftPlan* p) { return 3ULL * p->n[0] * p->n[1] * p->K2; }
 
 static int zpass_blocks(const FftPlan* p) {
+  if (p->fast) return fast_z_blocks(p->n[0], p->n[1], p->n[2]);
   const long long rows = 3LL * p->n[0] * p->n[1];
-  const long long pairs = p->fast ? fast_z_pairs(p->n[2]) : p->xpairs;
-  return (int)((rows + 2LL * pairs - 1) / (2LL * pairs));
+  return (int)((rows + 2LL * p->xpairs - 1) / (2LL * p->xpairs));
 }
 
 static int enr_blocks(int nX) {
@@ -688,9 +707,10 @@ static int enr_blocks(int nX) {
 int precondition_blocks(const FftPlan* p, int nX) { return zpass_blocks(p) + enr_blocks(nX); }
 
 template <typename T>
-cudaError_t launch_precondition(const FftPlan* p, const T* f, T* z, void* spec_v, long long stride,
+cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long long stride,
                                 int nX, const int* active, double* partials, int nparts,
-                                int n_rhs, cudaStream_t s, unsigned long long* units) {
+                                int n_rhs, cudaStream_t s, unsigned long long* units, const T* q,
+                                const RhsState* st) {
   typedef typename Cx<T>::type C;
   const bool dbl = sizeof(T) == 8;
   const int a2 = 2;  // z axis
@@ -710,22 +730,23 @@ cudaError_t launch_precondition(const FftPlan* p, const T* f, T* z, void* spec_v
       gs[a] = dbl ? (const void*)p->gsd[a] : (const void*)p->gsf[a];
     }
     const double ih[3] = {1.0 / p->g.h[0], 1.0 / p->g.h[1], 1.0 / p->g.h[2]};
-    cudaError_t e = fast_z_r2c<T>(p->n[2], f, spec, stride, sstride, rows, active, tw2, units, n_rhs, s);
+    cudaError_t e = fast_z_r2c<T>(p->n[2], f, spec, stride, sstride, p->n[0], p->n[1], active, tw2, units,
+                                  n_rhs, s, q, st);
     if (e == cudaSuccess) e = fast_y<T, false>(p->n[1], p->n[0], spec, sstride, p->K2, active, tw1, n_rhs, s);
     if (e == cudaSuccess)
       e = fast_x_green<T>(p->n[0], p->n[1], spec, sstride, p->K2, active, tw0, ge, gs, ih, 0.5 * p->g.vol_tet,
                           n_rhs, s);
     if (e == cudaSuccess) e = fast_y<T, true>(p->n[1], p->n[0], spec, sstride, p->K2, active, tw1, n_rhs, s);
     if (e == cudaSuccess)
-      e = fast_z_c2r<T>(p->n[2], spec, f, z, stride, sstride, rows,
+      e = fast_z_c2r<T>(p->n[2], spec, f, z, stride, sstride, p->n[0], p->n[1],
                         1.0 / ((double)p->n[0] * p->n[1] * p->n[2]), active, tw2, partials, nparts, n_rhs, s);
     if (e != cudaSuccess) return e;
     k_enr_identity<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, 3LL * nX,
-                                                                  active, partials, nparts, zb);
+                                                                  active, partials, nparts, zb, q, st);
     return cudaGetLastError();
   }
   k_fft_z_r2c<T><<<dim3(zb, n_rhs), kFftThreads, smem_z(p, cs), s>>>(
-      f, spec, stride, sstride, p->ax[2], p->K2, rows, p->xpairs, active, tw2, units);
+      f, spec, stride, sstride, p->ax[2], p->K2, rows, p->xpairs, active, tw2, units, q, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ytk = dbl ? p->ytk_d : p->ytk_f;
@@ -761,15 +782,15 @@ cudaError_t launch_precondition(const FftPlan* p, const T* f, T* z, void* spec_v
   if (e != cudaSuccess) return e;
   const long long N = g.N;
   k_enr_identity<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * N, 3LL * nX,
-                                                                active, partials, nparts, zb);
+                                                                active, partials, nparts, zb, q, st);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_precondition<float>(const FftPlan*, const float*, float*, void*,
-                                                long long, int, const int*, double*, int, int,
-                                                cudaStream_t, unsigned long long*);
-template cudaError_t launch_precondition<double>(const FftPlan*, const double*, double*, void*,
-                                                 long long, int, const int*, double*, int, int,
-                                                 cudaStream_t, unsigned long long*);
+template cudaError_t launch_precondition<float>(const FftPlan*, float*, float*, void*, long long, int,
+                                                const int*, double*, int, int, cudaStream_t,
+                                                unsigned long long*, const float*, const RhsState*);
+template cudaError_t launch_precondition<double>(const FftPlan*, double*, double*, void*, long long, int,
+                                                 const int*, double*, int, int, cudaStream_t,
+                                                 unsigned long long*, const double*, const RhsState*);
 
 }  // namespace xfft

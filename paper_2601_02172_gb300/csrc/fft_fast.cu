@@ -28,13 +28,15 @@ __device__ __forceinline__ void load_table(C* dst, const C* __restrict__ src, in
 }
 
 // ---------------------------------------------------------------- z axis, real -> complex
-// block: LPB row pairs, TL = N/E threads per pair
+// Spectrum layout of the fast path: [c][k2][j][i] (x fastest), so that x lines are contiguous.
+// Block: component c, row j, rows i0 .. i0 + 2 LPB - 1 (LPB row pairs, TL = N/E threads each).
 template <typename T, int N>
-__global__ void __launch_bounds__(256) kz_r2c(const T* __restrict__ f, typename Cplx<T>::type* __restrict__ spec,
-                                              long long stride, long long sstride, long long rows,
-                                              const int* __restrict__ active,
+__global__ void __launch_bounds__(256) kz_r2c(T* __restrict__ f, typename Cplx<T>::type* __restrict__ spec,
+                                              long long stride, long long sstride, int n0, int n1,
+                                              int itiles, const int* __restrict__ active,
                                               const typename Cplx<T>::type* __restrict__ tw,
-                                              unsigned long long* __restrict__ units) {
+                                              unsigned long long* __restrict__ units,
+                                              const T* __restrict__ q, const RhsState* __restrict__ st) {
   typedef typename Cplx<T>::type C;
   constexpr int TL = N / Plan<N>::E;
   constexpr int LPB = 256 / TL;
@@ -47,39 +49,56 @@ __global__ void __launch_bounds__(256) kz_r2c(const T* __restrict__ f, typename 
   C* tws = reinterpret_cast<C*>(smraw);
   C* buf = tws + N;
   load_table(tws, tw, N);
-  const long long row0 = 2LL * blockIdx.x * LPB;
-  const int nrows = (int)min((long long)2 * LPB, rows - row0);
-  const T* fr = f + rhs * stride + row0 * N;
+  const int it = blockIdx.x % itiles;
+  const int cj = blockIdx.x / itiles;  // c * n1 + j
+  const int c = cj / n1, j = cj - c * n1;
+  const int i0 = it * 2 * LPB;
+  const int nrows = min(2 * LPB, n0 - i0);
+  const long long N3 = (long long)n0 * n1 * N;
+  T* fr = f + rhs * stride + c * N3;
+  const T* qr = q ? q + rhs * stride + c * N3 : nullptr;
+  const T alpha = q ? (T)st[rhs].alpha : T(0);
   for (int idx = threadIdx.x; idx < 2 * LPB * N; idx += blockDim.x) {
     const int rl = idx / N, k = idx - rl * N;
-    const T v = rl < nrows ? fr[(long long)rl * N + k] : T(0);
+    T v = T(0);
+    if (rl < nrows) {
+      const long long o = ((long long)(i0 + rl) * n1 + j) * N + k;
+      v = fr[o];
+      if (q) {
+        v -= alpha * qr[o];  // fused CG update f -= alpha A d
+        fr[o] = v;
+      }
+    }
     T* dst = reinterpret_cast<T*>(&buf[(rl >> 1) * LS + k]);
     dst[rl & 1] = v;
   }
   __syncthreads();
   const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
   line_fft<C, N, false>(buf + line * LS, tws, t);
-  C* sp = spec + rhs * sstride + row0 * K2;
-  for (int idx = threadIdx.x; idx < LPB * K2; idx += blockDim.x) {
-    const int p = idx / K2, k = idx - p * K2;
-    if (2 * p >= nrows) continue;
+  C* sp = spec + rhs * sstride + (long long)c * K2 * n1 * n0 + (long long)j * n0 + i0;
+  for (int idx = threadIdx.x; idx < 2 * LPB * K2; idx += blockDim.x) {
+    const int k = idx / (2 * LPB), rl = idx - k * (2 * LPB);
+    if (rl >= nrows) continue;
+    const int p = rl >> 1;
     const C zk = buf[p * LS + k];
     const C zn = buf[p * LS + (k == 0 ? 0 : N - k)];
-    C X, Y;
-    X.x = T(0.5) * (zk.x + zn.x);
-    X.y = T(0.5) * (zk.y - zn.y);
-    Y.x = T(0.5) * (zk.y + zn.y);
-    Y.y = T(-0.5) * (zk.x - zn.x);
-    sp[(long long)(2 * p) * K2 + k] = X;
-    if (2 * p + 1 < nrows) sp[(long long)(2 * p + 1) * K2 + k] = Y;
+    C out;
+    if ((rl & 1) == 0) {  // X = (Z_k + conj Z_{N-k}) / 2
+      out.x = T(0.5) * (zk.x + zn.x);
+      out.y = T(0.5) * (zk.y - zn.y);
+    } else {  // Y = (Z_k - conj Z_{N-k}) / (2i)
+      out.x = T(0.5) * (zk.y + zn.y);
+      out.y = T(-0.5) * (zk.x - zn.x);
+    }
+    sp[(long long)k * n1 * n0 + rl] = out;
   }
 }
 
 // ---------------------------------------------------------------- y axis (complex)
-// block: TK lines (consecutive k2 of one (c, i) slab), TL threads per line
+// block: (c, k2) slab, ti consecutive i columns; each column is a line along j of length N = n1
 template <typename T, int N, bool INV>
 __global__ void __launch_bounds__(256) ky(typename Cplx<T>::type* __restrict__ spec, long long sstride,
-                                          int K2, int tk, int ntiles, const int* __restrict__ active,
+                                          int n0, int ti, int ntiles, const int* __restrict__ active,
                                           const typename Cplx<T>::type* __restrict__ tw) {
   typedef typename Cplx<T>::type C;
   constexpr int TL = N / Plan<N>::E;
@@ -90,32 +109,40 @@ __global__ void __launch_bounds__(256) ky(typename Cplx<T>::type* __restrict__ s
   C* tws = reinterpret_cast<C*>(smraw);
   C* buf = tws + N;
   load_table(tws, tw, N);
-  const long long slab = blockIdx.x / ntiles;
+  const long long slab = blockIdx.x / ntiles;  // c * K2 + k2
   const int tile = blockIdx.x - (int)slab * ntiles;
-  const int k0 = tile * tk;
-  const int tke = min(tk, K2 - k0);
-  C* sp = spec + rhs * sstride + slab * N * K2 + k0;
-  for (int idx = threadIdx.x; idx < N * tk; idx += blockDim.x) {
-    const int j = idx / tk, kk = idx - j * tk;
+  const int ii0 = tile * ti;
+  const int tie = min(ti, n0 - ii0);
+  C* sp = spec + rhs * sstride + slab * N * n0 + ii0;
+  for (int idx = threadIdx.x; idx < N * ti; idx += blockDim.x) {
+    const int j = idx / ti, kk = idx - j * ti;
     C v;
     v.x = T(0);
     v.y = T(0);
-    if (kk < tke) v = sp[(long long)j * K2 + kk];
+    if (kk < tie) v = sp[(long long)j * n0 + kk];
     buf[kk * LS + j] = v;
   }
   __syncthreads();
   const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
   line_fft<C, N, INV>(buf + line * LS, tws, t);
-  for (int idx = threadIdx.x; idx < N * tk; idx += blockDim.x) {
-    const int j = idx / tk, kk = idx - j * tk;
-    if (kk < tke) sp[(long long)j * K2 + kk] = buf[kk * LS + j];
+  for (int idx = threadIdx.x; idx < N * ti; idx += blockDim.x) {
+    const int j = idx / ti, kk = idx - j * ti;
+    if (kk < tie) sp[(long long)j * n0 + kk] = buf[kk * LS + j];
   }
 }
 
 // ---------------------------------------------------------------- x axis + Green + inverse
+// Cholesky factor of M(xi) = (|T|/2) sum_tets (|G|^2 I + G G^H) (see fft.cu); returns false
+// at xi = 0 or on a non-positive pivot (the Green operator then maps to 0).
 template <typename C, typename T>
-__device__ __forceinline__ void green3(C& F0, C& F1, C& F2, C e0, C e1, C e2, C s0, C s1, C s2, T ih0,
-                                       T ih1, T ih2, T halfvol) {
+struct GreenFactor {
+  T il00, il11, il22;
+  C l10, l20, l21;
+};
+
+template <typename C, typename T>
+__device__ __forceinline__ bool green_factor(GreenFactor<C, T>& gf, C e0, C e1, C e2, C s0, C s1, C s2,
+                                             T ih0, T ih1, T ih2, T halfvol) {
   C g[3];
   g[0].x = s0.x * ih0;
   g[0].y = s0.y * ih0;
@@ -127,15 +154,10 @@ __device__ __forceinline__ void green3(C& F0, C& F1, C& F2, C e0, C e1, C e2, C 
   const T a1 = g[1].x * g[1].x + g[1].y * g[1].y;
   const T a2 = g[2].x * g[2].x + g[2].y * g[2].y;
   const T S = a0 + a1 + a2;
-  C zero;
-  zero.x = T(0);
-  zero.y = T(0);
-  if (!(S > T(0))) {
-    F0 = F1 = F2 = zero;
-    return;
-  }
+  if (!(S > T(0))) return false;
   const C e[3] = {e0, e1, e2};
-  C m01 = zero, m02 = zero, m12 = zero;
+  C m01, m02, m12;
+  m01.x = m01.y = m02.x = m02.y = m12.x = m12.y = T(0);
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
     const int p = perm_p(t), q = perm_q(t), r = perm_r(t);
@@ -156,113 +178,120 @@ __device__ __forceinline__ void green3(C& F0, C& F1, C& F2, C e0, C e1, C e2, C 
   m02.y *= halfvol;
   m12.x *= halfvol;
   m12.y *= halfvol;
-  // Cholesky M = L L^H with M(1,0) = conj(m01), M(2,0) = conj(m02), M(2,1) = conj(m12)
-  const T il00 = T(1) / sqrt(d0);
-  C l10, l20, l21;
-  l10.x = m01.x * il00;
-  l10.y = -m01.y * il00;
-  l20.x = m02.x * il00;
-  l20.y = -m02.y * il00;
-  const T l11sq = d1 - (l10.x * l10.x + l10.y * l10.y);
-  if (!(l11sq > T(0))) {
-    F0 = F1 = F2 = zero;
-    return;
-  }
-  const T il11 = T(1) / sqrt(l11sq);
+  // M = L L^H with M(1,0) = conj(m01), M(2,0) = conj(m02), M(2,1) = conj(m12)
+  gf.il00 = T(1) / sqrt(d0);
+  gf.l10.x = m01.x * gf.il00;
+  gf.l10.y = -m01.y * gf.il00;
+  gf.l20.x = m02.x * gf.il00;
+  gf.l20.y = -m02.y * gf.il00;
+  const T l11sq = d1 - (gf.l10.x * gf.l10.x + gf.l10.y * gf.l10.y);
+  if (!(l11sq > T(0))) return false;
+  gf.il11 = T(1) / sqrt(l11sq);
   C m21;
   m21.x = m12.x;
   m21.y = -m12.y;
-  const C t21 = csub(m21, cmulc(l20, l10));
-  l21.x = t21.x * il11;
-  l21.y = t21.y * il11;
-  const T l22sq = d2 - (l20.x * l20.x + l20.y * l20.y) - (l21.x * l21.x + l21.y * l21.y);
-  if (!(l22sq > T(0))) {
-    F0 = F1 = F2 = zero;
-    return;
-  }
-  const T il22 = T(1) / sqrt(l22sq);
+  const C t21 = csub(m21, cmulc(gf.l20, gf.l10));
+  gf.l21.x = t21.x * gf.il11;
+  gf.l21.y = t21.y * gf.il11;
+  const T l22sq = d2 - (gf.l20.x * gf.l20.x + gf.l20.y * gf.l20.y) - (gf.l21.x * gf.l21.x + gf.l21.y * gf.l21.y);
+  if (!(l22sq > T(0))) return false;
+  gf.il22 = T(1) / sqrt(l22sq);
+  return true;
+}
+
+template <typename C, typename T>
+__device__ __forceinline__ void green_solve(const GreenFactor<C, T>& gf, C& F0, C& F1, C& F2) {
   C y0, y1, y2, t;
-  y0.x = F0.x * il00;
-  y0.y = F0.y * il00;
-  t = csub(F1, cmul(l10, y0));
-  y1.x = t.x * il11;
-  y1.y = t.y * il11;
-  t = csub(csub(F2, cmul(l20, y0)), cmul(l21, y1));
-  y2.x = t.x * il22;
-  y2.y = t.y * il22;
+  y0.x = F0.x * gf.il00;
+  y0.y = F0.y * gf.il00;
+  t = csub(F1, cmul(gf.l10, y0));
+  y1.x = t.x * gf.il11;
+  y1.y = t.y * gf.il11;
+  t = csub(csub(F2, cmul(gf.l20, y0)), cmul(gf.l21, y1));
+  y2.x = t.x * gf.il22;
+  y2.y = t.y * gf.il22;
   C x0, x1, x2;
-  x2.x = y2.x * il22;
-  x2.y = y2.y * il22;
-  t = csub(y1, cmulc(x2, l21));
-  x1.x = t.x * il11;
-  x1.y = t.y * il11;
-  t = csub(csub(y0, cmulc(x1, l10)), cmulc(x2, l20));
-  x0.x = t.x * il00;
-  x0.y = t.y * il00;
+  x2.x = y2.x * gf.il22;
+  x2.y = y2.y * gf.il22;
+  t = csub(y1, cmulc(x2, gf.l21));
+  x1.x = t.x * gf.il11;
+  x1.y = t.y * gf.il11;
+  t = csub(csub(y0, cmulc(x1, gf.l10)), cmulc(x2, gf.l20));
+  x0.x = t.x * gf.il00;
+  x0.y = t.y * gf.il00;
   F0 = x0;
   F1 = x1;
   F2 = x2;
 }
 
-// block: j, a k2 tile of width tk, all three components: 3 tk lines of length N = n0
+// block: (k2, j), all three components of a group of rg right-hand sides: 3 rg contiguous lines
+// of length N = n0.  The symbol of each frequency is factorised once and applied to every
+// right-hand side of the group.
 template <typename T, int N>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) kx_green(typename Cplx<T>::type* __restrict__ spec, long long sstride,
-                                                 int n1, int K2, int tk, int ntiles,
-                                                 const int* __restrict__ active,
-                                                 const typename Cplx<T>::type* __restrict__ tw,
-                                                 const typename Cplx<T>::type* __restrict__ ge0,
-                                                 const typename Cplx<T>::type* __restrict__ ge1,
-                                                 const typename Cplx<T>::type* __restrict__ ge2,
-                                                 const typename Cplx<T>::type* __restrict__ gs0,
-                                                 const typename Cplx<T>::type* __restrict__ gs1,
-                                                 const typename Cplx<T>::type* __restrict__ gs2, T ih0,
-                                                 T ih1, T ih2, T halfvol) {
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768)
+    kx_green(typename Cplx<T>::type* __restrict__ spec, long long sstride, int n1, int K2, int rg,
+             int n_rhs, const int* __restrict__ active, const typename Cplx<T>::type* __restrict__ tw,
+             const typename Cplx<T>::type* __restrict__ ge0, const typename Cplx<T>::type* __restrict__ ge1,
+             const typename Cplx<T>::type* __restrict__ ge2, const typename Cplx<T>::type* __restrict__ gs0,
+             const typename Cplx<T>::type* __restrict__ gs1, const typename Cplx<T>::type* __restrict__ gs2,
+             T ih0, T ih1, T ih2, T halfvol) {
   typedef typename Cplx<T>::type C;
   constexpr int TL = N / Plan<N>::E;
   constexpr int LS = N + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int rhs = blockIdx.y;
-  if (active && !active[rhs]) return;
+  __shared__ int live[64];
+  const int r0 = blockIdx.y * rg;
+  const int nr = min(rg, n_rhs - r0);
+  int any = 0;
+  for (int r = 0; r < nr; ++r) any |= (!active || active[r0 + r]) ? 1 : 0;
+  if (!any) return;  // uniform per block
+  if (threadIdx.x < nr) live[threadIdx.x] = (!active || active[r0 + threadIdx.x]) ? 1 : 0;
   C* tws = reinterpret_cast<C*>(smraw);
   C* buf = tws + N;
   load_table(tws, tw, N);
-  const int j = blockIdx.x / ntiles;
-  const int tile = blockIdx.x - j * ntiles;
-  const int k0 = tile * tk;
-  const int tke = min(tk, K2 - k0);
-  C* sp = spec + rhs * sstride;
-  const long long cstride = (long long)N * n1 * K2;
-  const long long istride = (long long)n1 * K2;
-  for (int idx = threadIdx.x; idx < 3 * N * tk; idx += blockDim.x) {
-    const int ci = idx / tk, kk = idx - ci * tk;
-    const int c = ci / N, i = ci - c * N;
+  const int k2 = blockIdx.x / n1;
+  const int j = blockIdx.x - k2 * n1;
+  const long long cstride = (long long)K2 * n1 * N;
+  const long long off = ((long long)k2 * n1 + j) * N;
+  const int lines = 3 * rg;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < lines * N; idx += blockDim.x) {
+    const int li = idx / N, i = idx - li * N;
+    const int r = li / 3, c = li - 3 * r;
     C v;
     v.x = T(0);
     v.y = T(0);
-    if (kk < tke) v = sp[c * cstride + i * istride + (long long)j * K2 + k0 + kk];
-    buf[(c * tk + kk) * LS + i] = v;
+    if (r < nr && live[r]) v = spec[(r0 + r) * sstride + c * cstride + off + i];
+    buf[li * LS + i] = v;
   }
   __syncthreads();
   const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
   line_fft<C, N, false>(buf + line * LS, tws, t);
-  const C e1 = ge1[j], s1 = gs1[j];
-  for (int idx = threadIdx.x; idx < N * tk; idx += blockDim.x) {
-    const int kk = idx / N, i = idx - kk * N;
-    if (kk >= tke) continue;
-    C F0 = buf[(0 * tk + kk) * LS + i];
-    C F1 = buf[(1 * tk + kk) * LS + i];
-    C F2 = buf[(2 * tk + kk) * LS + i];
-    green3<C, T>(F0, F1, F2, ge0[i], e1, ge2[k0 + kk], gs0[i], s1, gs2[k0 + kk], ih0, ih1, ih2, halfvol);
-    buf[(0 * tk + kk) * LS + i] = F0;
-    buf[(1 * tk + kk) * LS + i] = F1;
-    buf[(2 * tk + kk) * LS + i] = F2;
+  const C e1 = ge1[j], s1 = gs1[j], e2 = ge2[k2], s2 = gs2[k2];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    GreenFactor<C, T> gf;
+    const bool ok = green_factor<C, T>(gf, ge0[i], e1, e2, gs0[i], s1, s2, ih0, ih1, ih2, halfvol);
+    for (int r = 0; r < nr; ++r) {
+      C* b0 = buf + (3 * r + 0) * LS + i;
+      C* b1 = buf + (3 * r + 1) * LS + i;
+      C* b2 = buf + (3 * r + 2) * LS + i;
+      C F0 = *b0, F1 = *b1, F2 = *b2;
+      if (ok) {
+        green_solve<C, T>(gf, F0, F1, F2);
+      } else {
+        F0.x = F0.y = F1.x = F1.y = F2.x = F2.y = T(0);
+      }
+      *b0 = F0;
+      *b1 = F1;
+      *b2 = F2;
+    }
   }
   __syncthreads();
   line_fft<C, N, true>(buf + line * LS, tws, t);
-  for (int idx = threadIdx.x; idx < 3 * N * tk; idx += blockDim.x) {
-    const int ci = idx / tk, kk = idx - ci * tk;
-    const int c = ci / N, i = ci - c * N;
-    if (kk < tke) sp[c * cstride + i * istride + (long long)j * K2 + k0 + kk] = buf[(c * tk + kk) * LS + i];
+  for (int idx = threadIdx.x; idx < lines * N; idx += blockDim.x) {
+    const int li = idx / N, i = idx - li * N;
+    const int r = li / 3, c = li - 3 * r;
+    if (r < nr && live[r]) spec[(r0 + r) * sstride + c * cstride + off + i] = buf[li * LS + i];
   }
 }
 
@@ -270,7 +299,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) kx_green(typename 
 template <typename T, int N>
 __global__ void __launch_bounds__(256) kz_c2r(const typename Cplx<T>::type* __restrict__ spec,
                                               const T* __restrict__ f, T* __restrict__ z, long long stride,
-                                              long long sstride, long long rows, T scale,
+                                              long long sstride, int n0, int n1, int itiles, T scale,
                                               const int* __restrict__ active,
                                               const typename Cplx<T>::type* __restrict__ tw,
                                               double* __restrict__ partials, int nparts) {
@@ -287,42 +316,71 @@ __global__ void __launch_bounds__(256) kz_c2r(const typename Cplx<T>::type* __re
   C* tws = reinterpret_cast<C*>(smraw);
   C* buf = tws + N;
   load_table(tws, tw, N);
-  const long long row0 = 2LL * blockIdx.x * LPB;
-  const int nrows = (int)min((long long)2 * LPB, rows - row0);
-  const C* sp = spec + rhs * sstride + row0 * K2;
-  for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x) {
-    const int p = idx / N, k = idx - p * N;
-    C X, Y;
-    X.x = X.y = Y.x = Y.y = T(0);
-    if (2 * p < nrows) {
+  const int it = blockIdx.x % itiles;
+  const int cj = blockIdx.x / itiles;
+  const int c = cj / n1, j = cj - c * n1;
+  const int i0 = it * 2 * LPB;
+  const int nrows = min(2 * LPB, n0 - i0);
+  const C* sp = spec + rhs * sstride + (long long)c * K2 * n1 * n0 + (long long)j * n0 + i0;
+  // gather the half spectra of the row pairs: X (row 2p), Y (row 2p+1) at k2 = kk
+  for (int idx = threadIdx.x; idx < 2 * LPB * K2; idx += blockDim.x) {
+    const int kk = idx / (2 * LPB), rl = idx - kk * (2 * LPB);
+    C v;
+    v.x = v.y = T(0);
+    if (rl < nrows) v = sp[(long long)kk * n1 * n0 + rl];
+    if (kk == 0 || kk == half) v.y = T(0);
+    // stash X in .x/.y of slot (p, kk) and Y in slot (p, N - kk) (kk < half) temporarily:
+    // write to a scratch view of the same buffer after a barrier instead (two phases below)
+    T* tmp = reinterpret_cast<T*>(buf);
+    tmp[(rl * K2 + kk) * 2 + 0] = v.x;
+    tmp[(rl * K2 + kk) * 2 + 1] = v.y;
+  }
+  __syncthreads();
+  // build Z_k = X_k + i Y_k for k < N from the staged half spectra (in registers, then store)
+  C zv[Plan<N>::E];  // LPB * N / 256 = E values per thread
+  {
+    const T* tmp = reinterpret_cast<const T*>(buf);
+    int q = 0;
+    for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x, ++q) {
+      const int p = idx / N, k = idx - p * N;
       const int kk = k <= half ? k : N - k;
-      X = sp[(long long)(2 * p) * K2 + kk];
-      if (2 * p + 1 < nrows) Y = sp[(long long)(2 * p + 1) * K2 + kk];
-      if (k == 0 || k == half) {
-        X.y = T(0);
-        Y.y = T(0);
-      } else if (k > half) {
+      C X, Y;
+      X.x = tmp[((2 * p) * K2 + kk) * 2 + 0];
+      X.y = tmp[((2 * p) * K2 + kk) * 2 + 1];
+      Y.x = tmp[((2 * p + 1) * K2 + kk) * 2 + 0];
+      Y.y = tmp[((2 * p + 1) * K2 + kk) * 2 + 1];
+      if (k > half) {
         X.y = -X.y;
         Y.y = -Y.y;
       }
+      C Zc;
+      Zc.x = X.x - Y.y;
+      Zc.y = X.y + Y.x;
+      zv[q] = Zc;
     }
-    C Zc;
-    Zc.x = X.x - Y.y;
-    Zc.y = X.y + Y.x;
-    buf[p * LS + k] = Zc;
+  }
+  __syncthreads();
+  {
+    int q = 0;
+    for (int idx = threadIdx.x; idx < LPB * N; idx += blockDim.x, ++q) {
+      const int p = idx / N, k = idx - p * N;
+      buf[p * LS + k] = zv[q];
+    }
   }
   __syncthreads();
   const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
   line_fft<C, N, true>(buf + line * LS, tws, t);
-  const T* fr = f + rhs * stride + row0 * N;
-  T* zr = z + rhs * stride + row0 * N;
+  const long long N3 = (long long)n0 * n1 * N;
+  const T* fr = f + rhs * stride + c * N3;
+  T* zr = z + rhs * stride + c * N3;
   T tacc = T(0);
   for (int idx = threadIdx.x; idx < nrows * N; idx += blockDim.x) {
     const int rl = idx / N, k = idx - rl * N;
     const C v = buf[(rl >> 1) * LS + k];
     const T val = ((rl & 1) ? v.y : v.x) * scale;
-    zr[(long long)rl * N + k] = val;
-    tacc += val * fr[(long long)rl * N + k];
+    const long long o = ((long long)(i0 + rl) * n1 + j) * N + k;
+    zr[o] = val;
+    tacc += val * fr[o];
   }
   double vv[1] = {(double)tacc}, tot[1];
   block_sum<1>(vv, red, tot);
@@ -369,9 +427,9 @@ static cudaError_t set_smem(const void* fn, size_t bytes) {
 }
 
 template <typename T>
-cudaError_t fast_z_r2c(int n2, const T* f, void* spec, long long stride, long long sstride, long long rows,
+cudaError_t fast_z_r2c(int n2, T* f, void* spec, long long stride, long long sstride, int n0, int n1,
                        const int* active, const void* tw, unsigned long long* units, int n_rhs,
-                       cudaStream_t s) {
+                       cudaStream_t s, const T* q, const RhsState* st) {
   typedef typename Cplx<T>::type C;
   switch (n2) {
 #define X(n)                                                                                  \
@@ -380,9 +438,9 @@ cudaError_t fast_z_r2c(int n2, const T* f, void* spec, long long stride, long lo
     const size_t sm = sizeof(C) * (n + (size_t)LPB * (n + 1));                                 \
     cudaError_t e = set_smem<T>((const void*)fast::kz_r2c<T, n>, sm);                          \
     if (e != cudaSuccess) return e;                                                           \
-    const long long nb = (rows + 2 * LPB - 1) / (2 * LPB);                                     \
-    fast::kz_r2c<T, n><<<dim3((unsigned)nb, n_rhs), 256, sm, s>>>(                             \
-        f, (C*)spec, stride, sstride, rows, active, (const C*)tw, units);                      \
+    const int itiles = (n0 + 2 * LPB - 1) / (2 * LPB);                                         \
+    fast::kz_r2c<T, n><<<dim3(3 * n1 * itiles, n_rhs), 256, sm, s>>>(                          \
+        f, (C*)spec, stride, sstride, n0, n1, itiles, active, (const C*)tw, units, q, st);      \
     return cudaGetLastError();                                                                \
   }
     XFFT_FAST_SIZES(X)
@@ -392,22 +450,37 @@ cudaError_t fast_z_r2c(int n2, const T* f, void* spec, long long stride, long lo
   }
 }
 
+// number of blocks of one z pass (and partial-sum slots of the complex-to-real pass)
+int fast_z_blocks(int n0, int n1, int n2) {
+  switch (n2) {
+#define X(n)                                                          \
+  case n: {                                                           \
+    constexpr int LPB = 256 / (n / fast::Plan<n>::E);                  \
+    return 3 * n1 * ((n0 + 2 * LPB - 1) / (2 * LPB));                  \
+  }
+    XFFT_FAST_SIZES(X)
+#undef X
+    default:
+      return 0;
+  }
+}
+
 template <typename T>
 cudaError_t fast_z_c2r(int n2, const void* spec, const T* f, T* z, long long stride, long long sstride,
-                       long long rows, double scale, const int* active, const void* tw,
-                       double* partials, int nparts, int n_rhs, cudaStream_t s) {
+                       int n0, int n1, double scale, const int* active, const void* tw, double* partials,
+                       int nparts, int n_rhs, cudaStream_t s) {
   typedef typename Cplx<T>::type C;
   switch (n2) {
 #define X(n)                                                                                  \
   case n: {                                                                                   \
     constexpr int LPB = 256 / (n / fast::Plan<n>::E);                                          \
-    const size_t sm = sizeof(C) * (n + (size_t)LPB * (n + 1));                                 \
+    const size_t sm = sizeof(C) * (n + (size_t)LPB * (n + 2));                                 \
     cudaError_t e = set_smem<T>((const void*)fast::kz_c2r<T, n>, sm);                          \
     if (e != cudaSuccess) return e;                                                           \
-    const long long nb = (rows + 2 * LPB - 1) / (2 * LPB);                                     \
-    fast::kz_c2r<T, n><<<dim3((unsigned)nb, n_rhs), 256, sm, s>>>(                             \
-        (const C*)spec, f, z, stride, sstride, rows, (T)scale, active, (const C*)tw, partials,  \
-        nparts);                                                                              \
+    const int itiles = (n0 + 2 * LPB - 1) / (2 * LPB);                                         \
+    fast::kz_c2r<T, n><<<dim3(3 * n1 * itiles, n_rhs), 256, sm, s>>>(                          \
+        (const C*)spec, f, z, stride, sstride, n0, n1, itiles, (T)scale, active, (const C*)tw,  \
+        partials, nparts);                                                                    \
     return cudaGetLastError();                                                                \
   }
     XFFT_FAST_SIZES(X)
@@ -425,14 +498,14 @@ cudaError_t fast_y(int n1, int n0, void* spec, long long sstride, int K2, const 
 #define X(n)                                                                                  \
   case n: {                                                                                   \
     constexpr int TL = n / fast::Plan<n>::E;                                                   \
-    constexpr int TKMAX = 256 / TL;                                                            \
-    const int ntiles = (K2 + TKMAX - 1) / TKMAX;                                               \
-    const int tk = (K2 + ntiles - 1) / ntiles;                                                 \
-    const size_t sm = sizeof(C) * (n + (size_t)tk * (n + 1));                                  \
+    constexpr int TIMAX = 256 / TL;                                                            \
+    const int ntiles = (n0 + TIMAX - 1) / TIMAX;                                               \
+    const int ti = (n0 + ntiles - 1) / ntiles;                                                 \
+    const size_t sm = sizeof(C) * (n + (size_t)ti * (n + 1));                                  \
     cudaError_t e = set_smem<T>((const void*)fast::ky<T, n, INV>, sm);                         \
     if (e != cudaSuccess) return e;                                                           \
-    fast::ky<T, n, INV><<<dim3(3 * n0 * ntiles, n_rhs), tk * TL, sm, s>>>(                     \
-        (C*)spec, sstride, K2, tk, ntiles, active, (const C*)tw);                              \
+    fast::ky<T, n, INV><<<dim3(3 * K2 * ntiles, n_rhs), ti * TL, sm, s>>>(                     \
+        (C*)spec, sstride, n0, ti, ntiles, active, (const C*)tw);                              \
     return cudaGetLastError();                                                                \
   }
     XFFT_FAST_SIZES(X)
@@ -448,22 +521,23 @@ cudaError_t fast_x_green(int n0, int n1, void* spec, long long sstride, int K2, 
                          double halfvol, int n_rhs, cudaStream_t s) {
   typedef typename Cplx<T>::type C;
   switch (n0) {
-#define X(n)                                                                                  \
-  case n: {                                                                                   \
-    constexpr int TL = n / fast::Plan<n>::E;                                                   \
-    int tkmax = (sizeof(T) == 8 ? 384 : 768) / (3 * TL);                                       \
-    if (tkmax > 16) tkmax = 16;                                                                \
-    while (tkmax > 1 && sizeof(C) * (n + 3 * (size_t)tkmax * (n + 1)) > 160 * 1024) --tkmax;    \
-    const int ntiles = (K2 + tkmax - 1) / tkmax;                                               \
-    const int tk = (K2 + ntiles - 1) / ntiles;                                                 \
-    const size_t sm = sizeof(C) * (n + 3 * (size_t)tk * (n + 1));                              \
-    cudaError_t e = set_smem<T>((const void*)fast::kx_green<T, n>, sm);                        \
-    if (e != cudaSuccess) return e;                                                           \
-    fast::kx_green<T, n><<<dim3(n1 * ntiles, n_rhs), 3 * tk * TL, sm, s>>>(                    \
-        (C*)spec, sstride, n1, K2, tk, ntiles, active, (const C*)tw, (const C*)ge[0],          \
-        (const C*)ge[1], (const C*)ge[2], (const C*)gs[0], (const C*)gs[1], (const C*)gs[2],    \
-        (T)ih[0], (T)ih[1], (T)ih[2], (T)halfvol);                                             \
-    return cudaGetLastError();                                                                \
+#define X(n)                                                                                    \
+  case n: {                                                                                     \
+    constexpr int TL = n / fast::Plan<n>::E;                                                     \
+    const int maxthr = sizeof(T) == 8 ? 384 : 768;                                               \
+    int lmax = maxthr / TL; /* lines per block */                                                \
+    while (lmax > 3 && sizeof(C) * (n + (size_t)lmax * (n + 1)) > 160 * 1024) --lmax;            \
+    int rg = n_rhs < lmax / 3 ? n_rhs : lmax / 3;                                                \
+    if (rg < 1) rg = 1;                                                                          \
+    const int ngroups = (n_rhs + rg - 1) / rg;                                                   \
+    const size_t sm = sizeof(C) * (n + 3 * (size_t)rg * (n + 1));                                \
+    cudaError_t e = set_smem<T>((const void*)fast::kx_green<T, n>, sm);                          \
+    if (e != cudaSuccess) return e;                                                             \
+    fast::kx_green<T, n><<<dim3(n1 * K2, ngroups), 3 * rg * TL, sm, s>>>(                        \
+        (C*)spec, sstride, n1, K2, rg, n_rhs, active, (const C*)tw, (const C*)ge[0],             \
+        (const C*)ge[1], (const C*)ge[2], (const C*)gs[0], (const C*)gs[1], (const C*)gs[2],      \
+        (T)ih[0], (T)ih[1], (T)ih[2], (T)halfvol);                                               \
+    return cudaGetLastError();                                                                  \
   }
     XFFT_FAST_SIZES(X)
 #undef X
@@ -473,9 +547,10 @@ cudaError_t fast_x_green(int n0, int n1, void* spec, long long sstride, int K2, 
 }
 
 #define XFFT_INST(T)                                                                                  \
-  template cudaError_t fast_z_r2c<T>(int, const T*, void*, long long, long long, long long, const int*, \
-                                     const void*, unsigned long long*, int, cudaStream_t);            \
-  template cudaError_t fast_z_c2r<T>(int, const void*, const T*, T*, long long, long long, long long,  \
+  template cudaError_t fast_z_r2c<T>(int, T*, void*, long long, long long, int, int, const int*,       \
+                                     const void*, unsigned long long*, int, cudaStream_t, const T*,   \
+                                     const RhsState*);                                                \
+  template cudaError_t fast_z_c2r<T>(int, const void*, const T*, T*, long long, long long, int, int,   \
                                      double, const int*, const void*, double*, int, int, cudaStream_t); \
   template cudaError_t fast_y<T, false>(int, int, void*, long long, int, const int*, const void*, int, \
                                         cudaStream_t);                                                \

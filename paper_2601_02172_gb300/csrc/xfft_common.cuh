@@ -113,10 +113,12 @@ struct RhsState {
   double alpha, beta;
   double sig[6];    // int_Y sigma(u) (Mandel), tracked across iterations
   double sd[6];     // int_Y C grad^s d of the last apply
+  double rel;       // inner solves: relative reduction of rr^(1/2) to reach
   int active;       // 1 while iterating
   int iters;        // iterations performed
   int status;       // 0 running/converged, 4 not converged, 5 breakdown
   int converged;
+  int dpar;         // which of the two direction buffers holds the last direction d
 };
 
 }  // namespace xfft

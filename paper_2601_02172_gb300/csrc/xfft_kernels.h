@@ -65,6 +65,13 @@ struct ApplyArgs {
   unsigned long long* units_cut;
   int want_sig;            // 1: partials carry int_e sigma:eps and int_e sigma (always with eps);
                            // 0: partial 0 is <d, q> and the stress integrals are 0
+  // fused CG update in the stencil (standard DOFs): the operator is applied to
+  // d_new = z + beta d_old (d_old = the kernel's input d), d_new is stored to fdnew and
+  // u += alpha d_old at the block's own nodes; alpha and beta come from st[rhs]
+  const void* fz;          // z (same type as d) or nullptr (no fused update)
+  void* fdnew;
+  void* fu;
+  const RhsState* st;
 };
 template <typename T>
 cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
@@ -88,10 +95,12 @@ void fft_plan_destroy(FftPlan* p);
 size_t fft_spectrum_elems(const FftPlan* p);  // complex elements per RHS
 // z = P^-1 f per RHS (std part via FFT + Green, enr part identity); f^T z partials into
 // partials[rhs][nparts] (slots 0..nb-1).  spec: workspace of n_rhs * spectrum elems complex.
+// With q != nullptr the first pass also applies f -= alpha q (alpha = st[rhs].alpha) and stores f.
 template <typename T>
-cudaError_t launch_precondition(const FftPlan* p, const T* f, T* z, void* spec, long long stride,
+cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec, long long stride,
                                 int nX, const int* active, double* partials, int nparts,
-                                int n_rhs, cudaStream_t s, unsigned long long* units = nullptr);
+                                int n_rhs, cudaStream_t s, unsigned long long* units = nullptr,
+                                const T* q = nullptr, const RhsState* st = nullptr);
 int precondition_blocks(const FftPlan* p, int nX);
 
 // ---- CG vector ops and scalar finalisation (cg.cu)
@@ -107,6 +116,15 @@ cudaError_t launch_scale_copy(const Tin* x, Tout* y, double a, long long stride,
 template <typename T>
 cudaError_t launch_add_to_double(double* u, const T* dlt, long long stride, int n_rhs,
                                  const int* active, cudaStream_t s);
+// enriched block of the fused CG update: d_new = z + beta d_old, u += alpha d_old on [off, stride)
+template <typename T>
+cudaError_t launch_cg_update_tail(const T* z, const T* dold, T* dnew, T* u, const RhsState* st,
+                                  long long off, long long stride, int n_rhs, cudaStream_t s);
+// the update u += alpha d still pending after the last iteration (all right-hand sides); d is
+// dA or dB per right-hand side (RhsState::dpar)
+template <typename T>
+cudaError_t launch_cg_finish(T* u, const T* dA, const T* dB, const RhsState* st, long long stride,
+                             int n_rhs, cudaStream_t s);
 // mode: 0 = after the initial total apply (sig = partials 1..6), 1 = after an apply (alpha),
 // 2 = after a preconditioner application (rr, beta, stopping rule), 3 = initial precond
 struct FinArgs {
@@ -117,6 +135,11 @@ struct FinArgs {
   int maxit;
   int nparts;      // stride of the partial-sum rows
   int nparts_used; // valid partial sums per row
+  // mode 3 of an FP64 residual check in iterative refinement: set the per-RHS relative target
+  // of the next inner solve so that it aims at the outer tolerance (never below inner_floor)
+  int set_rel;
+  double inner_floor;
+  int parity;      // buffer index of the direction used in this iteration (recorded on exit)
 };
 // act[rhs] mirrors st[rhs].active for the kernels' early exit
 cudaError_t launch_finalize(RhsState* st, const double* partials, FinArgs fa, int n_rhs, int* act,
