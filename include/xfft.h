@@ -74,7 +74,8 @@ typedef struct {
   int maxit;           /* CG iteration cap (FP64) or inner cap per refinement step */
   double snap_tau;     /* |L| < snap_tau counts as on the interface (Sec. 3); <= 0: 1e-6 * min h */
   int enr_precond;     /* XFFT_ENR_IDENTITY (the paper's choice) */
-  double inner_tol;    /* FP32_REFINED: relative residual reduction per inner solve */
+  double inner_tol;    /* FP32_REFINED: smallest relative residual reduction asked of one FP32
+                          inner solve (each inner solve aims at half the outer tolerance) */
   int max_refine;      /* FP32_REFINED: cap on FP64 refinement steps */
   int poll_every;      /* iterations between host checks of the device convergence flags */
 } xfft_options;
@@ -89,7 +90,7 @@ typedef struct {
 } xfft_stats;
 
 /* Fill *opt with the defaults: FP64, tol 1e-10, maxit 10000, snap_tau 0 (=> 1e-6 min h),
- * identity enriched block, inner_tol 1e-4, max_refine 20, poll_every 8. */
+ * identity enriched block, inner_tol 1e-5, max_refine 20, poll_every 8. */
 xfft_status xfft_default_options(xfft_options* opt);
 
 /* Create a context for one grid.  stream: a cudaStream_t (or NULL for the legacy stream).

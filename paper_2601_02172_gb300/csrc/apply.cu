@@ -23,9 +23,9 @@
 
 namespace xfft {
 
-constexpr int kTZ = 32;  // threads along z (one warp)
-constexpr int kTY = 8;   // threads along y
-constexpr int kCX = 16;  // output planes per block along x
+constexpr int kTZ = 16;  // threads along z (half a warp; a warp covers two y rows)
+constexpr int kTY = 16;  // threads along y
+constexpr int kCX = 32;  // output planes per block along x
 
 template <typename T>
 __device__ __forceinline__ T cut_real(const CutData& cd, int f, int e);
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
       for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          const T up = __shfl_up_sync(0xffffffffu, F[dx + 2 * dy + 4][i], 1);
+          const T up = __shfl_up_sync(0xffffffffu, F[dx + 2 * dy + 4][i], 1, kTZ);
           G2[dx][dy][i] = F[dx + 2 * dy][i] + up;
         }
 #pragma unroll

@@ -58,16 +58,24 @@ __global__ void __launch_bounds__(256) kz_r2c(T* __restrict__ f, typename Cplx<T
   T* fr = f + rhs * stride + c * N3;
   const T* qr = q ? q + rhs * stride + c * N3 : nullptr;
   const T alpha = q ? (T)st[rhs].alpha : T(0);
-  for (int idx = threadIdx.x; idx < 2 * LPB * N; idx += blockDim.x) {
+  constexpr int PER = 2 * LPB * N / 256;  // = 2 E elements per thread (blockDim is 256)
+  T fv[PER], qv[PER];
+#pragma unroll
+  for (int e = 0; e < PER; ++e) {
+    const int idx = threadIdx.x + e * 256;
     const int rl = idx / N, k = idx - rl * N;
-    T v = T(0);
-    if (rl < nrows) {
-      const long long o = ((long long)(i0 + rl) * n1 + j) * N + k;
-      v = fr[o];
-      if (q) {
-        v -= alpha * qr[o];  // fused CG update f -= alpha A d
-        fr[o] = v;
-      }
+    const long long o = ((long long)(i0 + rl) * n1 + j) * N + k;
+    fv[e] = rl < nrows ? fr[o] : T(0);
+    qv[e] = (q && rl < nrows) ? qr[o] : T(0);
+  }
+#pragma unroll
+  for (int e = 0; e < PER; ++e) {
+    const int idx = threadIdx.x + e * 256;
+    const int rl = idx / N, k = idx - rl * N;
+    T v = fv[e];
+    if (q && rl < nrows) {
+      v -= alpha * qv[e];  // fused CG update f -= alpha A d
+      fr[((long long)(i0 + rl) * n1 + j) * N + k] = v;
     }
     T* dst = reinterpret_cast<T*>(&buf[(rl >> 1) * LS + k]);
     dst[rl & 1] = v;
@@ -114,18 +122,28 @@ __global__ void __launch_bounds__(256) ky(typename Cplx<T>::type* __restrict__ s
   const int ii0 = tile * ti;
   const int tie = min(ti, n0 - ii0);
   C* sp = spec + rhs * sstride + slab * N * n0 + ii0;
-  for (int idx = threadIdx.x; idx < N * ti; idx += blockDim.x) {
+  constexpr int E = Plan<N>::E;  // N ti elements over ti TL threads
+  C v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = threadIdx.x + e * blockDim.x;
     const int j = idx / ti, kk = idx - j * ti;
-    C v;
-    v.x = T(0);
-    v.y = T(0);
-    if (kk < tie) v = sp[(long long)j * n0 + kk];
-    buf[kk * LS + j] = v;
+    v[e].x = T(0);
+    v[e].y = T(0);
+    if (kk < tie) v[e] = sp[(long long)j * n0 + kk];
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = threadIdx.x + e * blockDim.x;
+    const int j = idx / ti, kk = idx - j * ti;
+    buf[kk * LS + j] = v[e];
   }
   __syncthreads();
   const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
   line_fft<C, N, INV>(buf + line * LS, tws, t);
-  for (int idx = threadIdx.x; idx < N * ti; idx += blockDim.x) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = threadIdx.x + e * blockDim.x;
     const int j = idx / ti, kk = idx - j * ti;
     if (kk < tie) sp[(long long)j * n0 + kk] = buf[kk * LS + j];
   }
@@ -255,14 +273,24 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768)
   const long long off = ((long long)k2 * n1 + j) * N;
   const int lines = 3 * rg;
   __syncthreads();
-  for (int idx = threadIdx.x; idx < lines * N; idx += blockDim.x) {
-    const int li = idx / N, i = idx - li * N;
-    const int r = li / 3, c = li - 3 * r;
-    C v;
-    v.x = T(0);
-    v.y = T(0);
-    if (r < nr && live[r]) v = spec[(r0 + r) * sstride + c * cstride + off + i];
-    buf[li * LS + i] = v;
+  constexpr int E = Plan<N>::E;  // lines N elements over lines TL threads
+  {
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int idx = threadIdx.x + e * blockDim.x;
+      const int li = idx / N, i = idx - li * N;
+      const int r = li / 3, c = li - 3 * r;
+      v[e].x = T(0);
+      v[e].y = T(0);
+      if (r < nr && live[r]) v[e] = spec[(r0 + r) * sstride + c * cstride + off + i];
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int idx = threadIdx.x + e * blockDim.x;
+      const int li = idx / N, i = idx - li * N;
+      buf[li * LS + i] = v[e];
+    }
   }
   __syncthreads();
   const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
@@ -288,7 +316,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768)
   }
   __syncthreads();
   line_fft<C, N, true>(buf + line * LS, tws, t);
-  for (int idx = threadIdx.x; idx < lines * N; idx += blockDim.x) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int idx = threadIdx.x + e * blockDim.x;
     const int li = idx / N, i = idx - li * N;
     const int r = li / 3, c = li - 3 * r;
     if (r < nr && live[r]) spec[(r0 + r) * sstride + c * cstride + off + i] = buf[li * LS + i];
@@ -323,17 +353,27 @@ __global__ void __launch_bounds__(256) kz_c2r(const typename Cplx<T>::type* __re
   const int nrows = min(2 * LPB, n0 - i0);
   const C* sp = spec + rhs * sstride + (long long)c * K2 * n1 * n0 + (long long)j * n0 + i0;
   // gather the half spectra of the row pairs: X (row 2p), Y (row 2p+1) at k2 = kk
-  for (int idx = threadIdx.x; idx < 2 * LPB * K2; idx += blockDim.x) {
-    const int kk = idx / (2 * LPB), rl = idx - kk * (2 * LPB);
-    C v;
-    v.x = v.y = T(0);
-    if (rl < nrows) v = sp[(long long)kk * n1 * n0 + rl];
-    if (kk == 0 || kk == half) v.y = T(0);
-    // stash X in .x/.y of slot (p, kk) and Y in slot (p, N - kk) (kk < half) temporarily:
-    // write to a scratch view of the same buffer after a barrier instead (two phases below)
+  {
+    constexpr int PER = (2 * LPB * K2 + 255) / 256;
+    C v[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      const int idx = threadIdx.x + e * 256;
+      const int kk = idx / (2 * LPB), rl = idx - kk * (2 * LPB);
+      v[e].x = v[e].y = T(0);
+      if (kk < K2 && rl < nrows) v[e] = sp[(long long)kk * n1 * n0 + rl];
+    }
+    // stage the half spectra (row rl, frequency kk) in the shared buffer
     T* tmp = reinterpret_cast<T*>(buf);
-    tmp[(rl * K2 + kk) * 2 + 0] = v.x;
-    tmp[(rl * K2 + kk) * 2 + 1] = v.y;
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      const int idx = threadIdx.x + e * 256;
+      const int kk = idx / (2 * LPB), rl = idx - kk * (2 * LPB);
+      if (kk < K2) {
+        tmp[(rl * K2 + kk) * 2 + 0] = v[e].x;
+        tmp[(rl * K2 + kk) * 2 + 1] = (kk == 0 || kk == half) ? T(0) : v[e].y;
+      }
+    }
   }
   __syncthreads();
   // build Z_k = X_k + i Y_k for k < N from the staged half spectra (in registers, then store)
@@ -374,13 +414,26 @@ __global__ void __launch_bounds__(256) kz_c2r(const typename Cplx<T>::type* __re
   const T* fr = f + rhs * stride + c * N3;
   T* zr = z + rhs * stride + c * N3;
   T tacc = T(0);
-  for (int idx = threadIdx.x; idx < nrows * N; idx += blockDim.x) {
-    const int rl = idx / N, k = idx - rl * N;
-    const C v = buf[(rl >> 1) * LS + k];
-    const T val = ((rl & 1) ? v.y : v.x) * scale;
-    const long long o = ((long long)(i0 + rl) * n1 + j) * N + k;
-    zr[o] = val;
-    tacc += val * fr[o];
+  {
+    constexpr int PER = 2 * LPB * N / 256;
+    T fv[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      const int idx = threadIdx.x + e * 256;
+      const int rl = idx / N, k = idx - rl * N;
+      fv[e] = rl < nrows ? fr[((long long)(i0 + rl) * n1 + j) * N + k] : T(0);
+    }
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      const int idx = threadIdx.x + e * 256;
+      const int rl = idx / N, k = idx - rl * N;
+      if (rl < nrows) {
+        const C v = buf[(rl >> 1) * LS + k];
+        const T val = ((rl & 1) ? v.y : v.x) * scale;
+        zr[((long long)(i0 + rl) * n1 + j) * N + k] = val;
+        tacc += val * fv[e];
+      }
+    }
   }
   double vv[1] = {(double)tacc}, tot[1];
   block_sum<1>(vv, red, tot);
