@@ -497,145 +497,206 @@ __device__ __forceinline__ void sym_mv(const T (&s)[6], const T* v, T (&out)[3])
   out[2] = s[4] * v[0] + s[3] * v[1] + s[2] * v[2];
 }
 
+// One thread per cut tet; the right-hand sides r0 .. r0+nr-1 are processed one after another
+// inside the thread, so the tet's geometry comes from HBM once per apply and from L1 for the
+// further right-hand sides.  Per-RHS sums are reduced per warp each tet and kept in shared
+// memory.
+// Loads that the compiler must not hoist out of the per-RHS loop (they hit L1 after the first
+// right-hand side; keeping them live in registers across the loop would spill).
+__device__ __forceinline__ int ld_keep(const int* p) {
+  int v;
+  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_keep(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_keep(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T cut_real_keep(const CutData& cd, int f, int e);
+template <>
+__device__ __forceinline__ double cut_real_keep<double>(const CutData& cd, int f, int e) {
+  return ld_keep(cd.dp + (long long)f * cd.ncut + e);
+}
+template <>
+__device__ __forceinline__ float cut_real_keep<float>(const CutData& cd, int f, int e) {
+  return ld_keep(cd.fp + (long long)f * cd.ncut + e);
+}
+
+constexpr int kCutThreads = 128;
+constexpr int kCutMaxR = 8;  // right-hand sides per launch (more are split over launches)
+
 template <typename T, bool TOTAL>
-__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4)
+__global__ void __launch_bounds__(kCutThreads, sizeof(T) == 8 ? 2 : 4)
     k_apply_cut(const T* __restrict__ d, T* __restrict__ q, const T* __restrict__ isD,
-                const CutData cd, const ApplyArgs a) {
-  const int rhs = blockIdx.y;
-  if (a.active && !a.active[rhs]) return;
-  if (a.units_cut && threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(a.units_cut, 1ULL);
-  __shared__ double red[7 * 32];
+                const CutData cd, const ApplyArgs a, int r0, int nr) {
+  constexpr int NW = kCutThreads / 32;
+  __shared__ double acc[kCutMaxR][7][NW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kCutMaxR * 7 * NW; i += kCutThreads) (&acc[0][0][0])[i] = 0.0;
+  if (a.units_cut && threadIdx.x == 0 && blockIdx.x == 0) {
+    unsigned long long n = 0;
+    for (int rr = 0; rr < nr; ++rr) n += (!a.active || a.active[r0 + rr]) ? 1 : 0;
+    atomicAdd(a.units_cut, n);
+  }
+  __syncthreads();
   const GridDev& g = a.g;
   const long long N = g.N;
   const int nX = a.nX;
   const int ncut = cd.ncut;
-  const T* dr = d + rhs * a.stride;
-  T* qr = q + rhs * a.stride;
+  const bool want_sig = a.want_sig != 0;
   T ih[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) ih[k] = (T)(1.0 / g.h[k]);
-  T E[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-  if (TOTAL) mandel_to_tensor(a.eps + 6 * rhs, E);
   const T lam_ph[2] = {(T)a.ph.lam[0], (T)a.ph.lam[1]};
   const T mu_ph[2] = {(T)a.ph.mu[0], (T)a.ph.mu[1]};
-  T en = T(0);
-  T sg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
-    int nd[4], ei[4];
+  for (int base = blockIdx.x * kCutThreads; base < ncut; base += gridDim.x * kCutThreads) {
+    const int e = base + threadIdx.x;
+    const bool ok = e < ncut;
+    const T sv = (ok && a.scale) ? (T)a.scale[cd.ip[8 * ncut + e]] : T(1);
+    for (int rr = 0; rr < nr; ++rr) {
+      const int rhs = r0 + rr;
+      if (a.active && !a.active[rhs]) continue;  // uniform over the block
+      T en = T(0);
+      T sg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+      if (ok) {
+        const T* dr = d + rhs * a.stride;
+        T* qr = q + rhs * a.stride;
+        int nd[4], ei[4];
+        T L[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      nd[k] = cd.ip[k * ncut + e];
-      ei[k] = cd.ip[(4 + k) * ncut + e];
-    }
-    const int vox = cd.ip[8 * ncut + e];
-    const int t = cd.ip[9 * ncut + e];
-    T gr[4][3];
-    tet_grads<T>(t, ih, gr);
-    T us[4][3], ws[4][3];
+        for (int k = 0; k < 4; ++k) {
+          nd[k] = ld_keep(cd.ip + k * ncut + e);
+          ei[k] = ld_keep(cd.ip + (4 + k) * ncut + e);
+          L[k] = cut_real_keep<T>(cd, cut_f_L(k), e);
+        }
+        const int t = ld_keep(cd.ip + 9 * ncut + e);
+        T gr[4][3];
+        tet_grads<T>(t, ih, gr);
+        T us[4][3], ws[4][3];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        us[k][c] = dr[c * N + nd[k]];
-        ws[k][c] = dr[3 * N + (long long)c * nX + ei[k]] * isD[(long long)c * nX + ei[k]];
+          for (int c = 0; c < 3; ++c) {
+            us[k][c] = dr[c * N + nd[k]];
+            ws[k][c] = dr[3 * N + (long long)c * nX + ei[k]] * ld_keep(isD + (long long)c * nX + ei[k]);
+          }
+        // standard and enriched symmetric gradients (constant on the tet)
+        T es[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, ew[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          es[0] += us[k][0] * gr[k][0];
+          es[1] += us[k][1] * gr[k][1];
+          es[2] += us[k][2] * gr[k][2];
+          es[3] += T(0.5) * (us[k][1] * gr[k][2] + us[k][2] * gr[k][1]);
+          es[4] += T(0.5) * (us[k][0] * gr[k][2] + us[k][2] * gr[k][0]);
+          es[5] += T(0.5) * (us[k][0] * gr[k][1] + us[k][1] * gr[k][0]);
+          ew[0] += ws[k][0] * gr[k][0];
+          ew[1] += ws[k][1] * gr[k][1];
+          ew[2] += ws[k][2] * gr[k][2];
+          ew[3] += T(0.5) * (ws[k][1] * gr[k][2] + ws[k][2] * gr[k][1]);
+          ew[4] += T(0.5) * (ws[k][0] * gr[k][2] + ws[k][2] * gr[k][0]);
+          ew[5] += T(0.5) * (ws[k][0] * gr[k][1] + ws[k][1] * gr[k][0]);
+        }
+        if (TOTAL) {
+          T E[6];
+          mandel_to_tensor(a.eps + 6 * rhs, E);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) es[k] += E[k];
+        }
+        T qs[4][3], qe[4][3];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) qs[k][c] = qe[k][c] = T(0);
+#pragma unroll
+        for (int si = 0; si < 2; ++si) {
+          const T s = si == 0 ? T(1) : T(-1);
+          const int ph = si == 0 ? 1 : 0;
+          const T lam = lam_ph[ph] * sv, mu = mu_ph[ph] * sv;
+          T c[4], gam[3] = {T(0), T(0), T(0)};
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            c[b] = fabs(L[b]) - s * L[b];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
+          }
+          T MM[10];
+#pragma unroll
+          for (int k = 0; k < 10; ++k) MM[k] = cut_real_keep<T>(cd, cut_f_M(si, k), e);
+          // weights: m_b = sum_c M_bc; P_b = sum_c M_bc c_c; rows of M
+          T mw[4], pw[4];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            mw[b] = MM[midx(b, 0)] + MM[midx(b, 1)] + MM[midx(b, 2)] + MM[midx(b, 3)];
+            pw[b] = MM[midx(b, 0)] * c[0] + MM[midx(b, 1)] * c[1] + MM[midx(b, 2)] * c[2] +
+                    MM[midx(b, 3)] * c[3];
+          }
+          T sbar[6], Tt[6];
+          side_stress(mw, c, es, ew, ws, gam, lam, mu, sbar);
+          side_stress(pw, c, es, ew, ws, gam, lam, mu, Tt);
+          if (want_sig) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sg[k] += sbar[k];
+          }
+#pragma unroll
+          for (int aa = 0; aa < 4; ++aa) {
+            const T row[4] = {MM[midx(aa, 0)], MM[midx(aa, 1)], MM[midx(aa, 2)], MM[midx(aa, 3)]};
+            T Ra[6];
+            side_stress(row, c, es, ew, ws, gam, lam, mu, Ra);
+            T v1[3], v2[3], v3[3];
+            sym_mv(sbar, gr[aa], v1);
+            sym_mv(Tt, gr[aa], v2);
+            sym_mv(Ra, gam, v3);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              qs[aa][i] += v1[i];
+              qe[aa][i] += v2[i] + v3[i];
+            }
+          }
+        }
+        // <d, q> of this element (d~ q~ = w q_raw on the enriched DOFs); equals int sigma : eps
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) en += us[k][c] * qs[k][c] + ws[k][c] * qe[k][c];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            atomicAdd(&qr[c * N + nd[k]], qs[k][c]);
+            atomicAdd(&qr[3 * N + (long long)c * nX + ei[k]],
+                      qe[k][c] * ld_keep(isD + (long long)c * nX + ei[k]));
+          }
       }
-    T L[4];
+      const T ew_sum = warp_sum(en);
+      if (lane == 0) acc[rr][0][wid] += (double)ew_sum;
+      if (want_sig) {
 #pragma unroll
-    for (int b = 0; b < 4; ++b) L[b] = cut_real<T>(cd, cut_f_L(b), e);
-    const T sv = a.scale ? (T)a.scale[vox] : T(1);
-    // standard and enriched symmetric gradients (constant on the tet)
-    T es[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, ew[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      es[0] += us[k][0] * gr[k][0];
-      es[1] += us[k][1] * gr[k][1];
-      es[2] += us[k][2] * gr[k][2];
-      es[3] += T(0.5) * (us[k][1] * gr[k][2] + us[k][2] * gr[k][1]);
-      es[4] += T(0.5) * (us[k][0] * gr[k][2] + us[k][2] * gr[k][0]);
-      es[5] += T(0.5) * (us[k][0] * gr[k][1] + us[k][1] * gr[k][0]);
-      ew[0] += ws[k][0] * gr[k][0];
-      ew[1] += ws[k][1] * gr[k][1];
-      ew[2] += ws[k][2] * gr[k][2];
-      ew[3] += T(0.5) * (ws[k][1] * gr[k][2] + ws[k][2] * gr[k][1]);
-      ew[4] += T(0.5) * (ws[k][0] * gr[k][2] + ws[k][2] * gr[k][0]);
-      ew[5] += T(0.5) * (ws[k][0] * gr[k][1] + ws[k][1] * gr[k][0]);
-    }
-    if (TOTAL) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) es[k] += E[k];
-    }
-    T qs[4][3], qe[4][3];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) qs[k][c] = qe[k][c] = T(0);
-#pragma unroll
-    for (int si = 0; si < 2; ++si) {
-      const T s = si == 0 ? T(1) : T(-1);
-      const int ph = si == 0 ? 1 : 0;
-      const T lam = lam_ph[ph] * sv, mu = mu_ph[ph] * sv;
-      T c[4], gam[3] = {T(0), T(0), T(0)};
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        c[b] = fabs(L[b]) - s * L[b];
-#pragma unroll
-        for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
-      }
-      T MM[10];
-#pragma unroll
-      for (int k = 0; k < 10; ++k) MM[k] = cut_real<T>(cd, cut_f_M(si, k), e);
-      // weights: m_b = sum_c M_bc; P_b = sum_c M_bc c_c; rows of M
-      T mw[4], pw[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        mw[b] = MM[midx(b, 0)] + MM[midx(b, 1)] + MM[midx(b, 2)] + MM[midx(b, 3)];
-        pw[b] = MM[midx(b, 0)] * c[0] + MM[midx(b, 1)] * c[1] + MM[midx(b, 2)] * c[2] + MM[midx(b, 3)] * c[3];
-      }
-      T sbar[6], Tt[6];
-      side_stress(mw, c, es, ew, ws, gam, lam, mu, sbar);
-      side_stress(pw, c, es, ew, ws, gam, lam, mu, Tt);
-      if (a.want_sig) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) sg[k] += sbar[k];
-      }
-#pragma unroll
-      for (int aa = 0; aa < 4; ++aa) {
-        const T row[4] = {MM[midx(aa, 0)], MM[midx(aa, 1)], MM[midx(aa, 2)], MM[midx(aa, 3)]};
-        T Ra[6];
-        side_stress(row, c, es, ew, ws, gam, lam, mu, Ra);
-        T v1[3], v2[3], v3[3];
-        sym_mv(sbar, gr[aa], v1);
-        sym_mv(Tt, gr[aa], v2);
-        sym_mv(Ra, gam, v3);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          qs[aa][i] += v1[i];
-          qe[aa][i] += v2[i] + v3[i];
+        for (int k = 0; k < 6; ++k) {
+          const T v = warp_sum(sg[k]);
+          if (lane == 0) acc[rr][1 + k][wid] += (double)v;
         }
       }
     }
-    // <d, q> of this element (d~ q~ = w q_raw on the enriched DOFs); equals int sigma : eps
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) en += us[k][c] * qs[k][c] + ws[k][c] * qe[k][c];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        atomicAdd(&qr[c * N + nd[k]], qs[k][c]);
-        atomicAdd(&qr[3 * N + (long long)c * nX + ei[k]], qe[k][c] * isD[(long long)c * nX + ei[k]]);
-      }
   }
-  double v[7] = {(double)en, (double)sg[0], (double)sg[1], (double)sg[2],
-                 (double)sg[3] * 1.41421356237309504880, (double)sg[4] * 1.41421356237309504880,
-                 (double)sg[5] * 1.41421356237309504880};
-  double tot[7];
-  block_sum<7>(v, red, tot);
-  if (threadIdx.x == 0) {
+  __syncthreads();
+  const double r2 = 1.41421356237309504880;
+  for (int i = threadIdx.x; i < nr * 7; i += kCutThreads) {
+    const int rr = i / 7, k = i - rr * 7;
+    const int rhs = r0 + rr;
+    if (a.active && !a.active[rhs]) continue;
+    double v = 0.0;
 #pragma unroll
-    for (int k = 0; k < 7; ++k)
-      a.partials[((long long)rhs * 7 + k) * a.nparts + a.part_offset_cut + blockIdx.x] = tot[k];
+    for (int w = 0; w < NW; ++w) v += acc[rr][k][w];
+    if (k >= 4) v *= r2;
+    a.partials[((long long)rhs * 7 + k) * a.nparts + a.part_offset_cut + blockIdx.x] = v;
   }
 }
 
@@ -646,9 +707,9 @@ int apply_uncut_blocks(const GridDev& g) {
   return gz * gy * gx;
 }
 
-constexpr int kCutBlocksMax = 1024;
+constexpr int kCutBlocksMax = 2 * 4 * 152;  // two waves of four resident blocks per SM
 int apply_cut_blocks(int ncut) {
-  const int nb = (ncut + 127) / 128;
+  const int nb = (ncut + kCutThreads - 1) / kCutThreads;
   return nb < 1 ? 1 : (nb > kCutBlocksMax ? kCutBlocksMax : nb);
 }
 
@@ -699,11 +760,14 @@ cudaError_t launch_apply_cut(const T* d, T* q, const T* isD, CutData cd, const A
       if (e != cudaSuccess) return e;
     }
   }
-  dim3 cgrid(apply_cut_blocks(cd.ncut), n_rhs, 1);
-  if (a.eps)
-    k_apply_cut<T, true><<<cgrid, 128, 0, s>>>(d, q, isD, cd, a);
-  else
-    k_apply_cut<T, false><<<cgrid, 128, 0, s>>>(d, q, isD, cd, a);
+  const int nb = apply_cut_blocks(cd.ncut);
+  for (int r0 = 0; r0 < n_rhs; r0 += kCutMaxR) {
+    const int nr = n_rhs - r0 < kCutMaxR ? n_rhs - r0 : kCutMaxR;
+    if (a.eps)
+      k_apply_cut<T, true><<<nb, kCutThreads, 0, s>>>(d, q, isD, cd, a, r0, nr);
+    else
+      k_apply_cut<T, false><<<nb, kCutThreads, 0, s>>>(d, q, isD, cd, a, r0, nr);
+  }
   return cudaGetLastError();
 }
 
