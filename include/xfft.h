@@ -59,7 +59,10 @@ typedef enum {
   XFFT_ESTATE = 8        /* call order violated (e.g. solve before set_microstructure) */
 } xfft_status;
 
-enum { XFFT_FP64 = 0, XFFT_FP32_REFINED = 1 };
+/* Arithmetic of the kernels.  XFFT_DW (double-word, an unevaluated sum of two floats, about 48
+ * significant bits, run on the FP32 units) is used by XFFT_FP32_REFINED for its residuals and
+ * stress integrals; xfft_apply also accepts it directly. */
+enum { XFFT_FP64 = 0, XFFT_FP32_REFINED = 1, XFFT_DW = 2 };
 enum { XFFT_ENR_IDENTITY = 0, XFFT_ENR_BLOCK3 = 1 };
 
 typedef struct {
@@ -68,7 +71,8 @@ typedef struct {
 } xfft_grid;
 
 typedef struct {
-  int precision;       /* XFFT_FP64 (all FP64) or XFFT_FP32_REFINED (FP32 CG, FP64 residuals) */
+  int precision;       /* XFFT_FP64 (all FP64) or XFFT_FP32_REFINED (FP32 CG; residuals of the
+                          FP64 iterate in double-word arithmetic) */
   double tol;          /* stopping rule sqrt(r^T P^-1 r / |Y|) <= tol * ||<sigma>_Y|| (eqs.
                           stoppingCriterion, convergence) */
   int maxit;           /* CG iteration cap (FP64) or inner cap per refinement step */
@@ -141,7 +145,8 @@ xfft_status xfft_grad(xfft_ctx* ctx, const double dL_dCeff[36], double dL_dlame[
  *   xfft_precondition: z = P^{-1} f with P = diag(A0_11, I) (eqs. scaledPreconditioner,
  *                      GreenHermitian); the standard part of f must have zero mean per
  *                      component.  rr (n_rhs, host, may be NULL) receives f^T z.
- * precision: XFFT_FP64 or 1 for the FP32 kernels (inputs and outputs stay double). */
+ * precision: XFFT_FP64, XFFT_FP32_REFINED (= 1, the FP32 kernels) or XFFT_DW (xfft_apply only:
+ * double-word kernels); inputs and outputs stay double.  Other values: XFFT_EINVAL. */
 xfft_status xfft_apply(xfft_ctx* ctx, int n_rhs, const double* d, const double* eps_bar,
                        double* q, double* sigma_int, int precision, int ptrs_on_device);
 xfft_status xfft_precondition(xfft_ctx* ctx, int n_rhs, const double* f, double* z,
@@ -163,7 +168,8 @@ enum {
   XFFT_PROF_APPLY_UNCUT_F32 = 0, XFFT_PROF_APPLY_CUT_F32 = 1, XFFT_PROF_APPLY_UNCUT_F64 = 2,
   XFFT_PROF_APPLY_CUT_F64 = 3, XFFT_PROF_PREC_F32 = 4, XFFT_PROF_PREC_F64 = 5,
   XFFT_PROF_VECTOR = 6, XFFT_PROF_FINALIZE = 7, XFFT_PROF_SETUP = 8, XFFT_PROF_GRAD = 9,
-  XFFT_PROF_POST = 10, XFFT_PROF_COUNT = 11
+  XFFT_PROF_POST = 10, XFFT_PROF_APPLY_UNCUT_DW = 11, XFFT_PROF_APPLY_CUT_DW = 12,
+  XFFT_PROF_COUNT = 13
 };
 xfft_status xfft_profile(xfft_ctx* ctx, int enable);
 xfft_status xfft_profile_read(xfft_ctx* ctx, double ms[16], long long launches[16],

@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "libxfft.so")
 
 XFFT_OK, XFFT_EINVAL, XFFT_ENOMEM, XFFT_ECUDA, XFFT_ENOTCONV, XFFT_EBREAKDOWN, XFFT_ETIMEOUT, \
     XFFT_EUNSUPPORTED, XFFT_ESTATE = range(9)
-XFFT_FP64, XFFT_FP32_REFINED = 0, 1
+XFFT_FP64, XFFT_FP32_REFINED, XFFT_DW = 0, 1, 2
+_PREC = {"fp64": XFFT_FP64, "fp32": XFFT_FP32_REFINED, "dw": XFFT_DW}
 
 EXPORTED = (
     "xfft_default_options", "xfft_create", "xfft_set_microstructure", "xfft_solve",
@@ -26,7 +27,8 @@ EXPORTED = (
 )
 NOALLOC_MAX_RHS = 8
 PROF_KINDS = ("apply_uncut_f32", "apply_cut_f32", "apply_uncut_f64", "apply_cut_f64", "prec_f32",
-              "prec_f64", "vector", "finalize", "setup", "grad", "post")
+              "prec_f64", "vector", "finalize", "setup", "grad", "post", "apply_uncut_dw",
+              "apply_cut_dw")
 
 
 class Grid(C.Structure):
@@ -241,7 +243,8 @@ class Solver:
         return dl, ds, ce.reshape(6, 6)
 
     def apply(self, d, eps=None, precision="fp64"):
-        """q = A d (+ b(eps)) on full DOF vectors (k x stride, scaled enriched part)."""
+        """q = A d (+ b(eps)) on full DOF vectors (k x stride, scaled enriched part).
+        precision: "fp64", "fp32" or "dw" (double-word kernels on FP64 data)."""
         d = np.ascontiguousarray(np.atleast_2d(d), dtype=np.float64)
         k = d.shape[0]
         q = np.empty_like(d)
@@ -251,8 +254,7 @@ class Solver:
         else:
             ep = None
         check(lib().xfft_apply(self._ctx, k, C.c_void_p(d.ctypes.data), ep, C.c_void_p(q.ctypes.data),
-                               sig.ctypes.data_as(C.POINTER(C.c_double)),
-                               0 if precision == "fp64" else 1, 0))
+                               sig.ctypes.data_as(C.POINTER(C.c_double)), _PREC[precision], 0))
         return q, sig
 
     def apply_noalloc(self, d, q, dAd_sig=None):

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "xfft_kernels.h"
 
 namespace xfft {
@@ -26,6 +28,15 @@ namespace xfft {
 constexpr int kTZ = 16;  // threads along z (half a warp; a warp covers two y rows)
 constexpr int kTY = 16;  // threads along y
 constexpr int kCX = 32;  // output planes per block along x
+#ifndef XFFT_UNCUT_MINB
+#define XFFT_UNCUT_MINB 2  // resident blocks per SM asked of the FP32 uncut kernel
+#endif
+#ifndef XFFT_UNCUT_MINB64
+#define XFFT_UNCUT_MINB64 2  // resident blocks per SM asked of the FP64 uncut kernel
+#endif
+#ifndef XFFT_UNCUT_MINBDW
+#define XFFT_UNCUT_MINBDW 1  // resident blocks per SM asked of the double-word uncut kernel
+#endif
 
 template <typename T>
 __device__ __forceinline__ T cut_real(const CutData& cd, int f, int e);
@@ -36,6 +47,10 @@ __device__ __forceinline__ double cut_real<double>(const CutData& cd, int f, int
 template <>
 __device__ __forceinline__ float cut_real<float>(const CutData& cd, int f, int e) {
   return cd.fp[(long long)f * cd.ncut + e];
+}
+template <>
+__device__ __forceinline__ dw cut_real<dw>(const CutData& cd, int f, int e) {
+  return dw(cd.dp[(long long)f * cd.ncut + e]);
 }
 
 // symmetric tensor stored as (00, 11, 22, 12, 02, 01)
@@ -227,8 +242,12 @@ __device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3]
 }
 
 template <typename T, bool TOTAL, bool SIG, bool UNIFORM, bool FUSED>
-__global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
-    k_apply_uncut(const T* __restrict__ d, T* __restrict__ q, const ApplyArgs a, int nxchunks) {
+__global__ void __launch_bounds__(kTZ* kTY, std::is_same<T, dw>::value     ? XFFT_UNCUT_MINBDW
+                                             : sizeof(T) == 8 ? XFFT_UNCUT_MINB64
+                                                              : XFFT_UNCUT_MINB)
+    k_apply_uncut(const typename Store<T>::type* __restrict__ d, typename Store<T>::type* __restrict__ q,
+                  const ApplyArgs a, int nxchunks) {
+  typedef typename Store<T>::type S;
   const int tz = threadIdx.x, ty = threadIdx.y;
   const int tid = tz + kTZ * ty;
   const int rhs = blockIdx.z / nxchunks;
@@ -242,8 +261,8 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
   const long long plane = (long long)n1 * n2;
   const int z0 = blockIdx.x * (kTZ - 1), y0 = blockIdx.y * (kTY - 1), x0 = xc * kCX;
   const int x1 = min(x0 + kCX, n0);
-  const T* dr = d + rhs * a.stride;
-  T* qr = q + rhs * a.stride;
+  const S* dr = d + rhs * a.stride;
+  S* qr = q + rhs * a.stride;
 
   __shared__ Node4<T> P[2][kTY + 1][kTZ + 1];
   __shared__ T Ys[2][3][kTY][kTZ];
@@ -297,9 +316,9 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
 
   // fused CG update: the block owns the plane nodes with 1 <= iy <= kTY-1, 1 <= iz <= kTZ-1
   // inside the grid; it stores d_new and updates u there (other blocks only read them as halo)
-  const T* zr = FUSED ? static_cast<const T*>(a.fz) + rhs * a.stride : nullptr;
-  T* dnr = FUSED ? static_cast<T*>(a.fdnew) + rhs * a.stride : nullptr;
-  T* ur = FUSED ? static_cast<T*>(a.fu) + rhs * a.stride : nullptr;
+  const S* zr = FUSED ? static_cast<const S*>(a.fz) + rhs * a.stride : nullptr;
+  S* dnr = FUSED ? static_cast<S*>(a.fdnew) + rhs * a.stride : nullptr;
+  S* ur = FUSED ? static_cast<S*>(a.fu) + rhs * a.stride : nullptr;
   const T fa = FUSED ? (T)a.st[rhs].alpha : T(0);
   const T fb = FUSED ? (T)a.st[rhs].beta : T(0);
   bool slot_own[2];
@@ -325,22 +344,22 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
         const long long nd = (long long)xp * plane + ld_off[k];
         pf_nd[k] = nd;
         if (FUSED) {
-          pf[k][0] = zr[nd];
-          pf[k][1] = zr[N + nd];
-          pf[k][2] = zr[2 * N + nd];
-          pf[k][3] = dr[nd];
-          pf[k][4] = dr[N + nd];
-          pf[k][5] = dr[2 * N + nd];
+          pf[k][0] = from_store<T>(zr[nd]);
+          pf[k][1] = from_store<T>(zr[N + nd]);
+          pf[k][2] = from_store<T>(zr[2 * N + nd]);
+          pf[k][3] = from_store<T>(dr[nd]);
+          pf[k][4] = from_store<T>(dr[N + nd]);
+          pf[k][5] = from_store<T>(dr[2 * N + nd]);
           pf_own[k] = own_plane && slot_own[k];
           if (pf_own[k]) {
-            pf[k][6] = ur[nd];
-            pf[k][7] = ur[N + nd];
-            pf[k][8] = ur[2 * N + nd];
+            pf[k][6] = from_store<T>(ur[nd]);
+            pf[k][7] = from_store<T>(ur[N + nd]);
+            pf[k][8] = from_store<T>(ur[2 * N + nd]);
           }
         } else {
-          pf[k][0] = dr[nd];
-          pf[k][1] = dr[N + nd];
-          pf[k][2] = dr[2 * N + nd];
+          pf[k][0] = from_store<T>(dr[nd]);
+          pf[k][1] = from_store<T>(dr[N + nd]);
+          pf[k][2] = from_store<T>(dr[2 * N + nd]);
         }
       }
     }
@@ -357,12 +376,12 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
           v.z = pf[k][2] + fb * pf[k][5];
           if (pf_own[k]) {
             const long long nd = pf_nd[k];
-            dnr[nd] = v.x;
-            dnr[N + nd] = v.y;
-            dnr[2 * N + nd] = v.z;
-            ur[nd] = pf[k][6] + fa * pf[k][3];
-            ur[N + nd] = pf[k][7] + fa * pf[k][4];
-            ur[2 * N + nd] = pf[k][8] + fa * pf[k][5];
+            dnr[nd] = to_store(v.x);
+            dnr[N + nd] = to_store(v.y);
+            dnr[2 * N + nd] = to_store(v.z);
+            ur[nd] = to_store(pf[k][6] + fa * pf[k][3]);
+            ur[N + nd] = to_store(pf[k][7] + fa * pf[k][4]);
+            ur[2 * N + nd] = to_store(pf[k][8] + fa * pf[k][5]);
           }
         } else {
           v.x = pf[k][0];
@@ -396,7 +415,7 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
     for (int c = 0; c < 8; ++c) u[c] = P[(s + (c & 1)) & 1][ty + ((c >> 1) & 1)][tz + ((c >> 2) & 1)];
     const long long vox = (long long)xw * plane + (long long)yv * n2 + zv;
     const unsigned code = a.code[vox];
-    const T sv = a.scale ? (T)a.scale[vox] : T(1);
+    const T sv = a.scale ? from_store<T>(a.scale[vox]) : T(1);
     Coef<T, UNIFORM> cf;
 #pragma unroll
     for (int ph = 0; ph < 2; ++ph)
@@ -428,7 +447,7 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
       for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          const T up = __shfl_up_sync(0xffffffffu, F[dx + 2 * dy + 4][i], 1, kTZ);
+          const T up = shfl_up_t<T>(0xffffffffu, F[dx + 2 * dy + 4][i], 1, kTZ);
           G2[dx][dy][i] = F[dx + 2 * dy][i] + up;
         }
 #pragma unroll
@@ -446,9 +465,9 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
       if (s >= 1) {
         const long long nd = (long long)xw * plane + (long long)yv * n2 + zv;
         const T q0 = pend[0] + H0[0], q1 = pend[1] + H0[1], q2 = pend[2] + H0[2];
-        qr[nd] = q0;
-        qr[N + nd] = q1;
-        qr[2 * N + nd] = q2;
+        qr[nd] = to_store(q0);
+        qr[N + nd] = to_store(q1);
+        qr[2 * N + nd] = to_store(q2);
         if (!SIG) en += q0 * u[0].x + q1 * u[0].y + q2 * u[0].z;  // <d, q> of this node
       }
 #pragma unroll
@@ -456,8 +475,8 @@ __global__ void __launch_bounds__(kTZ* kTY, sizeof(T) == 8 ? 2 : 3)
     }
   }
   const double r2 = 1.41421356237309504880;
-  double v[7] = {(double)en, (double)sg[0], (double)sg[1], (double)sg[2], (double)sg[3] * r2,
-                 (double)sg[4] * r2, (double)sg[5] * r2};
+  double v[7] = {to_double(en), to_double(sg[0]), to_double(sg[1]), to_double(sg[2]),
+                 to_double(sg[3]) * r2, to_double(sg[4]) * r2, to_double(sg[5]) * r2};
   double tot[7];
   block_sum<7>(v, red, tot);
   if (tid == 0) {
@@ -528,14 +547,20 @@ template <>
 __device__ __forceinline__ float cut_real_keep<float>(const CutData& cd, int f, int e) {
   return ld_keep(cd.fp + (long long)f * cd.ncut + e);
 }
+template <>
+__device__ __forceinline__ dw cut_real_keep<dw>(const CutData& cd, int f, int e) {
+  return dw(ld_keep(cd.dp + (long long)f * cd.ncut + e));
+}
 
 constexpr int kCutThreads = 128;
 constexpr int kCutMaxR = 8;  // right-hand sides per launch (more are split over launches)
 
 template <typename T, bool TOTAL>
-__global__ void __launch_bounds__(kCutThreads, sizeof(T) == 8 ? 2 : 4)
-    k_apply_cut(const T* __restrict__ d, T* __restrict__ q, const T* __restrict__ isD,
-                const CutData cd, const ApplyArgs a, int r0, int nr) {
+__global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1 : sizeof(T) == 8 ? 2 : 4)
+    k_apply_cut(const typename Store<T>::type* __restrict__ d, typename Store<T>::type* __restrict__ q,
+                const typename Store<T>::type* __restrict__ isD, const CutData cd, const ApplyArgs a,
+                int r0, int nr) {
+  typedef typename Store<T>::type S;
   constexpr int NW = kCutThreads / 32;
   __shared__ double acc[kCutMaxR][7][NW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -559,15 +584,15 @@ __global__ void __launch_bounds__(kCutThreads, sizeof(T) == 8 ? 2 : 4)
   for (int base = blockIdx.x * kCutThreads; base < ncut; base += gridDim.x * kCutThreads) {
     const int e = base + threadIdx.x;
     const bool ok = e < ncut;
-    const T sv = (ok && a.scale) ? (T)a.scale[cd.ip[8 * ncut + e]] : T(1);
+    const T sv = (ok && a.scale) ? from_store<T>(a.scale[cd.ip[8 * ncut + e]]) : T(1);
     for (int rr = 0; rr < nr; ++rr) {
       const int rhs = r0 + rr;
       if (a.active && !a.active[rhs]) continue;  // uniform over the block
       T en = T(0);
       T sg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
       if (ok) {
-        const T* dr = d + rhs * a.stride;
-        T* qr = q + rhs * a.stride;
+        const S* dr = d + rhs * a.stride;
+        S* qr = q + rhs * a.stride;
         int nd[4], ei[4];
         T L[4];
 #pragma unroll
@@ -584,8 +609,9 @@ __global__ void __launch_bounds__(kCutThreads, sizeof(T) == 8 ? 2 : 4)
         for (int k = 0; k < 4; ++k)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            us[k][c] = dr[c * N + nd[k]];
-            ws[k][c] = dr[3 * N + (long long)c * nX + ei[k]] * ld_keep(isD + (long long)c * nX + ei[k]);
+            us[k][c] = from_store<T>(dr[c * N + nd[k]]);
+            ws[k][c] = from_store<T>(dr[3 * N + (long long)c * nX + ei[k]]) *
+                       from_store<T>(ld_keep(isD + (long long)c * nX + ei[k]));
           }
         // standard and enriched symmetric gradients (constant on the tet)
         T es[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, ew[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -623,7 +649,7 @@ __global__ void __launch_bounds__(kCutThreads, sizeof(T) == 8 ? 2 : 4)
           T c[4], gam[3] = {T(0), T(0), T(0)};
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
-            c[b] = fabs(L[b]) - s * L[b];
+            c[b] = absval(L[b]) - s * L[b];
 #pragma unroll
             for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
           }
@@ -670,18 +696,18 @@ __global__ void __launch_bounds__(kCutThreads, sizeof(T) == 8 ? 2 : 4)
         for (int k = 0; k < 4; ++k)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            atomicAdd(&qr[c * N + nd[k]], qs[k][c]);
+            atomicAdd(&qr[c * N + nd[k]], to_store(qs[k][c]));
             atomicAdd(&qr[3 * N + (long long)c * nX + ei[k]],
-                      qe[k][c] * ld_keep(isD + (long long)c * nX + ei[k]));
+                      to_store(qe[k][c] * from_store<T>(ld_keep(isD + (long long)c * nX + ei[k]))));
           }
       }
-      const T ew_sum = warp_sum(en);
-      if (lane == 0) acc[rr][0][wid] += (double)ew_sum;
+      const double ew_sum = (double)warp_sum(red_val(en));
+      if (lane == 0) acc[rr][0][wid] += ew_sum;
       if (want_sig) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          const T v = warp_sum(sg[k]);
-          if (lane == 0) acc[rr][1 + k][wid] += (double)v;
+          const double v = (double)warp_sum(red_val(sg[k]));
+          if (lane == 0) acc[rr][1 + k][wid] += v;
         }
       }
     }
@@ -714,7 +740,8 @@ int apply_cut_blocks(int ncut) {
 }
 
 template <typename T>
-cudaError_t launch_apply_uncut(const T* d, T* q, const ApplyArgs& a, int n_rhs, cudaStream_t s) {
+cudaError_t launch_apply_uncut(const typename Store<T>::type* d, typename Store<T>::type* q,
+                               const ApplyArgs& a, int n_rhs, cudaStream_t s) {
   const GridDev& g = a.g;
   const int gz = (g.n2 + kTZ - 2) / (kTZ - 1);
   const int gy = (g.n1 + kTY - 2) / (kTY - 1);
@@ -726,12 +753,17 @@ cudaError_t launch_apply_uncut(const T* d, T* q, const ApplyArgs& a, int n_rhs, 
 #define XFFT_LAUNCH(TOT, SG, UNI) k_apply_uncut<T, TOT, SG, UNI, false><<<grid, block, 0, s>>>(d, q, a, gx)
 #define XFFT_LAUNCH_F(SG, UNI) k_apply_uncut<T, false, SG, UNI, true><<<grid, block, 0, s>>>(d, q, a, gx)
   if (a.fz) {
-    if (sig) {
-      if (uni) XFFT_LAUNCH_F(true, true);
-      else XFFT_LAUNCH_F(true, false);
+    // the fused CG update serves the FP32 and FP64 solvers (not the double-word residuals)
+    if constexpr (!std::is_same<T, dw>::value) {
+      if (sig) {
+        if (uni) XFFT_LAUNCH_F(true, true);
+        else XFFT_LAUNCH_F(true, false);
+      } else {
+        if (uni) XFFT_LAUNCH_F(false, true);
+        else XFFT_LAUNCH_F(false, false);
+      }
     } else {
-      if (uni) XFFT_LAUNCH_F(false, true);
-      else XFFT_LAUNCH_F(false, false);
+      return cudaErrorInvalidValue;
     }
   } else if (a.eps) {
     if (uni) XFFT_LAUNCH(true, true, true);
@@ -751,12 +783,14 @@ cudaError_t launch_apply_uncut(const T* d, T* q, const ApplyArgs& a, int n_rhs, 
 // The enriched part of q only receives atomic contributions from the cut-tet kernel: it is
 // cleared first; the standard part must already hold the uncut kernel's plain stores.
 template <typename T>
-cudaError_t launch_apply_cut(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
+cudaError_t launch_apply_cut(const typename Store<T>::type* d, typename Store<T>::type* q,
+                             const typename Store<T>::type* isD, CutData cd, const ApplyArgs& a,
                              int n_rhs, cudaStream_t s) {
+  typedef typename Store<T>::type S;
   const GridDev& g = a.g;
   if (a.nX > 0) {
     for (int r = 0; r < n_rhs; ++r) {
-      cudaError_t e = cudaMemsetAsync(q + r * a.stride + 3 * g.N, 0, sizeof(T) * 3 * (size_t)a.nX, s);
+      cudaError_t e = cudaMemsetAsync(q + r * a.stride + 3 * g.N, 0, sizeof(S) * 3 * (size_t)a.nX, s);
       if (e != cudaSuccess) return e;
     }
   }
@@ -772,24 +806,27 @@ cudaError_t launch_apply_cut(const T* d, T* q, const T* isD, CutData cd, const A
 }
 
 template <typename T>
-cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
+cudaError_t launch_apply(const typename Store<T>::type* d, typename Store<T>::type* q,
+                         const typename Store<T>::type* isD, CutData cd, const ApplyArgs& a,
                          int n_rhs, cudaStream_t s) {
   cudaError_t e = launch_apply_uncut<T>(d, q, a, n_rhs, s);
   if (e != cudaSuccess) return e;
   return launch_apply_cut<T>(d, q, isD, cd, a, n_rhs, s);
 }
 
-template cudaError_t launch_apply<float>(const float*, float*, const float*, CutData,
-                                         const ApplyArgs&, int, cudaStream_t);
-template cudaError_t launch_apply<double>(const double*, double*, const double*, CutData,
-                                          const ApplyArgs&, int, cudaStream_t);
-template cudaError_t launch_apply_uncut<float>(const float*, float*, const ApplyArgs&, int, cudaStream_t);
-template cudaError_t launch_apply_uncut<double>(const double*, double*, const ApplyArgs&, int,
-                                                cudaStream_t);
-template cudaError_t launch_apply_cut<float>(const float*, float*, const float*, CutData,
-                                             const ApplyArgs&, int, cudaStream_t);
-template cudaError_t launch_apply_cut<double>(const double*, double*, const double*, CutData,
-                                              const ApplyArgs&, int, cudaStream_t);
+#define XFFT_INST(T)                                                                             \
+  template cudaError_t launch_apply<T>(const Store<T>::type*, Store<T>::type*,                  \
+                                       const Store<T>::type*, CutData, const ApplyArgs&, int,   \
+                                       cudaStream_t);                                           \
+  template cudaError_t launch_apply_uncut<T>(const Store<T>::type*, Store<T>::type*,            \
+                                             const ApplyArgs&, int, cudaStream_t);              \
+  template cudaError_t launch_apply_cut<T>(const Store<T>::type*, Store<T>::type*,              \
+                                           const Store<T>::type*, CutData, const ApplyArgs&, int, \
+                                           cudaStream_t);
+XFFT_INST(float)
+XFFT_INST(double)
+XFFT_INST(dw)
+#undef XFFT_INST
 
 // ---------------------------------------------------------------- per-voxel average stress
 __global__ void k_voxel_stress_uncut(const double* __restrict__ u, const ApplyArgs a,

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/xfft.h"
@@ -473,10 +474,12 @@ const float* isd_of<float>(const xfft_ctx* c) {
 }
 
 // q = A d (+ b(eps)); finalisation `mode` (0 or 1) on the apply partials
-template <typename T>
+// T: storage type of the vectors; A: arithmetic type of the kernels (T, or dw on FP64 data)
+template <typename T, typename A = T>
 static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev, int n_rhs,
                             const int* active, int fin_mode, double tol, int crit, int maxit,
                             const T* fz = nullptr, T* fdnew = nullptr, T* fu = nullptr, int parity = 0) {
+  static_assert(std::is_same<typename Store<A>::type, T>::value, "arithmetic/storage mismatch");
   ApplyArgs a = apply_args(c, eps_dev, active);
   a.fz = fz;
   a.fdnew = fdnew;
@@ -485,17 +488,18 @@ static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev
   // the relative stopping rule of the inner FP32 solve needs no stress integrals
   a.want_sig = (fin_mode == 1 && crit == 1) ? 0 : 1;
   const bool dbl = sizeof(T) == 8;
-  const int ku = dbl ? XFFT_PROF_APPLY_UNCUT_F64 : XFFT_PROF_APPLY_UNCUT_F32;
-  const int kc = dbl ? XFFT_PROF_APPLY_CUT_F64 : XFFT_PROF_APPLY_CUT_F32;
+  const bool dwa = std::is_same<A, dw>::value;
+  const int ku = dwa ? XFFT_PROF_APPLY_UNCUT_DW : dbl ? XFFT_PROF_APPLY_UNCUT_F64 : XFFT_PROF_APPLY_UNCUT_F32;
+  const int kc = dwa ? XFFT_PROF_APPLY_CUT_DW : dbl ? XFFT_PROF_APPLY_CUT_F64 : XFFT_PROF_APPLY_CUT_F32;
   a.units_uncut = punit(c, ku);
   a.units_cut = punit(c, kc);
   {
     ProfScope ps(c, ku, 1);
-    CU(launch_apply_uncut<T>(d, q, a, n_rhs, c->stream));
+    CU(launch_apply_uncut<A>(d, q, a, n_rhs, c->stream));
   }
   {
     ProfScope ps(c, kc, 1);
-    CU(launch_apply_cut<T>(fz ? fdnew : d, q, isd_of<T>(c), cutdata(c), a, n_rhs, c->stream));
+    CU(launch_apply_cut<A>(fz ? fdnew : d, q, isd_of<T>(c), cutdata(c), a, n_rhs, c->stream));
   }
   if (fin_mode >= 0) {
     ProfScope ps(c, XFFT_PROF_FINALIZE, 1);
@@ -680,8 +684,9 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
       CU(launch_scale_copy<float, float>(q, f, -1.0, stride, n_rhs, c->act, s));
     } else {
-      // FP64 residual of the current iterate and the stopping rule
-      TRY(do_apply<double>(c, u, r64, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit));
+      // residual of the accumulated FP64 iterate in double-word arithmetic (about 48 bits, far
+      // below the FP32 rounding it corrects) and the stopping rule
+      TRY((do_apply<double, dw>(c, u, r64, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit)));
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
       CU(launch_scale_copy<double, float>(r64, f, -1.0, stride, n_rhs, c->act, s));
     }
@@ -968,7 +973,7 @@ static xfft_status stage_out(xfft_ctx* c, const T* src, double* dst, size_t coun
   return XFFT_OK;
 }
 
-template <typename T>
+template <typename T, typename A = T>
 static xfft_status apply_entry(xfft_ctx* c, int n_rhs, const double* d, const double* eps_bar, double* q,
                                double* sigma_int, int on_dev) {
   const long long stride = stride_of(c);
@@ -981,7 +986,8 @@ static xfft_status apply_entry(xfft_ctx* c, int n_rhs, const double* d, const do
   CU(dalloc(&qq, tot));
   xfft_status st = stage_in<T>(c, d, dd, tot, on_dev, scratch);
   if (st == XFFT_OK && eps_bar) st = upload_eps(c, n_rhs, eps_bar);
-  if (st == XFFT_OK) st = do_apply<T>(c, dd, qq, eps_bar ? c->eps_d : nullptr, n_rhs, nullptr, -1, 0, 0, 0);
+  if (st == XFFT_OK)
+    st = do_apply<T, A>(c, dd, qq, eps_bar ? c->eps_d : nullptr, n_rhs, nullptr, -1, 0, 0, 0);
   if (st == XFFT_OK) st = stage_out<T>(c, qq, q, tot, on_dev, scratch);
   if (st == XFFT_OK && sigma_int) {
     const int nparts = nparts_of(c);
@@ -1009,8 +1015,12 @@ extern "C" xfft_status xfft_apply(xfft_ctx* c, int n_rhs, const double* d, const
   if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
   if (n_rhs < 1 || n_rhs > 64) return fail(XFFT_EINVAL, "n_rhs must be in [1, 64]");
   TRY(ensure_work(c, std::max(n_rhs, c->cap_rhs), c->cap_prec >= 0 ? c->cap_prec : c->opt.precision));
-  return precision == XFFT_FP64 ? apply_entry<double>(c, n_rhs, d, eps_bar, q, sigma_int, ptrs_on_device)
-                                : apply_entry<float>(c, n_rhs, d, eps_bar, q, sigma_int, ptrs_on_device);
+  if (precision == XFFT_FP64) return apply_entry<double>(c, n_rhs, d, eps_bar, q, sigma_int, ptrs_on_device);
+  if (precision == XFFT_DW)
+    return apply_entry<double, dw>(c, n_rhs, d, eps_bar, q, sigma_int, ptrs_on_device);
+  if (precision == XFFT_FP32_REFINED)
+    return apply_entry<float>(c, n_rhs, d, eps_bar, q, sigma_int, ptrs_on_device);
+  return fail(XFFT_EINVAL, "precision must be XFFT_FP64, XFFT_FP32_REFINED or XFFT_DW");
 }
 
 template <typename T>

@@ -245,8 +245,14 @@ __device__ __forceinline__ void green_solve(const GreenFactor<C, T>& gf, C& F0, 
 // block: (k2, j), all three components of a group of rg right-hand sides: 3 rg contiguous lines
 // of length N = n0.  The symbol of each frequency is factorised once and applied to every
 // right-hand side of the group.
+#ifndef XFFT_KX_MAXT
+#define XFFT_KX_MAXT 576  // FP32 x/Green kernel: largest block
+#endif
+#ifndef XFFT_KX_MINB
+#define XFFT_KX_MINB 2  // FP32 x/Green kernel: resident blocks per SM asked of the compiler
+#endif
 template <typename T, int N>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768)
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : XFFT_KX_MAXT, sizeof(T) == 8 ? 1 : XFFT_KX_MINB)
     kx_green(typename Cplx<T>::type* __restrict__ spec, long long sstride, int n1, int K2, int rg,
              int n_rhs, const int* __restrict__ active, const typename Cplx<T>::type* __restrict__ tw,
              const typename Cplx<T>::type* __restrict__ ge0, const typename Cplx<T>::type* __restrict__ ge1,
@@ -577,7 +583,7 @@ cudaError_t fast_x_green(int n0, int n1, void* spec, long long sstride, int K2, 
 #define X(n)                                                                                    \
   case n: {                                                                                     \
     constexpr int TL = n / fast::Plan<n>::E;                                                     \
-    const int maxthr = sizeof(T) == 8 ? 384 : 768;                                               \
+    const int maxthr = sizeof(T) == 8 ? 384 : XFFT_KX_MAXT;                                      \
     int lmax = maxthr / TL; /* lines per block */                                                \
     while (lmax > 3 && sizeof(C) * (n + (size_t)lmax * (n + 1)) > 160 * 1024) --lmax;            \
     int rg = n_rhs < lmax / 3 ? n_rhs : lmax / 3;                                                \

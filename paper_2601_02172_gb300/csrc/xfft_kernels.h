@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dw.cuh"
 #include "xfft_common.cuh"
 
 namespace xfft {
@@ -73,13 +74,18 @@ struct ApplyArgs {
   void* fu;
   const RhsState* st;
 };
+// T is the arithmetic type (float, double or dw = double-word on FP64 data); the vectors are
+// stored as Store<T>::type
 template <typename T>
-cudaError_t launch_apply(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
+cudaError_t launch_apply(const typename Store<T>::type* d, typename Store<T>::type* q,
+                         const typename Store<T>::type* isD, CutData cd, const ApplyArgs& a,
                          int n_rhs, cudaStream_t s);
 template <typename T>
-cudaError_t launch_apply_uncut(const T* d, T* q, const ApplyArgs& a, int n_rhs, cudaStream_t s);
+cudaError_t launch_apply_uncut(const typename Store<T>::type* d, typename Store<T>::type* q,
+                               const ApplyArgs& a, int n_rhs, cudaStream_t s);
 template <typename T>
-cudaError_t launch_apply_cut(const T* d, T* q, const T* isD, CutData cd, const ApplyArgs& a,
+cudaError_t launch_apply_cut(const typename Store<T>::type* d, typename Store<T>::type* q,
+                             const typename Store<T>::type* isD, CutData cd, const ApplyArgs& a,
                              int n_rhs, cudaStream_t s);
 int apply_uncut_blocks(const GridDev& g);
 int apply_cut_blocks(int ncut);

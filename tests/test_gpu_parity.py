@@ -79,7 +79,7 @@ def test_setup_matches_oracle(xf, name):
 
 
 @pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "dw"])
 def test_apply_matches_oracle(xf, name, prec):
     n, ell, L, lm, lp, sc = _case(name)
     s = xf.Solver(n, ell)
@@ -89,7 +89,7 @@ def test_apply_matches_oracle(xf, name, prec):
     rng = np.random.default_rng(5)
     d = rng.normal(size=(2, o.ndof))
     eps = rng.normal(size=(2, 6))
-    tol = 1e-12 if prec == "fp64" else 2e-5
+    tol = {"fp64": 1e-12, "dw": 1e-11, "fp32": 2e-5}[prec]
     q, sig = s.apply(d, precision=prec)
     for r in range(2):
         assert _rel(q[r], o.A @ d[r]) < tol
@@ -98,6 +98,28 @@ def test_apply_matches_oracle(xf, name, prec):
         assert _rel(q[r], o.A @ d[r] + o.rhs(eps[r])) < tol
         ref = np.asarray(o.Sm @ d[r]).ravel() + o.Cbar @ eps[r]
         assert _rel(sig[r], ref) < tol
+
+
+@pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell"])
+def test_dw_residual_at_the_solution(xf, name):
+    """At the exact solution the residual A u + b cancels to rounding: the double-word kernels
+    must resolve it to far below the FP32 level (what the refinement's stopping rule needs)."""
+    n, ell, L, lm, lp, sc = _case(name)
+    s = xf.Solver(n, ell)
+    s.set_microstructure(L, lm, lp, sc)
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o.assemble()
+    eps = np.eye(6)[[0, 3]]
+    u = np.stack([o.solve_direct(e) for e in eps])
+    bn = [np.linalg.norm(o.rhs(e)) for e in eps]
+    q64, _ = s.apply(u, eps=eps, precision="fp64")
+    qdw, _ = s.apply(u, eps=eps, precision="dw")
+    q32, _ = s.apply(u, eps=eps, precision="fp32")
+    for r in range(2):
+        assert np.linalg.norm(q64[r]) < 1e-10 * bn[r]  # u solves the system
+        assert np.linalg.norm(qdw[r] - q64[r]) < 1e-11 * bn[r]
+        # FP32 cannot resolve it: the check above would fail for the FP32 kernels
+        assert np.linalg.norm(q32[r] - q64[r]) > 1e-9 * bn[r]
 
 
 @pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell", "fast_mixed", "fast_radix5"])
