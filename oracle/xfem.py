@@ -509,6 +509,38 @@ class XFEM:
         Z = np.einsum("...j,kl->...jkl", c, np.eye(3)).reshape(n + (24, 3))
         return np.einsum("...ai,ab,...bj->...ij", Z.conj(), Av, Z)
 
+    def green_symbol_at(self, k):
+        """The 3x3 matrix Z(xi)^H A0_v Z(xi) of eq. GreenHermitian at the single integer frequency
+        k = (k1, k2, k3) (taken modulo the grid), without forming the full symbol array."""
+        Av = self.voxel_reference_matrix()
+        xi = np.array([np.fft.fftfreq(self.n[a])[int(k[a]) % self.n[a]] for a in range(3)])
+        c = np.exp(2j * np.pi * (VOXEL_CORNERS @ xi))  # (8,)
+        Z = np.kron(c[:, None], np.eye(3))  # (24, 3), DOFs node-major
+        return Z.conj().T @ Av @ Z
+
+    def precondition_modes(self, modes):
+        """P^{-1} (std part, eq. GreenHermitian) of the real field f = sum_m Re(a_m e^{2 pi i
+        k_m . x / N}) given as a list of (k_m, a_m) with a_m a complex 3-vector: since the Green
+        operator is diagonal in Fourier space with M(-xi) = conj M(xi), the result is
+        z = sum_m Re(M(k_m)^{-1} a_m e^{2 pi i k_m . x / N}) (the zero frequency maps to 0).
+        Returns (f, z), each of length 3 N (component-major)."""
+        n = self.n
+        i, j, k = np.meshgrid(*[np.arange(n[a]) for a in range(3)], indexing="ij")
+        f = np.zeros((3,) + n)
+        z = np.zeros((3,) + n)
+        for kv, a in modes:
+            kv = [int(v) % n[q] for q, v in enumerate(kv)]
+            a = np.asarray(a, dtype=complex)
+            ph = np.exp(2j * np.pi * (kv[0] * i / n[0] + kv[1] * j / n[1] + kv[2] * k / n[2]))
+            if kv == [0, 0, 0]:
+                b = np.zeros(3, dtype=complex)
+            else:
+                b = np.linalg.solve(self.green_symbol_at(kv), a)
+            for q in range(3):
+                f[q] += np.real(a[q] * ph)
+                z[q] += np.real(b[q] * ph)
+        return f.ravel(), z.ravel()
+
     def _green_fft(self):
         Mx = self.green_symbol()
         Mx[0, 0, 0] = np.eye(3)
