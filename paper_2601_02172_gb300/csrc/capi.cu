@@ -422,7 +422,8 @@ static xfft_status ensure_work(xfft_ctx* c, int n_rhs, int prec) {
   CU(dalloc(&c->outer_mask, 64));
   CU(dalloc(&c->eps_d, 6 * 64));
   const int na = apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut);
-  const int np = precondition_blocks(c->fft, c->nX);
+  const int np =
+      std::max(precondition_blocks(c->fft, c->nX, true), precondition_blocks(c->fft, c->nX, false));
   const int ng = grad_blocks_uncut(c->g) + grad_blocks_cut(c->ncut);
   const int nparts = std::max(na, np);
   c->partials_count = std::max((size_t)n_rhs * 7 * nparts, (size_t)25 * ng);
@@ -436,7 +437,7 @@ static xfft_status ensure_work(xfft_ctx* c, int n_rhs, int prec) {
 
 static int nparts_of(const xfft_ctx* c) {
   return std::max(apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut),
-                  precondition_blocks(c->fft, c->nX));
+                  std::max(precondition_blocks(c->fft, c->nX, true), precondition_blocks(c->fft, c->nX, false)));
 }
 
 static ApplyArgs apply_args(const xfft_ctx* c, const double* eps, const int* active) {
@@ -539,7 +540,7 @@ static xfft_status do_prec(xfft_ctx* c, T* f, T* z, int n_rhs, const int* active
     fa.volY = c->g.volY;
     fa.maxit = maxit;
     fa.nparts = nparts;
-    fa.nparts_used = precondition_blocks(c->fft, c->nX);
+    fa.nparts_used = precondition_blocks(c->fft, c->nX, sizeof(T) == 8);
     fa.set_rel = set_rel;
     fa.inner_floor = c->opt.inner_tol;
     fa.parity = parity;
@@ -918,7 +919,7 @@ extern "C" xfft_status xfft_grad(xfft_ctx* c, const double dL_dCeff[36], double 
   if (!c->dscale) CU(dalloc(&c->dscale, g.N));
   {
     ProfScope ps(c, XFFT_PROF_GRAD, 3);
-    CU(launch_grad(c->U6, c->isD, cutdata(c), a, c->dscale, s));
+    CU(launch_grad(c->U6, c->isD, cutdata(c), a, c->dscale, c->opt.precision == XFFT_FP32_REFINED, s));
     CU(launch_reduce_partials(c->partials, 25, a.nparts, a.nparts, c->red_out, s));
   }
   double red[25];
@@ -1042,8 +1043,9 @@ static xfft_status prec_entry(xfft_ctx* c, int n_rhs, const double* f, double* z
   if (st == XFFT_OK) st = stage_out<T>(c, zz, z, tot, on_dev, scratch);
   if (st == XFFT_OK && rr) {
     const int nparts = nparts_of(c);
-    cudaError_t e = launch_reduce_partials(c->partials, n_rhs, nparts, precondition_blocks(c->fft, c->nX),
-                                           c->red_out, c->stream);
+    cudaError_t e = launch_reduce_partials(c->partials, n_rhs, nparts,
+                                           precondition_blocks(c->fft, c->nX, sizeof(T) == 8), c->red_out,
+                                           c->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(rr, c->red_out, n_rhs * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

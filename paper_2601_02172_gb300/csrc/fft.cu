@@ -52,8 +52,22 @@ struct FftPlan {
   int ytk_d, ytiles_d, ytk_f, ytiles_f;  // k2 tile in the y passes (double / float)
   int gtk_d, gtiles_d, gtk_f, gtiles_f;  // k2 tile in the Green pass (double / float)
   bool fast;        // every axis has a compile-time line plan (fft_fast.cu)
+  bool slab;        // FP32 y-z plane path (fft_slab.cu)
+  float* gtab;      // its Green factor table
   void* pool;
 };
+
+// slab path (fft_slab.cu)
+bool slab_supported(int n0, int n1, int n2);
+size_t slab_table_floats(int n0);
+int slab_z_blocks(int n0);
+cudaError_t slab_green_table(float* table, int n0, const void* const* ge, const void* const* gs,
+                             const double* ih, double halfvol, cudaStream_t s);
+cudaError_t slab_precondition(int n0, float* f, float* z, void* spec, long long stride, long long sstride,
+                              const int* active, const void* tw0, const void* tw1, const void* tw2,
+                              const float* table, const void* const* ge, const void* const* gs,
+                              const double* ih, double halfvol, unsigned long long* units, const float* q,
+                              const RhsState* st, double* partials, int nparts, int n_rhs, cudaStream_t s);
 
 // fast path (fft_fast.cu)
 bool fast_fft_supported(int n);
@@ -667,6 +681,26 @@ FftPlan* fft_plan_create(const GridDev& g, cudaError_t* err) {
     delete p;
     return nullptr;
   }
+  // slab path: Green factor table (depends on the grid only)
+  p->slab = false;
+  p->gtab = nullptr;
+  if (p->fast && slab_supported(g.n0, g.n1, g.n2)) {
+    *err = cudaMalloc(&p->gtab, slab_table_floats(g.n0) * sizeof(float));
+    if (*err == cudaSuccess) {
+      const void* ge[3] = {p->gef[0], p->gef[1], p->gef[2]};
+      const void* gs[3] = {p->gsf[0], p->gsf[1], p->gsf[2]};
+      const double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
+      *err = slab_green_table(p->gtab, g.n0, ge, gs, ih, 0.5 * g.vol_tet, 0);
+      if (*err == cudaSuccess) *err = cudaDeviceSynchronize();
+    }
+    if (*err != cudaSuccess) {
+      if (p->gtab) cudaFree(p->gtab);
+      cudaFree(pool);
+      delete p;
+      return nullptr;
+    }
+    p->slab = true;
+  }
   const int big = (int)need;
   cudaFuncSetAttribute(k_fft_z_r2c<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_fft_z_r2c<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -685,12 +719,14 @@ FftPlan* fft_plan_create(const GridDev& g, cudaError_t* err) {
 void fft_plan_destroy(FftPlan* p) {
   if (!p) return;
   if (p->pool) cudaFree(p->pool);
+  if (p->gtab) cudaFree(p->gtab);
   delete p;
 }
 
 size_t fft_spectrum_elems(const FftPlan* p) { return 3ULL * p->n[0] * p->n[1] * p->K2; }
 
-static int zpass_blocks(const FftPlan* p) {
+static int zpass_blocks(const FftPlan* p, bool dbl) {
+  if (p->slab && !dbl) return slab_z_blocks(p->n[0]);
   if (p->fast) return fast_z_blocks(p->n[0], p->n[1], p->n[2]);
   const long long rows = 3LL * p->n[0] * p->n[1];
   return (int)((rows + 2LL * p->xpairs - 1) / (2LL * p->xpairs));
@@ -704,7 +740,7 @@ static int enr_blocks(int nX) {
   return (int)nb;
 }
 
-int precondition_blocks(const FftPlan* p, int nX) { return zpass_blocks(p) + enr_blocks(nX); }
+int precondition_blocks(const FftPlan* p, int nX, bool dbl) { return zpass_blocks(p, dbl) + enr_blocks(nX); }
 
 template <typename T>
 cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long long stride,
@@ -721,7 +757,19 @@ cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long
   const C* tw0 = reinterpret_cast<const C*>(dbl ? (const void*)p->twd[0] : (const void*)p->twf[0]);
   const C* tw1 = reinterpret_cast<const C*>(dbl ? (const void*)p->twd[1] : (const void*)p->twf[1]);
   const C* tw2 = reinterpret_cast<const C*>(dbl ? (const void*)p->twd[a2] : (const void*)p->twf[a2]);
-  const int zb = zpass_blocks(p);
+  const int zb = zpass_blocks(p, dbl);
+  if (p->slab && !dbl) {
+    const void* ge[3] = {p->gef[0], p->gef[1], p->gef[2]};
+    const void* gs[3] = {p->gsf[0], p->gsf[1], p->gsf[2]};
+    const double ih[3] = {1.0 / p->g.h[0], 1.0 / p->g.h[1], 1.0 / p->g.h[2]};
+    cudaError_t e = slab_precondition(p->n[0], (float*)f, (float*)z, spec, stride, sstride, active, p->twf[0],
+                                      p->twf[1], p->twf[2], p->gtab, ge, gs, ih, 0.5 * p->g.vol_tet, units,
+                                      (const float*)q, st, partials, nparts, n_rhs, s);
+    if (e != cudaSuccess) return e;
+    k_enr_identity<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, 3LL * nX,
+                                                                  active, partials, nparts, zb, q, st);
+    return cudaGetLastError();
+  }
   if (p->fast) {
     const void* ge[3];
     const void* gs[3];

@@ -38,6 +38,8 @@ XFFT_PLAN(192, 24, 8, 8, 3, 1)
 XFFT_PLAN(256, 8, 8, 8, 4, 1)
 XFFT_PLAN(384, 24, 8, 8, 2, 3)
 #undef XFFT_PLAN
+// every length with a plan (host-side dispatch lists)
+#define XFFT_FAST_SIZES(X) X(16) X(32) X(48) X(64) X(80) X(96) X(128) X(192) X(256) X(384)
 
 template <typename C>
 __device__ __forceinline__ C cmul(C a, C b) {
@@ -240,6 +242,167 @@ __device__ __forceinline__ void line_fft(C* line, const C* __restrict__ tw, int 
   stage<C, N, E, P::R1, N1, INV>(line, tw, t);
   stage<C, N, E, P::R2, N2, INV>(line, tw, t);
   stage<C, N, E, P::R3, N3, INV>(line, tw, t);
+}
+
+// ---------------------------------------------------------------- Green operator
+// Cholesky factor of M(xi) = (|T|/2) sum_tets (|G|^2 I + G G^H) (see fft.cu); returns false
+// at xi = 0 or on a non-positive pivot (the Green operator then maps to 0).
+template <typename C, typename T>
+struct GreenFactor {
+  T il00, il11, il22;
+  C l10, l20, l21;
+};
+
+template <typename C, typename T>
+__device__ __forceinline__ bool green_factor(GreenFactor<C, T>& gf, C e0, C e1, C e2, C s0, C s1, C s2,
+                                             T ih0, T ih1, T ih2, T halfvol) {
+  C g[3];
+  g[0].x = s0.x * ih0;
+  g[0].y = s0.y * ih0;
+  g[1].x = s1.x * ih1;
+  g[1].y = s1.y * ih1;
+  g[2].x = s2.x * ih2;
+  g[2].y = s2.y * ih2;
+  const T a0 = g[0].x * g[0].x + g[0].y * g[0].y;
+  const T a1 = g[1].x * g[1].x + g[1].y * g[1].y;
+  const T a2 = g[2].x * g[2].x + g[2].y * g[2].y;
+  const T S = a0 + a1 + a2;
+  if (!(S > T(0))) return false;
+  const C e[3] = {e0, e1, e2};
+  C m01, m02, m12;
+  m01.x = m01.y = m02.x = m02.y = m12.x = m12.y = T(0);
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const int p = perm_p(t), q = perm_q(t), r = perm_r(t);
+    C G[3];
+    G[p] = g[p];
+    G[q] = cmul(e[p], g[q]);
+    G[r] = cmul(cmul(e[p], e[q]), g[r]);
+    m01 = cadd(m01, cmulc(G[0], G[1]));
+    m02 = cadd(m02, cmulc(G[0], G[2]));
+    m12 = cadd(m12, cmulc(G[1], G[2]));
+  }
+  const T d0 = halfvol * T(6) * (S + a0);
+  const T d1 = halfvol * T(6) * (S + a1);
+  const T d2 = halfvol * T(6) * (S + a2);
+  m01.x *= halfvol;
+  m01.y *= halfvol;
+  m02.x *= halfvol;
+  m02.y *= halfvol;
+  m12.x *= halfvol;
+  m12.y *= halfvol;
+  // M = L L^H with M(1,0) = conj(m01), M(2,0) = conj(m02), M(2,1) = conj(m12)
+  gf.il00 = T(1) / sqrt(d0);
+  gf.l10.x = m01.x * gf.il00;
+  gf.l10.y = -m01.y * gf.il00;
+  gf.l20.x = m02.x * gf.il00;
+  gf.l20.y = -m02.y * gf.il00;
+  const T l11sq = d1 - (gf.l10.x * gf.l10.x + gf.l10.y * gf.l10.y);
+  if (!(l11sq > T(0))) return false;
+  gf.il11 = T(1) / sqrt(l11sq);
+  C m21;
+  m21.x = m12.x;
+  m21.y = -m12.y;
+  const C t21 = csub(m21, cmulc(gf.l20, gf.l10));
+  gf.l21.x = t21.x * gf.il11;
+  gf.l21.y = t21.y * gf.il11;
+  const T l22sq = d2 - (gf.l20.x * gf.l20.x + gf.l20.y * gf.l20.y) - (gf.l21.x * gf.l21.x + gf.l21.y * gf.l21.y);
+  if (!(l22sq > T(0))) return false;
+  gf.il22 = T(1) / sqrt(l22sq);
+  return true;
+}
+
+template <typename C, typename T>
+__device__ __forceinline__ void green_solve(const GreenFactor<C, T>& gf, C& F0, C& F1, C& F2) {
+  C y0, y1, y2, t;
+  y0.x = F0.x * gf.il00;
+  y0.y = F0.y * gf.il00;
+  t = csub(F1, cmul(gf.l10, y0));
+  y1.x = t.x * gf.il11;
+  y1.y = t.y * gf.il11;
+  t = csub(csub(F2, cmul(gf.l20, y0)), cmul(gf.l21, y1));
+  y2.x = t.x * gf.il22;
+  y2.y = t.y * gf.il22;
+  C x0, x1, x2;
+  x2.x = y2.x * gf.il22;
+  x2.y = y2.y * gf.il22;
+  t = csub(y1, cmulc(x2, gf.l21));
+  x1.x = t.x * gf.il11;
+  x1.y = t.y * gf.il11;
+  t = csub(csub(y0, cmulc(x1, gf.l10)), cmulc(x2, gf.l20));
+  x0.x = t.x * gf.il00;
+  x0.y = t.y * gf.il00;
+  F0 = x0;
+  F1 = x1;
+  F2 = x2;
+}
+
+// block: (k2, j), all three components of a group of rg right-hand sides: 3 rg contiguous lines
+// of length N = n0.  The symbol of each frequency is factorised once and applied to every
+// right-hand side of the group.
+
+// ---------------------------------------------------------------- lines with an address map
+// The same stages on a line whose element m lives at map.at(m) (any shared-memory layout; the
+// maps of different lines must be disjoint).  The first stage may read its inputs through a
+// different map `ld0` (ld0.get(m) returns the value).  Threads with act == false take part in
+// the barriers only.
+template <typename C, int N, int E, int R, int NS, bool INV, class LD, class MAP>
+__device__ __forceinline__ void stage_map(const LD& ld, const MAP& mp, const C* __restrict__ tw, int t,
+                                          bool act) {
+  if (R == 1) return;
+  constexpr int T = N / E;
+  constexpr int NR = N / R;
+  constexpr int BPT = E / R;
+  C v[BPT][R];
+  if (act) {
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+      const int j = t + b * T;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = ld.get(j + r * NR);
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+      const int j = t + b * T;
+      const int jm = j % NS;
+      if (NS > 1) {
+        constexpr int step = N / (NS * R);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const C w = tw[r * jm * step];
+          v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+        }
+      }
+      Dft<C, R, INV>::run(v[b]);
+      const int base = (j / NS) * NS * R + jm;
+#pragma unroll
+      for (int r = 0; r < R; ++r) *mp.at(base + r * NS) = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename C, class MAP>
+struct MapLoad {  // reads through the line's own map
+  const MAP& m;
+  __device__ __forceinline__ C get(int k) const { return *m.at(k); }
+};
+
+// Line transform with E elements per thread (E divisible by every radix of Plan<N>).
+template <typename C, int N, int E, bool INV, class LD0, class MAP>
+__device__ __forceinline__ void line_fft_map(const LD0& ld0, const MAP& mp, const C* __restrict__ tw, int t,
+                                             bool act) {
+  typedef Plan<N> P;
+  static_assert(E % P::R0 == 0 && E % P::R1 == 0 && E % P::R2 == 0 && E % P::R3 == 0, "E vs radices");
+  constexpr int N1 = P::R0, N2 = P::R0 * P::R1, N3 = P::R0 * P::R1 * P::R2;
+  const MapLoad<C, MAP> ld{mp};
+  stage_map<C, N, E, P::R0, 1, INV>(ld0, mp, tw, t, act);
+  stage_map<C, N, E, P::R1, N1, INV>(ld, mp, tw, t, act);
+  stage_map<C, N, E, P::R2, N2, INV>(ld, mp, tw, t, act);
+  stage_map<C, N, E, P::R3, N3, INV>(ld, mp, tw, t, act);
 }
 
 }  // namespace fast

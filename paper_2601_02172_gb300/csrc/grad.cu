@@ -10,6 +10,10 @@
 //   dL/dmu_p     += s_v sum_kl G_kl int 2 eps_k : eps_l / |Y|
 //   dL/ds_v      += sum_kl G_kl int eps_k : C_p : eps_l / |Y|
 // and the energy form C_kl = int eps_k : C : eps_l / |Y| as a by-product.
+//
+// Arithmetic type T: double for the FP64 solver; float for the mixed-precision solver, where the
+// displacement differences are still formed in FP64 (they cancel) and only the strains and
+// their products are FP32, each item's contribution being accumulated in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -30,11 +34,13 @@ __device__ __forceinline__ void unit_strain(int k, double (&e)[6]) {
   e[k] = k < 3 ? 1.0 : r;
 }
 
-__device__ __forceinline__ double dd6(const double* a, const double* b) {
-  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + 2.0 * (a[3] * b[3] + a[4] * b[4] + a[5] * b[5]);
+template <typename T>
+__device__ __forceinline__ T dd6(const T* a, const T* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + T(2) * (a[3] * b[3] + a[4] * b[4] + a[5] * b[5]);
 }
 
 // block: 32 voxels (x) by 6 tets (y)
+template <typename T>
 __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U, const GradArgs a,
                                                      double* __restrict__ dscale) {
   __shared__ double sds[6][32];
@@ -49,6 +55,7 @@ __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U
   double ih[3];
   for (int k = 0; k < 3; ++k) ih[k] = 1.0 / g.h[k];
   double acc[kNG];
+#pragma unroll
   for (int i = 0; i < kNG; ++i) acc[i] = 0.0;
   const long long ngroups = (g.N + 31) / 32;
   for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
@@ -63,7 +70,8 @@ __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U
         long long nd[4];
         for (int c = 0; c < 4; ++c) nd[c] = corner_node(g, i3, j3, k3, tet_corner(t, c));
         const int p = perm_p(t), q = perm_q(t), r = perm_r(t);
-        double eps[6][6], tr[6];
+        T eps[6][6], tr[6];
+#pragma unroll
         for (int k = 0; k < 6; ++k) {
           const double* uk = U + k * a.stride;
           double H[3][3];
@@ -76,31 +84,33 @@ __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U
           }
           double E[6];
           unit_strain(k, E);
-          eps[k][0] = H[0][0] + E[0];
-          eps[k][1] = H[1][1] + E[1];
-          eps[k][2] = H[2][2] + E[2];
-          eps[k][3] = 0.5 * (H[1][2] + H[2][1]) + E[3];
-          eps[k][4] = 0.5 * (H[0][2] + H[2][0]) + E[4];
-          eps[k][5] = 0.5 * (H[0][1] + H[1][0]) + E[5];
+          eps[k][0] = (T)(H[0][0] + E[0]);
+          eps[k][1] = (T)(H[1][1] + E[1]);
+          eps[k][2] = (T)(H[2][2] + E[2]);
+          eps[k][3] = (T)(0.5 * (H[1][2] + H[2][1]) + E[3]);
+          eps[k][4] = (T)(0.5 * (H[0][2] + H[2][0]) + E[4]);
+          eps[k][5] = (T)(0.5 * (H[0][1] + H[1][0]) + E[5]);
           tr[k] = eps[k][0] + eps[k][1] + eps[k][2];
         }
         const int ph = (int)cd;
-        const double lam = a.ph.lam[ph], mu = a.ph.mu[ph];
+        const T lam = (T)a.ph.lam[ph], mu = (T)a.ph.mu[ph];
         const double sv = a.scale ? (double)a.scale[v] : 1.0;
         const double w = g.vol_tet * inv;
-        double ql = 0.0, qm = 0.0;
+        T ql = T(0), qm = T(0);
+#pragma unroll
         for (int k = 0; k < 6; ++k)
+#pragma unroll
           for (int l = k; l < 6; ++l) {
-            const double tt = tr[k] * tr[l];
-            const double ee = 2.0 * dd6(eps[k], eps[l]);
-            const double gk = (k == l) ? Gs[k * 6 + l] : Gs[k * 6 + l] + Gs[l * 6 + k];
+            const T tt = tr[k] * tr[l];
+            const T ee = T(2) * dd6(eps[k], eps[l]);
+            const T gk = (T)((k == l) ? Gs[k * 6 + l] : Gs[k * 6 + l] + Gs[l * 6 + k]);
             ql += gk * tt;
             qm += gk * ee;
-            acc[4 + upper_idx(k, l)] += w * sv * (lam * tt + mu * ee);
+            acc[4 + upper_idx(k, l)] += w * sv * (double)(lam * tt + mu * ee);
           }
-        acc[ph] += w * sv * ql;
-        acc[2 + ph] += w * sv * qm;
-        contrib = w * (lam * ql + mu * qm);
+        acc[ph] += w * sv * (double)ql;
+        acc[2 + ph] += w * sv * (double)qm;
+        contrib = w * (double)(lam * ql + mu * qm);
       }
     }
     sds[t][lane] = contrib;
@@ -115,6 +125,7 @@ __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U
     for (int i = 0; i < kNG; ++i) a.partials[(long long)i * a.nparts + blockIdx.x] = tot[i];
 }
 
+template <typename T>
 __global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
                                                   const double* __restrict__ isD, const CutData cd,
                                                   const GradArgs a, double* __restrict__ dscale) {
@@ -126,6 +137,7 @@ __global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
   double ih[3];
   for (int k = 0; k < 3; ++k) ih[k] = 1.0 / g.h[k];
   double acc[kNG];
+#pragma unroll
   for (int i = 0; i < kNG; ++i) acc[i] = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
     int nd[4], ei[4];
@@ -150,10 +162,10 @@ __global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
         c[b] = fabs(L[b]) - s * L[b];
         for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
       }
-      double M[10];
-      for (int k = 0; k < 10; ++k) M[k] = cd.dp[(long long)cut_f_M(si, k) * ncut + e];
-      double Eb[6][4][6];  // [load case][b][component]
-      double trb[6][4];
+      T M[10];
+      for (int k = 0; k < 10; ++k) M[k] = (T)cd.dp[(long long)cut_f_M(si, k) * ncut + e];
+      T Eb[6][4][6];  // [load case][b][component]
+      T trb[6][4];
       for (int k = 0; k < 6; ++k) {
         const double* uk = U + k * a.stride;
         double us[4][3], ws[4][3];
@@ -185,28 +197,29 @@ __global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
                                 0.5 * (wb[1] * gam[2] + wb[2] * gam[1]),
                                 0.5 * (wb[0] * gam[2] + wb[2] * gam[0]),
                                 0.5 * (wb[0] * gam[1] + wb[1] * gam[0])};
-          for (int x = 0; x < 6; ++x) Eb[k][b][x] = es[x] + c[b] * ew[x] + sw[x];
+          for (int x = 0; x < 6; ++x) Eb[k][b][x] = (T)(es[x] + c[b] * ew[x] + sw[x]);
           trb[k][b] = Eb[k][b][0] + Eb[k][b][1] + Eb[k][b][2];
         }
       }
-      double ql = 0.0, qm = 0.0;
+      T ql = T(0), qm = T(0);
+      const T lamT = (T)lam, muT = (T)mu;
       for (int k = 0; k < 6; ++k)
         for (int l = k; l < 6; ++l) {
-          double tt = 0.0, ee = 0.0;
+          T tt = T(0), ee = T(0);
           for (int b = 0; b < 4; ++b)
             for (int cc = 0; cc < 4; ++cc) {
-              const double m = M[midx(b, cc)];
+              const T m = M[midx(b, cc)];
               tt += m * trb[k][b] * trb[l][cc];
-              ee += m * 2.0 * dd6(Eb[k][b], Eb[l][cc]);
+              ee += m * T(2) * dd6(Eb[k][b], Eb[l][cc]);
             }
-          const double gk = (k == l) ? a.G[k * 6 + l] : a.G[k * 6 + l] + a.G[l * 6 + k];
+          const T gk = (T)((k == l) ? a.G[k * 6 + l] : a.G[k * 6 + l] + a.G[l * 6 + k]);
           ql += gk * tt;
           qm += gk * ee;
-          acc[4 + upper_idx(k, l)] += inv * sv * (lam * tt + mu * ee);
+          acc[4 + upper_idx(k, l)] += inv * sv * (double)(lamT * tt + muT * ee);
         }
-      acc[ph] += inv * sv * ql;
-      acc[2 + ph] += inv * sv * qm;
-      contrib += inv * (lam * ql + mu * qm);
+      acc[ph] += inv * sv * (double)ql;
+      acc[2 + ph] += inv * sv * (double)qm;
+      contrib += inv * (double)(lamT * ql + muT * qm);
     }
     atomicAdd(&dscale[vox], contrib);
   }
@@ -227,11 +240,17 @@ int grad_blocks_cut(int ncut) {
 }
 
 cudaError_t launch_grad(const double* U, const double* isD, CutData cd, const GradArgs& a,
-                        double* dscale, cudaStream_t s) {
-  k_grad_uncut<<<grad_blocks_uncut(a.g), dim3(32, 6), 0, s>>>(U, a, dscale);
+                        double* dscale, bool fp32, cudaStream_t s) {
+  if (fp32)
+    k_grad_uncut<float><<<grad_blocks_uncut(a.g), dim3(32, 6), 0, s>>>(U, a, dscale);
+  else
+    k_grad_uncut<double><<<grad_blocks_uncut(a.g), dim3(32, 6), 0, s>>>(U, a, dscale);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_grad_cut<<<grad_blocks_cut(cd.ncut), 64, 0, s>>>(U, isD, cd, a, dscale);
+  if (fp32)
+    k_grad_cut<float><<<grad_blocks_cut(cd.ncut), 64, 0, s>>>(U, isD, cd, a, dscale);
+  else
+    k_grad_cut<double><<<grad_blocks_cut(cd.ncut), 64, 0, s>>>(U, isD, cd, a, dscale);
   return cudaGetLastError();
 }
 

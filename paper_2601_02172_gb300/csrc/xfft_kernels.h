@@ -107,7 +107,8 @@ cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec, long l
                                 int nX, const int* active, double* partials, int nparts,
                                 int n_rhs, cudaStream_t s, unsigned long long* units = nullptr,
                                 const T* q = nullptr, const RhsState* st = nullptr);
-int precondition_blocks(const FftPlan* p, int nX);
+// partial-sum slots written by one precondition call (FP64 or FP32 kernels)
+int precondition_blocks(const FftPlan* p, int nX, bool dbl);
 
 // ---- CG vector ops and scalar finalisation (cg.cu)
 template <typename T>
@@ -165,8 +166,9 @@ struct GradArgs {
   int nparts;
   int part_offset_cut;
 };
+// fp32: strain products in FP32 (mixed-precision solver), else all FP64
 cudaError_t launch_grad(const double* U, const double* isD, CutData cd, const GradArgs& a,
-                        double* dscale, cudaStream_t s);
+                        double* dscale, bool fp32, cudaStream_t s);
 int grad_blocks_uncut(const GridDev& g);
 int grad_blocks_cut(int ncut);
 cudaError_t launch_reduce_partials(const double* partials, int nvals, int nparts, int ncount,

@@ -196,6 +196,26 @@ def test_fp32_refined_effective_stiffness(xf):
     assert np.abs(C - Cs).max() < 1e-6 * np.abs(Cs).max()
 
 
+def test_fp32_refined_gradient(xf):
+    """Mixed-precision solver: FP32 strain products (FP64 differences and sums) stay within the
+    accuracy of the tol-limited solution."""
+    n, ell, L, lm, lp, sc = _case("ragged")
+    s = xf.Solver(n, ell, precision="fp32", tol=1e-10)
+    s.set_microstructure(L, lm, lp, sc)
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    C, st = s.effective_stiffness()
+    assert st["converged"], st
+    Cs, Ce, U = o.effective_stiffness()
+    G = np.random.default_rng(2).normal(size=(6, 6))
+    dl, ds, Cenergy = s.grad(G)
+    assert np.abs(Cenergy - Ce).max() < 1e-6 * np.abs(Ce).max()
+    dlr, dsr = o.stiffness_gradient(U)
+    ref_l = np.einsum("kl,pkl->p", G, dlr)
+    ref_s = np.einsum("kl,vkl->v", G, dsr)
+    assert np.abs(dl - ref_l).max() < 1e-5 * np.abs(ref_l).max()
+    assert _rel(ds.astype(np.float64), ref_s) < 1e-5
+
+
 def test_gradient_against_finite_differences(xf):
     n = (8, 8, 8)
     L = synth.sphere_levelset(n, (0.45, 0.5, 0.55), 0.3)
@@ -240,6 +260,49 @@ def test_laminate_closed_form_gpu(xf):
         C, st = s.effective_stiffness()
         assert st["converged"], st
         assert np.abs(C - Cref).max() < tol * np.abs(Cref).max(), (prec, np.abs(C - Cref).max())
+
+
+def _slab_modes(rng):
+    """Fourier modes for a 16 x 128 x 128 grid that reach every line type of the FP32 y-z plane
+    path: z frequencies 0 and 64 (real z lines) with y frequencies 0, 64 and others, x
+    frequencies 0 and 8 (Nyquist), odd and even y frequencies, and generic modes."""
+    ks = [(0, 0, 1), (1, 0, 0), (8, 0, 0), (3, 0, 64), (0, 64, 0), (8, 64, 64), (5, 64, 0),
+          (2, 7, 0), (6, 100, 0), (4, 9, 64), (7, 120, 64), (3, 64, 5), (1, 2, 3), (9, 33, 17),
+          (15, 127, 127), (8, 1, 63), (0, 77, 40), (11, 64, 64), (12, 0, 64), (0, 0, 64)]
+    ks += [tuple(int(v) for v in rng.integers(0, (16, 128, 128))) for _ in range(12)]
+    return [(k, rng.normal(size=3) + 1j * rng.normal(size=3)) for k in ks]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_precondition_plane_waves_yz128(xf, prec):
+    """y-z planes of 128 x 128 (the FP32 slab path) against the oracle's exact single-mode
+    preconditioner, element by element over the whole grid."""
+    n = (16, 128, 128)
+    s = xf.Solver(n)
+    s.set_microstructure(np.ones(n), synth.lame_from_E_nu(2.0, 0.3), synth.lame_from_E_nu(1.0, 0.3))
+    o = XFEM(np.ones(n), n)
+    f, zref = o.precondition_modes(_slab_modes(np.random.default_rng(11)))
+    z, rr = s.precondition(f[None, :], precision=prec)
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    assert _rel(z[0], zref) < tol
+    assert np.abs(z[0] - zref).max() < 10 * tol * np.abs(zref).max()
+    assert abs(rr[0] - f @ zref) <= 10 * tol * abs(f @ zref)
+
+
+def test_laminate_closed_form_yz128(xf):
+    """Full FP32-refined solve through the y-z plane path: planar interface, exact C_eff."""
+    from tests.test_oracle_pins import _laminate_closed_form
+    n = (16, 128, 128)
+    normal = (1, 2, 3)
+    L = synth.laminate_levelset(n, normal=normal, offset=0.1234567, fraction=0.5)
+    lm = synth.lame_from_E_nu(100.0, 0.2)
+    lp = synth.lame_from_E_nu(1.0, 0.3)
+    Cref = _laminate_closed_form(normal, 0.5, lm, lp)
+    s = xf.Solver(n, precision="fp32", tol=1e-11)
+    s.set_microstructure(L, lm, lp)
+    C, st = s.effective_stiffness()
+    assert st["converged"], st
+    assert np.abs(C - Cref).max() < 1e-6 * np.abs(Cref).max(), np.abs(C - Cref).max()
 
 
 def test_homogeneous_and_equal_phase_edge_cases(xf):
