@@ -38,6 +38,15 @@ XFFT_PLAN(192, 24, 8, 8, 3, 1)
 XFFT_PLAN(256, 8, 8, 8, 4, 1)
 XFFT_PLAN(384, 24, 8, 8, 2, 3)
 #undef XFFT_PLAN
+// radix sequence for E elements per thread (the default plan, or fewer passes where E allows)
+template <int N, int E>
+struct PlanE {
+  static constexpr int R0 = Plan<N>::R0, R1 = Plan<N>::R1, R2 = Plan<N>::R2, R3 = Plan<N>::R3;
+};
+template <>
+struct PlanE<128, 16> {
+  static constexpr int R0 = 16, R1 = 8, R2 = 1, R3 = 1;
+};
 // every length with a plan (host-side dispatch lists)
 #define XFFT_FAST_SIZES(X) X(16) X(32) X(48) X(64) X(80) X(96) X(128) X(192) X(256) X(384)
 
@@ -187,6 +196,54 @@ struct Dft<C, 8, INV> {
     v[6] = csub(e[2], w2);
     v[3] = cadd(e[3], w3);
     v[7] = csub(e[3], w3);
+  }
+};
+
+// radix 16 = 4 x 4: inputs n = 4a + b, outputs k = c + 4d; DFT4 over a, twiddle W16^(b c),
+// DFT4 over b.  c1 = cos(pi/8), s1 = sin(pi/8)
+template <typename C, bool INV>
+struct Dft<C, 16, INV> {
+  __device__ __forceinline__ static void run(C* v) {
+    typedef decltype(v[0].x) T;
+    const T c1 = (T)0.92387953251128675613;
+    const T s1 = (T)0.38268343236508977173;
+    const T r = (T)0.70710678118654752440;
+    const T sg = INV ? T(1) : T(-1);  // sign of the imaginary part of W16^1
+    C y[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      C t[4] = {v[b], v[b + 4], v[b + 8], v[b + 12]};
+      Dft<C, 4, INV>::run(t);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) y[b][c] = t[c];
+    }
+    C w1, w2, w3, w6, w9;
+    w1.x = c1;
+    w1.y = sg * s1;
+    w2.x = r;
+    w2.y = sg * r;
+    w3.x = s1;
+    w3.y = sg * c1;
+    w6.x = -r;
+    w6.y = sg * r;
+    w9.x = -c1;
+    w9.y = -sg * s1;
+    y[1][1] = cmul(y[1][1], w1);
+    y[1][2] = cmul(y[1][2], w2);
+    y[1][3] = cmul(y[1][3], w3);
+    y[2][1] = cmul(y[2][1], w2);
+    y[2][2] = mul_mi<C, INV>(y[2][2]);  // W16^4 = -+i
+    y[2][3] = cmul(y[2][3], w6);
+    y[3][1] = cmul(y[3][1], w3);
+    y[3][2] = cmul(y[3][2], w6);
+    y[3][3] = cmul(y[3][3], w9);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      C t[4] = {y[0][c], y[1][c], y[2][c], y[3][c]};
+      Dft<C, 4, INV>::run(t);
+#pragma unroll
+      for (int d = 0; d < 4; ++d) v[c + 4 * d] = t[d];
+    }
   }
 };
 
@@ -395,7 +452,7 @@ struct MapLoad {  // reads through the line's own map
 template <typename C, int N, int E, bool INV, class LD0, class MAP>
 __device__ __forceinline__ void line_fft_map(const LD0& ld0, const MAP& mp, const C* __restrict__ tw, int t,
                                              bool act) {
-  typedef Plan<N> P;
+  typedef PlanE<N, E> P;
   static_assert(E % P::R0 == 0 && E % P::R1 == 0 && E % P::R2 == 0 && E % P::R3 == 0, "E vs radices");
   constexpr int N1 = P::R0, N2 = P::R0 * P::R1, N3 = P::R0 * P::R1 * P::R2;
   const MapLoad<C, MAP> ld{mp};

@@ -32,6 +32,7 @@ constexpr int N1 = 128;                    // y length
 constexpr int N2 = 128;                    // z length
 constexpr int H2 = N2 / 2;
 constexpr int PL = N1 * N2 / 2;            // complex values per packed plane
+constexpr int RS = N2 + 1;                 // shared-memory row stride (odd: lines at distinct banks)
 constexpr int E = 16;                      // elements per thread of the y and z line transforms
 constexpr int NT = N1 * N2 / (2 * E);      // threads of the plane kernels (512)
 constexpr int kGF = 9;                     // floats per Green factor: il00, il11, il22, l10, l20, l21
@@ -57,7 +58,7 @@ struct RealPair {  // first forward z stage: rows 2p and 2p+1 as real and imagin
 struct YLine {  // y line: even positions in slot s0, odd positions in slot s1
   float2* buf;
   int s0, s1;
-  __device__ __forceinline__ float2* at(int m) const { return buf + (m >> 1) * N2 + ((m & 1) ? s1 : s0); }
+  __device__ __forceinline__ float2* at(int m) const { return buf + (m >> 1) * RS + ((m & 1) ? s1 : s0); }
 };
 __device__ __forceinline__ YLine yline(float2* buf, int L) {
   YLine y;
@@ -105,22 +106,23 @@ __global__ void __launch_bounds__(NT, 2) ks_fwd(float* __restrict__ f, float2* _
         v -= alpha * qv[e];  // fused CG update f -= alpha A d
         fp[idx] = v;
       }
-      bf[idx] = v;
+      // real row j goes to the first (j even) or second half of line j/2 (stride RS complex)
+      const int j = idx / N2, k = idx - j * N2;
+      bf[2 * (j >> 1) * RS + (j & 1) * N2 + k] = v;
     }
   }
   __syncthreads();
-  {  // z: one complex line per row pair (threads line-major)
-    constexpr int TL = N2 / E;
-    const int p = threadIdx.x / TL, t = threadIdx.x - p * TL;
-    const RealPair ld0{bf + 2 * p * N2, bf + (2 * p + 1) * N2};
-    const ZLine mp{buf + p * N2};
+  {  // z: one complex line per row pair (threads line-minor: a warp spans 32 lines)
+    const int p = threadIdx.x % (N1 / 2), t = threadIdx.x / (N1 / 2);
+    const RealPair ld0{bf + 2 * p * RS, bf + 2 * p * RS + N2};
+    const ZLine mp{buf + p * RS};
     line_fft_map<float2, N2, E, false>(ld0, mp, tws2, t, true);
   }
   // split each row pair into its two half spectra (in place) and move the real k2 = 0 and
   // k2 = n2/2 values into the packed y line
   for (int idx = threadIdx.x; idx < (N1 / 2) * H2; idx += NT) {
     const int p = idx / H2, k = idx - p * H2;
-    float2* row = buf + p * N2;
+    float2* row = buf + p * RS;
     if (k == 0) {
       const float2 a = row[0], b = row[H2];
       row[0] = make_float2(a.x, b.x);
@@ -148,9 +150,11 @@ __global__ void __launch_bounds__(NT, 2) ks_fwd(float* __restrict__ f, float2* _
     }
   }
   __syncthreads();
-  float4* out = reinterpret_cast<float4*>(spec + rhs * sstride + ((long long)c * n0 + i) * PL);
-  const float4* src = reinterpret_cast<const float4*>(buf);
-  for (int k = threadIdx.x; k < PL / 2; k += NT) out[k] = src[k];
+  float2* out = spec + rhs * sstride + ((long long)c * n0 + i) * PL;
+  for (int k = threadIdx.x; k < PL; k += NT) {
+    const int row = k / N2, sl = k - row * N2;
+    out[k] = buf[row * RS + sl];
+  }
 }
 
 // ---------------------------------------------------------------- inverse plane pass
@@ -171,14 +175,17 @@ __global__ void __launch_bounds__(NT, 2) ks_inv(const float2* __restrict__ spec,
   for (int k = threadIdx.x; k < N1; k += NT) tws1[k] = tw1[k];
   for (int k = threadIdx.x; k < N2; k += NT) tws2[k] = tw2[k];
   {
-    const float4* in = reinterpret_cast<const float4*>(spec + rhs * sstride + ((long long)c * n0 + i) * PL);
-    float4* dst = reinterpret_cast<float4*>(buf);
-    constexpr int PER = PL / 2 / NT;
-    float4 v[PER];
+    const float2* in = spec + rhs * sstride + ((long long)c * n0 + i) * PL;
+    constexpr int PER = PL / NT;
+    float2 v[PER];
 #pragma unroll
     for (int e = 0; e < PER; ++e) v[e] = in[threadIdx.x + e * NT];
 #pragma unroll
-    for (int e = 0; e < PER; ++e) dst[threadIdx.x + e * NT] = v[e];
+    for (int e = 0; e < PER; ++e) {
+      const int k = threadIdx.x + e * NT;
+      const int row = k / N2, sl = k - row * N2;
+      buf[row * RS + sl] = v[e];
+    }
   }
   __syncthreads();
   {  // rebuild the packed y line Y = A + i B (both Hermitian in ky)
@@ -200,7 +207,7 @@ __global__ void __launch_bounds__(NT, 2) ks_inv(const float2* __restrict__ spec,
   // undo the packing of the real z lines and rebuild Z_k = X_k + i Y_k of each row pair
   for (int idx = threadIdx.x; idx < (N1 / 2) * H2; idx += NT) {
     const int p = idx / H2, k = idx - p * H2;
-    float2* row = buf + p * N2;
+    float2* row = buf + p * RS;
     if (k == 0) {
       const float2 a = row[0], b = row[H2];
       row[0] = make_float2(a.x, b.x);
@@ -213,9 +220,8 @@ __global__ void __launch_bounds__(NT, 2) ks_inv(const float2* __restrict__ spec,
   }
   __syncthreads();
   {
-    constexpr int TL = N2 / E;
-    const int p = threadIdx.x / TL, t = threadIdx.x - p * TL;
-    const ZLine mp{buf + p * N2};
+    const int p = threadIdx.x % (N1 / 2), t = threadIdx.x / (N1 / 2);
+    const ZLine mp{buf + p * RS};
     line_fft_map<float2, N2, E, true>(MapLoad<float2, ZLine>{mp}, mp, tws2, t, true);
   }
   const long long N3 = (long long)n0 * N1 * N2;
@@ -232,7 +238,7 @@ __global__ void __launch_bounds__(NT, 2) ks_inv(const float2* __restrict__ spec,
       const int idx = threadIdx.x + e * NT;
       const int j = idx / N2, k = idx - j * N2;
       // row j is the real (j even) or imaginary (j odd) part of line j/2
-      const float val = bf[2 * ((j >> 1) * N2 + k) + (j & 1)] * scale;
+      const float val = bf[2 * ((j >> 1) * RS + k) + (j & 1)] * scale;
       zp[idx] = val;
       acc += val * fv[e];
     }
@@ -269,7 +275,7 @@ __device__ __forceinline__ void line_freq(int R, int s, int& ky, int& k2, bool& 
   }
 }
 
-// table[f][kx][R][s]: the Cholesky factor of the symbol at (kx, line (R, s)) (k2 = 0 for the
+// table[f][R][s][kx]: the Cholesky factor of the symbol at (kx, line (R, s)) (k2 = 0 for the
 // packed pairs); a zero factor where the symbol vanishes (xi = 0)
 __global__ void k_green_table(float* __restrict__ table, int n0, const float2* __restrict__ ge0,
                               const float2* __restrict__ ge1, const float2* __restrict__ ge2,
@@ -279,8 +285,8 @@ __global__ void k_green_table(float* __restrict__ table, int n0, const float2* _
   const long long n = (long long)n0 * PL;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int kx = (int)(idx / PL);
-    const int rs = (int)(idx - (long long)kx * PL);
+    const int rs = (int)(idx / n0);
+    const int kx = (int)(idx - (long long)rs * n0);
     const int R = rs / N2, s = rs - R * N2;
     int ky, k2;
     bool pair;
@@ -364,19 +370,20 @@ __global__ void __launch_bounds__(XCfg<N0>::THREADS, XCfg<N0>::MINB)
     }
   }
   __syncthreads();
-  const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
+  // threads line-minor (a warp spans consecutive lines; LS odd keeps them on distinct banks)
+  const int line = threadIdx.x % LINES, t = threadIdx.x / LINES;
   {
     const ZLine mp{buf + line * LS};
     line_fft_map<float2, N0, EX, false>(MapLoad<float2, ZLine>{mp}, mp, tws, t, true);
   }
   const long long ntab = (long long)N0 * PL;
   for (int it = threadIdx.x; it < ST * N0; it += NTX) {
-    const int sl = it % ST, kx = it / ST;
+    const int sl = it / N0, kx = it - sl * N0;
     const int s = s0 + sl;
     int ky, k2;
     bool pair;
     line_freq(R, s, ky, k2, pair);
-    const long long tidx = (long long)kx * PL + R * N2 + s;
+    const long long tidx = (long long)(R * N2 + s) * N0 + kx;
     if (!pair) {
       const fast::GreenFactor<float2, float> gf = load_factor(table, ntab, tidx);
       for (int r = 0; r < RG; ++r) {
@@ -475,7 +482,7 @@ cudaError_t slab_precondition(int n0, float* f, float* z, void* spec, long long 
                               const double* ih, double halfvol, unsigned long long* units, const float* q,
                               const RhsState* st, double* partials, int nparts, int n_rhs, cudaStream_t s) {
   using namespace slab;
-  const size_t smp = sizeof(float2) * (N1 + N2 + (size_t)PL);
+  const size_t smp = sizeof(float2) * (N1 + N2 + (size_t)(N1 / 2) * RS);
   cudaError_t e = slab_smem((const void*)ks_fwd, smp);
   if (e == cudaSuccess) e = slab_smem((const void*)ks_inv, smp);
   if (e != cudaSuccess) return e;
