@@ -317,6 +317,9 @@ class XFEM:
         """Scaling factors D0 per enriched DOF (eq. XFFT_diagonal, per-DOF reading) and the
         quadrature data of every cut tet."""
         self.D = np.zeros((self.nX, 3))
+        # Dblk[j] = int sym(grad N_X^j (x) e_k) : sym(grad N_X^j (x) e_l), k, l = 1..3: the 3x3
+        # node block of the enriched-enriched reference Gram matrix; its diagonal is D0
+        self.Dblk = np.zeros((self.nX, 3, 3))
         self.cut_data = []
         for v, t in self.cut_list:
             Lv, sides = self._cut_tet_points(v, t)
@@ -326,12 +329,16 @@ class XFEM:
                 bary, w = sides[s]
                 BX = self._enriched_B(G, Lv, s, bary)  # (nq, 6, 12)
                 sq = np.einsum("q,qrk->k", w, BX * BX).reshape(4, 3)
+                gram = np.einsum("q,qrk,qrl->kl", w, BX, BX)  # (12, 12)
                 for a in range(4):
                     self.D[eids[a]] += sq[a]
+                    self.Dblk[eids[a]] += gram[3 * a:3 * a + 3, 3 * a:3 * a + 3]
             self.cut_data.append((Lv, sides))
         if self.nX and np.any(self.D <= 0.0):
             raise ValueError("non-positive enrichment scaling factor")
         self.Dinvsqrt = 1.0 / np.sqrt(self.D) if self.nX else np.zeros((0, 3))
+        # scaled blocks (unit diagonal): the variant enriched preconditioner's 3x3 blocks
+        self.Bblk = self.Dblk * self.Dinvsqrt[:, :, None] * self.Dinvsqrt[:, None, :]
 
     def _C(self, s, v):
         lam, mu = self.lame[s]
@@ -554,13 +561,27 @@ class XFEM:
             return np.real(np.fft.ifftn(G, axes=(1, 2, 3))).ravel()
         return apply
 
-    def precondition(self, f, green="sparse"):
-        """z = P^{-1} f with P = diag(A0_11, I) (eq. scaledPreconditioner)."""
+    def _enr_precondition(self, fX, enr):
+        """Enriched part of P^{-1}: the identity on the scaled DOFs (eq. scaledPreconditioner,
+        the paper's choice) or, for enr="block3", the inverse of each enriched node's 3x3 block
+        of the scaled reference Gram matrix (a variant, not in the paper).  fX is component-major
+        (3, nX) flattened."""
+        if enr == "identity":
+            return fX.copy()
+        if enr != "block3":
+            raise ValueError(enr)
+        F = fX.reshape(3, self.nX).T  # (nX, 3)
+        Z = np.linalg.solve(self.Bblk, F[:, :, None])[:, :, 0]
+        return Z.T.ravel()
+
+    def precondition(self, f, green="sparse", enr="identity"):
+        """z = P^{-1} f with P = diag(A0_11, I) (eq. scaledPreconditioner); enr="block3" uses the
+        node blocks of the enriched reference Gram matrix instead of I."""
         n3 = 3 * self.nFE
         g = self._green_sparse() if green == "sparse" else self._green_fft()
         z = np.empty_like(f)
         z[:n3] = g(f[:n3])
-        z[n3:] = f[n3:]
+        z[n3:] = self._enr_precondition(f[n3:], enr)
         return z
 
     def mean_stress(self, u, eps):
@@ -569,7 +590,7 @@ class XFEM:
             self.assemble()
         return (np.asarray(self.Sm @ u).ravel() + self.Cbar @ np.asarray(eps, float)) / self.volY
 
-    def pcg(self, eps, tol=1e-10, maxit=10000, green="sparse", u0=None):
+    def pcg(self, eps, tol=1e-10, maxit=10000, green="sparse", u0=None, enr="identity"):
         """Linear CG of Algorithm 1 on A u = -b with the X-FFT preconditioner.
 
         Reading of Algorithm 1: f is the negative residual -b - A u, z = A d is the linear part
@@ -586,7 +607,7 @@ class XFEM:
         def P(f):
             z = np.empty_like(f)
             z[:n3] = gfun(f[:n3])
-            z[n3:] = f[n3:]
+            z[n3:] = self._enr_precondition(f[n3:], enr)
             return z
 
         b = self.rhs(eps)
