@@ -63,6 +63,13 @@ typedef enum {
  * significant bits, run on the FP32 units) is used by XFFT_FP32_REFINED for its residuals and
  * stress integrals; xfft_apply also accepts it directly. */
 enum { XFFT_FP64 = 0, XFFT_FP32_REFINED = 1, XFFT_DW = 2 };
+/* Preconditioner on the enriched DOFs.  XFFT_ENR_IDENTITY: the identity on the scaled DOFs,
+ * P = diag(A0_11, I) (eq. scaledPreconditioner; the paper's choice).  XFFT_ENR_BLOCK3 (a variant,
+ * not in the paper): per enriched node j the inverse of the 3x3 block
+ *   B_j,kl = D0_jk^-1/2 D0_jl^-1/2 int sym(grad N_X^j (x) e_k) : sym(grad N_X^j (x) e_l)
+ * of the scaled enriched reference Gram matrix (unit diagonal by eq. XFFT_diagonal), factorised
+ * in FP64 at xfft_set_microstructure (XFFT_EBREAKDOWN if a block is not positive definite).
+ * The discrete system and its solution do not depend on this choice; iteration counts do. */
 enum { XFFT_ENR_IDENTITY = 0, XFFT_ENR_BLOCK3 = 1 };
 
 typedef struct {
@@ -77,7 +84,7 @@ typedef struct {
                           stoppingCriterion, convergence) */
   int maxit;           /* CG iteration cap (FP64) or inner cap per refinement step */
   double snap_tau;     /* |L| < snap_tau counts as on the interface (Sec. 3); <= 0: 1e-6 * min h */
-  int enr_precond;     /* XFFT_ENR_IDENTITY (the paper's choice) */
+  int enr_precond;     /* XFFT_ENR_IDENTITY (the paper's choice) or XFFT_ENR_BLOCK3 */
   double inner_tol;    /* FP32_REFINED: smallest relative residual reduction asked of one FP32
                           inner solve (each inner solve aims at half the outer tolerance) */
   int max_refine;      /* FP32_REFINED: cap on FP64 refinement steps */

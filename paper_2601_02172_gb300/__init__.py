@@ -5,3 +5,9 @@ The compute path is the CUDA library ``libxfft.so`` (sources in ``csrc/``, C-ABI
 """
 from .build import build  # noqa: F401
 from .capi import Solver, XfftError, lib  # noqa: F401
+
+
+def effective_stiffness(solver, L, lame, scale=None):
+    """Differentiable C_eff (torch) of a microstructure; see ``autograd.py``."""
+    from .autograd import effective_stiffness as _f
+    return _f(solver, L, lame, scale)

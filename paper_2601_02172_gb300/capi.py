@@ -133,7 +133,8 @@ class Solver:
     """One grid on the current CUDA device (thin wrapper of ``xfft_ctx``)."""
 
     def __init__(self, n, length=(1.0, 1.0, 1.0), precision="fp64", tol=1e-10, maxit=10000,
-                 snap_tau=0.0, inner_tol=1e-5, max_refine=20, poll_every=8, stream=None):
+                 snap_tau=0.0, inner_tol=1e-5, max_refine=20, poll_every=8, stream=None,
+                 enr_precond="identity"):
         L = lib()
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
@@ -151,6 +152,7 @@ class Solver:
         o.inner_tol = inner_tol
         o.max_refine = max_refine
         o.poll_every = poll_every
+        o.enr_precond = {"identity": 0, "block3": 1}[enr_precond]
         self.precision = precision
         self._ctx = C.c_void_p()
         check(L.xfft_create(C.byref(self._ctx), C.byref(g), C.byref(o),

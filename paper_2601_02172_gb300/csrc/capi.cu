@@ -80,6 +80,10 @@ struct xfft_ctx {
   double* D = nullptr;
   double* isD = nullptr;
   float* isF = nullptr;
+  // block enriched preconditioner: off-diagonal block entries and the inverse blocks
+  double* Doff = nullptr;
+  double* eb64 = nullptr;
+  float* eb32 = nullptr;
   FftPlan* fft = nullptr;
   // solver workspace
   int cap_rhs = 0;
@@ -233,8 +237,8 @@ extern "C" xfft_status xfft_create(xfft_ctx** out, const xfft_grid* grid, const 
   if (opt) o = *opt;
   if (o.precision != XFFT_FP64 && o.precision != XFFT_FP32_REFINED)
     return fail(XFFT_EINVAL, "unknown precision");
-  if (o.enr_precond != XFFT_ENR_IDENTITY)
-    return fail(XFFT_EUNSUPPORTED, "only the identity enriched preconditioner is built");
+  if (o.enr_precond != XFFT_ENR_IDENTITY && o.enr_precond != XFFT_ENR_BLOCK3)
+    return fail(XFFT_EINVAL, "unknown enriched preconditioner");
   if (!(o.tol > 0.0) || o.maxit < 1 || o.poll_every < 1 || o.max_refine < 1 || !(o.inner_tol > 0.0))
     return fail(XFFT_EINVAL, "invalid options");
   xfft_ctx* c = new xfft_ctx();
@@ -283,6 +287,9 @@ static void free_micro(xfft_ctx* c) {
   dfree(c->D);
   dfree(c->isD);
   dfree(c->isF);
+  dfree(c->Doff);
+  dfree(c->eb64);
+  dfree(c->eb32);
   dfree(c->U6);
   dfree(c->dscale);
   dfree(c->dscale_f);
@@ -392,8 +399,23 @@ extern "C" xfft_status xfft_set_microstructure(xfft_ctx* c, const double* L, con
   CU(dalloc(&c->D, 3 * (size_t)c->nX));
   CU(dalloc(&c->isD, 3 * (size_t)c->nX));
   CU(dalloc(&c->isF, 3 * (size_t)c->nX));
-  CU(launch_cut_scaling(cd, c->D, c->nX, g, s));
+  const bool blk = c->opt.enr_precond == XFFT_ENR_BLOCK3;
+  if (blk) {
+    CU(dalloc(&c->Doff, 3 * (size_t)c->nX));
+    CU(dalloc(&c->eb64, 6 * (size_t)c->nX));
+    CU(dalloc(&c->eb32, 6 * (size_t)c->nX));
+  }
+  CU(launch_cut_scaling(cd, c->D, blk ? c->Doff : nullptr, c->nX, g, s));
   CU(launch_finish_scaling(c->D, c->isD, c->isF, c->nX, s));
+  if (blk) {
+    int* bad = c->d_tot + 2;
+    CU(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    CU(launch_block_inverse(c->D, c->Doff, c->isD, c->eb64, c->eb32, c->nX, bad, s));
+    int hbad = 0;
+    CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (hbad) return fail(XFFT_EBREAKDOWN, "an enriched 3x3 block is not positive definite");
+  }
   CU(launch_cut_to_float(c->cut_dp, c->cut_fp, (long long)kCutReals * c->ncut, s));
   CU(cudaEventRecord(c->ev1, s));
   CU(cudaStreamSynchronize(s));
@@ -474,6 +496,18 @@ const float* isd_of<float>(const xfft_ctx* c) {
   return c->isF;
 }
 
+// inverse enriched blocks (block enriched preconditioner) or nullptr (identity)
+template <typename T>
+static const T* enr_block_of(const xfft_ctx* c);
+template <>
+const double* enr_block_of<double>(const xfft_ctx* c) {
+  return c->opt.enr_precond == XFFT_ENR_BLOCK3 ? c->eb64 : nullptr;
+}
+template <>
+const float* enr_block_of<float>(const xfft_ctx* c) {
+  return c->opt.enr_precond == XFFT_ENR_BLOCK3 ? c->eb32 : nullptr;
+}
+
 // q = A d (+ b(eps)); finalisation `mode` (0 or 1) on the apply partials
 // T: storage type of the vectors; A: arithmetic type of the kernels (T, or dw on FP64 data)
 template <typename T, typename A = T>
@@ -529,7 +563,8 @@ static xfft_status do_prec(xfft_ctx* c, T* f, T* z, int n_rhs, const int* active
     const int kp = sizeof(T) == 8 ? XFFT_PROF_PREC_F64 : XFFT_PROF_PREC_F32;
     ProfScope ps(c, kp, 6);
     CU(launch_precondition<T>(c->fft, f, z, c->spec, stride_of(c), c->nX, active, c->partials, nparts,
-                              n_rhs, c->stream, punit(c, kp), qfuse, qfuse ? c->st : nullptr));
+                              n_rhs, c->stream, punit(c, kp), qfuse, qfuse ? c->st : nullptr,
+                              enr_block_of<T>(c)));
   }
   if (fin_mode >= 0) {
     ProfScope ps(c, XFFT_PROF_FINALIZE, 1);

@@ -516,12 +516,16 @@ __global__ void k_fft_z_c2r(const typename Cx<T>::type* __restrict__ spec, const
   if (threadIdx.x == 0) partials[(long long)rhs * nparts + blockIdx.x] = tot[0];
 }
 
-// ---------------------------------------------------------------- enriched block: identity
+// ---------------------------------------------------------------- enriched block
+// z_X = f_X (identity on the scaled enriched DOFs, eq. scaledPreconditioner) or, with eblk
+// (6 x nX: inverse of each node's 3x3 block, entries 00, 11, 22, 01, 02, 12), z_X = B^-1 f_X per
+// enriched node.  Enriched DOFs are component-major: f[off + c nX + j].
 template <typename T>
-__global__ void k_enr_identity(T* __restrict__ f, T* __restrict__ z, long long stride,
-                               long long off, long long count, const int* __restrict__ active,
-                               double* __restrict__ partials, int nparts, int slot0,
-                               const T* __restrict__ q, const RhsState* __restrict__ st) {
+__global__ void k_enr_precond(T* __restrict__ f, T* __restrict__ z, long long stride,
+                              long long off, int nX, const int* __restrict__ active,
+                              double* __restrict__ partials, int nparts, int slot0,
+                              const T* __restrict__ q, const RhsState* __restrict__ st,
+                              const T* __restrict__ eblk) {
   __shared__ double red[32];
   const int rhs = blockIdx.y;
   if (active && !active[rhs]) return;
@@ -530,15 +534,40 @@ __global__ void k_enr_identity(T* __restrict__ f, T* __restrict__ z, long long s
   const T* qr = q ? q + rhs * stride + off : nullptr;
   const T alpha = q ? (T)st[rhs].alpha : T(0);
   T acc = T(0);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-       i += (long long)gridDim.x * blockDim.x) {
-    T v = fr[i];
-    if (q) {
-      v -= alpha * qr[i];  // fused CG update f -= alpha A d
-      fr[i] = v;
+  if (!eblk) {
+    const long long count = 3LL * nX;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+      T v = fr[i];
+      if (q) {
+        v -= alpha * qr[i];  // fused CG update f -= alpha A d
+        fr[i] = v;
+      }
+      zr[i] = v;
+      acc += v * v;
     }
-    zr[i] = v;
-    acc += v * v;
+  } else {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nX; j += gridDim.x * blockDim.x) {
+      T v[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        v[c] = fr[(long long)c * nX + j];
+        if (q) {
+          v[c] -= alpha * qr[(long long)c * nX + j];
+          fr[(long long)c * nX + j] = v[c];
+        }
+      }
+      const T b00 = eblk[j], b11 = eblk[nX + j], b22 = eblk[2 * (long long)nX + j];
+      const T b01 = eblk[3 * (long long)nX + j], b02 = eblk[4 * (long long)nX + j];
+      const T b12 = eblk[5 * (long long)nX + j];
+      const T z0 = b00 * v[0] + b01 * v[1] + b02 * v[2];
+      const T z1 = b01 * v[0] + b11 * v[1] + b12 * v[2];
+      const T z2 = b02 * v[0] + b12 * v[1] + b22 * v[2];
+      zr[j] = z0;
+      zr[nX + j] = z1;
+      zr[2 * (long long)nX + j] = z2;
+      acc += v[0] * z0 + v[1] * z1 + v[2] * z2;
+    }
   }
   double vv[1] = {(double)acc}, tot[1];
   block_sum<1>(vv, red, tot);
@@ -746,7 +775,7 @@ template <typename T>
 cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long long stride,
                                 int nX, const int* active, double* partials, int nparts,
                                 int n_rhs, cudaStream_t s, unsigned long long* units, const T* q,
-                                const RhsState* st) {
+                                const RhsState* st, const T* eblk) {
   typedef typename Cx<T>::type C;
   const bool dbl = sizeof(T) == 8;
   const int a2 = 2;  // z axis
@@ -766,8 +795,8 @@ cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long
                                       p->twf[1], p->twf[2], p->gtab, ge, gs, ih, 0.5 * p->g.vol_tet, units,
                                       (const float*)q, st, partials, nparts, n_rhs, s);
     if (e != cudaSuccess) return e;
-    k_enr_identity<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, 3LL * nX,
-                                                                  active, partials, nparts, zb, q, st);
+    k_enr_precond<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, nX, active,
+                                                                 partials, nparts, zb, q, st, eblk);
     return cudaGetLastError();
   }
   if (p->fast) {
@@ -789,8 +818,8 @@ cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long
       e = fast_z_c2r<T>(p->n[2], spec, f, z, stride, sstride, p->n[0], p->n[1],
                         1.0 / ((double)p->n[0] * p->n[1] * p->n[2]), active, tw2, partials, nparts, n_rhs, s);
     if (e != cudaSuccess) return e;
-    k_enr_identity<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, 3LL * nX,
-                                                                  active, partials, nparts, zb, q, st);
+    k_enr_precond<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, nX, active,
+                                                                 partials, nparts, zb, q, st, eblk);
     return cudaGetLastError();
   }
   k_fft_z_r2c<T><<<dim3(zb, n_rhs), kFftThreads, smem_z(p, cs), s>>>(
@@ -829,16 +858,18 @@ cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long N = g.N;
-  k_enr_identity<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * N, 3LL * nX,
-                                                                active, partials, nparts, zb, q, st);
+  k_enr_precond<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * N, nX, active,
+                                                                 partials, nparts, zb, q, st, eblk);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_precondition<float>(const FftPlan*, float*, float*, void*, long long, int,
                                                 const int*, double*, int, int, cudaStream_t,
-                                                unsigned long long*, const float*, const RhsState*);
+                                                unsigned long long*, const float*, const RhsState*,
+                                                const float*);
 template cudaError_t launch_precondition<double>(const FftPlan*, double*, double*, void*, long long, int,
                                                  const int*, double*, int, int, cudaStream_t,
-                                                 unsigned long long*, const double*, const RhsState*);
+                                                 unsigned long long*, const double*, const RhsState*,
+                                                 const double*);
 
 }  // namespace xfft

@@ -380,8 +380,11 @@ cudaError_t launch_cut_eids(int* ip_mut, const int* enr_id, int ncut, cudaStream
 // On side s of a cut tet, grad N_X^a(x) = sum_b N_b(x) V_ab with V_ab = c_b g_a + delta_ab gamma,
 // c_b = |L_b| - s L_b, gamma = sum_b c_b g_b.  Hence
 //   D_{a,k} += 1/2 sum_bc M_bc (V_ab . V_ac + V_ab[k] V_ac[k]).
+// D (3 x nX): D0 per enriched DOF; Doff (3 x nX, may be null): the off-diagonal entries
+// (01, 02, 12) of each enriched node's 3x3 block int sym(g (x) e_k) : sym(g (x) e_l) = 1/2 int
+// g_k g_l (k != l), g = grad N_X (used by the block enriched preconditioner)
 __global__ void k_cut_scaling(const int* __restrict__ ip, const double* __restrict__ dp, int ncut,
-                              double* __restrict__ D, int nX, GridDev g) {
+                              double* __restrict__ D, double* __restrict__ Doff, int nX, GridDev g) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
     const int t = ip[9 * ncut + e];
     double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
@@ -390,6 +393,7 @@ __global__ void k_cut_scaling(const int* __restrict__ ip, const double* __restri
     double L[4];
     for (int b = 0; b < 4; ++b) L[b] = dp[cut_f_L(b) * (long long)ncut + e];
     double acc[4][3] = {};
+    double off[4][3] = {};
     for (int si = 0; si < 2; ++si) {
       const double s = si == 0 ? 1.0 : -1.0;
       double c[4], gam[3] = {0.0, 0.0, 0.0};
@@ -408,20 +412,80 @@ __global__ void k_cut_scaling(const int* __restrict__ ip, const double* __restri
             const double w = M[midx(b, cc)];
             const double dot = V[b][0] * V[cc][0] + V[b][1] * V[cc][1] + V[b][2] * V[cc][2];
             for (int x = 0; x < 3; ++x) acc[a][x] += 0.5 * w * (dot + V[b][x] * V[cc][x]);
+            if (Doff) {
+              off[a][0] += 0.5 * w * V[b][0] * V[cc][1];
+              off[a][1] += 0.5 * w * V[b][0] * V[cc][2];
+              off[a][2] += 0.5 * w * V[b][1] * V[cc][2];
+            }
           }
       }
     }
     for (int a = 0; a < 4; ++a) {
       const int j = ip[(4 + a) * ncut + e];
       for (int x = 0; x < 3; ++x) atomicAdd(&D[(long long)x * nX + j], acc[a][x]);
+      if (Doff)
+        for (int x = 0; x < 3; ++x) atomicAdd(&Doff[(long long)x * nX + j], off[a][x]);
     }
   }
 }
 
-cudaError_t launch_cut_scaling(CutData cd, double* D, int nX, GridDev g, cudaStream_t s) {
+cudaError_t launch_cut_scaling(CutData cd, double* D, double* Doff, int nX, GridDev g, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(D, 0, sizeof(double) * 3 * (size_t)nX, s);
+  if (e == cudaSuccess && Doff) e = cudaMemsetAsync(Doff, 0, sizeof(double) * 3 * (size_t)nX, s);
   if (e != cudaSuccess || cd.ncut == 0) return e;
-  k_cut_scaling<<<(cd.ncut + 127) / 128, 128, 0, s>>>(cd.ip, cd.dp, cd.ncut, D, nX, g);
+  k_cut_scaling<<<(cd.ncut + 127) / 128, 128, 0, s>>>(cd.ip, cd.dp, cd.ncut, D, Doff, nX, g);
+  return cudaGetLastError();
+}
+
+// Block enriched preconditioner: per enriched node the scaled block B = S Dblk S (S = D0^-1/2,
+// unit diagonal) is factorised B = L L^T in FP64 and its inverse L^-T L^-1 stored as (00, 11,
+// 22, 01, 02, 12) x nX in FP64 and FP32.  A non-positive pivot sets *bad.
+__global__ void k_block_inverse(const double* __restrict__ D, const double* __restrict__ Doff,
+                                const double* __restrict__ isd, double* __restrict__ b64,
+                                float* __restrict__ b32, int nX, int* __restrict__ bad) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nX; j += gridDim.x * blockDim.x) {
+    const double s0 = isd[j], s1 = isd[nX + j], s2 = isd[2 * (long long)nX + j];
+    const double a00 = D[j] * s0 * s0, a11 = D[nX + j] * s1 * s1, a22 = D[2 * (long long)nX + j] * s2 * s2;
+    const double a10 = Doff[j] * s0 * s1, a20 = Doff[nX + j] * s0 * s2, a21 = Doff[2 * (long long)nX + j] * s1 * s2;
+    double v[6] = {1.0, 1.0, 1.0, 0.0, 0.0, 0.0};
+    bool ok = a00 > 0.0;
+    if (ok) {
+      const double l00 = sqrt(a00);
+      const double l10 = a10 / l00, l20 = a20 / l00;
+      const double p11 = a11 - l10 * l10;
+      ok = p11 > 0.0;
+      if (ok) {
+        const double l11 = sqrt(p11);
+        const double l21 = (a21 - l20 * l10) / l11;
+        const double p22 = a22 - l20 * l20 - l21 * l21;
+        ok = p22 > 0.0;
+        if (ok) {
+          const double l22 = sqrt(p22);
+          const double m00 = 1.0 / l00, m11 = 1.0 / l11, m22 = 1.0 / l22;
+          const double m10 = -l10 * m00 * m11;
+          const double m21 = -l21 * m11 * m22;
+          const double m20 = -(l20 * m00 + l21 * m10) * m22;
+          v[0] = m00 * m00 + m10 * m10 + m20 * m20;
+          v[1] = m11 * m11 + m21 * m21;
+          v[2] = m22 * m22;
+          v[3] = m10 * m11 + m20 * m21;
+          v[4] = m20 * m22;
+          v[5] = m21 * m22;
+        }
+      }
+    }
+    if (!ok) atomicExch(bad, 1);
+    for (int k = 0; k < 6; ++k) {
+      b64[(long long)k * nX + j] = v[k];
+      b32[(long long)k * nX + j] = (float)v[k];
+    }
+  }
+}
+
+cudaError_t launch_block_inverse(const double* D, const double* Doff, const double* isd, double* b64,
+                                 float* b32, int nX, int* bad, cudaStream_t s) {
+  if (nX == 0) return cudaSuccess;
+  k_block_inverse<<<(nX + 255) / 256, 256, 0, s>>>(D, Doff, isd, b64, b32, nX, bad);
   return cudaGetLastError();
 }
 

@@ -44,7 +44,9 @@ cudaError_t launch_build_lists(const uint16_t* code, const int* cutoff, const in
 cudaError_t launch_cut_geometry(const double* Ls, CutData cd, double* dp_mut, int* ip_mut,
                                 GridDev g, cudaStream_t s);
 cudaError_t launch_cut_eids(int* ip_mut, const int* enr_id, int ncut, cudaStream_t s);
-cudaError_t launch_cut_scaling(CutData cd, double* D, int nX, GridDev g, cudaStream_t s);
+cudaError_t launch_cut_scaling(CutData cd, double* D, double* Doff, int nX, GridDev g, cudaStream_t s);
+cudaError_t launch_block_inverse(const double* D, const double* Doff, const double* isd, double* b64,
+                                 float* b32, int nX, int* bad, cudaStream_t s);
 cudaError_t launch_finish_scaling(const double* D, double* isd, float* isf, int nX,
                                   cudaStream_t s);
 cudaError_t launch_cut_to_float(const double* dp, float* fp, long long count, cudaStream_t s);
@@ -102,11 +104,13 @@ size_t fft_spectrum_elems(const FftPlan* p);  // complex elements per RHS
 // z = P^-1 f per RHS (std part via FFT + Green, enr part identity); f^T z partials into
 // partials[rhs][nparts] (slots 0..nb-1).  spec: workspace of n_rhs * spectrum elems complex.
 // With q != nullptr the first pass also applies f -= alpha q (alpha = st[rhs].alpha) and stores f.
+// eblk (6 x nX, may be null): inverse 3x3 blocks of the block enriched preconditioner.
 template <typename T>
 cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec, long long stride,
                                 int nX, const int* active, double* partials, int nparts,
                                 int n_rhs, cudaStream_t s, unsigned long long* units = nullptr,
-                                const T* q = nullptr, const RhsState* st = nullptr);
+                                const T* q = nullptr, const RhsState* st = nullptr,
+                                const T* eblk = nullptr);
 // partial-sum slots written by one precondition call (FP64 or FP32 kernels)
 int precondition_blocks(const FftPlan* p, int nX, bool dbl);
 

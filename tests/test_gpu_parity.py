@@ -143,6 +143,36 @@ def test_precondition_matches_oracle(xf, name, prec):
         assert abs(rr[r] - f[r] @ ref) <= tol * abs(f[r] @ ref) * 10
 
 
+@pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_block_enriched_preconditioner(xf, name, prec):
+    """Variant enriched preconditioner (3x3 node blocks): P^-1 against the oracle, and a solve
+    with it reaching the direct solution (the system does not depend on the preconditioner)."""
+    n, ell, L, lm, lp, sc = _case(name)
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    s = xf.Solver(n, ell, precision=prec, tol=1e-12 if prec == "fp64" else 1e-10, enr_precond="block3")
+    s.set_microstructure(L, lm, lp, sc)
+    rng = np.random.default_rng(13)
+    f = rng.normal(size=(2, o.ndof))
+    for r in range(2):
+        std = f[r, : 3 * o.nFE].reshape(3, -1)
+        std -= std.mean(axis=1, keepdims=True)
+    z, rr = s.precondition(f, precision=prec)
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    for r in range(2):
+        ref = o.precondition(f[r], green="sparse", enr="block3")
+        assert _rel(z[r], ref) < tol
+    eps = np.array([[0.2, -0.1, 0.3, 0.4, -0.2, 0.1]])
+    out = s.solve(eps, u=True)
+    assert out["converged"], out["stats"]
+    u = o.solve_direct(eps[0])
+    ms = o.mean_stress(u, eps[0])
+    ctol = 1e-10 if prec == "fp64" else 1e-6
+    assert np.abs(out["mean_stress"][0] - ms).max() < ctol * np.abs(ms).max()
+    if prec == "fp64":
+        assert _rel(out["u_std"][0], u[: 3 * o.nFE].reshape(3, -1)) < 1e-9
+
+
 @pytest.mark.parametrize("name", ["sphere16", "ragged"])
 def test_fp64_solve_matches_direct(xf, name):
     n, ell, L, lm, lp, sc = _case(name)
@@ -244,6 +274,34 @@ def test_gradient_against_finite_differences(xf):
         _, Cm = ceff((tm[0], tm[1]), (tm[2], tm[3]), sc)
         fd = (np.sum((Cp - Ct) ** 2) - np.sum((Cm - Ct) ** 2)) / (2 * h)
         assert abs(fd - dl[p]) < 1e-5 * max(abs(dl[p]), 1e-3 * np.abs(dl).max())
+
+
+def test_autograd_effective_stiffness(xf):
+    """torch.autograd path: backward of ||C_eff - C_t||^2 equals the library gradient and the
+    central finite difference in one Lame constant."""
+    torch = pytest.importorskip("torch")
+    n = (8, 8, 8)
+    L = synth.sphere_levelset(n, (0.45, 0.5, 0.55), 0.3)
+    sc = torch.tensor(synth.voxel_scale(n, 7).ravel(), dtype=torch.float32, requires_grad=True)
+    lame = torch.tensor(list(synth.lame_from_E_nu(8.0, 0.2)) + list(synth.lame_from_E_nu(1.0, 0.3)),
+                        dtype=torch.float64, requires_grad=True)
+    Ct = torch.tensor(np.random.default_rng(4).normal(size=(6, 6)))
+    s = xf.Solver(n, tol=1e-13)
+    C = xf.effective_stiffness(s, L, lame, sc)
+    loss = ((C - Ct) ** 2).sum()
+    loss.backward()
+    dl, ds, _ = s.grad(2.0 * (C.detach().numpy() - Ct.numpy()))
+    assert np.allclose(lame.grad.numpy(), dl, rtol=1e-12, atol=0)
+    assert np.allclose(sc.grad.numpy(), ds, rtol=1e-6, atol=0)
+    p, h = 1, 1e-6 * float(lame[1])
+    with torch.no_grad():
+        lp, lmn = lame.detach().clone(), lame.detach().clone()
+        lp[p] += h
+        lmn[p] -= h
+        fp = ((xf.effective_stiffness(s, L, lp, sc.detach()) - Ct) ** 2).sum().item()
+        fm = ((xf.effective_stiffness(s, L, lmn, sc.detach()) - Ct) ** 2).sum().item()
+    fd = (fp - fm) / (2 * h)
+    assert abs(fd - lame.grad[p].item()) < 1e-5 * abs(lame.grad[p].item())
 
 
 def test_laminate_closed_form_gpu(xf):
