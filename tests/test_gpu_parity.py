@@ -293,7 +293,7 @@ def test_autograd_effective_stiffness(xf):
     dl, ds, _ = s.grad(2.0 * (C.detach().numpy() - Ct.numpy()))
     assert np.allclose(lame.grad.numpy(), dl, rtol=1e-12, atol=0)
     assert np.allclose(sc.grad.numpy(), ds, rtol=1e-6, atol=0)
-    p, h = 1, 1e-6 * float(lame[1])
+    p, h = 1, 1e-6 * float(lame.detach()[1])
     with torch.no_grad():
         lp, lmn = lame.detach().clone(), lame.detach().clone()
         lp[p] += h
