@@ -388,6 +388,34 @@ def main():
                                "identity_cg_iters": steps_iters / args.steps,
                                "ceff_rel_diff_vs_identity": float(np.abs(Cb - C).max() / np.abs(C).max())}
         sb.close()
+        # many microstructures at once (16 uneven grids x 6 load cases, FP32-refined to 1e-8):
+        # one call, one host thread and stream per microstructure, against the same solvers in turn
+        from paper_2601_02172_gb300 import batch_effective_stiffness
+        bw = synth.batch_uneven(16, seed=3)
+        bsolvers = []
+        for wb in bw:
+            sv = Solver(wb["n"], precision="fp32", tol=1e-8)
+            sv.set_microstructure(wb["L"], wb["lame_minus"], wb["lame_plus"])
+            bsolvers.append(sv)
+        batch_effective_stiffness(bsolvers)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, bst = batch_effective_stiffness(bsolvers)
+        torch.cuda.synchronize()
+        t_bat = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for sv in bsolvers:
+            sv.effective_stiffness()
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        extra["batch16"] = {"microstructures": len(bw), "rhs": 6 * len(bw),
+                            "grids": [int(wb["n"][0]) for wb in bw], "tol": 1e-8,
+                            "solves_per_s_batched": len(bw) / t_bat,
+                            "solves_per_s_sequential": len(bw) / t_seq,
+                            "dof_iters_per_s_batched": sum(3.0 * (sb["n_fe"] + sb["n_x"]) * sum(sb["iters"])
+                                                           for sb in bst) / t_bat}
+        for sv in bsolvers:
+            sv.close()
         # cuFFT (torch.fft) R2C + C2R of the same 3 x 6 FP32 fields, beside the preconditioner
         x = torch.randn(18, *n, device=dev, dtype=torch.float32)
         for _ in range(3):

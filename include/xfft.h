@@ -133,6 +133,16 @@ xfft_status xfft_solve(xfft_ctx* ctx, int n_rhs, const double* eps_bar, double* 
  * The six converged fields stay in the context as the checkpoint for xfft_grad. */
 xfft_status xfft_effective_stiffness(xfft_ctx* ctx, double C_eff[36], xfft_stats* stats);
 
+/* Batch of microstructures (uneven grids allowed): xfft_effective_stiffness on each of the n
+ * contexts, all at once.  Each context's solve runs from its own host thread on its own stream,
+ * so kernels of different microstructures overlap on the GPU; within a context the iterations
+ * between two convergence polls replay as one captured CUDA graph.  Give every context its own
+ * non-legacy stream at xfft_create (contexts on the legacy stream serialise and run without
+ * graphs).  C_eff: n x 36 (host), stats: n entries or NULL.  The first error (or ENOTCONV) is
+ * returned with the context's index in the message; every context is solved regardless. */
+xfft_status xfft_batch_effective_stiffness(int n, xfft_ctx* const* ctxs, double* C_eff,
+                                           xfft_stats* stats);
+
 /* Gradient of a scalar loss through C_eff: given G = dLoss/dC_eff (6x6 row-major, host),
  * return dLoss/d(lambda_minus, mu_minus, lambda_plus, mu_plus) in dL_dlame[4] (host) and,
  * if dL_dscale != NULL, dLoss/ds_v (N floats, voxel order).  Uses the envelope identity

@@ -4,7 +4,7 @@ The compute path is the CUDA library ``libxfft.so`` (sources in ``csrc/``, C-ABI
 ``include/xfft.h``); this package only builds it and marshals arguments to it.
 """
 from .build import build  # noqa: F401
-from .capi import Solver, XfftError, lib  # noqa: F401
+from .capi import Solver, XfftError, batch_effective_stiffness, lib  # noqa: F401
 
 
 def effective_stiffness(solver, L, lame, scale=None):

@@ -24,6 +24,7 @@ EXPORTED = (
     "xfft_effective_stiffness", "xfft_grad", "xfft_apply", "xfft_precondition", "xfft_get_setup",
     "xfft_num_enriched", "xfft_num_cut_tets", "xfft_status_string", "xfft_last_error",
     "xfft_destroy", "xfft_profile", "xfft_profile_read", "xfft_apply_noalloc",
+    "xfft_batch_effective_stiffness",
 )
 NOALLOC_MAX_RHS = 8
 PROF_KINDS = ("apply_uncut_f32", "apply_cut_f32", "apply_uncut_f64", "apply_cut_f64", "prec_f32",
@@ -84,10 +85,11 @@ def lib():
     L.xfft_profile.argtypes = [vp, i]
     L.xfft_profile_read.argtypes = [vp, vp, vp, vp]
     L.xfft_apply_noalloc.argtypes = [vp, i, vp, vp, vp]
+    L.xfft_batch_effective_stiffness.argtypes = [i, vp, C.POINTER(d), C.POINTER(Stats)]
     for name in ("xfft_default_options", "xfft_create", "xfft_set_microstructure", "xfft_solve",
                  "xfft_effective_stiffness", "xfft_grad", "xfft_apply", "xfft_precondition",
                  "xfft_get_setup", "xfft_num_enriched", "xfft_num_cut_tets", "xfft_profile",
-                 "xfft_profile_read", "xfft_apply_noalloc"):
+                 "xfft_profile_read", "xfft_apply_noalloc", "xfft_batch_effective_stiffness"):
         getattr(L, name).restype = i
     _lib = L
     return L
@@ -129,8 +131,32 @@ def _dvec(a):
     return a, a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def _ordered(method):
+    """Order a library call after the caller's pending work on torch's current stream, and the
+    caller's later work after the call (the library runs on the solver's own stream)."""
+    import functools
+
+    @functools.wraps(method)
+    def wrapper(self, *args, **kwargs):
+        ts = self._tstream
+        if ts is None:
+            return method(self, *args, **kwargs)
+        import torch
+        cur = torch.cuda.current_stream()
+        ts.wait_stream(cur)
+        out = method(self, *args, **kwargs)
+        cur.wait_stream(ts)
+        return out
+    return wrapper
+
+
 class Solver:
-    """One grid on the current CUDA device (thin wrapper of ``xfft_ctx``)."""
+    """One grid on the current CUDA device (thin wrapper of ``xfft_ctx``).
+
+    stream: None (default) gives the solver its own CUDA stream (ordered against torch's current
+    stream at every call; the CG iterations then replay as captured CUDA graphs), "legacy" the
+    legacy default stream, or a ``torch.cuda.Stream`` / raw ``cudaStream_t`` handle.
+    """
 
     def __init__(self, n, length=(1.0, 1.0, 1.0), precision="fp64", tol=1e-10, maxit=10000,
                  snap_tau=0.0, inner_tol=1e-5, max_refine=20, poll_every=8, stream=None,
@@ -155,8 +181,18 @@ class Solver:
         o.enr_precond = {"identity": 0, "block3": 1}[enr_precond]
         self.precision = precision
         self._ctx = C.c_void_p()
+        self._tstream = None
+        handle = None
+        if stream is None or _is_torch(stream):
+            import torch
+            if stream is None:
+                stream = torch.cuda.Stream()
+            self._tstream = stream
+            handle = stream.cuda_stream
+        elif stream != "legacy":
+            handle = int(stream)
         check(L.xfft_create(C.byref(self._ctx), C.byref(g), C.byref(o),
-                            C.c_void_p(stream) if stream else None))
+                            C.c_void_p(handle) if handle else None))
 
     def close(self):
         if self._ctx:
@@ -177,6 +213,7 @@ class Solver:
     def stride(self):
         return 3 * (self.N + self.num_enriched)
 
+    @_ordered
     def set_microstructure(self, L, lame_minus, lame_plus, scale=None):
         Lp, dev = _ptr(L, np.float64)
         sp_, sdev = _ptr(scale, np.float32)
@@ -186,6 +223,7 @@ class Solver:
         lp, lpp = _dvec(lame_plus)
         check(lib().xfft_set_microstructure(self._ctx, Lp, lmp, lpp, sp_, int(dev)))
 
+    @_ordered
     def solve(self, eps, u=True, voxel_stress=False, device=None):
         """Solve for the Mandel strains ``eps`` (k x 6).  Host (NumPy) outputs unless
         ``device`` is a torch device, in which case outputs are CUDA tensors."""
@@ -218,6 +256,7 @@ class Solver:
         out["converged"] = status == XFFT_OK
         return out
 
+    @_ordered
     def effective_stiffness(self):
         Cm = np.empty(36)
         st = Stats()
@@ -225,6 +264,7 @@ class Solver:
                                                       C.byref(st)), allow=(XFFT_ENOTCONV,))
         return Cm.reshape(6, 6), dict(st.to_dict(), converged=status == XFFT_OK)
 
+    @_ordered
     def grad(self, G, scale_grad=True, device=None):
         """dLoss/d(lam-, mu-, lam+, mu+), dLoss/ds_v (float32) and the energy-form C_eff for
         G = dLoss/dC_eff of the last effective_stiffness call."""
@@ -244,6 +284,7 @@ class Solver:
                               ce.ctypes.data_as(C.POINTER(C.c_double)), int(bool(dev))))
         return dl, ds, ce.reshape(6, 6)
 
+    @_ordered
     def apply(self, d, eps=None, precision="fp64"):
         """q = A d (+ b(eps)) on full DOF vectors (k x stride, scaled enriched part).
         precision: "fp64", "fp32" or "dw" (double-word kernels on FP64 data)."""
@@ -259,6 +300,7 @@ class Solver:
                                sig.ctypes.data_as(C.POINTER(C.c_double)), _PREC[precision], 0))
         return q, sig
 
+    @_ordered
     def apply_noalloc(self, d, q, dAd_sig=None):
         """Allocation-free FP64 apply on caller-owned CUDA tensors (k x stride): q = A d; if
         given, dAd_sig (k x 7) receives <d, A d> and int_Y C grad^s d.  The library allocates
@@ -271,6 +313,7 @@ class Solver:
             raise TypeError("apply_noalloc takes CUDA tensors only")
         check(lib().xfft_apply_noalloc(self._ctx, k, dp, qp, sp_))
 
+    @_ordered
     def precondition(self, f, precision="fp64"):
         f = np.ascontiguousarray(np.atleast_2d(f), dtype=np.float64)
         k = f.shape[0]
@@ -285,6 +328,7 @@ class Solver:
         """Enable (and reset) or disable the library's per-kernel-group event timing."""
         check(lib().xfft_profile(self._ctx, int(bool(enable))))
 
+    @_ordered
     def profile_read(self):
         """{group: (ms, launches, rhs_units)} accumulated since profile(True)."""
         ms = np.zeros(16)
@@ -294,6 +338,7 @@ class Solver:
                                       C.c_void_p(un.ctypes.data)))
         return {k: (float(ms[i]), int(la[i]), int(un[i])) for i, k in enumerate(PROF_KINDS)}
 
+    @_ordered
     def setup_info(self):
         nX = self.num_enriched
         en = np.empty(max(nX, 1), dtype=np.int32)
@@ -302,3 +347,23 @@ class Solver:
         check(lib().xfft_get_setup(self._ctx, C.c_void_p(en.ctypes.data), C.c_void_p(D0.ctypes.data),
                                    C.c_void_p(code.ctypes.data)))
         return en[:nX], D0[:nX], code
+
+
+def batch_effective_stiffness(solvers):
+    """C_eff (list of 6x6) and stats of several solvers at once (``xfft_batch_effective_stiffness``:
+    one host thread and stream per solver, graph-replayed CG iterations)."""
+    import torch
+    n = len(solvers)
+    arr = (C.c_void_p * n)(*[sv._ctx for sv in solvers])
+    Cm = np.empty((n, 36))
+    st = (Stats * n)()
+    cur = torch.cuda.current_stream()
+    for sv in solvers:
+        if sv._tstream is not None:
+            sv._tstream.wait_stream(cur)
+    status = lib().xfft_batch_effective_stiffness(n, arr, Cm.ctypes.data_as(C.POINTER(C.c_double)), st)
+    for sv in solvers:
+        if sv._tstream is not None:
+            cur.wait_stream(sv._tstream)
+    check(status, allow=(XFFT_ENOTCONV,))
+    return [Cm[i].reshape(6, 6) for i in range(n)], [st[i].to_dict() for i in range(n)]

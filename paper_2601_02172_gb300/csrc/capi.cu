@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -80,6 +81,15 @@ struct xfft_ctx {
   double* D = nullptr;
   double* isD = nullptr;
   float* isF = nullptr;
+  // captured CG iteration chunks (poll_every iterations each), keyed by their arguments
+  struct CgGraph {
+    bool valid = false;
+    int tsz = 0, n_rhs = 0, crit = 0, maxit = 0, pe = 0;
+    double tol = 0.0;
+    const void* p[6] = {};
+    cudaGraphExec_t exec = nullptr;
+  } cg_graphs[4];
+  int cg_next = 0;
   // block enriched preconditioner: off-diagonal block entries and the inverse blocks
   double* Doff = nullptr;
   double* eb64 = nullptr;
@@ -270,7 +280,15 @@ extern "C" xfft_status xfft_create(xfft_ctx** out, const xfft_grid* grid, const 
   return XFFT_OK;
 }
 
+static void drop_graphs(xfft_ctx* c) {
+  for (auto& g : c->cg_graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = xfft_ctx::CgGraph();
+  }
+}
+
 static void free_micro(xfft_ctx* c) {
+  drop_graphs(c);
   dfree(c->Ls);
   dfree(c->Lin);
   dfree(c->code);
@@ -299,6 +317,7 @@ static void free_micro(xfft_ctx* c) {
 }
 
 static void free_work(xfft_ctx* c) {
+  drop_graphs(c);
   for (int k = 0; k < 6; ++k) {
     dfree(c->v64[k]);
     dfree(c->v32[k]);
@@ -612,26 +631,96 @@ static xfft_status read_states(xfft_ctx* c, int n_rhs) {
 //   q = A d_new, alpha = rr / <q, d_new>,
 //   f -= alpha q, z = P^-1 f (fused into the first FFT pass), beta = rr'/rr.
 // The last u += alpha d of each right-hand side is applied after the loop.
+// One CG iteration (Algorithm 1) for all right-hand sides: d_new = z + beta d_old and
+// u += alpha d_old (fused into the stencil), q = A d_new with <d, q>, alpha; f -= alpha q fused
+// into the preconditioner's first pass, z = P^-1 f with f^T z, beta and the stopping rule.
+template <typename T>
+static xfft_status cg_iter(xfft_ctx* c, int it, T* u, T* f, T* const* dbuf, T* z, T* q, int n_rhs,
+                           double tol, int crit, int maxit) {
+  const long long stride = stride_of(c);
+  T* dold = dbuf[it & 1];
+  T* dnew = dbuf[(it + 1) & 1];
+  const int par = (it + 1) & 1;
+  {
+    ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+    CU(launch_cg_update_tail<T>(z, dold, dnew, u, c->st, 3 * c->g.N, stride, n_rhs, c->stream));
+  }
+  TRY(do_apply<T>(c, dold, q, nullptr, n_rhs, c->act, 1, tol, crit, maxit, z, dnew, u, par));
+  TRY(do_prec<T>(c, f, z, n_rhs, c->act, 2, tol, crit, maxit, 0, q, par));
+  return XFFT_OK;
+}
+
+// Executable graph of poll_every iterations (captured once per argument set, then replayed:
+// the iterations between two convergence polls are fixed launch sequences whose scalars live
+// on the device).  Needs a non-legacy stream, an even poll_every and tracing off.
+template <typename T>
+static xfft_status cg_graph(xfft_ctx* c, T* u, T* f, T* const* dbuf, T* z, T* q, int n_rhs, double tol,
+                            int crit, int maxit, cudaGraphExec_t* out) {
+  const int pe = c->opt.poll_every;
+  const void* key[6] = {u, f, dbuf[0], dbuf[1], z, q};
+  for (auto& g : c->cg_graphs) {
+    if (g.valid && g.tsz == (int)sizeof(T) && g.n_rhs == n_rhs && g.crit == crit && g.maxit == maxit &&
+        g.pe == pe && g.tol == tol && std::equal(key, key + 6, g.p)) {
+      *out = g.exec;
+      return XFFT_OK;
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+  xfft_status st = XFFT_OK;
+  for (int j = 0; j < pe && st == XFFT_OK; ++j) st = cg_iter<T>(c, j, u, f, dbuf, z, q, n_rhs, tol, crit, maxit);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (st != XFFT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(XFFT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(XFFT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  auto& g = c->cg_graphs[c->cg_next];
+  c->cg_next = (c->cg_next + 1) % 4;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.valid = true;
+  g.tsz = (int)sizeof(T);
+  g.n_rhs = n_rhs;
+  g.crit = crit;
+  g.maxit = maxit;
+  g.pe = pe;
+  g.tol = tol;
+  std::copy(key, key + 6, g.p);
+  g.exec = exec;
+  *out = exec;
+  return XFFT_OK;
+}
+
 template <typename T>
 static xfft_status cg_loop(xfft_ctx* c, T* u, T* f, T* dA, T* dB, T* z, T* q, int n_rhs, double tol,
                            int crit, int maxit) {
   const long long stride = stride_of(c);
   T* dbuf[2] = {dA, dB};
-  for (int it = 0; it <= maxit; ++it) {
-    if (it % c->opt.poll_every == 0) {
+  const int pe = c->opt.poll_every;
+  const bool graphs = !c->prof && c->stream != nullptr && c->stream != cudaStreamLegacy &&
+                      c->stream != cudaStreamPerThread && pe % 2 == 0;
+  if (graphs) {
+    cudaGraphExec_t exec = nullptr;
+    TRY(cg_graph<T>(c, u, f, dbuf, z, q, n_rhs, tol, crit, maxit, &exec));
+    for (int it = 0; it <= maxit; it += pe) {
       int na = 0;
       TRY(poll_active(c, n_rhs, &na));
       if (na == 0) break;
+      CU(cudaGraphLaunch(exec, c->stream));
     }
-    T* dold = dbuf[it & 1];
-    T* dnew = dbuf[(it + 1) & 1];
-    const int par = (it + 1) & 1;
-    {
-      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-      CU(launch_cg_update_tail<T>(z, dold, dnew, u, c->st, 3 * c->g.N, stride, n_rhs, c->stream));
+  } else {
+    for (int it = 0; it <= maxit; ++it) {
+      if (it % pe == 0) {
+        int na = 0;
+        TRY(poll_active(c, n_rhs, &na));
+        if (na == 0) break;
+      }
+      TRY(cg_iter<T>(c, it, u, f, dbuf, z, q, n_rhs, tol, crit, maxit));
     }
-    TRY(do_apply<T>(c, dold, q, nullptr, n_rhs, c->act, 1, tol, crit, maxit, z, dnew, u, par));
-    TRY(do_prec<T>(c, f, z, n_rhs, c->act, 2, tol, crit, maxit, 0, q, par));
   }
   {
     ProfScope ps(c, XFFT_PROF_VECTOR, 1);
@@ -931,6 +1020,41 @@ extern "C" xfft_status xfft_effective_stiffness(xfft_ctx* c, double C_eff[36], x
   xfft_status st = status_of(R, 6);
   if (st == XFFT_OK) c->have6 = true;
   return st;
+}
+
+extern "C" xfft_status xfft_batch_effective_stiffness(int n, xfft_ctx* const* ctxs, double* C_eff,
+                                                      xfft_stats* stats) {
+  if (n < 1 || !ctxs || !C_eff) return fail(XFFT_EINVAL, "n >= 1 contexts and C_eff required");
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(XFFT_EINVAL, "NULL context");
+    if (!ctxs[i]->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return fail(XFFT_EINVAL, "a context appears twice in the batch");
+  }
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  std::vector<xfft_status> st(n, XFFT_OK);
+  std::vector<std::string> msg(n);
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int i = 0; i < n; ++i) {
+    th.emplace_back([&, i]() {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        st[i] = XFFT_ECUDA;
+        msg[i] = "cudaSetDevice in a batch thread";
+        return;
+      }
+      st[i] = xfft_effective_stiffness(ctxs[i], C_eff + 36 * (size_t)i, stats ? stats + i : nullptr);
+      if (st[i] != XFFT_OK) msg[i] = g_err;
+    });
+  }
+  for (auto& t : th) t.join();
+  for (int i = 0; i < n; ++i)
+    if (st[i] != XFFT_OK && st[i] != XFFT_ENOTCONV)
+      return fail(st[i], "context " + std::to_string(i) + ": " + msg[i]);
+  for (int i = 0; i < n; ++i)
+    if (st[i] != XFFT_OK) return fail(st[i], "context " + std::to_string(i) + ": " + msg[i]);
+  return XFFT_OK;
 }
 
 extern "C" xfft_status xfft_grad(xfft_ctx* c, const double dL_dCeff[36], double dL_dlame[4],

@@ -304,6 +304,48 @@ def test_autograd_effective_stiffness(xf):
     assert abs(fd - lame.grad[p].item()) < 1e-5 * abs(lame.grad[p].item())
 
 
+def test_batch_uneven_microstructures(xf):
+    """Batch of microstructures on uneven grids solved at once (one host thread and stream per
+    context, graph-replayed iterations), FP32-refined to 1e-8: each C_eff against its own FP64
+    solve, against the same solver run alone, and (16^3 member) against the oracle."""
+    ws = synth.batch_uneven(count=6, seed=5, sizes=(16, 32, 48))
+    ws[0] = dict(ws[0], n=(16, 16, 16), L=synth.sphere_levelset((16, 16, 16), (0.5, 0.5, 0.5), 0.3))
+    solvers = []
+    for w in ws:
+        sv = xf.Solver(w["n"], precision="fp32", tol=1e-8)
+        sv.set_microstructure(w["L"], w["lame_minus"], w["lame_plus"])
+        solvers.append(sv)
+    Cs, sts = xf.batch_effective_stiffness(solvers)
+    for w, C, st, sv in zip(ws, Cs, sts, solvers):
+        s64 = xf.Solver(w["n"], precision="fp64", tol=1e-11)
+        s64.set_microstructure(w["L"], w["lame_minus"], w["lame_plus"])
+        C64, st64 = s64.effective_stiffness()
+        assert st64["converged"]
+        assert np.abs(C - C64).max() < 1e-6 * np.abs(C64).max(), (w["n"], np.abs(C - C64).max())
+        C1, st1 = sv.effective_stiffness()  # the same context alone
+        assert st1["converged"]
+        assert np.abs(C1 - C).max() < 1e-7 * np.abs(C).max()
+    o = XFEM(ws[0]["L"], ws[0]["n"], lame_minus=ws[0]["lame_minus"], lame_plus=ws[0]["lame_plus"])
+    Co, _, _ = o.effective_stiffness()
+    assert np.abs(Cs[0] - Co).max() < 1e-6 * np.abs(Co).max()
+
+
+def test_legacy_stream_matches_own_stream(xf):
+    """The same solve on the legacy stream (plain launches) and on the solver's own stream
+    (graph-replayed iterations) gives the same result."""
+    n, ell, L, lm, lp, sc = _case("ragged")
+    out = []
+    for stream in ("legacy", None):
+        s = xf.Solver(n, ell, precision="fp32", tol=1e-10, stream=stream)
+        s.set_microstructure(L, lm, lp, sc)
+        C, st = s.effective_stiffness()
+        assert st["converged"]
+        out.append((C, st["iters"]))
+    # FP32 atomics make the sums order-dependent: equal up to rounding, not bit for bit
+    assert all(abs(a - b) <= 2 for a, b in zip(out[0][1], out[1][1]))
+    assert np.abs(out[0][0] - out[1][0]).max() < 1e-8 * np.abs(out[0][0]).max()
+
+
 def test_laminate_closed_form_gpu(xf):
     from tests.test_oracle_pins import _laminate_closed_form
     n = (32, 32, 32)
