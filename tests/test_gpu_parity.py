@@ -405,6 +405,46 @@ def test_laminate_closed_form_yz128(xf):
     assert np.abs(C - Cref).max() < 1e-6 * np.abs(Cref).max(), np.abs(C - Cref).max()
 
 
+def test_full_size_laminate_384(xf):
+    """Precision at scale: the 384^3 laminate tilted by (1,2,3)/sqrt(14), contrast 100,
+    FP32-refined, against its closed-form C_eff to 1e-6 (the X-FEM solution is exact for a
+    laminate, so the closed form holds at any grid size)."""
+    from tests.test_oracle_pins import _laminate_closed_form
+    w = synth.make_workload("laminate")
+    s = xf.Solver(w["n"], precision="fp32", tol=1e-9)
+    s.set_microstructure(w["L"], w["lame_minus"], w["lame_plus"])
+    C, st = s.effective_stiffness()
+    assert st["converged"], st
+    Cref = _laminate_closed_form(w["info"]["normal"], w["info"]["fraction"], w["lame_minus"], w["lame_plus"])
+    assert np.abs(C - Cref).max() < 1e-6 * np.abs(Cref).max(), np.abs(C - Cref).max()
+
+
+def test_full_size_fibers_256(xf):
+    """Precision at scale: 256^3 with 60 periodic fibers (contrast 100): FP32-refined against plain
+    FP64 to 1e-6; C_eff symmetric, positive definite and between the Reuss and Voigt bounds of the
+    phase volume fractions (properties that hold at any size)."""
+    from oracle import iso_stiffness
+    w = synth.make_workload("fibers60")
+    out = {}
+    for prec, tol in (("fp32", 1e-8), ("fp64", 1e-10)):
+        s = xf.Solver(w["n"], precision=prec, tol=tol)
+        s.set_microstructure(w["L"], w["lame_minus"], w["lame_plus"])
+        out[prec], st = s.effective_stiffness()
+        assert st["converged"], (prec, st)
+        s.close()
+    C, C64 = out["fp32"], out["fp64"]
+    assert np.abs(C - C64).max() < 1e-6 * np.abs(C64).max(), np.abs(C - C64).max()
+    assert np.abs(C64 - C64.T).max() < 1e-8 * np.abs(C64).max()
+    assert np.linalg.eigvalsh(0.5 * (C64 + C64.T)).min() > 0.0
+    f = float(np.mean(w["L"] < 0.0))  # nodal estimate of the fibre fraction
+    Ci, Cm = iso_stiffness(*w["lame_minus"]), iso_stiffness(*w["lame_plus"])
+    voigt = f * Ci + (1 - f) * Cm
+    reuss = np.linalg.inv(f * np.linalg.inv(Ci) + (1 - f) * np.linalg.inv(Cm))
+    sym = 0.5 * (C64 + C64.T)
+    assert np.linalg.eigvalsh(voigt - sym).min() > -1e-2 * np.abs(C64).max()
+    assert np.linalg.eigvalsh(sym - reuss).min() > -1e-2 * np.abs(C64).max()
+
+
 def test_homogeneous_and_equal_phase_edge_cases(xf):
     n = (4, 4, 4)
     lp = synth.lame_from_E_nu(2.0, 0.3)
