@@ -165,10 +165,20 @@ struct Coef {
 // One uncut Kuhn tet: the displacement-gradient columns of the tet are the node differences
 // along its path 0 -> e_p -> e_p+e_q -> (1,1,1); the edge tensions T_k = w_k sigma e_k move
 // the corner forces: F[0] -= T_p, F[c1] += T_p - T_q, F[c2] += T_q - T_r, F[7] += T_r.
-template <typename T, int t, bool TOTAL, bool SIG, bool UNIFORM>
+// Edge tensions of a voxel, summed over its tets: first edges 0 -> e_p (TE0[p]), middle edges
+// e_p -> e_p + e_q (TEM[p][q]), last edges e_p + e_q -> (1,1,1) (TEL[r], r the third axis).
+template <typename T>
+struct EdgeT {
+  T e0[3][3], em[3][3][3], el[3][3];
+};
+
+// EDGE: add the tet's tensions to the voxel's edge sums (corner forces formed once per voxel by
+// edge_forces); otherwise add them to the corner forces F directly.
+template <typename T, int t, bool TOTAL, bool SIG, bool UNIFORM, bool EDGE = false>
 __device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3], unsigned code,
                                             const Coef<T, UNIFORM>& cf, const T (&ih)[3],
-                                            const T (&hk)[3], const T (&Eb)[3][3], T& en, T (&sg)[6]) {
+                                            const T (&hk)[3], const T (&Eb)[3][3], T& en, T (&sg)[6],
+                                            EdgeT<T>* te = nullptr) {
   constexpr int p = perm_p(t), q = perm_q(t), r = perm_r(t);
   constexpr int c1 = tet_c1(t), c2 = tet_c2(t);
   const unsigned cd = (code >> (2 * t)) & 3u;
@@ -218,12 +228,21 @@ __device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3]
     Tn[1][2] = cf.m(ph, 1) * s12;
     Tn[2][1] = cf.m(ph, 2) * s12;
   }
+  if (EDGE) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    F[0][i] -= Tn[p][i];
-    F[c1][i] += Tn[p][i] - Tn[q][i];
-    F[c2][i] += Tn[q][i] - Tn[r][i];
-    F[7][i] += Tn[r][i];
+    for (int i = 0; i < 3; ++i) {
+      te->e0[p][i] += Tn[p][i];
+      te->em[p][q][i] += Tn[q][i];
+      te->el[r][i] += Tn[r][i];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      F[0][i] -= Tn[p][i];
+      F[c1][i] += Tn[p][i] - Tn[q][i];
+      F[c2][i] += Tn[q][i] - Tn[r][i];
+      F[7][i] += Tn[r][i];
+    }
   }
   if (SIG) {
     // |T| sigma_ik = h_k Tn[k][i]; |T| sigma : eps = sum_k hk[k] Tn[k] . Dr[k]
@@ -240,6 +259,27 @@ __device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3]
     en += e;
   }
 }
+
+// Corner forces of a voxel from its edge tensions: each edge pulls its end corner and pushes
+// its start corner (corner index bits: x = 1, y = 2, z = 4).
+template <typename T>
+__device__ __forceinline__ void edge_forces(const EdgeT<T>& te, T (&F)[8][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    F[0][i] = -(te.e0[0][i] + te.e0[1][i] + te.e0[2][i]);
+    F[7][i] = te.el[0][i] + te.el[1][i] + te.el[2][i];
+    F[1][i] = te.e0[0][i] - te.em[0][1][i] - te.em[0][2][i];
+    F[2][i] = te.e0[1][i] - te.em[1][0][i] - te.em[1][2][i];
+    F[4][i] = te.e0[2][i] - te.em[2][0][i] - te.em[2][1][i];
+    F[3][i] = te.em[0][1][i] + te.em[1][0][i] - te.el[2][i];
+    F[5][i] = te.em[0][2][i] + te.em[2][0][i] - te.el[1][i];
+    F[6][i] = te.em[1][2][i] + te.em[2][1][i] - te.el[0][i];
+  }
+}
+
+#ifndef XFFT_EDGE_FORCES
+#define XFFT_EDGE_FORCES 1  // corner forces from per-voxel edge tension sums
+#endif
 
 template <typename T, bool TOTAL, bool SIG, bool UNIFORM, bool FUSED>
 __global__ void __launch_bounds__(kTZ* kTY, std::is_same<T, dw>::value     ? XFFT_UNCUT_MINBDW
@@ -401,21 +441,27 @@ __global__ void __launch_bounds__(kTZ* kTY, std::is_same<T, dw>::value     ? XFF
   fetch(xfirst, false);
   commit(0);
   fetch(xfirst + 1 == n0 ? 0 : xfirst + 1, x0 < x1);
+  // the voxel's phase code and modulus scale are loaded one x step ahead as well
+  const long long yz = (long long)yv * n2 + zv;
+  unsigned nx_code = a.code[(long long)xfirst * plane + yz];
+  float nx_scale = a.scale ? a.scale[(long long)xfirst * plane + yz] : 1.0f;
   for (int s = 0; s <= x1 - x0; ++s) {
     const int xv = x0 - 1 + s;
     const int xw = (xv % n0 + n0) % n0;
+    const unsigned code = nx_code;
+    const T sv = from_store<T>(nx_scale);
     commit((s + 1) & 1);  // plane x0 + s
     if (s + 1 <= x1 - x0) {
+      const int x1w = xw + 1 >= n0 ? xw + 1 - n0 : xw + 1;  // voxel of the next step
       const int xn = xw + 2 >= n0 ? xw + 2 - n0 : xw + 2;  // plane x0 + s + 1
       fetch(xn, x0 + s + 1 < x1);
+      nx_code = a.code[(long long)x1w * plane + yz];
+      if (a.scale) nx_scale = a.scale[(long long)x1w * plane + yz];
     }
     __syncthreads();
     Node4<T> u[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) u[c] = P[(s + (c & 1)) & 1][ty + ((c >> 1) & 1)][tz + ((c >> 2) & 1)];
-    const long long vox = (long long)xw * plane + (long long)yv * n2 + zv;
-    const unsigned code = a.code[vox];
-    const T sv = a.scale ? from_store<T>(a.scale[vox]) : T(1);
     Coef<T, UNIFORM> cf;
 #pragma unroll
     for (int ph = 0; ph < 2; ++ph)
@@ -425,16 +471,37 @@ __global__ void __launch_bounds__(kTZ* kTY, std::is_same<T, dw>::value     ? XFF
         cf.mw[ph][k] = mw0[ph][k] * sv;
       }
     T F[8][3];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) F[c][0] = F[c][1] = F[c][2] = T(0);
     T ven = T(0);
     T vsg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#if XFFT_EDGE_FORCES
+    {
+      EdgeT<T> te;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          te.e0[k][i] = te.el[k][i] = T(0);
+#pragma unroll
+          for (int l = 0; l < 3; ++l) te.em[k][l][i] = T(0);
+        }
+      tet_stencil<T, 0, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 1, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 2, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 3, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 4, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 5, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      edge_forces(te, F);
+    }
+#else
+#pragma unroll
+    for (int c = 0; c < 8; ++c) F[c][0] = F[c][1] = F[c][2] = T(0);
     tet_stencil<T, 0, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
     tet_stencil<T, 1, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
     tet_stencil<T, 2, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
     tet_stencil<T, 3, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
     tet_stencil<T, 4, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
     tet_stencil<T, 5, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+#endif
     if (SIG && own && s >= 1) {
       en += ven;
 #pragma unroll
@@ -555,8 +622,13 @@ __device__ __forceinline__ dw cut_real_keep<dw>(const CutData& cd, int f, int e)
 constexpr int kCutThreads = 128;
 constexpr int kCutMaxR = 8;  // right-hand sides per launch (more are split over launches)
 
+#ifndef XFFT_CUT_MINB
+#define XFFT_CUT_MINB 4  // resident blocks per SM asked of the FP32 cut kernel
+#endif
 template <typename T, bool TOTAL>
-__global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1 : sizeof(T) == 8 ? 2 : 4)
+__global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1
+                                               : sizeof(T) == 8       ? 2
+                                                                      : XFFT_CUT_MINB)
     k_apply_cut(const typename Store<T>::type* __restrict__ d, typename Store<T>::type* __restrict__ q,
                 const typename Store<T>::type* __restrict__ isD, const CutData cd, const ApplyArgs a,
                 int r0, int nr) {
@@ -641,7 +713,9 @@ __global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1 : 
         for (int k = 0; k < 4; ++k)
 #pragma unroll
           for (int c = 0; c < 3; ++c) qs[k][c] = qe[k][c] = T(0);
-#pragma unroll
+        // double-word sides run one after the other (register pressure)
+        constexpr int kSides = std::is_same<T, dw>::value ? 1 : 2;
+#pragma unroll kSides
         for (int si = 0; si < 2; ++si) {
           const T s = si == 0 ? T(1) : T(-1);
           const int ph = si == 0 ? 1 : 0;
