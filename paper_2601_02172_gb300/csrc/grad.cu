@@ -39,7 +39,73 @@ __device__ __forceinline__ T dd6(const T* a, const T* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + T(2) * (a[3] * b[3] + a[4] * b[4] + a[5] * b[5]);
 }
 
-// block: 32 voxels (x) by 6 tets (y)
+// One uncut tet t (compile time) of voxel v: strains of the six load cases, their pair products,
+// the phase sums and the energy-form entries (accumulated in T per thread; FP32 sums of a few
+// dozen items are exact to ~1e-7), and the voxel-scale contribution.
+template <typename T, int t>
+__device__ __forceinline__ void grad_uncut_tet(const double* __restrict__ U, const GradArgs& a,
+                                               const double* Gs, long long v, unsigned cd, T (&acc)[kNG],
+                                               double& contrib) {
+  const GridDev& g = a.g;
+  constexpr int p = perm_p(t), q = perm_q(t), r = perm_r(t);
+  const int k3 = (int)(v % g.n2);
+  const int j3 = (int)((v / g.n2) % g.n1);
+  const int i3 = (int)(v / ((long long)g.n1 * g.n2));
+  long long nd[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) nd[c] = corner_node(g, i3, j3, k3, tet_corner(t, c));
+  const T ih[3] = {(T)(1.0 / g.h[0]), (T)(1.0 / g.h[1]), (T)(1.0 / g.h[2])};
+  const T rs = (T)0.70710678118654752440;
+  T eps[6][6], tr[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double* uk = U + k * a.stride;
+    T H[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double u0 = uk[i * g.N + nd[0]], u1 = uk[i * g.N + nd[1]];
+      const double u2 = uk[i * g.N + nd[2]], u3 = uk[i * g.N + nd[3]];
+      // the differences cancel: formed in FP64, then scaled in T
+      H[i][p] = (T)(u1 - u0) * ih[p];
+      H[i][q] = (T)(u2 - u1) * ih[q];
+      H[i][r] = (T)(u3 - u2) * ih[r];
+    }
+    eps[k][0] = H[0][0];
+    eps[k][1] = H[1][1];
+    eps[k][2] = H[2][2];
+    eps[k][3] = T(0.5) * (H[1][2] + H[2][1]);
+    eps[k][4] = T(0.5) * (H[0][2] + H[2][0]);
+    eps[k][5] = T(0.5) * (H[0][1] + H[1][0]);
+    eps[k][k] += k < 3 ? T(1) : rs;  // unit Mandel strain E_k
+    tr[k] = eps[k][0] + eps[k][1] + eps[k][2];
+  }
+  const T lam = (T)a.ph.lam[cd], mu = (T)a.ph.mu[cd];
+  const double sv = a.scale ? (double)a.scale[v] : 1.0;
+  const double w = g.vol_tet / g.volY;
+  const T wsv = (T)(w * sv);
+  T ql = T(0), qm = T(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int l = k; l < 6; ++l) {
+      const T tt = tr[k] * tr[l];
+      const T ee = T(2) * dd6(eps[k], eps[l]);
+      const T gk = (T)((k == l) ? Gs[k * 6 + l] : Gs[k * 6 + l] + Gs[l * 6 + k]);
+      ql += gk * tt;
+      qm += gk * ee;
+      acc[4 + upper_idx(k, l)] += wsv * (lam * tt + mu * ee);
+    }
+  if (cd == 0u) {
+    acc[0] += wsv * ql;
+    acc[2] += wsv * qm;
+  } else {
+    acc[1] += wsv * ql;
+    acc[3] += wsv * qm;
+  }
+  contrib = w * (double)(lam * ql + mu * qm);
+}
+
+// block: 32 voxels (x) by 6 tets (y); each warp handles one tet of 32 voxels
 template <typename T>
 __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U, const GradArgs a,
                                                      double* __restrict__ dscale) {
@@ -51,12 +117,9 @@ __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U
   if (tid < 36) Gs[tid] = a.G[tid];
   __syncthreads();
   const GridDev& g = a.g;
-  const double inv = 1.0 / g.volY;
-  double ih[3];
-  for (int k = 0; k < 3; ++k) ih[k] = 1.0 / g.h[k];
-  double acc[kNG];
+  T acc[kNG];
 #pragma unroll
-  for (int i = 0; i < kNG; ++i) acc[i] = 0.0;
+  for (int i = 0; i < kNG; ++i) acc[i] = T(0);
   const long long ngroups = (g.N + 31) / 32;
   for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const long long v = grp * 32 + lane;
@@ -64,53 +127,14 @@ __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U
     if (v < g.N) {
       const unsigned cd = (a.code[v] >> (2 * t)) & 3u;
       if (cd != 2u) {
-        const int k3 = (int)(v % g.n2);
-        const int j3 = (int)((v / g.n2) % g.n1);
-        const int i3 = (int)(v / ((long long)g.n1 * g.n2));
-        long long nd[4];
-        for (int c = 0; c < 4; ++c) nd[c] = corner_node(g, i3, j3, k3, tet_corner(t, c));
-        const int p = perm_p(t), q = perm_q(t), r = perm_r(t);
-        T eps[6][6], tr[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          const double* uk = U + k * a.stride;
-          double H[3][3];
-          for (int i = 0; i < 3; ++i) {
-            const double u0 = uk[i * g.N + nd[0]], u1 = uk[i * g.N + nd[1]];
-            const double u2 = uk[i * g.N + nd[2]], u3 = uk[i * g.N + nd[3]];
-            H[i][p] = (u1 - u0) * ih[p];
-            H[i][q] = (u2 - u1) * ih[q];
-            H[i][r] = (u3 - u2) * ih[r];
-          }
-          double E[6];
-          unit_strain(k, E);
-          eps[k][0] = (T)(H[0][0] + E[0]);
-          eps[k][1] = (T)(H[1][1] + E[1]);
-          eps[k][2] = (T)(H[2][2] + E[2]);
-          eps[k][3] = (T)(0.5 * (H[1][2] + H[2][1]) + E[3]);
-          eps[k][4] = (T)(0.5 * (H[0][2] + H[2][0]) + E[4]);
-          eps[k][5] = (T)(0.5 * (H[0][1] + H[1][0]) + E[5]);
-          tr[k] = eps[k][0] + eps[k][1] + eps[k][2];
+        switch (t) {  // uniform per warp
+          case 0: grad_uncut_tet<T, 0>(U, a, Gs, v, cd, acc, contrib); break;
+          case 1: grad_uncut_tet<T, 1>(U, a, Gs, v, cd, acc, contrib); break;
+          case 2: grad_uncut_tet<T, 2>(U, a, Gs, v, cd, acc, contrib); break;
+          case 3: grad_uncut_tet<T, 3>(U, a, Gs, v, cd, acc, contrib); break;
+          case 4: grad_uncut_tet<T, 4>(U, a, Gs, v, cd, acc, contrib); break;
+          default: grad_uncut_tet<T, 5>(U, a, Gs, v, cd, acc, contrib); break;
         }
-        const int ph = (int)cd;
-        const T lam = (T)a.ph.lam[ph], mu = (T)a.ph.mu[ph];
-        const double sv = a.scale ? (double)a.scale[v] : 1.0;
-        const double w = g.vol_tet * inv;
-        T ql = T(0), qm = T(0);
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-#pragma unroll
-          for (int l = k; l < 6; ++l) {
-            const T tt = tr[k] * tr[l];
-            const T ee = T(2) * dd6(eps[k], eps[l]);
-            const T gk = (T)((k == l) ? Gs[k * 6 + l] : Gs[k * 6 + l] + Gs[l * 6 + k]);
-            ql += gk * tt;
-            qm += gk * ee;
-            acc[4 + upper_idx(k, l)] += w * sv * (double)(lam * tt + mu * ee);
-          }
-        acc[ph] += w * sv * (double)ql;
-        acc[2 + ph] += w * sv * (double)qm;
-        contrib = w * (double)(lam * ql + mu * qm);
       }
     }
     sds[t][lane] = contrib;
@@ -119,8 +143,10 @@ __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U
       dscale[v] = sds[0][lane] + sds[1][lane] + sds[2][lane] + sds[3][lane] + sds[4][lane] + sds[5][lane];
     __syncthreads();
   }
-  double tot[kNG];
-  block_sum<kNG>(acc, red, tot);
+  double accd[kNG], tot[kNG];
+#pragma unroll
+  for (int i = 0; i < kNG; ++i) accd[i] = (double)acc[i];
+  block_sum<kNG>(accd, red, tot);
   if (tid == 0)
     for (int i = 0; i < kNG; ++i) a.partials[(long long)i * a.nparts + blockIdx.x] = tot[i];
 }
