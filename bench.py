@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the block-preconditioner, batch and cuFFT side measurements")
     ap.add_argument("--cpu-n", type=int, default=16)
     return ap.parse_args()
 
@@ -375,64 +377,65 @@ def main():
                 "ceff_rel_err_fp64_vs_fp64_tol1e-10": float(np.abs(C64 - Cref).max() / np.abs(Cref).max())}
             s64.close()
             sref.close()
-        # variant enriched preconditioner (3x3 node blocks): same system, iteration count and rate
-        sb = Solver(n, precision="fp32", tol=args.tol, enr_precond="block3")
-        sb.set_microstructure(L_d, lm, lp, s_d)
-        sb.effective_stiffness()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Cb, stb = sb.effective_stiffness()
-        torch.cuda.synchronize()
-        extra["enr_block3"] = {"solves_per_s": 1.0 / (time.perf_counter() - t0),
-                               "cg_iters": int(sum(stb["iters"])),
-                               "identity_cg_iters": steps_iters / args.steps,
-                               "ceff_rel_diff_vs_identity": float(np.abs(Cb - C).max() / np.abs(C).max())}
-        sb.close()
-        # many microstructures at once (16 uneven grids x 6 load cases, FP32-refined to 1e-8):
-        # one call, one host thread and stream per microstructure, against the same solvers in turn
-        from paper_2601_02172_gb300 import batch_effective_stiffness
-        bw = synth.batch_uneven(16, seed=3)
-        bsolvers = []
-        for wb in bw:
-            sv = Solver(wb["n"], precision="fp32", tol=1e-8)
-            sv.set_microstructure(wb["L"], wb["lame_minus"], wb["lame_plus"])
-            bsolvers.append(sv)
-        batch_effective_stiffness(bsolvers)  # warm-up (graph capture)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, bst = batch_effective_stiffness(bsolvers)
-        torch.cuda.synchronize()
-        t_bat = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        for sv in bsolvers:
-            sv.effective_stiffness()
-        torch.cuda.synchronize()
-        t_seq = time.perf_counter() - t0
-        extra["batch16"] = {"microstructures": len(bw), "rhs": 6 * len(bw),
-                            "grids": [int(wb["n"][0]) for wb in bw], "tol": 1e-8,
-                            "solves_per_s_batched": len(bw) / t_bat,
-                            "solves_per_s_sequential": len(bw) / t_seq,
-                            "dof_iters_per_s_batched": sum(3.0 * (sb["n_fe"] + sb["n_x"]) * sum(sb["iters"])
-                                                           for sb in bst) / t_bat}
-        for sv in bsolvers:
-            sv.close()
-        # cuFFT (torch.fft) R2C + C2R of the same 3 x 6 FP32 fields, beside the preconditioner
-        x = torch.randn(18, *n, device=dev, dtype=torch.float32)
-        for _ in range(3):
-            torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=n, dim=(1, 2, 3))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(10):
-            torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=n, dim=(1, 2, 3))
-        e1.record()
-        torch.cuda.synchronize()
-        pms, _, punits = prof["prec_f32"]
-        extra["fft_baseline"] = {"cufft_r2c_c2r_ms_per_rhs": e0.elapsed_time(e1) / 10 / 6,
-                                 "xfft_precondition_ms_per_rhs": pms / max(punits, 1),
-                                 "note": "cuFFT: 3 fields R2C + C2R per RHS (no Green solve); xfft: "
-                                         "the whole preconditioner (3 passes, Green solve, fused "
-                                         "update and dot product)"}
-        del x
+        if not args.no_extras:
+            # variant enriched preconditioner (3x3 node blocks): same system, iteration count and rate
+            sb = Solver(n, precision="fp32", tol=args.tol, enr_precond="block3")
+            sb.set_microstructure(L_d, lm, lp, s_d)
+            sb.effective_stiffness()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Cb, stb = sb.effective_stiffness()
+            torch.cuda.synchronize()
+            extra["enr_block3"] = {"solves_per_s": 1.0 / (time.perf_counter() - t0),
+                                   "cg_iters": int(sum(stb["iters"])),
+                                   "identity_cg_iters": steps_iters / args.steps,
+                                   "ceff_rel_diff_vs_identity": float(np.abs(Cb - C).max() / np.abs(C).max())}
+            sb.close()
+            # many microstructures at once (16 uneven grids x 6 load cases, FP32-refined to 1e-8):
+            # one call, one host thread and stream per microstructure, against the same solvers in turn
+            from paper_2601_02172_gb300 import batch_effective_stiffness
+            bw = synth.batch_uneven(16, seed=3)
+            bsolvers = []
+            for wb in bw:
+                sv = Solver(wb["n"], precision="fp32", tol=1e-8)
+                sv.set_microstructure(wb["L"], wb["lame_minus"], wb["lame_plus"])
+                bsolvers.append(sv)
+            batch_effective_stiffness(bsolvers)  # warm-up (graph capture)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, bst = batch_effective_stiffness(bsolvers)
+            torch.cuda.synchronize()
+            t_bat = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            for sv in bsolvers:
+                sv.effective_stiffness()
+            torch.cuda.synchronize()
+            t_seq = time.perf_counter() - t0
+            extra["batch16"] = {"microstructures": len(bw), "rhs": 6 * len(bw),
+                                "grids": [int(wb["n"][0]) for wb in bw], "tol": 1e-8,
+                                "solves_per_s_batched": len(bw) / t_bat,
+                                "solves_per_s_sequential": len(bw) / t_seq,
+                                "dof_iters_per_s_batched": sum(3.0 * (sb["n_fe"] + sb["n_x"]) * sum(sb["iters"])
+                                                               for sb in bst) / t_bat}
+            for sv in bsolvers:
+                sv.close()
+            # cuFFT (torch.fft) R2C + C2R of the same 3 x 6 FP32 fields, beside the preconditioner
+            x = torch.randn(18, *n, device=dev, dtype=torch.float32)
+            for _ in range(3):
+                torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=n, dim=(1, 2, 3))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=n, dim=(1, 2, 3))
+            e1.record()
+            torch.cuda.synchronize()
+            pms, _, punits = prof["prec_f32"]
+            extra["fft_baseline"] = {"cufft_r2c_c2r_ms_per_rhs": e0.elapsed_time(e1) / 10 / 6,
+                                     "xfft_precondition_ms_per_rhs": pms / max(punits, 1),
+                                     "note": "cuFFT: 3 fields R2C + C2R per RHS (no Green solve); xfft: "
+                                             "the whole preconditioner (3 passes, Green solve, fused "
+                                             "update and dot product)"}
+            del x
         cpu = None
         if not args.no_cpu and world == 1:
             try:
