@@ -38,16 +38,16 @@ WORKLOAD = ("ellipsoids40: 128^3 periodic grid, 40 random ellipsoids (aspect 1-3
 # algorithmic bytes per processed right-hand side and launch ("Roofline")
 def algorithmic_bytes(kind, N, nX, ncut, has_scale):
     geo = N * (2 + (4 if has_scale else 0))
-    if kind == "apply_uncut_f32":
-        return 24 * N + geo
+    if kind == "apply_uncut_f32":  # the fused CG form: z, d_old, u in; d_new, u, q out
+        return 72 * N + geo
     if kind == "apply_uncut_f64":
         return 48 * N + geo
-    if kind == "prec_f32":
-        return 24 * (N + nX)
+    if kind == "prec_f32":  # fused form: f, q in; f (f -= alpha q) and z out
+        return 48 * (N + nX)
     if kind == "prec_f64":
         return 48 * (N + nX)
-    if kind == "apply_cut_f32":
-        return 408 * ncut
+    if kind == "apply_cut_f32":  # per RHS: geometry (168 B per tet, once per 6 RHS) + 24 gathers
+        return (28 + 240) * ncut   # (incl. 1/sqrt(D0)) + 24 atomic adds
     if kind == "apply_cut_f64":
         return 776 * ncut
     return None
