@@ -27,7 +27,10 @@ namespace xfft {
 
 constexpr int kTZ = 16;  // threads along z (half a warp; a warp covers two y rows)
 constexpr int kTY = 16;  // threads along y
-constexpr int kCX = 32;  // output planes per block along x
+#ifndef XFFT_UNCUT_CX
+#define XFFT_UNCUT_CX 32
+#endif
+constexpr int kCX = XFFT_UNCUT_CX;  // output planes per block along x
 #ifndef XFFT_UNCUT_MINB
 #define XFFT_UNCUT_MINB 2  // resident blocks per SM asked of the FP32 uncut kernel
 #endif
@@ -807,7 +810,10 @@ int apply_uncut_blocks(const GridDev& g) {
   return gz * gy * gx;
 }
 
-constexpr int kCutBlocksMax = 2 * 4 * 152;  // two waves of four resident blocks per SM
+#ifndef XFFT_CUT_WAVES
+#define XFFT_CUT_WAVES 2
+#endif
+constexpr int kCutBlocksMax = XFFT_CUT_WAVES * 4 * 152;  // waves of four resident blocks per SM
 int apply_cut_blocks(int ncut) {
   const int nb = (ncut + kCutThreads - 1) / kCutThreads;
   return nb < 1 ? 1 : (nb > kCutBlocksMax ? kCutBlocksMax : nb);
