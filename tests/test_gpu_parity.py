@@ -173,6 +173,17 @@ def test_block_enriched_preconditioner(xf, name, prec):
         assert _rel(out["u_std"][0], u[: 3 * o.nFE].reshape(3, -1)) < 1e-9
 
 
+def test_one_call_solve(xf):
+    """The one-call Python solve equals the oracle's direct solution (sphere16)."""
+    n, ell, L, lm, lp, sc = _case("sphere16")
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    eps = np.array([[0.3, 0.1, -0.2, 0.0, 0.5, 0.0]])
+    out = xf.solve(L, lm, lp, eps, precision="fp64", tol=1e-12)
+    assert out["converged"]
+    u = o.solve_direct(eps[0])
+    assert _rel(out["u_std"][0], u[: 3 * o.nFE].reshape(3, -1)) < 1e-9
+
+
 @pytest.mark.parametrize("name", ["sphere16", "ragged"])
 def test_fp64_solve_matches_direct(xf, name):
     n, ell, L, lm, lp, sc = _case(name)
@@ -443,6 +454,64 @@ def test_full_size_fibers_256(xf):
     sym = 0.5 * (C64 + C64.T)
     assert np.linalg.eigvalsh(voigt - sym).min() > -1e-2 * np.abs(C64).max()
     assert np.linalg.eigvalsh(sym - reuss).min() > -1e-2 * np.abs(C64).max()
+
+
+def test_full_size_spheres27_64(xf):
+    """Config 2 at full size (64^3, 27 spheres, vf 20 %, contrast 100, six load cases): C_eff
+    against the oracle's (tests/golden/spheres27_64_ceff.json, written from oracle/ alone by
+    make_spheres27_ceff.py), FP64 to 1e-9 and FP32-refined to 1e-6; the setup counts exactly."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "spheres27_64_ceff.json")))
+    Cg = np.array(gold["C_stress"])
+    w = synth.make_workload("spheres27")
+    for prec, tol, bar in (("fp64", 1e-12, 1e-9), ("fp32", 1e-9, 1e-6)):
+        s = xf.Solver(w["n"], precision=prec, tol=tol)
+        s.set_microstructure(w["L"], w["lame_minus"], w["lame_plus"])
+        assert s.num_enriched == gold["n_enriched"] and s.num_cut_tets == gold["n_cut_tets"]
+        C, st = s.effective_stiffness()
+        assert st["converged"], (prec, st)
+        assert np.abs(C - Cg).max() < bar * np.abs(Cg).max(), (prec, np.abs(C - Cg).max())
+        s.close()
+
+
+def test_full_size_gradient_128(xf):
+    """Differentiation at full size: 128^3, 40 ellipsoids, per-voxel modulus scale, loss
+    ||C_eff - C_t||^2.  The FP64 adjoint against central finite differences (h = 1e-6 relative,
+    FP64 solves) in one Lame constant of each phase; the FP32-refined gradient against the FP64
+    one."""
+    w = synth.make_workload("ellipsoids40")
+    n, L, sc = w["n"], w["L"], w["scale"]
+    theta = [*w["lame_minus"], *w["lame_plus"]]
+
+    def solve(th, prec="fp64", tol=1e-12):
+        s = xf.Solver(n, precision=prec, tol=tol)
+        s.set_microstructure(L, (th[0], th[1]), (th[2], th[3]), sc)
+        C, st = s.effective_stiffness()
+        assert st["converged"], st
+        return s, C
+
+    s64, C0 = solve(theta)
+    G = np.random.default_rng(4).normal(size=(6, 6))
+    G = 0.5 * (G + G.T)
+    Ct = C0 + 0.05 * np.linalg.norm(C0) / np.linalg.norm(G) * G
+    dl, ds, _ = s64.grad(2.0 * (C0 - Ct))
+    s64.close()
+    for p in (0, 3):
+        h = 1e-6 * theta[p]
+        tp, tm = list(theta), list(theta)
+        tp[p] += h
+        tm[p] -= h
+        sp_, Cp = solve(tp)
+        sp_.close()
+        sm_, Cm = solve(tm)
+        sm_.close()
+        fd = (np.sum((Cp - Ct) ** 2) - np.sum((Cm - Ct) ** 2)) / (2 * h)
+        assert abs(fd - dl[p]) < 1e-5 * np.abs(dl).max(), (p, fd, dl[p])
+    s32, C32 = solve(theta, "fp32", 1e-8)
+    dl32, ds32, _ = s32.grad(2.0 * (C32 - Ct))
+    assert np.abs(dl32 - dl).max() < 1e-5 * np.abs(dl).max()
+    assert _rel(ds32.astype(np.float64), ds.astype(np.float64)) < 1e-4
 
 
 def test_homogeneous_and_equal_phase_edge_cases(xf):
