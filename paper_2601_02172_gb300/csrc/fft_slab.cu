@@ -37,7 +37,10 @@ constexpr int E = 16;                      // elements per thread of the y and z
 constexpr int NT = N1 * N2 / (2 * E);      // threads of the plane kernels (512)
 constexpr int kGF = 9;                     // floats per Green factor: il00, il11, il22, l10, l20, l21
 constexpr int ST = 8;                      // slots per x-pass block (one 64-byte segment)
-constexpr int RG = 2;                      // right-hand sides per x-pass block
+#ifndef XFFT_KXS_RG
+#define XFFT_KXS_RG 2
+#endif
+constexpr int RG = XFFT_KXS_RG;            // right-hand sides per x-pass block
 // x pass: elements per thread and block size for x length N0
 template <int N0>
 struct XCfg {
