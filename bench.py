@@ -229,6 +229,19 @@ def traffic_for(kind):
     return ent
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time of the timed region (every rank gets it)."""
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, ms):
+    """Whole-job rate: every replica solved `steps` six-case problems in `ms` (the max over ranks)."""
+    return world * steps / (ms / 1000.0)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -312,13 +325,11 @@ def main():
     solver.profile(False)
     ms = ev0.elapsed_time(ev1)
     if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         dist.barrier()
     steps_iters = info["iters"]
     dofit_rate = info["dofit"] / (ms / 1000.0)
-    value = world * args.steps / (ms / 1000.0)
+    value = job_value(world, args.steps, ms)
 
     # live roofline of the dominant kernel group
     peak, peak_kind = load_peaks()
