@@ -590,7 +590,15 @@ class XFEM:
             self.assemble()
         return (np.asarray(self.Sm @ u).ravel() + self.Cbar @ np.asarray(eps, float)) / self.volY
 
-    def pcg(self, eps, tol=1e-10, maxit=10000, green="sparse", u0=None, enr="identity"):
+    def basic_step(self):
+        """Step size s0 = 2 / (C_- + C_+) of the basic scheme (eq. stepsize): C_- (C_+) is the
+        smallest (largest) eigenvalue of the stiffness tensors of all materials; with isotropic
+        phases the eigenvalues are 2 mu and 3 lambda + 2 mu, times the extreme voxel scales."""
+        ev = [e for lam, mu in self.lame.values() for e in (2.0 * mu, 3.0 * lam + 2.0 * mu)]
+        return 2.0 / (min(ev) * float(self.scale.min()) + max(ev) * float(self.scale.max()))
+
+    def pcg(self, eps, tol=1e-10, maxit=10000, green="sparse", u0=None, enr="identity",
+            scheme="cg", step=None):
         """Linear CG of Algorithm 1 on A u = -b with the X-FFT preconditioner.
 
         Reading of Algorithm 1: f is the negative residual -b - A u, z = A d is the linear part
@@ -603,6 +611,10 @@ class XFEM:
             self.assemble()
         gfun = self._green_sparse() if green == "sparse" else self._green_fft()
         n3 = 3 * self.nFE
+        if scheme not in ("cg", "basic", "bb"):
+            raise ValueError(scheme)
+        s0 = self.basic_step() if step is None else float(step)
+        prev_cauchy = s0
 
         def P(f):
             z = np.empty_like(f)
@@ -628,12 +640,19 @@ class XFEM:
             if k >= maxit:
                 break
             z = self.A @ d
-            alpha = rr / float(z @ d)
+            cauchy = rr / float(z @ d)  # exact line search step along d
+            if scheme == "cg":
+                alpha = cauchy
+            elif scheme == "basic":  # Richardson / gradient descent with the fixed step s0
+                alpha = s0
+            else:  # Barzilai-Borwein (BB1 in the P metric): the previous Cauchy step, s0 first
+                alpha = s0 if k == 0 else prev_cauchy
+            prev_cauchy = cauchy
             u += alpha * d
             f -= alpha * z
             zz = P(f)
             rr_new = float(f @ zz)
-            beta = rr_new / rr
+            beta = rr_new / rr if scheme == "cg" else 0.0
             d = zz + beta * d
             rr = rr_new
             k += 1

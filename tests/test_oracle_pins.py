@@ -376,6 +376,32 @@ def test_enriched_block_preconditioner():
     assert np.linalg.norm(ui - ud) < 1e-9 * np.linalg.norm(ud)
 
 
+def test_basic_and_barzilai_borwein_schemes():
+    """The basic scheme (Richardson with s0 = 2/(C_- + C_+), eq. stepsize) and Barzilai-Borwein
+    on the same X-FFT system reach the direct solution; the basic scheme's iteration count grows
+    about linearly with the contrast and much faster than linear CG's (Sec. 2.3's remarks on
+    O(kappa) and O(sqrt kappa)); BB needs far fewer iterations than the basic scheme."""
+    n = (8, 8, 8)
+    L = synth.sphere_levelset(n, (0.45, 0.5, 0.55), 0.3)
+    e = np.eye(6)[0]
+    its = {}
+    for contrast in (10.0, 50.0):
+        o = XFEM(L, n, lame_minus=synth.lame_from_E_nu(contrast, 0.2), lame_plus=synth.lame_from_E_nu(1.0, 0.3))
+        ud = o.solve_direct(e)
+        lam, mu = o.lame[-1]
+        assert math.isclose(o.basic_step(), 2.0 / (2 * o.lame[1][1] + 3 * lam + 2 * mu), rel_tol=1e-15)
+        for scheme in ("cg", "basic", "bb"):
+            u, info = o.pcg(e, tol=1e-10, maxit=5000, scheme=scheme)
+            assert info["converged"], (contrast, scheme)
+            assert np.linalg.norm(u - ud) < 1e-8 * np.linalg.norm(ud)
+            its[scheme, contrast] = info["iters"]
+    assert its["basic", 50.0] > 3.0 * its["basic", 10.0]
+    assert its["basic", 50.0] / its["basic", 10.0] > 1.5 * its["cg", 50.0] / its["cg", 10.0]
+    for c in (10.0, 50.0):
+        assert its["bb", c] < 0.5 * its["basic", c]
+        assert its["cg", c] <= its["bb", c]
+
+
 def test_hashin_dof_overhead_matches_paper():
     """Sec. 4.2: 36% more DOFs at N = 16 for the coated sphere (both interfaces enriched)."""
     g = json.load(open(os.path.join(HERE, "golden", "hashin_neutral_inclusion.json")))
