@@ -77,6 +77,14 @@ typedef struct {
   double len[3];  /* cell edge lengths */
 } xfft_grid;
 
+/* Iteration scheme on the same system and preconditioner (Sec. 2.3, next to Algorithm 1):
+ * XFFT_SCHEME_CG the linear CG of Algorithm 1; XFFT_SCHEME_BASIC the basic scheme, a
+ * preconditioned Richardson iteration u += s0 P^-1 f with s0 = 2 / (C_- + C_+) (eq. stepsize;
+ * C_-, C_+ the smallest and largest eigenvalues 2 mu, 3 lambda + 2 mu of the phases' stiffness,
+ * times the extreme voxel scales); XFFT_SCHEME_BB Barzilai-Borwein in the P metric, whose step
+ * is the previous iteration's exact line-search step f^T P^-1 f / <d, A d> (s0 first). */
+enum { XFFT_SCHEME_CG = 0, XFFT_SCHEME_BASIC = 1, XFFT_SCHEME_BB = 2 };
+
 typedef struct {
   int precision;       /* XFFT_FP64 (all FP64) or XFFT_FP32_REFINED (FP32 CG; residuals of the
                           FP64 iterate in double-word arithmetic) */
@@ -89,6 +97,8 @@ typedef struct {
                           inner solve (each inner solve aims at half the outer tolerance) */
   int max_refine;      /* FP32_REFINED: cap on FP64 refinement steps */
   int poll_every;      /* iterations between host checks of the device convergence flags */
+  int scheme;          /* XFFT_SCHEME_CG (Algorithm 1, default), _BASIC or _BB */
+  double step;         /* step of the basic / BB schemes; <= 0: s0 = 2 / (C_- + C_+) */
 } xfft_options;
 
 typedef struct {
@@ -101,7 +111,7 @@ typedef struct {
 } xfft_stats;
 
 /* Fill *opt with the defaults: FP64, tol 1e-10, maxit 10000, snap_tau 0 (=> 1e-6 min h),
- * identity enriched block, inner_tol 1e-5, max_refine 20, poll_every 8. */
+ * identity enriched block, inner_tol 1e-5, max_refine 20, poll_every 8, linear CG. */
 xfft_status xfft_default_options(xfft_options* opt);
 
 /* Create a context for one grid.  stream: a cudaStream_t (or NULL for the legacy stream).

@@ -39,7 +39,8 @@ class Grid(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
                 ("snap_tau", C.c_double), ("enr_precond", C.c_int), ("inner_tol", C.c_double),
-                ("max_refine", C.c_int), ("poll_every", C.c_int)]
+                ("max_refine", C.c_int), ("poll_every", C.c_int), ("scheme", C.c_int),
+                ("step", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -160,7 +161,7 @@ class Solver:
 
     def __init__(self, n, length=(1.0, 1.0, 1.0), precision="fp64", tol=1e-10, maxit=10000,
                  snap_tau=0.0, inner_tol=1e-5, max_refine=20, poll_every=8, stream=None,
-                 enr_precond="identity"):
+                 enr_precond="identity", scheme="cg", step=0.0):
         L = lib()
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
@@ -179,6 +180,8 @@ class Solver:
         o.max_refine = max_refine
         o.poll_every = poll_every
         o.enr_precond = {"identity": 0, "block3": 1}[enr_precond]
+        o.scheme = {"cg": 0, "basic": 1, "bb": 2}[scheme]
+        o.step = step
         self.precision = precision
         self._ctx = C.c_void_p()
         self._tstream = None

@@ -90,6 +90,7 @@ struct xfft_ctx {
     cudaGraphExec_t exec = nullptr;
   } cg_graphs[4];
   int cg_next = 0;
+  double step0 = 0.0;  // step of the basic / Barzilai-Borwein schemes
   // block enriched preconditioner: off-diagonal block entries and the inverse blocks
   double* Doff = nullptr;
   double* eb64 = nullptr;
@@ -228,6 +229,8 @@ extern "C" xfft_status xfft_default_options(xfft_options* opt) {
   opt->inner_tol = 1e-5;
   opt->max_refine = 20;
   opt->poll_every = 8;
+  opt->scheme = XFFT_SCHEME_CG;
+  opt->step = 0.0;
   return XFFT_OK;
 }
 
@@ -249,6 +252,8 @@ extern "C" xfft_status xfft_create(xfft_ctx** out, const xfft_grid* grid, const 
     return fail(XFFT_EINVAL, "unknown precision");
   if (o.enr_precond != XFFT_ENR_IDENTITY && o.enr_precond != XFFT_ENR_BLOCK3)
     return fail(XFFT_EINVAL, "unknown enriched preconditioner");
+  if (o.scheme != XFFT_SCHEME_CG && o.scheme != XFFT_SCHEME_BASIC && o.scheme != XFFT_SCHEME_BB)
+    return fail(XFFT_EINVAL, "unknown iteration scheme");
   if (!(o.tol > 0.0) || o.maxit < 1 || o.poll_every < 1 || o.max_refine < 1 || !(o.inner_tol > 0.0))
     return fail(XFFT_EINVAL, "invalid options");
   xfft_ctx* c = new xfft_ctx();
@@ -395,6 +400,26 @@ extern "C" xfft_status xfft_set_microstructure(xfft_ctx* c, const double* L, con
     c->has_scale = true;
   } else {
     c->has_scale = false;
+  }
+  // step of the basic and Barzilai-Borwein schemes, s0 = 2 / (C_- + C_+) (eq. stepsize): the
+  // extreme stiffness eigenvalues (2 mu, 3 lambda + 2 mu per phase) times the extreme scales
+  c->step0 = c->opt.step;
+  if (c->opt.scheme != XFFT_SCHEME_CG && !(c->step0 > 0.0)) {
+    double smin = 1.0, smax = 1.0;
+    if (voxel_scale) {
+      std::vector<float> hs(N);
+      CU(cudaMemcpyAsync(hs.data(), c->scale, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      smin = smax = hs[0];
+      for (long long i = 1; i < N; ++i) {
+        smin = std::min(smin, (double)hs[i]);
+        smax = std::max(smax, (double)hs[i]);
+      }
+    }
+    const double ev[4] = {2.0 * lame_minus[1], 3.0 * lame_minus[0] + 2.0 * lame_minus[1], 2.0 * lame_plus[1],
+                          3.0 * lame_plus[0] + 2.0 * lame_plus[1]};
+    const double cmin = *std::min_element(ev, ev + 4) * smin, cmax = *std::max_element(ev, ev + 4) * smax;
+    c->step0 = 2.0 / (cmin + cmax);
   }
   ProfScope ps_setup(c, XFFT_PROF_SETUP, 14);
   CU(launch_snap_classify(Ldev, c->Ls, c->code, c->cutcount, c->enr_flag, g, c->tau, s));
@@ -558,6 +583,8 @@ static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev
   if (fin_mode >= 0) {
     ProfScope ps(c, XFFT_PROF_FINALIZE, 1);
     FinArgs fa;
+    fa.scheme = c->opt.scheme;
+    fa.step0 = c->step0;
     fa.mode = fin_mode;
     fa.crit = crit;
     fa.tol = tol;
@@ -588,6 +615,8 @@ static xfft_status do_prec(xfft_ctx* c, T* f, T* z, int n_rhs, const int* active
   if (fin_mode >= 0) {
     ProfScope ps(c, XFFT_PROF_FINALIZE, 1);
     FinArgs fa;
+    fa.scheme = c->opt.scheme;
+    fa.step0 = c->step0;
     fa.mode = fin_mode;
     fa.crit = crit;
     fa.tol = tol;

@@ -214,8 +214,10 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
       s.alpha = 0.0;
       s.dpar = fa.parity;
     } else {
-      s.alpha = a;
-      for (int k = 0; k < 6; ++k) s.sig[k] += a * s.sd[k];
+      const double step = fa.scheme == 1 ? fa.step0 : fa.scheme == 2 ? (s.iters == 0 ? fa.step0 : s.cauchy) : a;
+      s.cauchy = a;
+      s.alpha = step;
+      for (int k = 0; k < 6; ++k) s.sig[k] += step * s.sd[k];
     }
   } else {
     const double rr = tot[0];
@@ -241,7 +243,7 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
         s.rel = rel;
       }
     } else {
-      s.beta = s.rr > 0.0 ? rr / s.rr : 0.0;
+      s.beta = (fa.scheme == 0 && s.rr > 0.0) ? rr / s.rr : 0.0;  // 0: steepest descent
       s.rr = rr;
       s.iters += 1;
       s.dpar = fa.parity;
@@ -267,7 +269,7 @@ __global__ void k_init_state(RhsState* st, int* act, int n_rhs, const int* mask)
   const int r = threadIdx.x;
   if (r >= n_rhs) return;
   RhsState s;
-  s.rr = s.rr0 = s.dq = s.alpha = s.beta = s.rel = 0.0;
+  s.rr = s.rr0 = s.dq = s.alpha = s.beta = s.rel = s.cauchy = 0.0;
   for (int k = 0; k < 6; ++k) s.sig[k] = s.sd[k] = 0.0;
   s.active = mask ? mask[r] : 1;
   s.dpar = 0;

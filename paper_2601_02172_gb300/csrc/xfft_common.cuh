@@ -119,6 +119,7 @@ struct RhsState {
   int status;       // 0 running/converged, 4 not converged, 5 breakdown
   int converged;
   int dpar;         // which of the two direction buffers holds the last direction d
+  double cauchy;    // rr / <d, A d> of the last iteration (Barzilai-Borwein step)
 };
 
 }  // namespace xfft

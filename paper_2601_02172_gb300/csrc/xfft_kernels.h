@@ -151,6 +151,11 @@ struct FinArgs {
   int set_rel;
   double inner_floor;
   int parity;      // buffer index of the direction used in this iteration (recorded on exit)
+  // iteration scheme on the same operator: 0 linear CG (Algorithm 1), 1 basic scheme (fixed
+  // step step0, steepest-descent directions), 2 Barzilai-Borwein (step = the previous Cauchy
+  // step rr / <d, A d>, step0 first)
+  int scheme;
+  double step0;
 };
 // act[rhs] mirrors st[rhs].active for the kernels' early exit
 cudaError_t launch_finalize(RhsState* st, const double* partials, FinArgs fa, int n_rhs, int* act,

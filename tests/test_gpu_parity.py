@@ -173,6 +173,30 @@ def test_block_enriched_preconditioner(xf, name, prec):
         assert _rel(out["u_std"][0], u[: 3 * o.nFE].reshape(3, -1)) < 1e-9
 
 
+@pytest.mark.parametrize("scheme", ["basic", "bb"])
+def test_basic_and_bb_schemes(xf, scheme):
+    """The basic (Richardson, step s0 of eq. stepsize) and Barzilai-Borwein schemes on the same
+    system: FP64 iteration counts as the oracle's (up to rounding) and the direct solution; the
+    FP32-refined form reaches the same mean stress to 1e-6."""
+    n, ell, L, lm, lp, sc = _case("sphere16")
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    eps = np.array([[0.2, -0.1, 0.3, 0.4, -0.2, 0.1]])
+    u_ref = o.solve_direct(eps[0])
+    _, info = o.pcg(eps[0], tol=1e-10, maxit=5000, scheme=scheme, green="fft")
+    s = xf.Solver(n, ell, tol=1e-10, maxit=5000, scheme=scheme)
+    s.set_microstructure(L, lm, lp, sc)
+    out = s.solve(eps, u=True)
+    assert out["converged"], out["stats"]
+    assert abs(out["stats"]["iters"][0] - info["iters"]) <= 2, (out["stats"]["iters"], info["iters"])
+    assert _rel(out["u_std"][0], u_ref[: 3 * o.nFE].reshape(3, -1)) < 1e-8
+    ms = o.mean_stress(u_ref, eps[0])
+    s32 = xf.Solver(n, ell, precision="fp32", tol=1e-9, maxit=5000, scheme=scheme)
+    s32.set_microstructure(L, lm, lp, sc)
+    out32 = s32.solve(eps, u=False)
+    assert out32["converged"], out32["stats"]
+    assert np.abs(out32["mean_stress"][0] - ms).max() < 1e-6 * np.abs(ms).max()
+
+
 def test_one_call_solve(xf):
     """The one-call Python solve equals the oracle's direct solution (sphere16)."""
     n, ell, L, lm, lp, sc = _case("sphere16")
