@@ -402,6 +402,22 @@ def test_basic_and_barzilai_borwein_schemes():
         assert its["cg", c] <= its["bb", c]
 
 
+def test_extreme_contrasts_with_both_enriched_preconditioners():
+    """Contrast 1e-4 (nearly a pore) and 1e4 (nearly rigid): PCG with the identity and with the
+    block enriched preconditioner both reach the direct solution (the preconditioner changes
+    the iteration count only)."""
+    n = (8, 8, 8)
+    L = synth.sphere_levelset(n, (0.45, 0.5, 0.55), 0.3)
+    e = np.eye(6)[0]
+    for contrast in (1e-4, 1e4):
+        o = XFEM(L, n, lame_minus=synth.lame_from_E_nu(contrast, 0.3), lame_plus=synth.lame_from_E_nu(1.0, 0.3))
+        ud = o.solve_direct(e)
+        for enr in ("identity", "block3"):
+            u, info = o.pcg(e, tol=1e-10, maxit=5000, enr=enr)
+            assert info["converged"], (contrast, enr)
+            assert np.linalg.norm(u - ud) < 1e-6 * np.linalg.norm(ud), (contrast, enr)
+
+
 def test_hashin_dof_overhead_matches_paper():
     """Sec. 4.2: 36% more DOFs at N = 16 for the coated sphere (both interfaces enriched)."""
     g = json.load(open(os.path.join(HERE, "golden", "hashin_neutral_inclusion.json")))
