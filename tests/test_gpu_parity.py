@@ -480,6 +480,39 @@ def test_full_size_fibers_256(xf):
     assert np.linalg.eigvalsh(sym - reuss).min() > -1e-2 * np.abs(C64).max()
 
 
+def test_full_size_apply_and_precondition_128(xf):
+    """The bench workload at its full size (128^3, 40 ellipsoids, voxel scale), in the kernels'
+    bench launch shapes: the preconditioner on a superposition of Fourier modes against the
+    oracle's exact values everywhere (enriched part: identity), and the stiffness operator's
+    properties - symmetry, rigid translations in its kernel, FP32 and double-word applies
+    against FP64."""
+    w = synth.make_workload("ellipsoids40")
+    n = w["n"]
+    s = xf.Solver(n)
+    s.set_microstructure(w["L"], w["lame_minus"], w["lame_plus"], w["scale"])
+    N, nX = int(np.prod(n)), s.num_enriched
+    rng = np.random.default_rng(21)
+    og = XFEM(np.ones(n), n)
+    ks = [(0, 0, 1), (64, 0, 0), (3, 64, 0), (0, 5, 64), (64, 64, 64), (7, 100, 3), (127, 1, 33), (20, 0, 64)]
+    ks += [tuple(int(v) for v in rng.integers(0, 128, 3)) for _ in range(6)]
+    f_std, z_std = og.precondition_modes([(k, rng.normal(size=3) + 1j * rng.normal(size=3)) for k in ks])
+    f = np.concatenate([f_std, rng.normal(size=3 * nX)])[None, :]
+    for prec, tol in (("fp64", 1e-11), ("fp32", 2e-5)):
+        z, rr = s.precondition(f, precision=prec)
+        assert _rel(z[0, : 3 * N], z_std) < tol, prec
+        assert _rel(z[0, 3 * N:], f[0, 3 * N:]) < tol, prec
+    x = rng.normal(size=(2, 3 * (N + nX)))
+    Ax, _ = s.apply(x, precision="fp64")
+    assert abs(x[0] @ Ax[1] - x[1] @ Ax[0]) < 1e-11 * abs(x[0] @ Ax[1]) + 1e-12 * np.linalg.norm(Ax[0]) * np.linalg.norm(x[1])
+    t = np.zeros((1, 3 * (N + nX)))
+    t[0, N: 2 * N] = 1.0  # rigid translation along y
+    At, _ = s.apply(t, precision="fp64")
+    assert np.linalg.norm(At) < 1e-11 * np.linalg.norm(Ax[0]) * np.linalg.norm(t) / np.linalg.norm(x[0])
+    for prec, tol in (("dw", 1e-11), ("fp32", 2e-5)):
+        Ap, _ = s.apply(x, precision=prec)
+        assert _rel(Ap, Ax) < tol, prec
+
+
 def test_full_size_spheres27_64(xf):
     """Config 2 at full size (64^3, 27 spheres, vf 20 %, contrast 100, six load cases): C_eff
     against the oracle's (tests/golden/spheres27_64_ceff.json, written from oracle/ alone by
