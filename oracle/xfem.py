@@ -25,7 +25,9 @@ Parity pins (tests/test_oracle_*.py): homogeneous cells, the tilted laminate's c
 Voigt/Reuss bounds, symmetry, axis-permutation invariance, PCG = direct solve, dense
 brute-force eigen-analysis on tiny grids, FFT symbol = assembled operator, quadrature
 exactness, sub-tetrahedron volumes, the DOF overhead printed for Hashin's inclusion, finite
-differences and Euler homogeneity of the gradient.
+differences and Euler homogeneity of the gradient; with several interfaces (Sec. 4.2's coated
+sphere) the three-layer laminate's closed form, Hashin's neutral-inclusion bulk modulus and the
+reduction to one interface.
 """
 from __future__ import annotations
 
@@ -199,9 +201,18 @@ class XFEM:
 
     Parameters
     ----------
-    L : nodal level set, shape ``n`` (C order), ``L < 0`` = phase "minus".
+    L : nodal level set, shape ``n`` (C order), ``L < 0`` = phase "minus"; or, with
+        ``phases``, K nodal level sets, shape ``(K,) + n``.
     n : voxels per axis (N1, N2, N3); length: cell edge lengths.
     lame_minus, lame_plus : (lambda, mu) of the ``L < 0`` and ``L > 0`` phases.
+    phases : several interfaces (Sec. 4.2's coated sphere): K + 1 pairs (lambda, mu).  A point
+        belongs to phase k, the index of the first level set that is negative there, or to
+        phase K where none is.  Each interface k is the zero set of L_k where the level sets
+        before it are positive; a cut tet is cut by one interface only (the paper's setting:
+        one interface per element) and is enriched with the modified abs of that interface's
+        level set.  The enrichment function of a node is then the sum of the per-interface
+        functions, which have disjoint supports.  One level set with (lame_minus, lame_plus)
+        is the case K = 1.
     scale : optional per-voxel modulus scale s_v (shape ``n``); C = s_v C_phase.
     tau : snap threshold; nodal values with |L| < tau become 0 (Sec. 3: "below 1e-6").
           Default ``1e-6 * min(h)`` (the paper's absolute 1e-6 at its N = 16, h ~ 1 um scale).
@@ -212,7 +223,7 @@ class XFEM:
     """
 
     def __init__(self, L, n, length=(1.0, 1.0, 1.0), lame_minus=(1.0, 1.0),
-                 lame_plus=(1.0, 1.0), scale=None, tau=None):
+                 lame_plus=(1.0, 1.0), scale=None, tau=None, phases=None):
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
         self.h = np.array([self.length[a] / self.n[a] for a in range(3)])
@@ -220,9 +231,17 @@ class XFEM:
         self.nvox = self.nFE
         self.volY = float(np.prod(self.length))
         self.tau = 1e-6 * float(np.min(self.h)) if tau is None else float(tau)
-        L = np.asarray(L, dtype=float).reshape(self.n)
-        self.L = np.where(np.abs(L) < self.tau, 0.0, L).ravel()
-        self.lame = {-1: tuple(map(float, lame_minus)), +1: tuple(map(float, lame_plus))}
+        if phases is None:
+            phases = (lame_minus, lame_plus)
+            L = np.asarray(L, dtype=float).reshape((1,) + self.n)
+        else:
+            L = np.asarray(L, dtype=float).reshape((-1,) + self.n)
+        self.nL = L.shape[0]
+        if len(phases) != self.nL + 1:
+            raise ValueError("K level sets need K + 1 phases")
+        self.Ls = np.where(np.abs(L) < self.tau, 0.0, L).reshape(self.nL, -1)
+        self.L = self.Ls[0]
+        self.phases = [tuple(map(float, p)) for p in phases]
         self.scale = (np.ones(self.nvox) if scale is None
                       else np.asarray(scale, dtype=np.float64).ravel().copy())
         self._geometry()
@@ -265,11 +284,17 @@ class XFEM:
         self.B_std = [symgrad_operator(G) for G in self.tet_grads]  # 6 x 12 per tet type
 
     def _classify(self):
-        Lt = self.L[self.tet_nodes]  # (nvox, 6, 4)
-        self.cut = (Lt.min(axis=2) < 0.0) & (Lt.max(axis=2) > 0.0)
-        # phase of an uncut tet: minus if some vertex is negative, else plus (a tet whose
-        # vertices are all 0 lies on the interface; it gets the plus phase)
-        self.tet_phase = np.where((Lt < 0.0).any(axis=2), -1, 1)
+        K = self.nL
+        Lt = self.Ls[:, self.tet_nodes]  # (K, nvox, 6, 4)
+        neg = Lt.min(axis=3) < 0.0
+        pos = Lt.max(axis=3) > 0.0
+        # first level set negative somewhere on the tet (K if none): the phase of an uncut tet
+        # (a tet whose vertices are all 0 lies on the interface; it gets the plus phase), the
+        # minus phase of a cut one
+        first = np.where(neg.any(axis=0), neg.argmax(axis=0), K)
+        kk = np.minimum(first, K - 1)
+        self.cut = (first < K) & np.take_along_axis(pos, kk[None], axis=0)[0]
+        self.tet_phase = first
         J = np.unique(self.tet_nodes[self.cut])
         self.enr_nodes = J
         self.nX = int(J.size)
@@ -277,14 +302,25 @@ class XFEM:
         self.enr_id[J] = np.arange(self.nX)
         cv, ct = np.nonzero(self.cut)
         self.cut_list = np.stack([cv, ct], axis=1) if cv.size else np.zeros((0, 2), np.int64)
+        # interface of each cut tet and the phases of its minus and plus sides: the plus side
+        # lies in the first later level set that is negative on the tet, else in phase K; a
+        # later level set that also changes sign there would put two interfaces in one element
+        ki = first[cv, ct]
+        later = np.arange(K)[:, None] > ki[None, :]
+        lneg = neg[:, cv, ct] & later
+        if np.any(lneg & pos[:, cv, ct]):
+            raise ValueError("a tet is cut by two interfaces")
+        pp = np.where(lneg.any(axis=0), lneg.argmax(axis=0), K)
+        self.cut_iface = ki
+        self.cut_phase = {-1: ki, +1: pp}
 
     # ------------------------------------------------------------------ cut elements
-    def _cut_tet_points(self, v, t):
-        """Quadrature data of cut tet (v, t): per side, points' barycentric coordinates and
-        weights, for the sub-tetrahedra of the linearised interface (Sec. 3)."""
+    def _cut_tet_points(self, v, t, k):
+        """Quadrature data of cut tet (v, t) of interface k: per side, points' barycentric
+        coordinates and weights, for the sub-tetrahedra of the linearised interface (Sec. 3)."""
         off = self.tet_offsets[t]
         X = off * self.h
-        Lv = self.L[self.tet_nodes[v, t]]
+        Lv = self.Ls[k][self.tet_nodes[v, t]]
         J = np.stack([X[1] - X[0], X[2] - X[0], X[3] - X[0]])
         Jinv = np.linalg.inv(J)
         sides = {}
@@ -321,8 +357,8 @@ class XFEM:
         # node block of the enriched-enriched reference Gram matrix; its diagonal is D0
         self.Dblk = np.zeros((self.nX, 3, 3))
         self.cut_data = []
-        for v, t in self.cut_list:
-            Lv, sides = self._cut_tet_points(v, t)
+        for (v, t), k in zip(self.cut_list, self.cut_iface):
+            Lv, sides = self._cut_tet_points(v, t, k)
             G = self.tet_grads[t]
             eids = self.enr_id[self.tet_nodes[v, t]]
             for s in (+1, -1):
@@ -340,9 +376,13 @@ class XFEM:
         # scaled blocks (unit diagonal): the variant enriched preconditioner's 3x3 blocks
         self.Bblk = self.Dblk * self.Dinvsqrt[:, :, None] * self.Dinvsqrt[:, None, :]
 
-    def _C(self, s, v):
-        lam, mu = self.lame[s]
+    def _C(self, p, v):
+        """Stiffness of phase p in voxel v."""
+        lam, mu = self.phases[p]
         return self.scale[v] * iso_stiffness(lam, mu)
+
+    def _side_phase(self, idx, s):
+        return int(self.cut_phase[s][idx])
 
     def cut_element(self, idx):
         """Scaled element matrix (24x24), stress matrix (6x24, eq. Sapp_q) and DOF indices of
@@ -360,7 +400,7 @@ class XFEM:
             bary, w = sides[s]
             BX = self._enriched_B(G, Lv, s, bary)
             Bf = np.concatenate([np.broadcast_to(Bs, BX.shape), BX], axis=2) * scale
-            C = self._C(s, v)
+            C = self._C(self._side_phase(idx, s), v)
             CB = np.matmul(C, Bf)  # (nq, 6, 24)
             K += np.tensordot(Bf * w[:, None, None], CB, axes=([0, 1], [0, 1]))
             S += np.tensordot(w, CB, axes=(0, 0))
@@ -388,8 +428,8 @@ class XFEM:
                 S = np.broadcast_to(vol * B, (vox.size, 6, 12))
             else:
                 ph = self.tet_phase[vox, t]
-                lam = np.where(ph < 0, self.lame[-1][0], self.lame[1][0]) * self.scale[vox]
-                mu = np.where(ph < 0, self.lame[-1][1], self.lame[1][1]) * self.scale[vox]
+                lam = np.array([p[0] for p in self.phases])[ph] * self.scale[vox]
+                mu = np.array([p[1] for p in self.phases])[ph] * self.scale[vox]
                 Cl = iso_stiffness(1.0, 0.0)
                 Cm = iso_stiffness(0.0, 1.0)
                 Kl = vol * B.T @ Cl @ B
@@ -416,9 +456,9 @@ class XFEM:
         for t in range(6):
             vox = np.flatnonzero(~self.cut[:, t])
             ph = self.tet_phase[vox, t]
-            for s in (-1, 1):
-                sel = vox[ph == s]
-                Cbar += self.tet_vol[t] * float(self.scale[sel].sum()) * iso_stiffness(*self.lame[s])
+            for p in range(self.nL + 1):
+                sel = vox[ph == p]
+                Cbar += self.tet_vol[t] * float(self.scale[sel].sum()) * iso_stiffness(*self.phases[p])
         for idx in range(len(self.cut_list)):
             dofs, K, S = self.cut_element(idx)
             rows.append(np.repeat(dofs, 24))
@@ -430,7 +470,7 @@ class XFEM:
             v, t = self.cut_list[idx]
             _, sides = self.cut_data[idx]
             for s in (+1, -1):
-                Cbar += float(sides[s][1].sum()) * self._C(s, v)
+                Cbar += float(sides[s][1].sum()) * self._C(self._side_phase(idx, s), v)
         A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                           shape=(self.ndof, self.ndof)).tocsr()
         Sm = sp.coo_matrix((np.concatenate(Svals), (np.concatenate(Srows), np.concatenate(Scols))),
@@ -594,7 +634,7 @@ class XFEM:
         """Step size s0 = 2 / (C_- + C_+) of the basic scheme (eq. stepsize): C_- (C_+) is the
         smallest (largest) eigenvalue of the stiffness tensors of all materials; with isotropic
         phases the eigenvalues are 2 mu and 3 lambda + 2 mu, times the extreme voxel scales."""
-        ev = [e for lam, mu in self.lame.values() for e in (2.0 * mu, 3.0 * lam + 2.0 * mu)]
+        ev = [e for lam, mu in self.phases for e in (2.0 * mu, 3.0 * lam + 2.0 * mu)]
         return 2.0 / (min(ev) * float(self.scale.min()) + max(ev) * float(self.scale.max()))
 
     def pcg(self, eps, tol=1e-10, maxit=10000, green="sparse", u0=None, enr="identity",
@@ -687,16 +727,16 @@ class XFEM:
         for t in range(6):
             vox = np.flatnonzero(~self.cut[:, t])
             ph = self.tet_phase[vox, t]
-            for s in (-1, 1):
-                sel = vox[ph == s]
-                out[sel] += (self.tet_vol[t] * self.scale[sel])[:, None] * (iso_stiffness(*self.lame[s]) @ eps)[None, :]
+            for p in range(self.nL + 1):
+                sel = vox[ph == p]
+                out[sel] += (self.tet_vol[t] * self.scale[sel])[:, None] * (iso_stiffness(*self.phases[p]) @ eps)[None, :]
         for idx in range(len(self.cut_list)):
             dofs, K, S = self.cut_element(idx)
             v, t = self.cut_list[idx]
             _, sides = self.cut_data[idx]
             out[v] += S @ u[dofs]
             for s in (+1, -1):
-                out[v] += float(sides[s][1].sum()) * (self._C(s, v) @ eps)
+                out[v] += float(sides[s][1].sum()) * (self._C(self._side_phase(idx, s), v) @ eps)
         return out / float(np.prod(self.h))
 
     # ------------------------------------------------------------------ gradient
@@ -712,13 +752,14 @@ class XFEM:
         the per-voxel scale: dC_kl/dtheta = (1/|Y|) int eps_k : dC/dtheta : eps_l with
         eps_k = E_k + grad^s u_k (envelope identity; the basis does not depend on C).
 
-        Returns (dC_dlame (4,6,6) in order lam_minus, mu_minus, lam_plus, mu_plus;
-        dC_ds (nvox,6,6)).
+        Returns (dC_dlame (2(K+1),6,6) in order lam_0, mu_0, lam_1, mu_1, ... (one interface:
+        lam_minus, mu_minus, lam_plus, mu_plus); dC_ds (nvox,6,6)).
         """
         E = np.eye(6) if E is None else np.asarray(E, float)
         nr = U.shape[0]
-        Al = {s: np.zeros((self.nvox, nr, nr)) for s in (-1, 1)}  # int tr eps_k tr eps_l
-        Am = {s: np.zeros((self.nvox, nr, nr)) for s in (-1, 1)}  # int 2 eps_k : eps_l
+        nph = self.nL + 1
+        Al = [np.zeros((self.nvox, nr, nr)) for _ in range(nph)]  # int tr eps_k tr eps_l
+        Am = [np.zeros((self.nvox, nr, nr)) for _ in range(nph)]  # int 2 eps_k : eps_l
         m = np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
         for t in range(6):
             vox = np.flatnonzero(~self.cut[:, t])
@@ -730,10 +771,10 @@ class XFEM:
             vol = self.tet_vol[t]
             al = vol * np.einsum("km,lm->mkl", tr, tr)
             am = 2.0 * vol * np.einsum("kmr,lmr->mkl", eps, eps)
-            for s in (-1, 1):
-                sel = ph == s
-                np.add.at(Al[s], vox[sel], al[sel])
-                np.add.at(Am[s], vox[sel], am[sel])
+            for p in range(nph):
+                sel = ph == p
+                np.add.at(Al[p], vox[sel], al[sel])
+                np.add.at(Am[p], vox[sel], am[sel])
         for idx in range(len(self.cut_list)):
             v, t = self.cut_list[idx]
             Lv, sides = self.cut_data[idx]
@@ -751,14 +792,13 @@ class XFEM:
                 Bf = np.concatenate([np.broadcast_to(self.B_std[t], BX.shape), BX], axis=2)
                 eps = np.einsum("qrj,nj->nqr", Bf, ue) + E[:, None, :]
                 tr = eps @ m
-                Al[s][v] += np.einsum("q,kq,lq->kl", w, tr, tr)
-                Am[s][v] += 2.0 * np.einsum("q,kqr,lqr->kl", w, eps, eps)
+                p = self._side_phase(idx, s)
+                Al[p][v] += np.einsum("q,kq,lq->kl", w, tr, tr)
+                Am[p][v] += 2.0 * np.einsum("q,kqr,lqr->kl", w, eps, eps)
         sc = self.scale[:, None, None]
-        dl = np.stack([(sc * Al[-1]).sum(0), (sc * Am[-1]).sum(0) / 1.0,
-                       (sc * Al[1]).sum(0), (sc * Am[1]).sum(0)]) / self.volY
-        ds = (self.lame[-1][0] * Al[-1] + self.lame[-1][1] * Am[-1]
-              + self.lame[1][0] * Al[1] + self.lame[1][1] * Am[1]) / self.volY
-        return dl, ds
+        dl = np.stack([x for p in range(nph) for x in ((sc * Al[p]).sum(0), (sc * Am[p]).sum(0))])
+        ds = sum(self.phases[p][0] * Al[p] + self.phases[p][1] * Am[p] for p in range(nph))
+        return dl / self.volY, ds / self.volY
 
     # ------------------------------------------------------------------ local evaluation
     def apply(self, d, eps=None):

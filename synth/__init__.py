@@ -8,6 +8,9 @@ moduli and per-voxel modulus-scale fields.  It holds none of the method's arithm
 from .geometry import (  # noqa: F401
     node_coords,
     sphere_levelset,
+    coated_sphere_levelsets,
+    hashin_neutral_inclusion,
+    HASHIN,
     spheres_levelset,
     rsa_spheres,
     rsa_ellipsoids,
@@ -17,6 +20,7 @@ from .geometry import (  # noqa: F401
     laminate_levelset,
     voxel_scale,
     lame_from_E_nu,
+    lame_from_K_nu,
     WORKLOADS,
     make_workload,
 )

@@ -47,6 +47,37 @@ def sphere_levelset(n, center, radius, length=(1.0, 1.0, 1.0)):
     return np.sqrt(dx * dx + dy * dy + dz * dz) - radius
 
 
+def coated_sphere_levelsets(n, center, r_inclusion, r_coating, length=(1.0, 1.0, 1.0)):
+    """Two level sets of a coated sphere, innermost first (shape (2,) + n): negative inside
+    the inclusion, and inside the coating's outer sphere.  With the phase of a point taken from
+    the first negative level set, the phases are inclusion, coating, matrix."""
+    return np.stack([sphere_levelset(n, center, r_inclusion, length),
+                     sphere_levelset(n, center, r_coating, length)])
+
+
+# Hashin's neutral inclusion (Sec. 4.2, table "Geometry and parameters"): a 16 um cubic cell,
+# a coated sphere in its centre with inclusion radius 6e/5 um and coating radius 2 pi um, bulk
+# moduli 8.080240 / 0.808024 / 1.0 MPa (inclusion / coating / matrix), Poisson's ratio 0.25 in
+# all phases; load eps_bar = I.  The composite-sphere formula gives K_eff = K_matrix.
+HASHIN = {
+    "cell_um": 16.0,
+    "r_inclusion_um": 6.0 * math.e / 5.0,
+    "r_coating_um": 2.0 * math.pi,
+    "bulk_MPa": (8.080240, 0.808024, 1.0),
+    "poisson": 0.25,
+}
+
+
+def hashin_neutral_inclusion(N):
+    """Level sets (2, N, N, N), phases [(lambda, mu)] * 3 (inclusion, coating, matrix) and the
+    cell edge lengths of Hashin's neutral inclusion on an N^3 grid."""
+    ell = (HASHIN["cell_um"],) * 3
+    c = tuple(x / 2.0 for x in ell)
+    Ls = coated_sphere_levelsets((N, N, N), c, HASHIN["r_inclusion_um"], HASHIN["r_coating_um"], ell)
+    phases = [lame_from_K_nu(K, HASHIN["poisson"]) for K in HASHIN["bulk_MPa"]]
+    return Ls, phases, ell
+
+
 def spheres_levelset(n, centers, radii, length=(1.0, 1.0, 1.0)):
     """Minimum over spheres of the periodic signed distances."""
     L = np.full(tuple(n), np.inf)
@@ -310,6 +341,12 @@ def voxel_scale(n, seed, lo=0.8, hi=1.2):
     """Per-voxel modulus scale field, iid uniform in ``[lo, hi]``, float32, shape ``n``."""
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=tuple(n)).astype(np.float32)
+
+
+def lame_from_K_nu(K, nu):
+    """Return ``(lambda, mu)`` of an isotropic material from its bulk modulus and Poisson ratio."""
+    mu = 3.0 * K * (1.0 - 2.0 * nu) / (2.0 * (1.0 + nu))
+    return (float(K - 2.0 * mu / 3.0), float(mu))
 
 
 def lame_from_E_nu(E, nu):

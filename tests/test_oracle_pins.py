@@ -162,9 +162,10 @@ def test_equal_phases_with_cut_give_zero_fluctuation():
     assert np.allclose(Cs, iso_stiffness(*lam), atol=1e-12)
 
 
-def _laminate_closed_form(normal, fraction, lm, lp):
-    """Effective stiffness of a two-phase laminate (Mandel 6x6): continuity of traction and
-    of the in-plane strain; jump a_p along the normal in each layer."""
+def _laminate_closed_form(normal, fraction, lm, lp, layers=None):
+    """Effective stiffness of a laminate (Mandel 6x6): continuity of traction and of the
+    in-plane strain; jump a_p along the normal in each layer.  Two phases (volume fraction of
+    ``lm``), or ``layers`` = [(fraction, (lambda, mu)), ...]."""
     nrm = np.asarray(normal, float) / np.linalg.norm(normal)
     d = np.eye(3)
 
@@ -172,7 +173,9 @@ def _laminate_closed_form(normal, fraction, lm, lp):
         return (lam * np.einsum("ij,kl->ijkl", d, d)
                 + mu * (np.einsum("ik,jl->ijkl", d, d) + np.einsum("il,jk->ijkl", d, d)))
 
-    phases = [(fraction, C4(*lm)), (1.0 - fraction, C4(*lp))]
+    if layers is None:
+        layers = [(fraction, lm), (1.0 - fraction, lp)]
+    phases = [(f, C4(*lame)) for f, lame in layers]
     out = np.zeros((6, 6))
     for k in range(6):
         E = _unmandel(np.eye(6)[k])
@@ -247,9 +250,9 @@ def test_voigt_reuss_bounds(sphere10):
     o, Cs, Ce, U, lm, lp = sphere10
     vol = {-1: 0.0, 1: 0.0}
     for t in range(6):
-        ph = o.tet_phase[~o.cut[:, t], t]
+        ph = o.tet_phase[~o.cut[:, t], t]  # phase index: 0 minus, 1 plus
         for s in (-1, 1):
-            vol[s] += o.tet_vol[t] * np.sum(ph == s)
+            vol[s] += o.tet_vol[t] * np.sum(ph == (s + 1) // 2)
     for idx in range(len(o.cut_list)):
         _, sides = o.cut_data[idx]
         for s in (-1, 1):
@@ -388,8 +391,8 @@ def test_basic_and_barzilai_borwein_schemes():
     for contrast in (10.0, 50.0):
         o = XFEM(L, n, lame_minus=synth.lame_from_E_nu(contrast, 0.2), lame_plus=synth.lame_from_E_nu(1.0, 0.3))
         ud = o.solve_direct(e)
-        lam, mu = o.lame[-1]
-        assert math.isclose(o.basic_step(), 2.0 / (2 * o.lame[1][1] + 3 * lam + 2 * mu), rel_tol=1e-15)
+        lam, mu = o.phases[0]
+        assert math.isclose(o.basic_step(), 2.0 / (2 * o.phases[1][1] + 3 * lam + 2 * mu), rel_tol=1e-15)
         for scheme in ("cg", "basic", "bb"):
             u, info = o.pcg(e, tol=1e-10, maxit=5000, scheme=scheme)
             assert info["converged"], (contrast, scheme)
