@@ -129,6 +129,22 @@ xfft_status xfft_set_microstructure(xfft_ctx* ctx, const double* L, const double
                                     const double lame_plus[2], const float* voxel_scale,
                                     int ptrs_on_device);
 
+/* Several interfaces (Sec. 4.2: the coated sphere of Hashin's neutral inclusion has an
+ * inclusion, a coating and a matrix phase).  n_levelsets = K (1 .. XFFT_MAX_LEVELSETS) nodal
+ * level sets L (K x N doubles, level set after level set, node order) and K + 1 phases, lame
+ * ((K + 1) x 2 doubles, host: lambda, mu of phase 0, 1, ...).  A point lies in phase k if L_k is
+ * the first level set that is negative there, in phase K if none is: for nested inclusions pass
+ * the innermost first (coated sphere: L_0 = r - r_inclusion, L_1 = r - r_coating).  Each tet is
+ * cut by at most one interface, the zero set of its first level set with a negative vertex, and
+ * is enriched with the modified abs of that level set (eq. modifiedabsEnrichment); one
+ * enrichment vector per node.  K = 1 with lame = {lambda_-, mu_-, lambda_+, mu_+} is
+ * xfft_set_microstructure.  Errors as xfft_set_microstructure, and EINVAL if some tet is cut
+ * by two interfaces (the two zero sets pass through one element).  Gradients: xfft_grad_phases. */
+#define XFFT_MAX_LEVELSETS 2
+xfft_status xfft_set_microstructure_phases(xfft_ctx* ctx, int n_levelsets, const double* L,
+                                           const double* lame, const float* voxel_scale,
+                                           int ptrs_on_device);
+
 /* Solve the cell problem for n_rhs (1..64) macroscopic strains eps_bar (n_rhs x 6 Mandel,
  * host).  Outputs (each may be NULL): u_std (n_rhs x 3 x N), u_enr (n_rhs x 3 x nX, unscaled
  * u_X), voxel_stress (n_rhs x 6 x N: per-voxel average stress, voxel order),
@@ -159,9 +175,16 @@ xfft_status xfft_batch_effective_stiffness(int n, xfft_ctx* const* ctxs, double*
  * dC_kl/dtheta = (1/|Y|) int eps_k : dC/dtheta : eps_l on the six checkpointed load cases
  * of the last xfft_effective_stiffness call (not in the paper; App. A gives the identity's
  * ingredients).  C_energy (36, host, may be NULL) receives the energy-form C_eff.
- * Errors: ESTATE if no six-case solve is stored. */
+ * Errors: ESTATE if no six-case solve is stored; EINVAL for a microstructure of more than two
+ * phases (use xfft_grad_phases). */
 xfft_status xfft_grad(xfft_ctx* ctx, const double dL_dCeff[36], double dL_dlame[4],
                       float* dL_dscale, double C_energy[36], int ptrs_on_device);
+
+/* xfft_grad for any number of phases (xfft_set_microstructure_phases): dL_dlame receives
+ * 2 (K + 1) values, dLoss/d(lambda_0, mu_0, lambda_1, mu_1, ...) (host).  Two phases: the
+ * same values and order as xfft_grad. */
+xfft_status xfft_grad_phases(xfft_ctx* ctx, const double dL_dCeff[36], double* dL_dlame,
+                             float* dL_dscale, double C_energy[36], int ptrs_on_device);
 
 /* Step-level entry points (each is one piece of Algorithm 1 and is what the parity tests
  * call).  Vectors here use the *scaled* enriched coefficients u~_X of eq. scaledEnrichedU and

@@ -20,8 +20,9 @@ XFFT_FP64, XFFT_FP32_REFINED, XFFT_DW = 0, 1, 2
 _PREC = {"fp64": XFFT_FP64, "fp32": XFFT_FP32_REFINED, "dw": XFFT_DW}
 
 EXPORTED = (
-    "xfft_default_options", "xfft_create", "xfft_set_microstructure", "xfft_solve",
-    "xfft_effective_stiffness", "xfft_grad", "xfft_apply", "xfft_precondition", "xfft_get_setup",
+    "xfft_default_options", "xfft_create", "xfft_set_microstructure",
+    "xfft_set_microstructure_phases", "xfft_solve",
+    "xfft_effective_stiffness", "xfft_grad", "xfft_grad_phases", "xfft_apply", "xfft_precondition", "xfft_get_setup",
     "xfft_num_enriched", "xfft_num_cut_tets", "xfft_status_string", "xfft_last_error",
     "xfft_destroy", "xfft_profile", "xfft_profile_read", "xfft_apply_noalloc",
     "xfft_batch_effective_stiffness",
@@ -70,9 +71,11 @@ def lib():
     L.xfft_default_options.argtypes = [C.POINTER(Options)]
     L.xfft_create.argtypes = [C.POINTER(vp), C.POINTER(Grid), C.POINTER(Options), vp]
     L.xfft_set_microstructure.argtypes = [vp, vp, C.POINTER(d), C.POINTER(d), vp, i]
+    L.xfft_set_microstructure_phases.argtypes = [vp, i, vp, C.POINTER(d), vp, i]
     L.xfft_solve.argtypes = [vp, i, C.POINTER(d), vp, vp, vp, C.POINTER(d), C.POINTER(Stats), i]
     L.xfft_effective_stiffness.argtypes = [vp, C.POINTER(d), C.POINTER(Stats)]
     L.xfft_grad.argtypes = [vp, C.POINTER(d), C.POINTER(d), vp, C.POINTER(d), i]
+    L.xfft_grad_phases.argtypes = [vp, C.POINTER(d), C.POINTER(d), vp, C.POINTER(d), i]
     L.xfft_apply.argtypes = [vp, i, vp, C.POINTER(d), vp, C.POINTER(d), i, i]
     L.xfft_precondition.argtypes = [vp, i, vp, vp, C.POINTER(d), i, i]
     L.xfft_get_setup.argtypes = [vp, vp, vp, vp]
@@ -87,8 +90,9 @@ def lib():
     L.xfft_profile_read.argtypes = [vp, vp, vp, vp]
     L.xfft_apply_noalloc.argtypes = [vp, i, vp, vp, vp]
     L.xfft_batch_effective_stiffness.argtypes = [i, vp, C.POINTER(d), C.POINTER(Stats)]
-    for name in ("xfft_default_options", "xfft_create", "xfft_set_microstructure", "xfft_solve",
-                 "xfft_effective_stiffness", "xfft_grad", "xfft_apply", "xfft_precondition",
+    for name in ("xfft_default_options", "xfft_create", "xfft_set_microstructure",
+                 "xfft_set_microstructure_phases", "xfft_solve",
+                 "xfft_effective_stiffness", "xfft_grad", "xfft_grad_phases", "xfft_apply", "xfft_precondition",
                  "xfft_get_setup", "xfft_num_enriched", "xfft_num_cut_tets", "xfft_profile",
                  "xfft_profile_read", "xfft_apply_noalloc", "xfft_batch_effective_stiffness"):
         getattr(L, name).restype = i
@@ -183,6 +187,7 @@ class Solver:
         o.scheme = {"cg": 0, "basic": 1, "bb": 2}[scheme]
         o.step = step
         self.precision = precision
+        self.num_phases = 0
         self._ctx = C.c_void_p()
         self._tstream = None
         handle = None
@@ -225,6 +230,25 @@ class Solver:
         lm, lmp = _dvec(lame_minus)
         lp, lpp = _dvec(lame_plus)
         check(lib().xfft_set_microstructure(self._ctx, Lp, lmp, lpp, sp_, int(dev)))
+        self.num_phases = 2
+
+    @_ordered
+    def set_microstructure_phases(self, Ls, phases, scale=None):
+        """Several interfaces: ``Ls`` holds K nodal level sets (shape (K,) + n), ``phases`` the
+        K + 1 pairs (lambda, mu); a point lies in phase k if L_k is the first negative level
+        set there, in phase K if none is (see ``xfft_set_microstructure_phases``)."""
+        Lp, dev = _ptr(Ls, np.float64)
+        sp_, sdev = _ptr(scale, np.float32)
+        if scale is not None and sdev != dev:
+            raise TypeError("Ls and scale must both be host or both be device arrays")
+        K = int(Ls.shape[0]) if Ls.ndim == 4 else 1
+        if int(np.prod(Ls.shape)) != K * self.N:
+            raise ValueError("Ls must hold K level sets of the grid's N nodes")
+        lame, lp = _dvec(np.asarray(phases, dtype=np.float64).reshape(-1))
+        if lame.size != 2 * (K + 1):
+            raise ValueError("K level sets need K + 1 phases (lambda, mu)")
+        check(lib().xfft_set_microstructure_phases(self._ctx, K, Lp, lp, sp_, int(dev)))
+        self.num_phases = K + 1
 
     @_ordered
     def solve(self, eps, u=True, voxel_stress=False, device=None):
@@ -269,10 +293,11 @@ class Solver:
 
     @_ordered
     def grad(self, G, scale_grad=True, device=None):
-        """dLoss/d(lam-, mu-, lam+, mu+), dLoss/ds_v (float32) and the energy-form C_eff for
-        G = dLoss/dC_eff of the last effective_stiffness call."""
+        """dLoss/d(lam-, mu-, lam+, mu+) (several interfaces: lam_0, mu_0, lam_1, mu_1, ...),
+        dLoss/ds_v (float32) and the energy-form C_eff for G = dLoss/dC_eff of the last
+        effective_stiffness call."""
         g, gp = _dvec(np.asarray(G, dtype=np.float64).reshape(36))
-        dl = np.empty(4)
+        dl = np.empty(2 * max(self.num_phases, 2))
         ce = np.empty(36)
         if scale_grad:
             if device is not None:
@@ -283,7 +308,7 @@ class Solver:
         else:
             ds = None
         dsp, dev = _ptr(ds, np.float32)
-        check(lib().xfft_grad(self._ctx, gp, dl.ctypes.data_as(C.POINTER(C.c_double)), dsp,
+        check(lib().xfft_grad_phases(self._ctx, gp, dl.ctypes.data_as(C.POINTER(C.c_double)), dsp,
                               ce.ctypes.data_as(C.POINTER(C.c_double)), int(bool(dev))))
         return dl, ds, ce.reshape(6, 6)
 

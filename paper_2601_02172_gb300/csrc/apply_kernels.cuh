@@ -16,6 +16,8 @@
 //   std force  q_a   = (sum_b m_b S_b) g_a
 //   enr force  q~_a  = D_a^{-1/2} [ (sum_b (sum_c M_bc c_c) S_b) g_a + (sum_b M_ab S_b) gamma ]
 // with S_b = C_s E_b.  Contributions are scatter-added with atomics after the uncut kernel.
+#pragma once
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -96,14 +98,15 @@ __device__ __forceinline__ T ddot(const T (&s)[6], const T (&e)[6]) {
 // its energy/stress integrals to the accumulators.
 template <typename T, int t, bool TOTAL>
 __device__ __forceinline__ void tet_uncut(const T (&u)[8][3], T (&F)[8][3], unsigned code,
-                                          const T (&lm)[2], const T (&mu2)[2], const T (&ih)[3],
+                                          const T (&lm)[kMaxPhases], const T (&mu2)[kMaxPhases],
+                                          const T (&ih)[3],
                                           const T (&w)[3], T vol, const T (&E)[6], T& en,
                                           T (&sg)[6]) {
   constexpr int p = perm_p(t), q = perm_q(t), r = perm_r(t);
   constexpr int c1 = tet_c1(t), c2 = tet_c2(t);
   const unsigned cd = (code >> (2 * t)) & 3u;
-  if (cd == 2u) return;
-  const T lam = lm[cd], mu = mu2[cd];
+  if (cd == kCodeCut) return;
+  const T lam = lm[code_phase(cd)], mu = mu2[code_phase(cd)];
   T H[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -154,13 +157,14 @@ __device__ __forceinline__ T comp(const Node4<T>& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : v.z);
 }
 
-// Per-voxel coefficients of the uncut tets, per phase ph (0 minus, 1 plus) and axis k:
+// Per-voxel coefficients of the uncut tets, per phase ph (one interface: 0 minus, 1 plus; NPH
+// phases in all) and axis k:
 //   lw[ph][k] = lambda w_k s_v, mw[ph][k] = mu w_k s_v with w_k = |T| / h_k^2 on a uniform grid
 //   (raw node differences) or |T| / h_k otherwise (differences scaled by 1/h_k).
-template <typename T, bool UNIFORM>
+template <typename T, bool UNIFORM, int NPH>
 struct Coef {
-  T lw[2][UNIFORM ? 1 : 3];
-  T mw[2][UNIFORM ? 1 : 3];
+  T lw[NPH][UNIFORM ? 1 : 3];
+  T mw[NPH][UNIFORM ? 1 : 3];
   __device__ __forceinline__ T l(int ph, int k) const { return lw[ph][UNIFORM ? 0 : k]; }
   __device__ __forceinline__ T m(int ph, int k) const { return mw[ph][UNIFORM ? 0 : k]; }
 };
@@ -177,16 +181,16 @@ struct EdgeT {
 
 // EDGE: add the tet's tensions to the voxel's edge sums (corner forces formed once per voxel by
 // edge_forces); otherwise add them to the corner forces F directly.
-template <typename T, int t, bool TOTAL, bool SIG, bool UNIFORM, bool EDGE = false>
+template <typename T, int t, bool TOTAL, bool SIG, bool UNIFORM, int NPH, bool EDGE = false>
 __device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3], unsigned code,
-                                            const Coef<T, UNIFORM>& cf, const T (&ih)[3],
+                                            const Coef<T, UNIFORM, NPH>& cf, const T (&ih)[3],
                                             const T (&hk)[3], const T (&Eb)[3][3], T& en, T (&sg)[6],
                                             EdgeT<T>* te = nullptr) {
   constexpr int p = perm_p(t), q = perm_q(t), r = perm_r(t);
   constexpr int c1 = tet_c1(t), c2 = tet_c2(t);
   const unsigned cd = (code >> (2 * t)) & 3u;
-  if (cd == 2u) return;
-  const int ph = (int)cd;
+  if (cd == kCodeCut) return;
+  const int ph = NPH == 2 ? (int)cd : code_phase(cd);
   T G[3][3];  // G[k][i]: column k (axis k) of the gradient, component i
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -284,7 +288,7 @@ __device__ __forceinline__ void edge_forces(const EdgeT<T>& te, T (&F)[8][3]) {
 #define XFFT_EDGE_FORCES 1  // corner forces from per-voxel edge tension sums
 #endif
 
-template <typename T, bool TOTAL, bool SIG, bool UNIFORM, bool FUSED>
+template <typename T, bool TOTAL, bool SIG, bool UNIFORM, bool FUSED, int NPH>
 __global__ void __launch_bounds__(kTZ* kTY, std::is_same<T, dw>::value     ? XFFT_UNCUT_MINBDW
                                              : sizeof(T) == 8 ? XFFT_UNCUT_MINB64
                                                               : XFFT_UNCUT_MINB)
@@ -334,12 +338,12 @@ __global__ void __launch_bounds__(kTZ* kTY, std::is_same<T, dw>::value     ? XFF
     hk[k] = (T)g.h[k];
   }
   // phase coefficients without the voxel scale (converted once; no FP64 work in the loop)
-  T lw0[2][3], mw0[2][3];
+  T lw0[NPH][3], mw0[NPH][3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const double wk = UNIFORM ? g.vol_tet / (g.h[0] * g.h[0]) : g.vol_tet / g.h[k];
 #pragma unroll
-    for (int ph = 0; ph < 2; ++ph) {
+    for (int ph = 0; ph < NPH; ++ph) {
       lw0[ph][k] = (T)(a.ph.lam[ph] * wk);
       mw0[ph][k] = (T)(a.ph.mu[ph] * wk);
     }
@@ -465,9 +469,9 @@ __global__ void __launch_bounds__(kTZ* kTY, std::is_same<T, dw>::value     ? XFF
     Node4<T> u[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) u[c] = P[(s + (c & 1)) & 1][ty + ((c >> 1) & 1)][tz + ((c >> 2) & 1)];
-    Coef<T, UNIFORM> cf;
+    Coef<T, UNIFORM, NPH> cf;
 #pragma unroll
-    for (int ph = 0; ph < 2; ++ph)
+    for (int ph = 0; ph < NPH; ++ph)
 #pragma unroll
       for (int k = 0; k < (UNIFORM ? 1 : 3); ++k) {
         cf.lw[ph][k] = lw0[ph][k] * sv;
@@ -487,23 +491,23 @@ __global__ void __launch_bounds__(kTZ* kTY, std::is_same<T, dw>::value     ? XFF
 #pragma unroll
           for (int l = 0; l < 3; ++l) te.em[k][l][i] = T(0);
         }
-      tet_stencil<T, 0, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
-      tet_stencil<T, 1, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
-      tet_stencil<T, 2, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
-      tet_stencil<T, 3, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
-      tet_stencil<T, 4, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
-      tet_stencil<T, 5, TOTAL, SIG, UNIFORM, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 0, TOTAL, SIG, UNIFORM, NPH, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 1, TOTAL, SIG, UNIFORM, NPH, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 2, TOTAL, SIG, UNIFORM, NPH, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 3, TOTAL, SIG, UNIFORM, NPH, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 4, TOTAL, SIG, UNIFORM, NPH, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
+      tet_stencil<T, 5, TOTAL, SIG, UNIFORM, NPH, true>(u, F, code, cf, ih, hk, Eb, ven, vsg, &te);
       edge_forces(te, F);
     }
 #else
 #pragma unroll
     for (int c = 0; c < 8; ++c) F[c][0] = F[c][1] = F[c][2] = T(0);
-    tet_stencil<T, 0, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
-    tet_stencil<T, 1, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
-    tet_stencil<T, 2, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
-    tet_stencil<T, 3, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
-    tet_stencil<T, 4, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
-    tet_stencil<T, 5, TOTAL, SIG, UNIFORM>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 0, TOTAL, SIG, UNIFORM, NPH>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 1, TOTAL, SIG, UNIFORM, NPH>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 2, TOTAL, SIG, UNIFORM, NPH>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 3, TOTAL, SIG, UNIFORM, NPH>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 4, TOTAL, SIG, UNIFORM, NPH>(u, F, code, cf, ih, hk, Eb, ven, vsg);
+    tet_stencil<T, 5, TOTAL, SIG, UNIFORM, NPH>(u, F, code, cf, ih, hk, Eb, ven, vsg);
 #endif
     if (SIG && own && s >= 1) {
       en += ven;
@@ -628,7 +632,7 @@ constexpr int kCutMaxR = 8;  // right-hand sides per launch (more are split over
 #ifndef XFFT_CUT_MINB
 #define XFFT_CUT_MINB 4  // resident blocks per SM asked of the FP32 cut kernel
 #endif
-template <typename T, bool TOTAL>
+template <typename T, bool TOTAL, int NPH>
 __global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1
                                                : sizeof(T) == 8       ? 2
                                                                       : XFFT_CUT_MINB)
@@ -654,8 +658,12 @@ __global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1
   T ih[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) ih[k] = (T)(1.0 / g.h[k]);
-  const T lam_ph[2] = {(T)a.ph.lam[0], (T)a.ph.lam[1]};
-  const T mu_ph[2] = {(T)a.ph.mu[0], (T)a.ph.mu[1]};
+  T lam_ph[NPH], mu_ph[NPH];
+#pragma unroll
+  for (int p = 0; p < NPH; ++p) {
+    lam_ph[p] = (T)a.ph.lam[p];
+    mu_ph[p] = (T)a.ph.mu[p];
+  }
   for (int base = blockIdx.x * kCutThreads; base < ncut; base += gridDim.x * kCutThreads) {
     const int e = base + threadIdx.x;
     const bool ok = e < ncut;
@@ -677,6 +685,8 @@ __global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1
           L[k] = cut_real_keep<T>(cd, cut_f_L(k), e);
         }
         const int t = ld_keep(cd.ip + 9 * ncut + e);
+        // phases of the two sides: minus / plus with one interface, else per tet
+        const int sph = NPH == 2 ? (0 | (1 << 8)) : ld_keep(cd.ip + kCutFieldPhases * ncut + e);
         T gr[4][3];
         tet_grads<T>(t, ih, gr);
         T us[4][3], ws[4][3];
@@ -721,8 +731,15 @@ __global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1
 #pragma unroll kSides
         for (int si = 0; si < 2; ++si) {
           const T s = si == 0 ? T(1) : T(-1);
-          const int ph = si == 0 ? 1 : 0;
-          const T lam = lam_ph[ph] * sv, mu = mu_ph[ph] * sv;
+          const int ph = si == 0 ? cut_phase_plus(sph) : cut_phase_minus(sph);
+          T lam, mu;
+          if (NPH == 2) {
+            lam = lam_ph[ph] * sv;
+            mu = mu_ph[ph] * sv;
+          } else {  // selects, not a local-memory array
+            lam = (ph == 0 ? lam_ph[0] : ph == 1 ? lam_ph[1] : lam_ph[NPH - 1]) * sv;
+            mu = (ph == 0 ? mu_ph[0] : ph == 1 ? mu_ph[1] : mu_ph[NPH - 1]) * sv;
+          }
           T c[4], gam[3] = {T(0), T(0), T(0)};
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
@@ -803,25 +820,11 @@ __global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1
   }
 }
 
-int apply_uncut_blocks(const GridDev& g) {
-  const int gz = (g.n2 + kTZ - 2) / (kTZ - 1);
-  const int gy = (g.n1 + kTY - 2) / (kTY - 1);
-  const int gx = (g.n0 + kCX - 1) / kCX;
-  return gz * gy * gx;
-}
-
-#ifndef XFFT_CUT_WAVES
-#define XFFT_CUT_WAVES 2
-#endif
-constexpr int kCutBlocksMax = XFFT_CUT_WAVES * 4 * 152;  // waves of four resident blocks per SM
-int apply_cut_blocks(int ncut) {
-  const int nb = (ncut + kCutThreads - 1) / kCutThreads;
-  return nb < 1 ? 1 : (nb > kCutBlocksMax ? kCutBlocksMax : nb);
-}
-
-template <typename T>
-cudaError_t launch_apply_uncut(const typename Store<T>::type* d, typename Store<T>::type* q,
-                               const ApplyArgs& a, int n_rhs, cudaStream_t s) {
+// Kernel launches of one phase count NPH (2: one interface; 3: two interfaces).  The phase
+// counts are instantiated in separate translation units (apply.cu, apply_multi.cu).
+template <typename T, int NPH>
+cudaError_t launch_uncut_nph(const typename Store<T>::type* d, typename Store<T>::type* q,
+                             const ApplyArgs& a, int n_rhs, cudaStream_t s) {
   const GridDev& g = a.g;
   const int gz = (g.n2 + kTZ - 2) / (kTZ - 1);
   const int gy = (g.n1 + kTY - 2) / (kTY - 1);
@@ -830,8 +833,8 @@ cudaError_t launch_apply_uncut(const typename Store<T>::type* d, typename Store<
   dim3 grid(gz, gy, gx * n_rhs);
   const bool uni = g.h[0] == g.h[1] && g.h[1] == g.h[2];
   const bool sig = a.want_sig || a.eps;
-#define XFFT_LAUNCH(TOT, SG, UNI) k_apply_uncut<T, TOT, SG, UNI, false><<<grid, block, 0, s>>>(d, q, a, gx)
-#define XFFT_LAUNCH_F(SG, UNI) k_apply_uncut<T, false, SG, UNI, true><<<grid, block, 0, s>>>(d, q, a, gx)
+#define XFFT_LAUNCH(TOT, SG, UNI) k_apply_uncut<T, TOT, SG, UNI, false, NPH><<<grid, block, 0, s>>>(d, q, a, gx)
+#define XFFT_LAUNCH_F(SG, UNI) k_apply_uncut<T, false, SG, UNI, true, NPH><<<grid, block, 0, s>>>(d, q, a, gx)
   if (a.fz) {
     // the fused CG update serves the FP32 and FP64 solvers (not the double-word residuals)
     if constexpr (!std::is_same<T, dw>::value) {
@@ -860,192 +863,26 @@ cudaError_t launch_apply_uncut(const typename Store<T>::type* d, typename Store<
   return cudaGetLastError();
 }
 
-// The enriched part of q only receives atomic contributions from the cut-tet kernel: it is
-// cleared first; the standard part must already hold the uncut kernel's plain stores.
-template <typename T>
-cudaError_t launch_apply_cut(const typename Store<T>::type* d, typename Store<T>::type* q,
-                             const typename Store<T>::type* isD, CutData cd, const ApplyArgs& a,
-                             int n_rhs, cudaStream_t s) {
-  typedef typename Store<T>::type S;
-  const GridDev& g = a.g;
-  if (a.nX > 0) {
-    for (int r = 0; r < n_rhs; ++r) {
-      cudaError_t e = cudaMemsetAsync(q + r * a.stride + 3 * g.N, 0, sizeof(S) * 3 * (size_t)a.nX, s);
-      if (e != cudaSuccess) return e;
-    }
-  }
+template <typename T, int NPH>
+cudaError_t launch_cut_nph(const typename Store<T>::type* d, typename Store<T>::type* q,
+                           const typename Store<T>::type* isD, CutData cd, const ApplyArgs& a,
+                           int n_rhs, cudaStream_t s) {
   const int nb = apply_cut_blocks(cd.ncut);
   for (int r0 = 0; r0 < n_rhs; r0 += kCutMaxR) {
     const int nr = n_rhs - r0 < kCutMaxR ? n_rhs - r0 : kCutMaxR;
     if (a.eps)
-      k_apply_cut<T, true><<<nb, kCutThreads, 0, s>>>(d, q, isD, cd, a, r0, nr);
+      k_apply_cut<T, true, NPH><<<nb, kCutThreads, 0, s>>>(d, q, isD, cd, a, r0, nr);
     else
-      k_apply_cut<T, false><<<nb, kCutThreads, 0, s>>>(d, q, isD, cd, a, r0, nr);
+      k_apply_cut<T, false, NPH><<<nb, kCutThreads, 0, s>>>(d, q, isD, cd, a, r0, nr);
   }
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_apply(const typename Store<T>::type* d, typename Store<T>::type* q,
-                         const typename Store<T>::type* isD, CutData cd, const ApplyArgs& a,
-                         int n_rhs, cudaStream_t s) {
-  cudaError_t e = launch_apply_uncut<T>(d, q, a, n_rhs, s);
-  if (e != cudaSuccess) return e;
-  return launch_apply_cut<T>(d, q, isD, cd, a, n_rhs, s);
-}
-
-#define XFFT_INST(T)                                                                             \
-  template cudaError_t launch_apply<T>(const Store<T>::type*, Store<T>::type*,                  \
-                                       const Store<T>::type*, CutData, const ApplyArgs&, int,   \
-                                       cudaStream_t);                                           \
-  template cudaError_t launch_apply_uncut<T>(const Store<T>::type*, Store<T>::type*,            \
-                                             const ApplyArgs&, int, cudaStream_t);              \
-  template cudaError_t launch_apply_cut<T>(const Store<T>::type*, Store<T>::type*,              \
-                                           const Store<T>::type*, CutData, const ApplyArgs&, int, \
-                                           cudaStream_t);
-XFFT_INST(float)
-XFFT_INST(double)
-XFFT_INST(dw)
-#undef XFFT_INST
-
-// ---------------------------------------------------------------- per-voxel average stress
-__global__ void k_voxel_stress_uncut(const double* __restrict__ u, const ApplyArgs a,
-                                     double* __restrict__ out) {
-  const int rhs = blockIdx.y;
-  const GridDev& g = a.g;
-  const double* ur = u + rhs * a.stride;
-  double E[6];
-  mandel_to_tensor(a.eps + 6 * rhs, E);
-  double ih[3], w[3];
-  for (int k = 0; k < 3; ++k) {
-    ih[k] = 1.0 / g.h[k];
-    w[k] = g.vol_tet / g.h[k];
-  }
-  const double lm[2] = {a.ph.lam[0], a.ph.lam[1]};
-  const double mu2[2] = {a.ph.mu[0], a.ph.mu[1]};
-  const double ivox = 1.0 / (6.0 * g.vol_tet);
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.N;
-       v += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(v % g.n2);
-    const int j = (int)((v / g.n2) % g.n1);
-    const int i = (int)(v / ((long long)g.n1 * g.n2));
-    double uu[8][3];
-    for (int c = 0; c < 8; ++c) {
-      const long long nd = corner_node(g, i, j, k, c);
-      for (int x = 0; x < 3; ++x) uu[c][x] = ur[x * g.N + nd];
-    }
-    const double sv = a.scale ? (double)a.scale[v] : 1.0;
-    double lms[2] = {lm[0] * sv, lm[1] * sv}, mus[2] = {mu2[0] * sv, mu2[1] * sv};
-    double F[8][3] = {};
-    double en = 0.0, sg[6] = {0, 0, 0, 0, 0, 0};
-    const unsigned code = a.code[v];
-    tet_uncut<double, 0, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
-    tet_uncut<double, 1, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
-    tet_uncut<double, 2, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
-    tet_uncut<double, 3, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
-    tet_uncut<double, 4, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
-    tet_uncut<double, 5, true>(uu, F, code, lms, mus, ih, w, g.vol_tet, E, en, sg);
-    const double r2 = 1.41421356237309504880;
-    double* o = out + (long long)rhs * 6 * g.N;
-    o[0 * g.N + v] = sg[0] * ivox;
-    o[1 * g.N + v] = sg[1] * ivox;
-    o[2 * g.N + v] = sg[2] * ivox;
-    o[3 * g.N + v] = sg[3] * r2 * ivox;
-    o[4 * g.N + v] = sg[4] * r2 * ivox;
-    o[5 * g.N + v] = sg[5] * r2 * ivox;
-  }
-}
-
-__global__ void k_voxel_stress_cut(const double* __restrict__ u, const double* __restrict__ isD,
-                                   const CutData cd, const ApplyArgs a, double* __restrict__ out) {
-  const int rhs = blockIdx.y;
-  const GridDev& g = a.g;
-  const long long N = g.N;
-  const int nX = a.nX, ncut = cd.ncut;
-  const double* ur = u + rhs * a.stride;
-  double E[6];
-  mandel_to_tensor(a.eps + 6 * rhs, E);
-  double ih[3];
-  for (int k = 0; k < 3; ++k) ih[k] = 1.0 / g.h[k];
-  const double ivox = 1.0 / (6.0 * g.vol_tet);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
-    int nd[4], ei[4];
-    for (int k = 0; k < 4; ++k) {
-      nd[k] = cd.ip[k * ncut + e];
-      ei[k] = cd.ip[(4 + k) * ncut + e];
-    }
-    const int vox = cd.ip[8 * ncut + e];
-    const int t = cd.ip[9 * ncut + e];
-    double gr[4][3];
-    tet_grads<double>(t, ih, gr);
-    double us[4][3], ws[4][3];
-    for (int k = 0; k < 4; ++k)
-      for (int c = 0; c < 3; ++c) {
-        us[k][c] = ur[c * N + nd[k]];
-        ws[k][c] = ur[3 * N + (long long)c * nX + ei[k]] * isD[(long long)c * nX + ei[k]];
-      }
-    double L[4];
-    for (int b = 0; b < 4; ++b) L[b] = cd.dp[(long long)cut_f_L(b) * ncut + e];
-    const double sv = a.scale ? (double)a.scale[vox] : 1.0;
-    double es[6] = {0, 0, 0, 0, 0, 0}, ew[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = 0; k < 4; ++k) {
-      es[0] += us[k][0] * gr[k][0];
-      es[1] += us[k][1] * gr[k][1];
-      es[2] += us[k][2] * gr[k][2];
-      es[3] += 0.5 * (us[k][1] * gr[k][2] + us[k][2] * gr[k][1]);
-      es[4] += 0.5 * (us[k][0] * gr[k][2] + us[k][2] * gr[k][0]);
-      es[5] += 0.5 * (us[k][0] * gr[k][1] + us[k][1] * gr[k][0]);
-      ew[0] += ws[k][0] * gr[k][0];
-      ew[1] += ws[k][1] * gr[k][1];
-      ew[2] += ws[k][2] * gr[k][2];
-      ew[3] += 0.5 * (ws[k][1] * gr[k][2] + ws[k][2] * gr[k][1]);
-      ew[4] += 0.5 * (ws[k][0] * gr[k][2] + ws[k][2] * gr[k][0]);
-      ew[5] += 0.5 * (ws[k][0] * gr[k][1] + ws[k][1] * gr[k][0]);
-    }
-    for (int k = 0; k < 6; ++k) es[k] += E[k];
-    double tot[6] = {0, 0, 0, 0, 0, 0};
-    for (int si = 0; si < 2; ++si) {
-      const double s = si == 0 ? 1.0 : -1.0;
-      const int ph = si == 0 ? 1 : 0;
-      const double lam = a.ph.lam[ph] * sv, mu = a.ph.mu[ph] * sv;
-      double c[4], gam[3] = {0, 0, 0};
-      for (int b = 0; b < 4; ++b) {
-        c[b] = fabs(L[b]) - s * L[b];
-        for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
-      }
-      for (int b = 0; b < 4; ++b) {
-        const double mb = cd.dp[(long long)cut_f_m(si, b) * ncut + e];
-        const double* wb = ws[b];
-        double eb[6] = {es[0] + c[b] * ew[0] + wb[0] * gam[0], es[1] + c[b] * ew[1] + wb[1] * gam[1],
-                        es[2] + c[b] * ew[2] + wb[2] * gam[2],
-                        es[3] + c[b] * ew[3] + 0.5 * (wb[1] * gam[2] + wb[2] * gam[1]),
-                        es[4] + c[b] * ew[4] + 0.5 * (wb[0] * gam[2] + wb[2] * gam[0]),
-                        es[5] + c[b] * ew[5] + 0.5 * (wb[0] * gam[1] + wb[1] * gam[0])};
-        double sb[6];
-        iso_stress(eb, lam, mu, sb);
-        for (int k = 0; k < 6; ++k) tot[k] += mb * sb[k];
-      }
-    }
-    const double r2 = 1.41421356237309504880;
-    double* o = out + (long long)rhs * 6 * N;
-    atomicAdd(&o[0 * N + vox], tot[0] * ivox);
-    atomicAdd(&o[1 * N + vox], tot[1] * ivox);
-    atomicAdd(&o[2 * N + vox], tot[2] * ivox);
-    atomicAdd(&o[3 * N + vox], tot[3] * r2 * ivox);
-    atomicAdd(&o[4 * N + vox], tot[4] * r2 * ivox);
-    atomicAdd(&o[5 * N + vox], tot[5] * r2 * ivox);
-  }
-}
-
-cudaError_t launch_voxel_stress(const double* u, const double* isD, CutData cd,
-                                const ApplyArgs& a, double* out, int n_rhs, cudaStream_t s) {
-  long long nb = (a.g.N + 255) / 256;
-  if (nb > 65535) nb = 65535;
-  k_voxel_stress_uncut<<<dim3((unsigned)nb, n_rhs), 256, 0, s>>>(u, a, out);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || cd.ncut == 0) return e;
-  k_voxel_stress_cut<<<dim3(apply_cut_blocks(cd.ncut), n_rhs), 128, 0, s>>>(u, isD, cd, a, out);
-  return cudaGetLastError();
-}
+#define XFFT_APPLY_INST_NPH(EXT, T, NPH)                                                         \
+  EXT template cudaError_t launch_uncut_nph<T, NPH>(const Store<T>::type*, Store<T>::type*,      \
+                                                    const ApplyArgs&, int, cudaStream_t);        \
+  EXT template cudaError_t launch_cut_nph<T, NPH>(const Store<T>::type*, Store<T>::type*,        \
+                                                  const Store<T>::type*, CutData, const ApplyArgs&, \
+                                                  int, cudaStream_t);
 
 }  // namespace xfft

@@ -367,20 +367,32 @@ extern "C" xfft_status xfft_set_microstructure(xfft_ctx* c, const double* L, con
                                                const double lame_plus[2], const float* voxel_scale,
                                                int ptrs_on_device) {
   if (!c || !L || !lame_minus || !lame_plus) return fail(XFFT_EINVAL, "NULL argument");
-  if (!(lame_minus[1] > 0.0) || !(lame_plus[1] > 0.0) ||
-      !(3.0 * lame_minus[0] + 2.0 * lame_minus[1] > 0.0) || !(3.0 * lame_plus[0] + 2.0 * lame_plus[1] > 0.0))
-    return fail(XFFT_EINVAL, "Lame constants must give a positive definite stiffness");
+  const double lame[4] = {lame_minus[0], lame_minus[1], lame_plus[0], lame_plus[1]};
+  return xfft_set_microstructure_phases(c, 1, L, lame, voxel_scale, ptrs_on_device);
+}
+
+extern "C" xfft_status xfft_set_microstructure_phases(xfft_ctx* c, int n_levelsets, const double* L,
+                                                      const double* lame, const float* voxel_scale,
+                                                      int ptrs_on_device) {
+  if (!c || !L || !lame) return fail(XFFT_EINVAL, "NULL argument");
+  if (n_levelsets < 1 || n_levelsets > XFFT_MAX_LEVELSETS)
+    return fail(XFFT_EINVAL, "n_levelsets must be 1 .. XFFT_MAX_LEVELSETS");
+  const int nph = n_levelsets + 1;
+  for (int p = 0; p < nph; ++p)
+    if (!(lame[2 * p + 1] > 0.0) || !(3.0 * lame[2 * p] + 2.0 * lame[2 * p + 1] > 0.0))
+      return fail(XFFT_EINVAL, "Lame constants must give a positive definite stiffness");
   free_micro(c);
   const GridDev& g = c->g;
   const long long N = g.N;
   cudaStream_t s = c->stream;
   CU(cudaEventRecord(c->ev0, s));
-  c->ph.lam[0] = lame_minus[0];
-  c->ph.mu[0] = lame_minus[1];
-  c->ph.lam[1] = lame_plus[0];
-  c->ph.mu[1] = lame_plus[1];
+  for (int p = 0; p < kMaxPhases; ++p) {
+    c->ph.lam[p] = p < nph ? lame[2 * p] : 0.0;
+    c->ph.mu[p] = p < nph ? lame[2 * p + 1] : 0.0;
+  }
+  c->ph.nph = nph;
   c->tau = c->opt.snap_tau > 0.0 ? c->opt.snap_tau : 1e-6 * std::min(g.h[0], std::min(g.h[1], g.h[2]));
-  CU(dalloc(&c->Ls, N));
+  CU(dalloc(&c->Ls, (size_t)n_levelsets * N));
   CU(dalloc(&c->code, N));
   CU(dalloc(&c->cutcount, N));
   CU(dalloc(&c->enr_flag, N));
@@ -389,8 +401,8 @@ extern "C" xfft_status xfft_set_microstructure(xfft_ctx* c, const double* L, con
   CU(dalloc(&c->d_tot, 4));
   const double* Ldev = L;
   if (!ptrs_on_device) {
-    CU(dalloc(&c->Lin, N));
-    CU(cudaMemcpyAsync(c->Lin, L, N * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(dalloc(&c->Lin, (size_t)n_levelsets * N));
+    CU(cudaMemcpyAsync(c->Lin, L, n_levelsets * N * sizeof(double), cudaMemcpyHostToDevice, s));
     Ldev = c->Lin;
   }
   if (voxel_scale) {
@@ -416,19 +428,25 @@ extern "C" xfft_status xfft_set_microstructure(xfft_ctx* c, const double* L, con
         smax = std::max(smax, (double)hs[i]);
       }
     }
-    const double ev[4] = {2.0 * lame_minus[1], 3.0 * lame_minus[0] + 2.0 * lame_minus[1], 2.0 * lame_plus[1],
-                          3.0 * lame_plus[0] + 2.0 * lame_plus[1]};
-    const double cmin = *std::min_element(ev, ev + 4) * smin, cmax = *std::max_element(ev, ev + 4) * smax;
+    double ev[2 * kMaxPhases];
+    for (int p = 0; p < nph; ++p) {
+      ev[2 * p] = 2.0 * lame[2 * p + 1];
+      ev[2 * p + 1] = 3.0 * lame[2 * p] + 2.0 * lame[2 * p + 1];
+    }
+    const double cmin = *std::min_element(ev, ev + 2 * nph) * smin;
+    const double cmax = *std::max_element(ev, ev + 2 * nph) * smax;
     c->step0 = 2.0 / (cmin + cmax);
   }
   ProfScope ps_setup(c, XFFT_PROF_SETUP, 14);
-  CU(launch_snap_classify(Ldev, c->Ls, c->code, c->cutcount, c->enr_flag, g, c->tau, s));
+  CU(launch_snap_classify(Ldev, c->Ls, n_levelsets, c->code, c->cutcount, c->enr_flag, c->d_tot + 3,
+                          g, c->tau, s));
   // enriched ids (scan of node flags) and cut-tet offsets (scan of per-voxel counts)
   CU(launch_scan(c->enr_flag, c->enr_id, N, c->d_tot + 0, c->scan_tmp, s));
   CU(launch_scan(c->cutcount, c->cutcount, N, c->d_tot + 1, c->scan_tmp, s));
-  int tot[2];
-  CU(cudaMemcpyAsync(tot, c->d_tot, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  int tot[4];
+  CU(cudaMemcpyAsync(tot, c->d_tot, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
+  if (tot[3] > 0) return fail(XFFT_EINVAL, "a tet is cut by two interfaces (one interface per element)");
   c->nX = tot[0];
   c->ncut = tot[1];
   CU(dalloc(&c->enr_nodes, c->nX));
@@ -438,7 +456,7 @@ extern "C" xfft_status xfft_set_microstructure(xfft_ctx* c, const double* L, con
   CU(launch_build_lists(c->code, c->cutcount, c->enr_flag, c->enr_id, c->enr_nodes, c->cut_ip,
                         c->ncut, g, s));
   CutData cd = cutdata(c);
-  CU(launch_cut_geometry(c->Ls, cd, c->cut_dp, c->cut_ip, g, s));
+  CU(launch_cut_geometry(c->Ls, n_levelsets, cd, c->cut_dp, c->cut_ip, g, s));
   CU(launch_cut_eids(c->cut_ip, c->enr_id, c->ncut, s));
   CU(dalloc(&c->D, 3 * (size_t)c->nX));
   CU(dalloc(&c->isD, 3 * (size_t)c->nX));
@@ -492,7 +510,7 @@ static xfft_status ensure_work(xfft_ctx* c, int n_rhs, int prec) {
       std::max(precondition_blocks(c->fft, c->nX, true), precondition_blocks(c->fft, c->nX, false));
   const int ng = grad_blocks_uncut(c->g) + grad_blocks_cut(c->ncut);
   const int nparts = std::max(na, np);
-  c->partials_count = std::max((size_t)n_rhs * 7 * nparts, (size_t)25 * ng);
+  c->partials_count = std::max((size_t)n_rhs * 7 * nparts, (size_t)kGradValues * ng);
   CU(dalloc(&c->partials, c->partials_count));
   CU(dalloc(&c->red_out, 64));
   c->cap_rhs = n_rhs;
@@ -1088,6 +1106,13 @@ extern "C" xfft_status xfft_batch_effective_stiffness(int n, xfft_ctx* const* ct
 
 extern "C" xfft_status xfft_grad(xfft_ctx* c, const double dL_dCeff[36], double dL_dlame[4],
                                  float* dL_dscale, double C_energy[36], int ptrs_on_device) {
+  if (c && c->have_micro && c->ph.nph != 2)
+    return fail(XFFT_EINVAL, "more than two phases: use xfft_grad_phases");
+  return xfft_grad_phases(c, dL_dCeff, dL_dlame, dL_dscale, C_energy, ptrs_on_device);
+}
+
+extern "C" xfft_status xfft_grad_phases(xfft_ctx* c, const double dL_dCeff[36], double* dL_dlame,
+                                        float* dL_dscale, double C_energy[36], int ptrs_on_device) {
   if (!c || !dL_dCeff || !dL_dlame) return fail(XFFT_EINVAL, "NULL argument");
   if (!c->have_micro || !c->have6) return fail(XFFT_ESTATE, "xfft_effective_stiffness first");
   TRY(ensure_work(c, 6, c->cap_prec >= 0 ? c->cap_prec : c->opt.precision));
@@ -1108,9 +1133,9 @@ extern "C" xfft_status xfft_grad(xfft_ctx* c, const double dL_dCeff[36], double 
   {
     ProfScope ps(c, XFFT_PROF_GRAD, 3);
     CU(launch_grad(c->U6, c->isD, cutdata(c), a, c->dscale, c->opt.precision == XFFT_FP32_REFINED, s));
-    CU(launch_reduce_partials(c->partials, 25, a.nparts, a.nparts, c->red_out, s));
+    CU(launch_reduce_partials(c->partials, kGradValues, a.nparts, a.nparts, c->red_out, s));
   }
-  double red[25];
+  double red[kGradValues];
   CU(cudaMemcpyAsync(red, c->red_out, sizeof(red), cudaMemcpyDeviceToHost, s));
   if (dL_dscale) {
     ProfScope ps(c, XFFT_PROF_GRAD, 1);
@@ -1123,16 +1148,16 @@ extern "C" xfft_status xfft_grad(xfft_ctx* c, const double dL_dCeff[36], double 
     }
   }
   CU(cudaStreamSynchronize(s));
-  dL_dlame[0] = red[0];  // lambda_minus
-  dL_dlame[1] = red[2];  // mu_minus
-  dL_dlame[2] = red[1];  // lambda_plus
-  dL_dlame[3] = red[3];  // mu_plus
+  for (int p = 0; p < c->ph.nph; ++p) {
+    dL_dlame[2 * p] = red[p];                   // lambda_p
+    dL_dlame[2 * p + 1] = red[kMaxPhases + p];  // mu_p
+  }
   if (C_energy) {
     int idx = 0;
     for (int k = 0; k < 6; ++k)
       for (int l = k; l < 6; ++l, ++idx) {
-        C_energy[k * 6 + l] = red[4 + idx];
-        C_energy[l * 6 + k] = red[4 + idx];
+        C_energy[k * 6 + l] = red[2 * kMaxPhases + idx];
+        C_energy[l * 6 + k] = red[2 * kMaxPhases + idx];
       }
   }
   return XFFT_OK;

@@ -21,7 +21,9 @@
 
 namespace xfft {
 
-constexpr int kNG = 25;  // partial values: dl[2], dm[2], C_energy (21 upper entries)
+// partial values: dlambda[p] (p < kMaxPhases), dmu[p], C_energy (21 upper entries)
+constexpr int kNG = kGradValues;
+constexpr int kNGC = 2 * kMaxPhases;  // first C_energy slot
 
 __device__ __forceinline__ int upper_idx(int k, int l) {
   // k <= l, row-major upper triangle of 6x6
@@ -44,7 +46,7 @@ __device__ __forceinline__ T dd6(const T* a, const T* b) {
 // dozen items are exact to ~1e-7), and the voxel-scale contribution.
 template <typename T, int t>
 __device__ __forceinline__ void grad_uncut_tet(const double* __restrict__ U, const GradArgs& a,
-                                               const double* Gs, long long v, unsigned cd, T (&acc)[kNG],
+                                               const double* Gs, long long v, int ph, T (&acc)[kNG],
                                                double& contrib) {
   const GridDev& g = a.g;
   constexpr int p = perm_p(t), q = perm_q(t), r = perm_r(t);
@@ -79,7 +81,7 @@ __device__ __forceinline__ void grad_uncut_tet(const double* __restrict__ U, con
     eps[k][k] += k < 3 ? T(1) : rs;  // unit Mandel strain E_k
     tr[k] = eps[k][0] + eps[k][1] + eps[k][2];
   }
-  const T lam = (T)a.ph.lam[cd], mu = (T)a.ph.mu[cd];
+  const T lam = (T)a.ph.lam[ph], mu = (T)a.ph.mu[ph];
   const double sv = a.scale ? (double)a.scale[v] : 1.0;
   const double w = g.vol_tet / g.volY;
   const T wsv = (T)(w * sv);
@@ -93,14 +95,18 @@ __device__ __forceinline__ void grad_uncut_tet(const double* __restrict__ U, con
       const T gk = (T)((k == l) ? Gs[k * 6 + l] : Gs[k * 6 + l] + Gs[l * 6 + k]);
       ql += gk * tt;
       qm += gk * ee;
-      acc[4 + upper_idx(k, l)] += wsv * (lam * tt + mu * ee);
+      acc[kNGC + upper_idx(k, l)] += wsv * (lam * tt + mu * ee);
     }
-  if (cd == 0u) {
+  // per-phase sums with compile-time slots (no local-memory indexing)
+  if (ph == 0) {
     acc[0] += wsv * ql;
-    acc[2] += wsv * qm;
-  } else {
+    acc[kMaxPhases] += wsv * qm;
+  } else if (ph == 1) {
     acc[1] += wsv * ql;
-    acc[3] += wsv * qm;
+    acc[kMaxPhases + 1] += wsv * qm;
+  } else {
+    acc[2] += wsv * ql;
+    acc[kMaxPhases + 2] += wsv * qm;
   }
   contrib = w * (double)(lam * ql + mu * qm);
 }
@@ -126,14 +132,15 @@ __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U
     double contrib = 0.0;
     if (v < g.N) {
       const unsigned cd = (a.code[v] >> (2 * t)) & 3u;
-      if (cd != 2u) {
+      if (cd != kCodeCut) {
+        const int ph = code_phase(cd);
         switch (t) {  // uniform per warp
-          case 0: grad_uncut_tet<T, 0>(U, a, Gs, v, cd, acc, contrib); break;
-          case 1: grad_uncut_tet<T, 1>(U, a, Gs, v, cd, acc, contrib); break;
-          case 2: grad_uncut_tet<T, 2>(U, a, Gs, v, cd, acc, contrib); break;
-          case 3: grad_uncut_tet<T, 3>(U, a, Gs, v, cd, acc, contrib); break;
-          case 4: grad_uncut_tet<T, 4>(U, a, Gs, v, cd, acc, contrib); break;
-          default: grad_uncut_tet<T, 5>(U, a, Gs, v, cd, acc, contrib); break;
+          case 0: grad_uncut_tet<T, 0>(U, a, Gs, v, ph, acc, contrib); break;
+          case 1: grad_uncut_tet<T, 1>(U, a, Gs, v, ph, acc, contrib); break;
+          case 2: grad_uncut_tet<T, 2>(U, a, Gs, v, ph, acc, contrib); break;
+          case 3: grad_uncut_tet<T, 3>(U, a, Gs, v, ph, acc, contrib); break;
+          case 4: grad_uncut_tet<T, 4>(U, a, Gs, v, ph, acc, contrib); break;
+          default: grad_uncut_tet<T, 5>(U, a, Gs, v, ph, acc, contrib); break;
         }
       }
     }
@@ -173,6 +180,7 @@ __global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
     }
     const int vox = cd.ip[8 * ncut + e];
     const int t = cd.ip[9 * ncut + e];
+    const int sph = cd.ip[kCutFieldPhases * ncut + e];
     double gr[4][3];
     tet_grads<double>(t, ih, gr);
     double L[4];
@@ -181,7 +189,7 @@ __global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
     double contrib = 0.0;
     for (int si = 0; si < 2; ++si) {
       const double s = si == 0 ? 1.0 : -1.0;
-      const int ph = si == 0 ? 1 : 0;
+      const int ph = si == 0 ? cut_phase_plus(sph) : cut_phase_minus(sph);
       const double lam = a.ph.lam[ph], mu = a.ph.mu[ph];
       double c[4], gam[3] = {0, 0, 0};
       for (int b = 0; b < 4; ++b) {
@@ -241,10 +249,10 @@ __global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
           const T gk = (T)((k == l) ? a.G[k * 6 + l] : a.G[k * 6 + l] + a.G[l * 6 + k]);
           ql += gk * tt;
           qm += gk * ee;
-          acc[4 + upper_idx(k, l)] += inv * sv * (double)(lamT * tt + muT * ee);
+          acc[kNGC + upper_idx(k, l)] += inv * sv * (double)(lamT * tt + muT * ee);
         }
       acc[ph] += inv * sv * (double)ql;
-      acc[2 + ph] += inv * sv * (double)qm;
+      acc[kMaxPhases + ph] += inv * sv * (double)qm;
       contrib += inv * (double)(lamT * ql + muT * qm);
     }
     atomicAdd(&dscale[vox], contrib);

@@ -5,6 +5,13 @@
 //  * A P1 tet is cut iff its nodal level-set values take both signs (the modified abs
 //    enrichment, eq. modifiedabsEnrichment, vanishes identically otherwise); the enriched
 //    nodes J are all nodes of cut tets (eq. X-FEM_space).  Enriched ids follow the node order.
+//  * Several interfaces (K level sets, Sec. 4.2's coated sphere): a point lies in phase k if
+//    L_k is the first negative level set there, in phase K if none is.  A tet's first level set
+//    that is negative at a vertex gives the phase of an uncut tet; if that level set also takes
+//    a positive value the tet is cut by its interface, the minus side in phase k and the plus
+//    side in the first later level set negative on the tet (else K).  One interface per
+//    element: a later level set changing sign on a cut tet is an error.  Each cut tet is
+//    enriched with the modified abs of its own interface's level set.
 //  * Each side s of a cut tet (s = +: L_h > 0, s = -: L_h < 0) is a tetrahedron or a
 //    triangular prism bounded by the linearised interface L_h = 0 (Sec. 3, Fig. subdivision).
 //    Instead of quadrature points we store its exact moments int N_b and int N_b N_c of the
@@ -29,53 +36,87 @@ __global__ void k_snap(const double* __restrict__ L, double* __restrict__ Ls, lo
   }
 }
 
-__global__ void k_classify(const double* __restrict__ Ls, GridDev g, uint16_t* __restrict__ code,
-                           int* __restrict__ cutcount, int* __restrict__ enr_flag) {
+// Classification of tet (a, b, c, d vertex values per level set): returns the 2-bit code and,
+// for a cut tet, the minus / plus phases; *two is set if a second interface cuts the tet.
+__device__ inline unsigned classify_tet(const double* const* Lv, int nL, int* pm, int* pp,
+                                        bool* two) {
+  int first = nL;
+  bool cut = false;
+  for (int l = 0; l < nL; ++l) {
+    const double* x = Lv[l];
+    const double mn = fmin(fmin(x[0], x[1]), fmin(x[2], x[3]));
+    const double mx = fmax(fmax(x[0], x[1]), fmax(x[2], x[3]));
+    if (first == nL) {
+      if (mn < 0.0) {  // minus phase if any vertex is negative
+        first = l;
+        cut = mx > 0.0;
+        *pp = nL;
+      }
+    } else if (cut && mn < 0.0) {
+      if (mx > 0.0) *two = true;
+      if (*pp == nL) *pp = l;
+    }
+  }
+  *pm = first;
+  return cut ? kCodeCut : phase_code(first);
+}
+
+__global__ void k_classify(const double* __restrict__ Ls, int nL, GridDev g, uint16_t* __restrict__ code,
+                           int* __restrict__ cutcount, int* __restrict__ enr_flag, int* __restrict__ bad) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.N;
        v += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(v % g.n2);
     const int j = (int)((v / g.n2) % g.n1);
     const int i = (int)(v / ((long long)g.n1 * g.n2));
-    double Lc[8];
+    double Lc[kMaxPhases - 1][8];
     long long nd[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      nd[c] = corner_node(g, i, j, k, c);
-      Lc[c] = Ls[nd[c]];
-    }
+    for (int c = 0; c < 8; ++c) nd[c] = corner_node(g, i, j, k, c);
+    for (int l = 0; l < nL; ++l)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) Lc[l][c] = Ls[l * g.N + nd[c]];
     unsigned cd = 0;
     int cnt = 0;
+    bool two = false;
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
-      const double a = Lc[0], b = Lc[tet_c1(t)], c = Lc[tet_c2(t)], d = Lc[7];
-      const double mn = fmin(fmin(a, b), fmin(c, d));
-      const double mx = fmax(fmax(a, b), fmax(c, d));
-      unsigned bits;
-      if (mn < 0.0 && mx > 0.0) {
-        bits = 2u;
+      double tv[kMaxPhases - 1][4];
+      const double* pv[kMaxPhases - 1];
+      for (int l = 0; l < nL; ++l) {
+        tv[l][0] = Lc[l][0];
+        tv[l][1] = Lc[l][tet_c1(t)];
+        tv[l][2] = Lc[l][tet_c2(t)];
+        tv[l][3] = Lc[l][7];
+        pv[l] = tv[l];
+      }
+      int pm, pp;
+      const unsigned bits = classify_tet(pv, nL, &pm, &pp, &two);
+      if (bits == kCodeCut) {
         ++cnt;
         enr_flag[nd[0]] = 1;
         enr_flag[nd[tet_c1(t)]] = 1;
         enr_flag[nd[tet_c2(t)]] = 1;
         enr_flag[nd[7]] = 1;
-      } else {
-        bits = mn < 0.0 ? 0u : 1u;  // minus phase if any vertex is negative
       }
       cd |= bits << (2 * t);
     }
     code[v] = (uint16_t)cd;
     cutcount[v] = cnt;
+    if (two) atomicAdd(bad, 1);
   }
 }
 
-cudaError_t launch_snap_classify(const double* L, double* Ls, uint16_t* code, int* cutcount,
-                                 int* enr_flag, GridDev g, double tau, cudaStream_t s) {
+cudaError_t launch_snap_classify(const double* L, double* Ls, int nL, uint16_t* code, int* cutcount,
+                                 int* enr_flag, int* bad, GridDev g, double tau, cudaStream_t s) {
+  if (nL < 1 || nL > kMaxPhases - 1) return cudaErrorInvalidValue;
   const int nb = (int)((g.N + kThreads - 1) / kThreads);
   const int grid = nb < 65535 * 16 ? nb : 65535 * 16;
   cudaError_t e = cudaMemsetAsync(enr_flag, 0, sizeof(int) * g.N, s);
   if (e != cudaSuccess) return e;
-  k_snap<<<grid, kThreads, 0, s>>>(L, Ls, g.N, tau);
-  k_classify<<<grid, kThreads, 0, s>>>(Ls, g, code, cutcount, enr_flag);
+  e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_snap<<<grid, kThreads, 0, s>>>(L, Ls, nL * g.N, tau);
+  k_classify<<<grid, kThreads, 0, s>>>(Ls, nL, g, code, cutcount, enr_flag, bad);
   return cudaGetLastError();
 }
 
@@ -331,7 +372,7 @@ __device__ void side_moments(const double L[4], int s, double vol, Moments& out)
   }
 }
 
-__global__ void k_cut_geometry(const double* __restrict__ Ls, int* __restrict__ ip,
+__global__ void k_cut_geometry(const double* __restrict__ Ls, int nL, int* __restrict__ ip,
                                double* __restrict__ dp, int ncut, GridDev g) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
     const long long v = ip[8 * ncut + e];
@@ -339,11 +380,25 @@ __global__ void k_cut_geometry(const double* __restrict__ Ls, int* __restrict__ 
     const int k = (int)(v % g.n2);
     const int j = (int)((v / g.n2) % g.n1);
     const int i = (int)(v / ((long long)g.n1 * g.n2));
+    long long nd[4];
+    double tv[kMaxPhases - 1][4];
+    const double* pv[kMaxPhases - 1];
+    for (int a = 0; a < 4; ++a) {
+      nd[a] = corner_node(g, i, j, k, tet_corner(t, a));
+      ip[a * ncut + e] = (int)nd[a];
+    }
+    for (int l = 0; l < nL; ++l) {
+      for (int a = 0; a < 4; ++a) tv[l][a] = Ls[l * g.N + nd[a]];
+      pv[l] = tv[l];
+    }
+    // the cutting interface is the tet's first level set with a negative vertex
+    int pm = 0, pp = 1;
+    bool two = false;
+    classify_tet(pv, nL, &pm, &pp, &two);
+    ip[kCutFieldPhases * ncut + e] = pm | (pp << 8);
     double L[4];
     for (int a = 0; a < 4; ++a) {
-      const long long nd = corner_node(g, i, j, k, tet_corner(t, a));
-      ip[a * ncut + e] = (int)nd;
-      L[a] = Ls[nd];
+      L[a] = tv[pm][a];
       dp[cut_f_L(a) * (long long)ncut + e] = L[a];
     }
     for (int si = 0; si < 2; ++si) {
@@ -361,11 +416,11 @@ __global__ void k_cut_eids(int* __restrict__ ip, const int* __restrict__ enr_id,
   }
 }
 
-cudaError_t launch_cut_geometry(const double* Ls, CutData cd, double* dp_mut, int* ip_mut,
+cudaError_t launch_cut_geometry(const double* Ls, int nL, CutData cd, double* dp_mut, int* ip_mut,
                                 GridDev g, cudaStream_t s) {
   if (cd.ncut == 0) return cudaSuccess;
   const int nb = (cd.ncut + 127) / 128;
-  k_cut_geometry<<<nb, 128, 0, s>>>(Ls, ip_mut, dp_mut, cd.ncut, g);
+  k_cut_geometry<<<nb, 128, 0, s>>>(Ls, nL, ip_mut, dp_mut, cd.ncut, g);
   return cudaGetLastError();
 }
 

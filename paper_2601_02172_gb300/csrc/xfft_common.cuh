@@ -22,11 +22,21 @@ struct GridDev {
   double volY;       // cell volume
 };
 
-// Phase data passed by value to the kernels.  Phase index 0 = minus (L < 0), 1 = plus.
+// Phase data passed by value to the kernels.  One level set: phase 0 = minus (L < 0),
+// 1 = plus.  K level sets (several interfaces, Sec. 4.2's coated sphere): phase k where L_k is
+// the first negative level set, phase K where none is; nph = K + 1 <= kMaxPhases.
+constexpr int kMaxPhases = 3;
 struct PhaseDev {
-  double lam[2];
-  double mu[2];
+  double lam[kMaxPhases];
+  double mu[kMaxPhases];
+  int nph;
 };
+
+// Per-voxel tet codes, 2 bits per Kuhn tet t at bits 2t: 0, 1 and 3 = uncut in phase 0, 1 and
+// 2; 2 = cut (handled by the cut-tet kernels).
+constexpr unsigned kCodeCut = 2u;
+__host__ __device__ constexpr int code_phase(unsigned cd) { return cd == 3u ? 2 : (int)cd; }
+__host__ __device__ constexpr unsigned phase_code(int p) { return p == 2 ? 3u : (unsigned)p; }
 
 __host__ __device__ constexpr int perm_p(int t) { return t < 2 ? 0 : (t < 4 ? 1 : 2); }
 __host__ __device__ constexpr int perm_q(int t) {

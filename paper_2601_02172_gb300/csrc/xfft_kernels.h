@@ -10,7 +10,8 @@
 namespace xfft {
 
 // Per-cut-tet data, structure of arrays of length ncut.
-//   ints   (10 fields): node[a] (a<4), eid[a] (a<4), voxel, tet
+//   ints   (11 fields): node[a] (a<4), eid[a] (a<4), voxel, tet, side phases (minus phase in
+//                       bits 0..7, plus phase in bits 8..15)
 //   reals  (32 fields): L[b] (b<4), then for side s = 0 (plus) and 1 (minus):
 //                       m[s][b] = int_side N_b (b<4) and M[s][k] = int_side N_b N_c
 //                       (k<10, packed (00,01,02,03,11,12,13,22,23,33))
@@ -20,7 +21,10 @@ struct CutData {
   const float* fp;
   int ncut;
 };
-constexpr int kCutInts = 10;
+constexpr int kCutInts = 11;
+constexpr int kCutFieldPhases = 10;
+__host__ __device__ constexpr int cut_phase_minus(int f) { return f & 0xff; }
+__host__ __device__ constexpr int cut_phase_plus(int f) { return (f >> 8) & 0xff; }
 constexpr int kCutReals = 32;
 __host__ __device__ constexpr int cut_f_L(int b) { return b; }
 __host__ __device__ constexpr int cut_f_m(int s, int b) { return 4 + 14 * s + b; }
@@ -32,8 +36,9 @@ __host__ __device__ constexpr int midx(int b, int c) {
 }
 
 // ---- setup (setup.cu)
-cudaError_t launch_snap_classify(const double* L, double* Ls, uint16_t* code, int* cutcount,
-                                 int* enr_flag, GridDev g, double tau, cudaStream_t s);
+// nL level sets (node order, nL x N); *bad (device int) counts tets cut by two interfaces
+cudaError_t launch_snap_classify(const double* L, double* Ls, int nL, uint16_t* code, int* cutcount,
+                                 int* enr_flag, int* bad, GridDev g, double tau, cudaStream_t s);
 // exclusive scan of n ints into out (may alias in); writes the total to *d_total (device)
 cudaError_t launch_scan(const int* in, int* out, long long n, int* d_total, int* d_tmp,
                         cudaStream_t s);
@@ -41,7 +46,7 @@ size_t scan_tmp_ints(long long n);
 cudaError_t launch_build_lists(const uint16_t* code, const int* cutoff, const int* enr_flag,
                                int* enr_id, int* enr_nodes, int* cut_ints, int ncut, GridDev g,
                                cudaStream_t s);
-cudaError_t launch_cut_geometry(const double* Ls, CutData cd, double* dp_mut, int* ip_mut,
+cudaError_t launch_cut_geometry(const double* Ls, int nL, CutData cd, double* dp_mut, int* ip_mut,
                                 GridDev g, cudaStream_t s);
 cudaError_t launch_cut_eids(int* ip_mut, const int* enr_id, int ncut, cudaStream_t s);
 cudaError_t launch_cut_scaling(CutData cd, double* D, double* Doff, int nX, GridDev g, cudaStream_t s);
@@ -163,6 +168,9 @@ cudaError_t launch_finalize(RhsState* st, const double* partials, FinArgs fa, in
 cudaError_t launch_init_state(RhsState* st, int* act, int n_rhs, const int* mask, cudaStream_t s);
 
 // ---- gradient (grad.cu)
+// values reduced per gradient call: dLoss/dlambda_p (p < kMaxPhases), dLoss/dmu_p, then the 21
+// upper entries of the energy-form C_eff
+constexpr int kGradValues = 2 * kMaxPhases + 21;
 struct GradArgs {
   GridDev g;
   PhaseDev ph;
@@ -171,7 +179,7 @@ struct GradArgs {
   long long stride;
   int nX;
   double G[36];           // dLoss/dC_eff
-  double* partials;       // [25][nparts]: dlam[2], dmu[2], C_energy upper triangle (21)
+  double* partials;       // [kGradValues][nparts]: dlam[3], dmu[3], C_energy upper triangle (21)
   int nparts;
   int part_offset_cut;
 };

@@ -72,7 +72,7 @@ def test_setup_matches_oracle(xf, name):
     # tet codes: 2 = cut, else 0 / 1 = minus / plus phase
     exp = np.zeros(o.nvox, dtype=np.uint16)
     for t in range(6):
-        bits = np.where(o.cut[:, t], 2, np.where(o.tet_phase[:, t] < 0, 0, 1)).astype(np.uint16)
+        bits = np.where(o.cut[:, t], 2, o.tet_phase[:, t]).astype(np.uint16)
         exp |= bits << (2 * t)
     assert np.array_equal(code, exp)
     assert _rel(D0, o.D) < 1e-12

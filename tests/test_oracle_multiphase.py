@@ -115,3 +115,33 @@ def test_two_interfaces_in_one_element_refused():
     ph = [(1.0, 1.0), (2.0, 2.0), (3.0, 3.0)]
     with pytest.raises(ValueError, match="two interfaces"):
         XFEM(Ls, n, phases=ph)
+
+
+def test_three_phase_gradient_matches_finite_differences():
+    """The envelope identity per phase (all six Lame constants and the voxel scale): central
+    differences of the energy-form C_eff, and Euler homogeneity of degree one."""
+    n = (10, 10, 10)
+    Ls = synth.coated_sphere_levelsets(n, (0.45, 0.5, 0.55), 0.18, 0.4)
+    ph = [synth.lame_from_E_nu(8.0, 0.2), synth.lame_from_E_nu(0.5, 0.35), synth.lame_from_E_nu(1.0, 0.3)]
+    s = synth.voxel_scale(n, 5)
+
+    def ceff(phases, scale):
+        o = XFEM(Ls, n, phases=phases, scale=scale)
+        return o, o.effective_stiffness()
+
+    o, (Cs, Ce, U) = ceff(ph, s)
+    assert set(np.unique(o.cut_iface)) == {0, 1}
+    dl, ds = o.stiffness_gradient(U)
+    theta = [x for p in ph for x in p]
+    assert np.allclose(sum(t * g for t, g in zip(theta, dl)), Ce, atol=1e-12 * np.abs(Ce).max())
+    assert np.allclose(np.einsum("v,vkl->kl", s.ravel().astype(float), ds), Ce,
+                       atol=1e-12 * np.abs(Ce).max())
+    for p in (1, 2, 3, 4):  # mu_0, lambda_1, mu_1, lambda_2
+        hp = 1e-6 * theta[p]
+        tp, tm = list(theta), list(theta)
+        tp[p] += hp
+        tm[p] -= hp
+        _, (_, Cp, _) = ceff([tuple(tp[2 * q:2 * q + 2]) for q in range(3)], s)
+        _, (_, Cm, _) = ceff([tuple(tm[2 * q:2 * q + 2]) for q in range(3)], s)
+        fd = (Cp - Cm) / (2 * hp)
+        assert np.abs(fd - dl[p]).max() < 1e-6 * np.abs(dl[p]).max(), p
