@@ -36,8 +36,19 @@ WORKLOAD = ("ellipsoids40: 128^3 periodic grid, 40 random ellipsoids (aspect 1-3
             "scale U[0.8,1.2]; six unit Mandel load cases; loss ||C_eff - C_target||_F^2")
 
 # algorithmic bytes per processed right-hand side and launch ("Roofline")
-def algorithmic_bytes(kind, N, nX, ncut, has_scale):
+def algorithmic_bytes(kind, N, nX, ncut, has_scale, cut_cache=False):
+    """Algorithmic bytes of one kernel group as (per launch, per right-hand side)."""
     geo = N * (2 + (4 if has_scale else 0))
+    if kind == "apply_cut_f32" and cut_cache:
+        # cached element matrices: per launch each cut tet's packed matrix (1200 B) and node and
+        # enriched ids (32 B); per RHS the DOFs of the enriched nodes (all nodes of cut tets):
+        # std and enr d read (24 B) and std and enr q atomically updated (48 B)
+        return 1232 * ncut, 72 * nX
+    per = _per_rhs_bytes(kind, N, nX, ncut, geo)
+    return (0, per) if per is not None else None
+
+
+def _per_rhs_bytes(kind, N, nX, ncut, geo):
     if kind == "apply_uncut_f32":  # the fused CG form: z, d_old, u in; d_new, u, q out
         return 72 * N + geo
     if kind == "apply_uncut_f64":
@@ -66,6 +77,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the block-preconditioner, batch and cuFFT side measurements")
     ap.add_argument("--cpu-n", type=int, default=16)
+    ap.add_argument("--cut-cache", action="store_true",
+                    help="run the timed solves with the cached cut-tet element matrices")
     return ap.parse_args()
 
 
@@ -274,7 +287,7 @@ def main():
     s_d = torch.from_numpy(s_h).to(dev)
     L_pin = torch.from_numpy(L_h).pin_memory()  # e2e inputs come from pinned host memory
     s_pin = torch.from_numpy(s_h).pin_memory()
-    solver = Solver(n, precision="fp32", tol=args.tol)
+    solver = Solver(n, precision="fp32", tol=args.tol, cut_cache=args.cut_cache)
 
     # C_target: a random SPD perturbation of C_eff (seeded)
     solver.set_microstructure(L_d, lm, lp, s_d)
@@ -337,11 +350,12 @@ def main():
     dom = max(kinds, key=lambda k: prof[k][0])
     kms, klaunch, kunits = prof[dom]
     nX = info["nX"]
-    bpu = algorithmic_bytes(dom, N, nX, info["ncut"], True)
-    achieved = bpu * kunits / (kms / 1000.0) / 1e9 if kms > 0 else 0.0
-    tr = traffic_for(dom)
+    bpl, bpu = algorithmic_bytes(dom, N, nX, info["ncut"], True, cut_cache=args.cut_cache)
+    achieved = (bpl * klaunch + bpu * kunits) / (kms / 1000.0) / 1e9 if kms > 0 else 0.0
+    tr = traffic_for(dom + ("_cached" if args.cut_cache and dom == "apply_cut_f32" else ""))
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_kind, "bytes_per_rhs_launch": bpu,
+            "frac": achieved / peak, "peak_source": peak_kind, "bytes_per_launch": bpl,
+            "bytes_per_rhs": bpu,
             "launches": klaunch, "rhs_units": kunits, "avg_launch_ms": kms / max(klaunch, 1),
             "traffic": (tr["dram_bytes_per_rhs"] * kunits / max(klaunch, 1)) if tr else None,
             "groups_ms": {k: round(v[0], 3) for k, v in prof.items()}}
@@ -464,6 +478,30 @@ def main():
                 hashin["enriched_node_share"] = sv.num_enriched / 128 ** 3
                 sv.close()
             extra["hashin_neutral_inclusion"] = hashin
+            # the paper's caching trade-off: cut-tet element matrices cached (option cut_cache)
+            # against their action recomputed from the per-side moments at every apply (default)
+            cc = {"cache_bytes": 1200 * info["ncut"]}
+            for cached in (True, False):
+                sv = Solver(n, precision="fp32", tol=args.tol, cut_cache=cached)
+                sv.set_microstructure(L_d, lm, lp, s_d)
+                sv.effective_stiffness()
+                sv.profile(True)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                Cc, _ = sv.effective_stiffness()
+                torch.cuda.synchronize()
+                tc = time.perf_counter() - t0
+                pc = sv.profile_read()
+                sv.profile(False)
+                key = "cached" if cached else "on_the_fly"
+                cc["solves_per_s_" + key] = 1.0 / tc
+                cc["cut_ms_per_launch_" + key] = pc["apply_cut_f32"][0] / max(pc["apply_cut_f32"][1], 1)
+                cc["ceff_" + key] = Cc
+                sv.close()
+            cc["ceff_rel_diff"] = float(np.abs(cc.pop("ceff_cached") - cc["ceff_on_the_fly"]).max()
+                                        / np.abs(cc["ceff_on_the_fly"]).max())
+            cc.pop("ceff_on_the_fly")
+            extra["cut_cache"] = cc
             # cuFFT (torch.fft) R2C + C2R of the same 3 x 6 FP32 fields, beside the preconditioner
             x = torch.randn(18, *n, device=dev, dtype=torch.float32)
             for _ in range(3):

@@ -99,6 +99,13 @@ typedef struct {
   int poll_every;      /* iterations between host checks of the device convergence flags */
   int scheme;          /* XFFT_SCHEME_CG (Algorithm 1, default), _BASIC or _BB */
   double step;         /* step of the basic / BB schemes; <= 0: s0 = 2 / (C_- + C_+) */
+  int cut_cache;       /* FP32_REFINED: 1 caches each cut tet's scaled 24 x 24 element matrix
+                          (FP32, packed upper triangle, 1200 bytes per cut tet) at
+                          xfft_set_microstructure and applies it in the FP32 CG iterations (the
+                          paper's caching strategy, Sec. 2.3); 0 (default) recomputes the element
+                          action from the 32 per-side moments at every apply, which is about three
+                          times faster on GB300 (the cached matrices make the kernel wait on
+                          memory) */
 } xfft_options;
 
 typedef struct {
@@ -111,7 +118,7 @@ typedef struct {
 } xfft_stats;
 
 /* Fill *opt with the defaults: FP64, tol 1e-10, maxit 10000, snap_tau 0 (=> 1e-6 min h),
- * identity enriched block, inner_tol 1e-5, max_refine 20, poll_every 8, linear CG. */
+ * identity enriched block, inner_tol 1e-5, max_refine 20, poll_every 8, linear CG, cut_cache 0. */
 xfft_status xfft_default_options(xfft_options* opt);
 
 /* Create a context for one grid.  stream: a cudaStream_t (or NULL for the legacy stream).
@@ -192,6 +199,8 @@ xfft_status xfft_grad_phases(xfft_ctx* ctx, const double dL_dCeff[36], double* d
  *   xfft_apply:        q = A d  (+ b(eps_bar) when eps_bar != NULL), i.e. the residual map of
  *                      eq. resVector with the sign of eq. linearSystem; also returns, per RHS,
  *                      int_Y C (eps_bar + grad^s d) in sigma_int (n_rhs x 6, host, may be NULL).
+ *                      With eps_bar and sigma_int both NULL and XFFT_FP32_REFINED it runs the
+ *                      kernels of the FP32 CG iterations (cached cut-tet matrices if cut_cache).
  *   xfft_precondition: z = P^{-1} f with P = diag(A0_11, I) (eqs. scaledPreconditioner,
  *                      GreenHermitian); the standard part of f must have zero mean per
  *                      component.  rr (n_rhs, host, may be NULL) receives f^T z.

@@ -41,7 +41,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
                 ("snap_tau", C.c_double), ("enr_precond", C.c_int), ("inner_tol", C.c_double),
                 ("max_refine", C.c_int), ("poll_every", C.c_int), ("scheme", C.c_int),
-                ("step", C.c_double)]
+                ("step", C.c_double), ("cut_cache", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -165,7 +165,7 @@ class Solver:
 
     def __init__(self, n, length=(1.0, 1.0, 1.0), precision="fp64", tol=1e-10, maxit=10000,
                  snap_tau=0.0, inner_tol=1e-5, max_refine=20, poll_every=8, stream=None,
-                 enr_precond="identity", scheme="cg", step=0.0):
+                 enr_precond="identity", scheme="cg", step=0.0, cut_cache=False):
         L = lib()
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
@@ -186,6 +186,7 @@ class Solver:
         o.enr_precond = {"identity": 0, "block3": 1}[enr_precond]
         o.scheme = {"cg": 0, "basic": 1, "bb": 2}[scheme]
         o.step = step
+        o.cut_cache = int(bool(cut_cache))
         self.precision = precision
         self.num_phases = 0
         self._ctx = C.c_void_p()
@@ -313,19 +314,22 @@ class Solver:
         return dl, ds, ce.reshape(6, 6)
 
     @_ordered
-    def apply(self, d, eps=None, precision="fp64"):
+    def apply(self, d, eps=None, precision="fp64", stress=True):
         """q = A d (+ b(eps)) on full DOF vectors (k x stride, scaled enriched part).
-        precision: "fp64", "fp32" or "dw" (double-word kernels on FP64 data)."""
+        precision: "fp64", "fp32" or "dw" (double-word kernels on FP64 data).  stress=False
+        (without eps) skips the stress integrals (sig is None): with "fp32" these are the
+        kernels of the FP32 CG iterations."""
         d = np.ascontiguousarray(np.atleast_2d(d), dtype=np.float64)
         k = d.shape[0]
         q = np.empty_like(d)
-        sig = np.empty((k, 6))
+        sig = np.empty((k, 6)) if (stress or eps is not None) else None
         if eps is not None:
             e, ep = _dvec(np.atleast_2d(eps))
         else:
             ep = None
         check(lib().xfft_apply(self._ctx, k, C.c_void_p(d.ctypes.data), ep, C.c_void_p(q.ctypes.data),
-                               sig.ctypes.data_as(C.POINTER(C.c_double)), _PREC[precision], 0))
+                               sig.ctypes.data_as(C.POINTER(C.c_double)) if sig is not None else None,
+                               _PREC[precision], 0))
         return q, sig
 
     @_ordered

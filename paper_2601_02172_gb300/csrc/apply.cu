@@ -31,6 +31,103 @@ cudaError_t launch_apply_uncut(const typename Store<T>::type* d, typename Store<
   return a.ph.nph > 2 ? launch_uncut_nph<T, 3>(d, q, a, n_rhs, s) : launch_uncut_nph<T, 2>(d, q, a, n_rhs, s);
 }
 
+// ---------------------------------------------------------------- cut tets from cached matrices
+// FP32 cut-tet apply with the cached scaled element matrices (setup.cu, k_cut_matrix) for the
+// applies of the inner CG iterations (no eps_bar, no stress integrals): q_e = K_e d_e on the
+// local DOFs (std 3a + x, scaled enr 12 + 3a + x; the D0^-1/2 scaling is inside K_e).
+// A block takes 32 cut tets at a time (threadIdx.x) for nr right-hand sides (threadIdx.y):
+// the group's 32 packed matrices are staged in shared memory with coalesced loads once and read
+// by every right-hand side (one warp per right-hand side, conflict-free [entry][tet] layout).
+constexpr int kCacheTets = 32;
+
+__global__ void __launch_bounds__(kCacheTets* kCutMaxR)
+    k_apply_cut_cached(const float* __restrict__ d, float* __restrict__ q, const CutData cd,
+                       const float* __restrict__ kc, const ApplyArgs a, int r0, int nr) {
+  __shared__ float sK[kCutPacked * kCacheTets];
+  __shared__ double acc[kCutMaxR];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = tx + kCacheTets * ty, nth = kCacheTets * nr;
+  const int rhs = r0 + ty;
+  const bool act = !a.active || a.active[rhs];
+  if (a.units_cut && tid == 0 && blockIdx.x == 0) {
+    unsigned long long n = 0;
+    for (int rr = 0; rr < nr; ++rr) n += (!a.active || a.active[r0 + rr]) ? 1 : 0;
+    atomicAdd(a.units_cut, n);
+  }
+  const long long N = a.g.N;
+  const int nX = a.nX, ncut = cd.ncut;
+  const float* dr = d + rhs * a.stride;
+  float* qr = q + rhs * a.stride;
+  float en = 0.0f;
+  for (int base = blockIdx.x * kCacheTets; base < ncut; base += gridDim.x * kCacheTets) {
+    __syncthreads();  // the previous group's matrices are no longer read
+    for (int i = tid; i < kCutPacked * kCacheTets; i += nth) {
+      const int k = i / kCacheTets, tt = i - k * kCacheTets;
+      const int e = base + tt;
+      sK[i] = e < ncut ? kc[(long long)k * ncut + e] : 0.0f;
+    }
+    __syncthreads();
+    const int e = base + tx;
+    if (e < ncut && act) {
+      int nd[4], ei[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        nd[k] = cd.ip[k * ncut + e];
+        ei[k] = cd.ip[(4 + k) * ncut + e];
+      }
+      float de[24], qe[24];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          de[3 * k + c] = dr[c * N + nd[k]];
+          de[12 + 3 * k + c] = dr[3 * N + (long long)c * nX + ei[k]];
+        }
+#pragma unroll
+      for (int i = 0; i < 24; ++i) qe[i] = 0.0f;
+      const float* Kt = sK + tx;
+#pragma unroll
+      for (int i = 0; i < 24; ++i) {
+#pragma unroll
+        for (int j = i; j < 24; ++j) {
+          const float kij = Kt[(i * 24 - (i * (i - 1)) / 2 + (j - i)) * kCacheTets];
+          qe[i] += kij * de[j];
+          if (j != i) qe[j] += kij * de[i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 24; ++i) en += de[i] * qe[i];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          atomicAdd(&qr[c * N + nd[k]], qe[3 * k + c]);
+          atomicAdd(&qr[3 * N + (long long)c * nX + ei[k]], qe[12 + 3 * k + c]);
+        }
+    }
+  }
+  // <d, q> per right-hand side: one warp per right-hand side (every acc[ty < nr] is written)
+  const double w = (double)warp_sum(en);
+  if (tx == 0) acc[ty] = w;
+  __syncthreads();
+  for (int i = tid; i < nr * 7; i += nth) {
+    const int rr = i / 7, k = i - rr * 7;
+    if (a.active && !a.active[r0 + rr]) continue;
+    a.partials[((long long)(r0 + rr) * 7 + k) * a.nparts + a.part_offset_cut + blockIdx.x] =
+        k == 0 ? acc[rr] : 0.0;
+  }
+}
+
+static cudaError_t launch_cut_cached(const float* d, float* q, CutData cd, const ApplyArgs& a, int n_rhs,
+                                     cudaStream_t s) {
+  const int nb = apply_cut_blocks(cd.ncut);
+  for (int r0 = 0; r0 < n_rhs; r0 += kCutMaxR) {
+    const int nr = n_rhs - r0 < kCutMaxR ? n_rhs - r0 : kCutMaxR;
+    k_apply_cut_cached<<<nb, dim3(kCacheTets, nr), 0, s>>>(d, q, cd, a.kcache, a, r0, nr);
+  }
+  return cudaGetLastError();
+}
+
 // The enriched part of q only receives atomic contributions from the cut-tet kernel: it is
 // cleared first; the standard part must already hold the uncut kernel's plain stores.
 template <typename T>
@@ -44,6 +141,9 @@ cudaError_t launch_apply_cut(const typename Store<T>::type* d, typename Store<T>
       cudaError_t e = cudaMemsetAsync(q + r * a.stride + 3 * g.N, 0, sizeof(S) * 3 * (size_t)a.nX, s);
       if (e != cudaSuccess) return e;
     }
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (a.kcache && !a.eps && !a.want_sig && cd.ncut > 0) return launch_cut_cached(d, q, cd, a, n_rhs, s);
   }
   return a.ph.nph > 2 ? launch_cut_nph<T, 3>(d, q, isD, cd, a, n_rhs, s)
                       : launch_cut_nph<T, 2>(d, q, isD, cd, a, n_rhs, s);

@@ -65,6 +65,7 @@ struct xfft_ctx {
   double tau = 0.0;
   double* Ls = nullptr;
   double* Lin = nullptr;  // device copy of a host level set
+  float* kcache = nullptr;  // cached FP32 cut-tet element matrices (kCutPacked x ncut)
   uint16_t* code = nullptr;
   int* cutcount = nullptr;
   int* enr_flag = nullptr;
@@ -231,6 +232,7 @@ extern "C" xfft_status xfft_default_options(xfft_options* opt) {
   opt->poll_every = 8;
   opt->scheme = XFFT_SCHEME_CG;
   opt->step = 0.0;
+  opt->cut_cache = 0;
   return XFFT_OK;
 }
 
@@ -254,6 +256,7 @@ extern "C" xfft_status xfft_create(xfft_ctx** out, const xfft_grid* grid, const 
     return fail(XFFT_EINVAL, "unknown enriched preconditioner");
   if (o.scheme != XFFT_SCHEME_CG && o.scheme != XFFT_SCHEME_BASIC && o.scheme != XFFT_SCHEME_BB)
     return fail(XFFT_EINVAL, "unknown iteration scheme");
+  if (o.cut_cache != 0 && o.cut_cache != 1) return fail(XFFT_EINVAL, "cut_cache must be 0 or 1");
   if (!(o.tol > 0.0) || o.maxit < 1 || o.poll_every < 1 || o.max_refine < 1 || !(o.inner_tol > 0.0))
     return fail(XFFT_EINVAL, "invalid options");
   xfft_ctx* c = new xfft_ctx();
@@ -296,6 +299,7 @@ static void free_micro(xfft_ctx* c) {
   drop_graphs(c);
   dfree(c->Ls);
   dfree(c->Lin);
+  dfree(c->kcache);
   dfree(c->code);
   dfree(c->cutcount);
   dfree(c->enr_flag);
@@ -479,6 +483,10 @@ extern "C" xfft_status xfft_set_microstructure_phases(xfft_ctx* c, int n_levelse
     if (hbad) return fail(XFFT_EBREAKDOWN, "an enriched 3x3 block is not positive definite");
   }
   CU(launch_cut_to_float(c->cut_dp, c->cut_fp, (long long)kCutReals * c->ncut, s));
+  if (c->opt.precision == XFFT_FP32_REFINED && c->opt.cut_cache && c->ncut > 0) {
+    CU(dalloc(&c->kcache, (size_t)kCutPacked * c->ncut));
+    CU(launch_cut_matrix(cd, c->isD, c->nX, g, c->ph, c->has_scale ? c->scale : nullptr, c->kcache, s));
+  }
   CU(cudaEventRecord(c->ev1, s));
   CU(cudaStreamSynchronize(s));
   c->have_micro = true;
@@ -540,6 +548,7 @@ static ApplyArgs apply_args(const xfft_ctx* c, const double* eps, const int* act
   a.units_uncut = nullptr;
   a.units_cut = nullptr;
   a.want_sig = 1;
+  a.kcache = c->kcache;
   a.fz = nullptr;
   a.fdnew = nullptr;
   a.fu = nullptr;
@@ -575,7 +584,8 @@ const float* enr_block_of<float>(const xfft_ctx* c) {
 template <typename T, typename A = T>
 static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev, int n_rhs,
                             const int* active, int fin_mode, double tol, int crit, int maxit,
-                            const T* fz = nullptr, T* fdnew = nullptr, T* fu = nullptr, int parity = 0) {
+                            const T* fz = nullptr, T* fdnew = nullptr, T* fu = nullptr, int parity = 0,
+                            int want_sig = -1) {
   static_assert(std::is_same<typename Store<A>::type, T>::value, "arithmetic/storage mismatch");
   ApplyArgs a = apply_args(c, eps_dev, active);
   a.fz = fz;
@@ -583,7 +593,7 @@ static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev
   a.fu = fu;
   a.st = c->st;
   // the relative stopping rule of the inner FP32 solve needs no stress integrals
-  a.want_sig = (fin_mode == 1 && crit == 1) ? 0 : 1;
+  a.want_sig = want_sig >= 0 ? want_sig : (fin_mode == 1 && crit == 1) ? 0 : 1;
   const bool dbl = sizeof(T) == 8;
   const bool dwa = std::is_same<A, dw>::value;
   const int ku = dwa ? XFFT_PROF_APPLY_UNCUT_DW : dbl ? XFFT_PROF_APPLY_UNCUT_F64 : XFFT_PROF_APPLY_UNCUT_F32;
@@ -1201,7 +1211,8 @@ static xfft_status apply_entry(xfft_ctx* c, int n_rhs, const double* d, const do
   xfft_status st = stage_in<T>(c, d, dd, tot, on_dev, scratch);
   if (st == XFFT_OK && eps_bar) st = upload_eps(c, n_rhs, eps_bar);
   if (st == XFFT_OK)
-    st = do_apply<T, A>(c, dd, qq, eps_bar ? c->eps_d : nullptr, n_rhs, nullptr, -1, 0, 0, 0);
+    st = do_apply<T, A>(c, dd, qq, eps_bar ? c->eps_d : nullptr, n_rhs, nullptr, -1, 0, 0, 0, nullptr,
+                        nullptr, nullptr, 0, (sigma_int || eps_bar) ? 1 : 0);
   if (st == XFFT_OK) st = stage_out<T>(c, qq, q, tot, on_dev, scratch);
   if (st == XFFT_OK && sigma_int) {
     const int nparts = nparts_of(c);
@@ -1383,6 +1394,7 @@ extern "C" xfft_status xfft_apply_noalloc(xfft_ctx* c, int n_rhs, const double* 
   a.units_uncut = nullptr;
   a.units_cut = nullptr;
   a.want_sig = 1;
+  a.kcache = c->kcache;
   a.fz = nullptr;
   a.fdnew = nullptr;
   a.fu = nullptr;

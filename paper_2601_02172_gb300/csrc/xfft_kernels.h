@@ -55,6 +55,10 @@ cudaError_t launch_block_inverse(const double* D, const double* Doff, const doub
 cudaError_t launch_finish_scaling(const double* D, double* isd, float* isf, int nX,
                                   cudaStream_t s);
 cudaError_t launch_cut_to_float(const double* dp, float* fp, long long count, cudaStream_t s);
+// cached scaled element matrices of the cut tets (packed upper triangle, FP32; isD: D0^-1/2)
+constexpr int kCutPacked = 24 * 25 / 2;
+cudaError_t launch_cut_matrix(CutData cd, const double* isD, int nX, GridDev g, PhaseDev ph,
+                              const float* scale, float* kc, cudaStream_t s);
 
 // ---- stiffness apply (apply.cu)
 struct ApplyArgs {
@@ -80,6 +84,9 @@ struct ApplyArgs {
   void* fdnew;
   void* fu;
   const RhsState* st;
+  // FP32 cached cut-tet matrices (kCutPacked x ncut) or nullptr; used by the FP32 cut apply of
+  // linear applies without stress integrals (the inner CG iterations)
+  const float* kcache = nullptr;
 };
 // T is the arithmetic type (float, double or dw = double-word on FP64 data); the vectors are
 // stored as Store<T>::type

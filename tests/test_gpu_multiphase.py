@@ -93,6 +93,20 @@ def test_apply_matches_oracle(xf, name, prec):
 
 
 @pytest.mark.parametrize("name", ["coated16", "coated_aniso"])
+def test_cached_cut_apply_matches_oracle(xf, name):
+    """The FP32 CG iterations' apply with the cached element matrices of three-phase cut tets."""
+    n, ell, Ls, ph, sc = _case(name)
+    o = XFEM(Ls, n, ell, phases=ph, scale=sc)
+    o.assemble()
+    d = np.random.default_rng(23).normal(size=(2, o.ndof))
+    s = xf.Solver(n, ell, precision="fp32", cut_cache=True)
+    s.set_microstructure_phases(Ls, ph, sc)
+    q, _ = s.apply(d, precision="fp32", stress=False)
+    for r in range(2):
+        assert _rel(q[r], o.A @ d[r]) < 2e-5
+
+
+@pytest.mark.parametrize("name", ["coated16", "coated_aniso"])
 def test_solve_matches_oracle(xf, name):
     n, ell, Ls, ph, sc = _case(name)
     o = XFEM(Ls, n, ell, phases=ph, scale=sc)

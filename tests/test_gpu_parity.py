@@ -101,6 +101,40 @@ def test_apply_matches_oracle(xf, name, prec):
 
 
 @pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell"])
+def test_cached_cut_apply_matches_oracle(xf, name):
+    """The apply of the FP32 CG iterations (no stress integrals): the cut tets from the cached
+    scaled element matrices (option cut_cache) and from the per-side moments (the default), both
+    against the oracle's assembled operator."""
+    n, ell, L, lm, lp, sc = _case(name)
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o.assemble()
+    d = np.random.default_rng(21).normal(size=(3, o.ndof))
+    for cache in (True, False):
+        s = xf.Solver(n, ell, precision="fp32", cut_cache=cache)
+        s.set_microstructure(L, lm, lp, sc)
+        q, sig = s.apply(d, precision="fp32", stress=False)
+        assert sig is None
+        for r in range(3):
+            assert _rel(q[r], o.A @ d[r]) < 2e-5, (cache, r)
+
+
+def test_fp32_solve_with_cut_cache(xf):
+    """FP32-refined C_eff with the cached cut-tet matrices in the CG iterations (graph-replayed)
+    equals the default solve and the oracle's."""
+    n, ell, L, lm, lp, sc = _case("ragged")
+    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    Cs, _, _ = o.effective_stiffness()
+    out = {}
+    for cache in (True, False):
+        s = xf.Solver(n, ell, precision="fp32", tol=1e-8, cut_cache=cache)
+        s.set_microstructure(L, lm, lp, sc)
+        out[cache], st = s.effective_stiffness()
+        assert st["converged"]
+        assert np.abs(out[cache] - Cs).max() < 1e-6 * np.abs(Cs).max()
+    assert np.abs(out[True] - out[False]).max() < 1e-6 * np.abs(Cs).max()
+
+
+@pytest.mark.parametrize("name", ["sphere16", "ragged", "aniso_cell"])
 def test_dw_residual_at_the_solution(xf, name):
     """At the exact solution the residual A u + b cancels to rounding: the double-word kernels
     must resolve it to far below the FP32 level (what the refinement's stopping rule needs)."""
