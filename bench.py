@@ -460,11 +460,13 @@ def main():
             extra["enr_contrast_sweep"] = sweep
             # Hashin's neutral inclusion (three phases, two interfaces) at N = 128, tol 1e-7,
             # eps_bar = I: K_eff against K_matrix = 1 and the iteration counts of the three schemes
-            # (the paper prints 48 for linear CG, 115 for Barzilai-Borwein and 668 for the basic scheme)
+            # (the paper prints 48 for linear CG, 60 for nonlinear CG, 115 for Barzilai-Borwein and
+            # 668 for the basic scheme)
             Lh, phh, ellh = synth.hashin_neutral_inclusion(128)
             eh = np.array([[1.0, 1.0, 1.0, 0.0, 0.0, 0.0]])
             hashin = {"N": 128, "tol": 1e-7}
-            for prec, scheme in (("fp64", "cg"), ("fp64", "bb"), ("fp64", "basic"), ("fp32", "cg")):
+            for prec, scheme in (("fp64", "cg"), ("fp64", "nlcg"), ("fp64", "bb"), ("fp64", "basic"),
+                                 ("fp32", "cg")):
                 sv = Solver((128, 128, 128), ellh, precision=prec, tol=1e-7, scheme=scheme, maxit=5000)
                 sv.set_microstructure_phases(Lh, phh)
                 sv.solve(eh, u=False)

@@ -82,8 +82,10 @@ typedef struct {
  * preconditioned Richardson iteration u += s0 P^-1 f with s0 = 2 / (C_- + C_+) (eq. stepsize;
  * C_-, C_+ the smallest and largest eigenvalues 2 mu, 3 lambda + 2 mu of the phases' stiffness,
  * times the extreme voxel scales); XFFT_SCHEME_BB Barzilai-Borwein in the P metric, whose step
- * is the previous iteration's exact line-search step f^T P^-1 f / <d, A d> (s0 first). */
-enum { XFFT_SCHEME_CG = 0, XFFT_SCHEME_BASIC = 1, XFFT_SCHEME_BB = 2 };
+ * is the previous iteration's exact line-search step f^T P^-1 f / <d, A d> (s0 first);
+ * XFFT_SCHEME_NLCG the nonlinear CG the paper compares (Sec. 2.3): the fixed step s0 without a
+ * line search and the Fletcher-Reeves momentum beta = f_k^T P^-1 f_k / f_{k-1}^T P^-1 f_{k-1}. */
+enum { XFFT_SCHEME_CG = 0, XFFT_SCHEME_BASIC = 1, XFFT_SCHEME_BB = 2, XFFT_SCHEME_NLCG = 3 };
 
 typedef struct {
   int precision;       /* XFFT_FP64 (all FP64) or XFFT_FP32_REFINED (FP32 CG; residuals of the
@@ -97,7 +99,7 @@ typedef struct {
                           inner solve (each inner solve aims at half the outer tolerance) */
   int max_refine;      /* FP32_REFINED: cap on FP64 refinement steps */
   int poll_every;      /* iterations between host checks of the device convergence flags */
-  int scheme;          /* XFFT_SCHEME_CG (Algorithm 1, default), _BASIC or _BB */
+  int scheme;          /* XFFT_SCHEME_CG (Algorithm 1, default), _BASIC, _BB or _NLCG */
   double step;         /* step of the basic / BB schemes; <= 0: s0 = 2 / (C_- + C_+) */
   int cut_cache;       /* FP32_REFINED: 1 caches each cut tet's scaled 24 x 24 element matrix
                           (FP32, packed upper triangle, 1200 bytes per cut tet) at

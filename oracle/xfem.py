@@ -646,12 +646,17 @@ class XFEM:
         loop stops once sqrt(f^T P^{-1} f / |Y|) <= tol ||<sigma(u)>_Y|| (eqs.
         stoppingCriterion, convergence; the 1/|Y| makes both sides stresses) or after maxit
         iterations.  Returns (u, info) with iteration count and residual history.
+
+        The other schemes of Sec. 2.3 on the same system and preconditioner: "basic" (fixed
+        step s0 of eq. stepsize, beta = 0), "bb" (Barzilai-Borwein: the previous exact
+        line-search step, s0 first, beta = 0) and "nlcg" (nonlinear CG: fixed step s0, no line
+        search, Fletcher-Reeves beta = res^2 / res_old^2).
         """
         if not hasattr(self, "A"):
             self.assemble()
         gfun = self._green_sparse() if green == "sparse" else self._green_fft()
         n3 = 3 * self.nFE
-        if scheme not in ("cg", "basic", "bb"):
+        if scheme not in ("cg", "basic", "bb", "nlcg"):
             raise ValueError(scheme)
         s0 = self.basic_step() if step is None else float(step)
         prev_cauchy = s0
@@ -683,7 +688,7 @@ class XFEM:
             cauchy = rr / float(z @ d)  # exact line search step along d
             if scheme == "cg":
                 alpha = cauchy
-            elif scheme == "basic":  # Richardson / gradient descent with the fixed step s0
+            elif scheme in ("basic", "nlcg"):  # fixed step s0 (no line search)
                 alpha = s0
             else:  # Barzilai-Borwein (BB1 in the P metric): the previous Cauchy step, s0 first
                 alpha = s0 if k == 0 else prev_cauchy
@@ -692,7 +697,8 @@ class XFEM:
             f -= alpha * z
             zz = P(f)
             rr_new = float(f @ zz)
-            beta = rr_new / rr if scheme == "cg" else 0.0
+            # Fletcher-Reeves momentum for linear and nonlinear CG; none for basic / BB
+            beta = rr_new / rr if scheme in ("cg", "nlcg") else 0.0
             d = zz + beta * d
             rr = rr_new
             k += 1

@@ -184,7 +184,7 @@ class Solver:
         o.max_refine = max_refine
         o.poll_every = poll_every
         o.enr_precond = {"identity": 0, "block3": 1}[enr_precond]
-        o.scheme = {"cg": 0, "basic": 1, "bb": 2}[scheme]
+        o.scheme = {"cg": 0, "basic": 1, "bb": 2, "nlcg": 3}[scheme]
         o.step = step
         o.cut_cache = int(bool(cut_cache))
         self.precision = precision

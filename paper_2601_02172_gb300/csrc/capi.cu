@@ -254,7 +254,8 @@ extern "C" xfft_status xfft_create(xfft_ctx** out, const xfft_grid* grid, const 
     return fail(XFFT_EINVAL, "unknown precision");
   if (o.enr_precond != XFFT_ENR_IDENTITY && o.enr_precond != XFFT_ENR_BLOCK3)
     return fail(XFFT_EINVAL, "unknown enriched preconditioner");
-  if (o.scheme != XFFT_SCHEME_CG && o.scheme != XFFT_SCHEME_BASIC && o.scheme != XFFT_SCHEME_BB)
+  if (o.scheme != XFFT_SCHEME_CG && o.scheme != XFFT_SCHEME_BASIC && o.scheme != XFFT_SCHEME_BB &&
+      o.scheme != XFFT_SCHEME_NLCG)
     return fail(XFFT_EINVAL, "unknown iteration scheme");
   if (o.cut_cache != 0 && o.cut_cache != 1) return fail(XFFT_EINVAL, "cut_cache must be 0 or 1");
   if (!(o.tol > 0.0) || o.maxit < 1 || o.poll_every < 1 || o.max_refine < 1 || !(o.inner_tol > 0.0))

@@ -214,7 +214,9 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
       s.alpha = 0.0;
       s.dpar = fa.parity;
     } else {
-      const double step = fa.scheme == 1 ? fa.step0 : fa.scheme == 2 ? (s.iters == 0 ? fa.step0 : s.cauchy) : a;
+      // 0 CG: exact line search; 1 basic and 3 nonlinear CG: fixed step s0; 2 BB: previous Cauchy
+      const double step = (fa.scheme == 1 || fa.scheme == 3) ? fa.step0
+                          : fa.scheme == 2 ? (s.iters == 0 ? fa.step0 : s.cauchy) : a;
       s.cauchy = a;
       s.alpha = step;
       for (int k = 0; k < 6; ++k) s.sig[k] += step * s.sd[k];
@@ -243,7 +245,8 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
         s.rel = rel;
       }
     } else {
-      s.beta = (fa.scheme == 0 && s.rr > 0.0) ? rr / s.rr : 0.0;  // 0: steepest descent
+      // Fletcher-Reeves momentum for linear and nonlinear CG; basic and BB: steepest descent
+      s.beta = ((fa.scheme == 0 || fa.scheme == 3) && s.rr > 0.0) ? rr / s.rr : 0.0;
       s.rr = rr;
       s.iters += 1;
       s.dpar = fa.parity;

@@ -165,7 +165,7 @@ struct FinArgs {
   int parity;      // buffer index of the direction used in this iteration (recorded on exit)
   // iteration scheme on the same operator: 0 linear CG (Algorithm 1), 1 basic scheme (fixed
   // step step0, steepest-descent directions), 2 Barzilai-Borwein (step = the previous Cauchy
-  // step rr / <d, A d>, step0 first)
+  // step rr / <d, A d>, step0 first), 3 nonlinear CG (fixed step step0, Fletcher-Reeves momentum)
   int scheme;
   double step0;
 };

@@ -237,5 +237,7 @@ def test_hashin_neutral_inclusion(xf):
     assert 40 <= it <= 56, it
     _, it_basic, okb, _ = _hashin_run(xf, 128, scheme="basic")
     assert okb and 600 <= it_basic <= 740, it_basic
+    _, it_nl, oknl, _ = _hashin_run(xf, 128, scheme="nlcg")
+    assert oknl and it < it_nl <= 2 * it, it_nl  # the paper: 60
     K128f, _, okf, _ = _hashin_run(xf, 128, precision="fp32")
     assert okf and abs(K128f - K128) < 1e-6

@@ -207,11 +207,11 @@ def test_block_enriched_preconditioner(xf, name, prec):
         assert _rel(out["u_std"][0], u[: 3 * o.nFE].reshape(3, -1)) < 1e-9
 
 
-@pytest.mark.parametrize("scheme", ["basic", "bb"])
+@pytest.mark.parametrize("scheme", ["basic", "bb", "nlcg"])
 def test_basic_and_bb_schemes(xf, scheme):
-    """The basic (Richardson, step s0 of eq. stepsize) and Barzilai-Borwein schemes on the same
-    system: FP64 iteration counts as the oracle's (up to rounding) and the direct solution; the
-    FP32-refined form reaches the same mean stress to 1e-6."""
+    """The basic (Richardson, step s0 of eq. stepsize), Barzilai-Borwein and nonlinear CG schemes
+    on the same system: FP64 iteration counts as the oracle's (up to rounding) and the direct
+    solution; the FP32-refined form reaches the same mean stress to 1e-6."""
     n, ell, L, lm, lp, sc = _case("sphere16")
     o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
     eps = np.array([[0.2, -0.1, 0.3, 0.4, -0.2, 0.1]])

@@ -380,10 +380,11 @@ def test_enriched_block_preconditioner():
 
 
 def test_basic_and_barzilai_borwein_schemes():
-    """The basic scheme (Richardson with s0 = 2/(C_- + C_+), eq. stepsize) and Barzilai-Borwein
-    on the same X-FFT system reach the direct solution; the basic scheme's iteration count grows
-    about linearly with the contrast and much faster than linear CG's (Sec. 2.3's remarks on
-    O(kappa) and O(sqrt kappa)); BB needs far fewer iterations than the basic scheme."""
+    """The basic scheme (Richardson with s0 = 2/(C_- + C_+), eq. stepsize), Barzilai-Borwein and
+    nonlinear CG on the same X-FFT system reach the direct solution; the basic scheme's iteration
+    count grows about linearly with the contrast and much faster than linear CG's (Sec. 2.3's
+    remarks on O(kappa) and O(sqrt kappa)); BB needs far fewer iterations than the basic scheme;
+    nonlinear CG needs more than linear CG but at most twice as many (Sec. 2.3)."""
     n = (8, 8, 8)
     L = synth.sphere_levelset(n, (0.45, 0.5, 0.55), 0.3)
     e = np.eye(6)[0]
@@ -393,7 +394,7 @@ def test_basic_and_barzilai_borwein_schemes():
         ud = o.solve_direct(e)
         lam, mu = o.phases[0]
         assert math.isclose(o.basic_step(), 2.0 / (2 * o.phases[1][1] + 3 * lam + 2 * mu), rel_tol=1e-15)
-        for scheme in ("cg", "basic", "bb"):
+        for scheme in ("cg", "basic", "bb", "nlcg"):
             u, info = o.pcg(e, tol=1e-10, maxit=5000, scheme=scheme)
             assert info["converged"], (contrast, scheme)
             assert np.linalg.norm(u - ud) < 1e-8 * np.linalg.norm(ud)
@@ -403,6 +404,7 @@ def test_basic_and_barzilai_borwein_schemes():
     for c in (10.0, 50.0):
         assert its["bb", c] < 0.5 * its["basic", c]
         assert its["cg", c] <= its["bb", c]
+        assert its["cg", c] < its["nlcg", c] <= 2 * its["cg", c]
 
 
 def test_extreme_contrasts_with_both_enriched_preconditioners():
