@@ -35,7 +35,7 @@ WORKLOAD = ("ellipsoids40: 128^3 periodic grid, 40 random ellipsoids (aspect 1-3
             "orientation, vf 25%), contrast E_incl/E_matrix = 50 (nu 0.2/0.3), per-voxel modulus "
             "scale U[0.8,1.2]; six unit Mandel load cases; loss ||C_eff - C_target||_F^2")
 
-# algorithmic bytes per processed right-hand side and launch ("Roofline")
+# algorithmic bytes per launch and per processed right-hand side of the timed kernel groups
 def algorithmic_bytes(kind, N, nX, ncut, has_scale, cut_cache=False):
     """Algorithmic bytes of one kernel group as (per launch, per right-hand side)."""
     geo = N * (2 + (4 if has_scale else 0))

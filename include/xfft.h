@@ -55,7 +55,7 @@ typedef enum {
   XFFT_ENOTCONV = 4,     /* maxit reached before the stopping rule held */
   XFFT_EBREAKDOWN = 5,   /* CG breakdown: <A d, d> <= 0 or a NaN/Inf scalar */
   XFFT_ETIMEOUT = 6,     /* reserved: a bounded device wait gave up */
-  XFFT_EUNSUPPORTED = 7, /* valid request that this build does not implement */
+  XFFT_EUNSUPPORTED = 7, /* valid request that the library does not implement */
   XFFT_ESTATE = 8        /* call order violated (e.g. solve before set_microstructure) */
 } xfft_status;
 

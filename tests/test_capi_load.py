@@ -30,6 +30,7 @@ def test_library_builds_loads_and_exports_header_symbols():
     # host-only entry points work without a GPU
     o = capi.Options()
     assert L.xfft_default_options(o) == 0 and o.tol == 1e-10 and o.poll_every == 8
+    assert o.scheme == 0 and o.cut_cache == 0 and o.enr_precond == 0 and o.inner_tol == 1e-5
     assert L.xfft_status_string(4).decode() == "not converged"
 
 
