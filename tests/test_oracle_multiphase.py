@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import XFEM
+from oracle import XFEM, iso_stiffness
 from test_oracle_pins import _laminate_closed_form
 
 
@@ -145,3 +145,25 @@ def test_three_phase_gradient_matches_finite_differences():
         _, (_, Cm, _) = ceff([tuple(tm[2 * q:2 * q + 2]) for q in range(3)], s)
         fd = (Cp - Cm) / (2 * hp)
         assert np.abs(fd - dl[p]).max() < 1e-6 * np.abs(dl[p]).max(), p
+
+
+def test_three_phase_voxel_stress_averages_to_mean_stress():
+    """The per-voxel average stresses of a three-phase solution average (voxel volumes over the
+    cell volume) to the mean stress, and in a voxel of one uncut phase the stress is that
+    phase's C (eps_bar + grad^s u) on each tet."""
+    n = (10, 10, 10)
+    Ls = synth.coated_sphere_levelsets(n, (0.45, 0.5, 0.55), 0.18, 0.4)
+    ph = [synth.lame_from_E_nu(8.0, 0.2), synth.lame_from_E_nu(0.5, 0.35), synth.lame_from_E_nu(1.0, 0.3)]
+    o = XFEM(Ls, n, phases=ph)
+    e = np.array([0.3, -0.1, 0.2, 0.4, 0.0, -0.2])
+    u = o.solve_direct(e)
+    vs = o.voxel_stress(u, e)
+    assert np.allclose(vs.mean(axis=0), o.mean_stress(u, e), atol=1e-12 * np.abs(vs).max())
+    # every phase occurs in uncut voxels; there the average stress is C_p applied to the
+    # average strain of the voxel's six tets
+    full = ~o.cut.any(axis=1)
+    for p in range(3):
+        vox = np.flatnonzero(full & (o.tet_phase == p).all(axis=1))
+        assert vox.size > 0, p
+        strain = e + sum(o._strains_uncut(u[None], t, vox)[0] for t in range(6)) / 6.0
+        assert np.allclose(vs[vox], strain @ iso_stiffness(*ph[p]).T, atol=1e-12 * np.abs(vs).max())
