@@ -7,7 +7,6 @@ basis that the method allows (the enrichment scaling D0 per node instead of per 
 XFFT_diagonal leaves this open) is the negative control: the pin still holds.
 """
 import numpy as np
-import pytest
 
 import synth
 from oracle import XFEM, symgrad_operator
