@@ -118,6 +118,34 @@ def test_cached_cut_apply_matches_oracle(xf, name):
             assert _rel(q[r], o.A @ d[r]) < 2e-5, (cache, r)
 
 
+@pytest.mark.parametrize("normal", [(1, 0, 1), (1, 0, 0)])
+def test_interfaces_through_nodes(xf, normal):
+    """Degenerate cut geometry (snapped zero vertices on every cut tet, or no cut tet at all):
+    setup bit-exact, apply as the oracle's, C_eff = the laminate closed form."""
+    from test_oracle_pins import _laminate_closed_form
+    n = (8, 8, 8)
+    L = synth.laminate_levelset(n, normal=normal, offset=0.25, fraction=0.5)
+    lm = synth.lame_from_E_nu(10.0, 0.2)
+    lp = synth.lame_from_E_nu(1.0, 0.3)
+    o = XFEM(L, n, lame_minus=lm, lame_plus=lp)
+    o.assemble()
+    s = xf.Solver(n, tol=1e-12)
+    s.set_microstructure(L, lm, lp)
+    en, D0, code = s.setup_info()
+    assert s.num_enriched == o.nX and s.num_cut_tets == len(o.cut_list)
+    assert np.array_equal(en, o.enr_nodes)
+    if o.nX:
+        assert _rel(D0, o.D) < 1e-12
+    d = np.random.default_rng(2).normal(size=(2, o.ndof))
+    q, _ = s.apply(d, precision="fp64")
+    for r in range(2):
+        assert _rel(q[r], o.A @ d[r]) < 1e-12
+    C, st = s.effective_stiffness()
+    assert st["converged"]
+    Cref = _laminate_closed_form(normal, 0.5, lm, lp)
+    assert np.abs(C - Cref).max() < 1e-9 * np.abs(Cref).max()
+
+
 def test_fp32_solve_with_cut_cache(xf):
     """FP32-refined C_eff with the cached cut-tet matrices in the CG iterations (graph-replayed)
     equals the default solve and the oracle's."""

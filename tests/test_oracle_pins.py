@@ -511,3 +511,30 @@ def test_gradient_matches_finite_differences_and_euler(grad_case):
     fd = (Cp - Cm) / (2 * hs)
     an = np.einsum("v,vkl->kl", dirn, ds)
     assert np.abs(fd - an).max() < 1e-6 * np.abs(an).max()
+
+
+@pytest.mark.parametrize("normal", [(1, 0, 1), (1, 0, 0)])
+def test_interfaces_through_nodes(normal):
+    """Degenerate cut geometry: laminate planes through node lines (normal (1,0,1)) or node
+    planes (normal (1,0,0)) at offset 1/4 on an 8^3 grid.  The snapped zero vertices put every
+    cut tet's interface through a vertex (the clip's degenerate cases), and a tet that touches
+    the interface only at zero vertices is not cut (with node planes no tet is cut and nothing is
+    enriched); the closed form still holds to rounding."""
+    n = (8, 8, 8)
+    L = synth.laminate_levelset(n, normal=normal, offset=0.25, fraction=0.5)
+    lm = synth.lame_from_E_nu(10.0, 0.2)
+    lp = synth.lame_from_E_nu(1.0, 0.3)
+    o = XFEM(L, n, lame_minus=lm, lame_plus=lp)
+    assert (o.L == 0.0).sum() == 128
+    if normal == (1, 0, 0):
+        assert len(o.cut_list) == 0 and o.nX == 0
+    else:
+        Lt = o.L[o.tet_nodes[o.cut]]
+        assert len(o.cut_list) > 0 and np.all((Lt == 0.0).any(axis=1))
+    o.assemble()
+    C = np.zeros((6, 6))
+    for k in range(6):
+        e = np.eye(6)[k]
+        C[:, k] = o.mean_stress(o.solve_direct(e), e)
+    Cref = _laminate_closed_form(normal, 0.5, lm, lp)
+    assert np.abs(C - Cref).max() < 1e-12 * np.abs(Cref).max()
