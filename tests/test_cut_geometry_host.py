@@ -1,0 +1,112 @@
+"""The CUDA path's per-tet setup geometry, compiled for the host (no GPU), against the oracle.
+
+`csrc/cut_geometry.cuh` holds the classification of a tet against K level sets and the exact
+side moments int N_b, int N_b N_c of a cut tet (case table of the linearised interface, Sec. 3,
+Fig. subdivision).  Here it is built into a host library and compared with the oracle's generic
+convex clip and 4-point quadrature, on random tets including snapped zero vertices, and with
+the oracle's phase rule for several interfaces.
+"""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import clip_tet, quad4
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+NVCC = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+
+pytestmark = pytest.mark.skipif(not os.path.exists(NVCC), reason="nvcc not available")
+
+
+@pytest.fixture(scope="module")
+def geo(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("hostgeo") / "libcutgeo.so")
+    src = os.path.join(ROOT, "tests", "host", "cut_geometry_host.cu")
+    inc = ["-I" + os.path.join(ROOT, "paper_2601_02172_gb300", "csrc"), "-I" + os.path.join(ROOT, "include")]
+    subprocess.run([NVCC, "-std=c++17", "-O2", "--expt-relaxed-constexpr", "-shared", "-Xcompiler", "-fPIC"]
+                   + inc + ["-o", out, src], check=True, capture_output=True)
+    lib = C.CDLL(out)
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int)
+    lib.host_side_moments.argtypes = [dp, C.c_int, C.c_double, dp, dp]
+    lib.host_classify_tet.argtypes = [dp, C.c_int, ip, ip, ip]
+    lib.host_classify_tet.restype = C.c_uint
+    return lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _oracle_moments(L, s):
+    """int_side N_b and int_side N_b N_c on the reference tet (volume 1/6) from the oracle's
+    clip and quadrature."""
+    X = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    qb, qw = quad4()
+    m = np.zeros(4)
+    M = np.zeros((4, 4))
+    for P in clip_tet(X, L, s):
+        vol = abs(np.linalg.det(np.stack([P[1] - P[0], P[2] - P[0], P[3] - P[0]]))) / 6.0
+        pts = qb @ P
+        bary = np.column_stack([1.0 - pts.sum(axis=1), pts])
+        w = qw * vol
+        m += w @ bary
+        M += np.einsum("q,qb,qc->bc", w, bary, bary)
+    return m, M
+
+
+PACK = [(0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]
+
+
+def test_side_moments_match_the_oracle_clip(geo):
+    rng = np.random.default_rng(7)
+    cases = [rng.normal(size=4) for _ in range(300)]
+    # snapped zero vertices: one or two zeros with both signs among the others
+    for _ in range(100):
+        L = rng.normal(size=4)
+        L[rng.choice(4, size=rng.integers(1, 3), replace=False)] = 0.0
+        cases.append(L)
+    n = 0
+    for L in cases:
+        if not (L.min() < 0.0 < L.max()):
+            continue
+        n += 1
+        for s in (+1, -1):
+            m = np.zeros(4)
+            Mp = np.zeros(10)
+            geo.host_side_moments(_ptr(np.ascontiguousarray(L)), s, 1.0 / 6.0, _ptr(m), _ptr(Mp))
+            mo, Mo = _oracle_moments(L, s)
+            assert np.allclose(m, mo, atol=1e-14), (L, s)
+            assert np.allclose(Mp, [Mo[b, c] for b, c in PACK], atol=1e-14), (L, s)
+    assert n > 250
+
+
+def test_classification_matches_the_oracle_phase_rule(geo):
+    """Random vertex values of K = 1 or 2 level sets (with zeros): the tet code, the side phases
+    of cut tets and the two-interface refusal agree with the oracle's rule."""
+    rng = np.random.default_rng(11)
+    seen = set()
+    for _ in range(2000):
+        K = int(rng.integers(1, 3))
+        Lv = np.round(rng.normal(size=(K, 4)), 1)  # many exact zeros
+        pm, pp, two = C.c_int(), C.c_int(), C.c_int()
+        code = geo.host_classify_tet(_ptr(np.ascontiguousarray(Lv)), K, C.byref(pm), C.byref(pp), C.byref(two))
+        neg = Lv.min(axis=1) < 0.0
+        pos = Lv.max(axis=1) > 0.0
+        first = int(np.argmax(neg)) if neg.any() else K
+        cut = first < K and pos[first]
+        if cut:
+            later = [l for l in range(first + 1, K) if neg[l]]
+            exp_two = any(pos[l] for l in later)
+            assert code == 2 and pm.value == first and bool(two.value) == exp_two
+            if not exp_two:
+                assert pp.value == (later[0] if later else K)
+            seen.add(("cut", first, exp_two))
+        else:
+            assert code == (3 if first == 2 else first) and not two.value
+            seen.add(("uncut", first))
+    assert ("cut", 0, True) in seen and ("cut", 1, False) in seen and ("uncut", 2) in seen
