@@ -51,27 +51,27 @@ struct PlanE<128, 16> {
 #define XFFT_FAST_SIZES(X) X(16) X(32) X(48) X(64) X(80) X(96) X(128) X(192) X(256) X(384)
 
 template <typename C>
-__device__ __forceinline__ C cmul(C a, C b) {
+__host__ __device__ __forceinline__ C cmul(C a, C b) {
   C r;
   r.x = a.x * b.x - a.y * b.y;
   r.y = a.x * b.y + a.y * b.x;
   return r;
 }
 template <typename C>
-__device__ __forceinline__ C cmulc(C a, C b) {  // a * conj(b)
+__host__ __device__ __forceinline__ C cmulc(C a, C b) {  // a * conj(b)
   C r;
   r.x = a.x * b.x + a.y * b.y;
   r.y = a.y * b.x - a.x * b.y;
   return r;
 }
 template <typename C>
-__device__ __forceinline__ C cadd(C a, C b) {
+__host__ __device__ __forceinline__ C cadd(C a, C b) {
   a.x += b.x;
   a.y += b.y;
   return a;
 }
 template <typename C>
-__device__ __forceinline__ C csub(C a, C b) {
+__host__ __device__ __forceinline__ C csub(C a, C b) {
   a.x -= b.x;
   a.y -= b.y;
   return a;
@@ -303,7 +303,8 @@ __device__ __forceinline__ void line_fft(C* line, const C* __restrict__ tw, int 
 
 // ---------------------------------------------------------------- Green operator
 // Cholesky factor of M(xi) = (|T|/2) sum_tets (|G|^2 I + G G^H) (see fft.cu); returns false
-// at xi = 0 or on a non-positive pivot (the Green operator then maps to 0).
+// at xi = 0 or on a non-positive pivot (the Green operator then maps to 0).  Host and device
+// (the host build is checked against the oracle's symbol on the CPU).
 template <typename C, typename T>
 struct GreenFactor {
   T il00, il11, il22;
@@ -311,8 +312,8 @@ struct GreenFactor {
 };
 
 template <typename C, typename T>
-__device__ __forceinline__ bool green_factor(GreenFactor<C, T>& gf, C e0, C e1, C e2, C s0, C s1, C s2,
-                                             T ih0, T ih1, T ih2, T halfvol) {
+__host__ __device__ __forceinline__ bool green_factor(GreenFactor<C, T>& gf, C e0, C e1, C e2, C s0, C s1,
+                                                      C s2, T ih0, T ih1, T ih2, T halfvol) {
   C g[3];
   g[0].x = s0.x * ih0;
   g[0].y = s0.y * ih0;
@@ -370,7 +371,7 @@ __device__ __forceinline__ bool green_factor(GreenFactor<C, T>& gf, C e0, C e1, 
 }
 
 template <typename C, typename T>
-__device__ __forceinline__ void green_solve(const GreenFactor<C, T>& gf, C& F0, C& F1, C& F2) {
+__host__ __device__ __forceinline__ void green_solve(const GreenFactor<C, T>& gf, C& F0, C& F1, C& F2) {
   C y0, y1, y2, t;
   y0.x = F0.x * gf.il00;
   y0.y = F0.y * gf.il00;
