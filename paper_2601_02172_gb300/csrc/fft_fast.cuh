@@ -78,7 +78,7 @@ __host__ __device__ __forceinline__ C csub(C a, C b) {
 }
 // multiply by -i (forward) or +i (inverse)
 template <typename C, bool INV>
-__device__ __forceinline__ C mul_mi(C a) {
+__host__ __device__ __forceinline__ C mul_mi(C a) {
   C r;
   if (INV) {
     r.x = -a.y;
@@ -96,7 +96,7 @@ struct Dft;
 
 template <typename C, bool INV>
 struct Dft<C, 2, INV> {
-  __device__ __forceinline__ static void run(C* v) {
+  __host__ __device__ __forceinline__ static void run(C* v) {
     const C a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
@@ -105,7 +105,7 @@ struct Dft<C, 2, INV> {
 
 template <typename C, bool INV>
 struct Dft<C, 4, INV> {
-  __device__ __forceinline__ static void run(C* v) {
+  __host__ __device__ __forceinline__ static void run(C* v) {
     const C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
     const C t2 = cadd(v[1], v[3]), t3 = mul_mi<C, INV>(csub(v[1], v[3]));
     v[0] = cadd(t0, t2);
@@ -118,7 +118,7 @@ struct Dft<C, 4, INV> {
 // y_k = sum_r v_r exp(-+2 pi i r k / 3):  with s = sin(2 pi / 3)
 template <typename C, bool INV>
 struct Dft<C, 3, INV> {
-  __device__ __forceinline__ static void run(C* v) {
+  __host__ __device__ __forceinline__ static void run(C* v) {
     typedef decltype(v[0].x) T;
     const T s = (T)0.86602540378443864676;  // sqrt(3) / 2
     const C t1 = cadd(v[1], v[2]);
@@ -138,7 +138,7 @@ struct Dft<C, 3, INV> {
 // radix 5 with c1 = cos(2 pi/5), c2 = cos(4 pi/5), s1 = sin(2 pi/5), s2 = sin(4 pi/5)
 template <typename C, bool INV>
 struct Dft<C, 5, INV> {
-  __device__ __forceinline__ static void run(C* v) {
+  __host__ __device__ __forceinline__ static void run(C* v) {
     typedef decltype(v[0].x) T;
     const T c1 = (T)0.30901699437494742410;   // (sqrt5 - 1) / 4
     const T c2 = (T)-0.80901699437494742410;  // -(sqrt5 + 1) / 4
@@ -167,7 +167,7 @@ struct Dft<C, 5, INV> {
 // radix 8 = two radix-4 DFTs on even / odd inputs combined with W8^k
 template <typename C, bool INV>
 struct Dft<C, 8, INV> {
-  __device__ __forceinline__ static void run(C* v) {
+  __host__ __device__ __forceinline__ static void run(C* v) {
     typedef decltype(v[0].x) T;
     const T r = (T)0.70710678118654752440;
     C e[4] = {v[0], v[2], v[4], v[6]};
@@ -203,7 +203,7 @@ struct Dft<C, 8, INV> {
 // DFT4 over b.  c1 = cos(pi/8), s1 = sin(pi/8)
 template <typename C, bool INV>
 struct Dft<C, 16, INV> {
-  __device__ __forceinline__ static void run(C* v) {
+  __host__ __device__ __forceinline__ static void run(C* v) {
     typedef decltype(v[0].x) T;
     const T c1 = (T)0.92387953251128675613;
     const T s1 = (T)0.38268343236508977173;
@@ -249,7 +249,7 @@ struct Dft<C, 16, INV> {
 
 template <typename C, bool INV>
 struct Dft<C, 1, INV> {
-  __device__ __forceinline__ static void run(C*) {}
+  __host__ __device__ __forceinline__ static void run(C*) {}
 };
 
 // One in-place Stockham stage of radix R on a line (stride-1 elements at `line`), thread t of

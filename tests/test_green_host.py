@@ -5,6 +5,7 @@ from the per-axis phase factors e_a = exp(i theta_a), s_a = e_a - 1 (theta_a = 2
 the tables the library builds) and solves M x = F by two triangular solves.  Here it is built
 into a host library and compared with a dense solve of the oracle's symbol, which the oracle
 forms from the assembled voxel reference matrix, at every frequency of an anisotropic grid.
+The radix butterflies of the same file's Stockham stages are checked against direct DFTs.
 """
 import ctypes as C
 import math
@@ -70,3 +71,31 @@ def test_green_solve_matches_the_oracle_symbol(green, dbl, tol):
         ref = np.linalg.solve(o.green_symbol_at(k), Fc)
         worst = max(worst, np.linalg.norm(x - ref) / np.linalg.norm(ref))
     assert worst < tol, worst
+
+
+@pytest.fixture(scope="module")
+def dft(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("hostdft") / "libdft.so")
+    src = os.path.join(ROOT, "tests", "host", "dft_host.cu")
+    inc = ["-I" + os.path.join(ROOT, "paper_2601_02172_gb300", "csrc"), "-I" + os.path.join(ROOT, "include")]
+    subprocess.run([NVCC, "-std=c++17", "-O2", "--expt-relaxed-constexpr", "-shared", "-Xcompiler", "-fPIC"]
+                   + inc + ["-o", out, src], check=True, capture_output=True)
+    lib = C.CDLL(out)
+    lib.host_dft.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
+    lib.host_dft.restype = C.c_int
+    return lib
+
+
+@pytest.mark.parametrize("R", [2, 3, 4, 5, 8, 16])
+@pytest.mark.parametrize("inv", [0, 1])
+def test_radix_butterflies_are_dfts(dft, R, inv):
+    """Each radix-R butterfly of the FFT stages is the length-R DFT, exp(-2 pi i jk/R)
+    forward and exp(+2 pi i jk/R) inverse (unnormalised)."""
+    rng = np.random.default_rng(R + 10 * inv)
+    x = rng.normal(size=R) + 1j * rng.normal(size=R)
+    v = np.column_stack([x.real, x.imag]).ravel().copy()
+    assert dft.host_dft(R, inv, _p(v)) == 1
+    y = v[0::2] + 1j * v[1::2]
+    jk = np.outer(np.arange(R), np.arange(R))
+    ref = np.exp((2j if inv else -2j) * np.pi * jk / R) @ x
+    assert np.abs(y - ref).max() < 1e-14 * max(1.0, np.abs(ref).max())
