@@ -1,6 +1,7 @@
 // Per-tet geometry of the X-FEM setup, shared by the setup kernels and a host-compiled check
-// (the functions are __host__ __device__): classification of a tet against K level sets and
-// the exact moments of the two sides of a cut tet.
+// (the functions are __host__ __device__): classification of a tet against K level sets, the
+// exact moments of the two sides of a cut tet, and the cut tet's scaled element matrix formed
+// from them (the optional cache of the FP32 iterations).
 #pragma once
 
 #include <math.h>
@@ -154,6 +155,82 @@ XFFT_HD inline void side_moments(const double L[4], int s, double vol, Moments& 
     add_subtet(out, v[1], v[2], v[3], v[4], vol);
     add_subtet(out, v[2], v[3], v[4], v[5], vol);
   }
+}
+
+// ---------------------------------------------------------------- cached element matrices
+// The paper's caching strategy (Sec. 2.3, next to Algorithm 1): the scaled element matrix of
+// every cut tet is formed once per microstructure instead of once per iteration.  On side s
+// the strain at the parent P1 function N_b is E_b = es + c_b ew + sym(w_b (x) gamma) (see the
+// apply kernels), so with the side moments M_bc = int N_b N_c every entry is a sum of
+//   beta(x, u; y, v) = sym(e_x (x) u) : C : sym(e_y (x) v)
+//                    = lambda u_x v_y + mu (delta_xy u.v + u_y v_x)
+// over u, v in {grad N_a, gamma} with the weights (per side)
+//   std (a,x)  - std (b,y):  V beta(x, g_a; y, g_b),  V = sum_bc M_bc
+//   std (a,x)  - enr (b,y):  d_by [P beta(x, g_a; y, g_b) + m_b beta(x, g_a; y, gamma)]
+//   enr (a,x)  - enr (b,y):  d_ax d_by [Q beta(x, g_a; y, g_b) + R_b beta(x, g_a; y, gamma)
+//                                        + R_a beta(x, gamma; y, g_b) + M_ab beta(x, gamma; y, gamma)]
+// with m_b = sum_c M_bc, R_a = sum_c M_ac c_c, P = sum_b m_b c_b, Q = sum_bc c_b M_bc c_c and
+// d = D0^-1/2 of the enriched DOF.  Computed in FP64, stored as FP32: the upper triangle of the
+// 24 x 24 matrix (local DOFs std 3a + x, then enr 12 + 3a + x) row by row, kCutPacked values
+// per cut tet, structure of arrays kc[k * ncut + e].
+XFFT_HD inline double beta_iso(int x, const double* u, int y, const double* v, double lam,
+                                           double mu) {
+  const double uv = x == y ? u[0] * v[0] + u[1] * v[1] + u[2] * v[2] : 0.0;
+  return lam * u[x] * v[y] + mu * (uv + u[y] * v[x]);
+}
+
+struct SideW {
+  double lam, mu, V, P, Q, m[4], R[4], M[4][4], gam[3];
+};
+
+// Per-side weights of a cut tet: the side's Lame constants, gamma = sum_b c_b grad N_b with
+// c_b = |L_b| - s L_b, the moments M_bc (packed as cut_f_M) and their sums V, m_b, R_b, P, Q.
+XFFT_HD inline void side_weights(const double L[4], double sgn, const double gr[4][3], const double Mp[10],
+                                 double lam, double mu, SideW& W) {
+  W.lam = lam;
+  W.mu = mu;
+  double c[4];
+  for (int b = 0; b < 4; ++b) c[b] = fabs(L[b]) - sgn * L[b];
+  for (int x = 0; x < 3; ++x) W.gam[x] = c[0] * gr[0][x] + c[1] * gr[1][x] + c[2] * gr[2][x] + c[3] * gr[3][x];
+  for (int b = 0; b < 4; ++b)
+    for (int cc = 0; cc < 4; ++cc) W.M[b][cc] = Mp[midx(b, cc)];
+  W.V = W.P = W.Q = 0.0;
+  for (int b = 0; b < 4; ++b) {
+    W.m[b] = W.M[b][0] + W.M[b][1] + W.M[b][2] + W.M[b][3];
+    W.R[b] = W.M[b][0] * c[0] + W.M[b][1] * c[1] + W.M[b][2] * c[2] + W.M[b][3] * c[3];
+    W.V += W.m[b];
+    W.P += W.m[b] * c[b];
+    W.Q += W.R[b] * c[b];
+  }
+}
+
+// Entry (i, j) of the scaled 24 x 24 element matrix (local DOFs std 3a + x, enr 12 + 3a + x),
+// summed over the two sides; dsc = D0^-1/2 of the tet's enriched DOFs.
+XFFT_HD inline double cut_element_entry(int i, int j, const SideW w[2], const double gr[4][3],
+                                        const double dsc[4][3]) {
+  if (j < i) {
+    const int tmp = i;
+    i = j;
+    j = tmp;
+  }
+  const bool ie = i >= 12, je = j >= 12;
+  const int a = (ie ? i - 12 : i) / 3, x = (ie ? i - 12 : i) % 3;
+  const int b = (je ? j - 12 : j) / 3, y = (je ? j - 12 : j) % 3;
+  double v = 0.0;
+  for (int si = 0; si < 2; ++si) {
+    const SideW& W = w[si];
+    const double bgg = beta_iso(x, gr[a], y, gr[b], W.lam, W.mu);
+    if (!je) {
+      v += W.V * bgg;
+    } else if (!ie) {
+      v += dsc[b][y] * (W.P * bgg + W.m[b] * beta_iso(x, gr[a], y, W.gam, W.lam, W.mu));
+    } else {
+      v += dsc[a][x] * dsc[b][y] *
+           (W.Q * bgg + W.R[b] * beta_iso(x, gr[a], y, W.gam, W.lam, W.mu) +
+            W.R[a] * beta_iso(x, W.gam, y, gr[b], W.lam, W.mu) + W.M[a][b] * beta_iso(x, W.gam, y, W.gam, W.lam, W.mu));
+    }
+  }
+  return v;
 }
 
 }  // namespace xfft

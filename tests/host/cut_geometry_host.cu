@@ -1,5 +1,6 @@
-// Host build of the CUDA path's per-tet setup geometry (classification against K level sets and
-// the exact side moments of a cut tet), for the CPU tests that compare it with the oracle.
+// Host build of the CUDA path's per-tet setup geometry (classification against K level sets, the
+// exact side moments of a cut tet and its scaled element matrix), for the CPU tests that compare
+// it with the oracle.
 // No kernels: every function called here is __host__ __device__.
 #include "cut_geometry.cuh"
 
@@ -23,6 +24,24 @@ unsigned host_classify_tet(const double* Lv, int nL, int* pm, int* pp, int* two)
   const unsigned c = xfft::classify_tet(pv, nL, pm, pp, &t);
   *two = t ? 1 : 0;
   return c;
+}
+
+// Scaled element matrix of a cut tet of type t (grid spacing h): packed upper triangle, 300
+// values; Mplus / Mminus: packed side moments; dsc: D0^-1/2 (4 x 3); lame: lambda, mu of the
+// plus side, then of the minus side (voxel scale included)
+void host_cut_element_matrix(const double* L, int t, const double* h, const double* Mplus,
+                             const double* Mminus, const double* dsc, const double* lame, double* K) {
+  const double ih[3] = {1.0 / h[0], 1.0 / h[1], 1.0 / h[2]};
+  double gr[4][3], d[4][3];
+  xfft::tet_grads<double>(t, ih, gr);
+  for (int a = 0; a < 4; ++a)
+    for (int x = 0; x < 3; ++x) d[a][x] = dsc[3 * a + x];
+  xfft::SideW w[2];
+  xfft::side_weights(L, 1.0, gr, Mplus, lame[0], lame[1], w[0]);
+  xfft::side_weights(L, -1.0, gr, Mminus, lame[2], lame[3], w[1]);
+  int k = 0;
+  for (int i = 0; i < 24; ++i)
+    for (int j = i; j < 24; ++j) K[k++] = xfft::cut_element_entry(i, j, w, gr, d);
 }
 
 }  // extern "C"

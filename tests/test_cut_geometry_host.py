@@ -4,7 +4,8 @@
 side moments int N_b, int N_b N_c of a cut tet (case table of the linearised interface, Sec. 3,
 Fig. subdivision).  Here it is built into a host library and compared with the oracle's generic
 convex clip and 4-point quadrature, on random tets including snapped zero vertices, and with
-the oracle's phase rule for several interfaces.
+the oracle's phase rule for several interfaces; the closed-form scaled element matrix of the
+optional cut-tet cache is compared with the oracle's quadrature-assembled element matrices.
 """
 import ctypes as C
 import os
@@ -14,7 +15,8 @@ import subprocess
 import numpy as np
 import pytest
 
-from oracle import clip_tet, quad4
+import synth
+from oracle import XFEM, clip_tet, quad4
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 NVCC = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
@@ -35,6 +37,7 @@ def geo(tmp_path_factory):
     lib.host_side_moments.argtypes = [dp, C.c_int, C.c_double, dp, dp]
     lib.host_classify_tet.argtypes = [dp, C.c_int, ip, ip, ip]
     lib.host_classify_tet.restype = C.c_uint
+    lib.host_cut_element_matrix.argtypes = [dp, C.c_int, dp, dp, dp, dp, dp, dp]
     return lib
 
 
@@ -110,3 +113,34 @@ def test_classification_matches_the_oracle_phase_rule(geo):
             assert code == (3 if first == 2 else first) and not two.value
             seen.add(("uncut", first))
     assert ("cut", 0, True) in seen and ("cut", 1, False) in seen and ("uncut", 2) in seen
+
+
+def test_cut_element_matrix_matches_the_oracle(geo):
+    """The cached element matrix (closed form from the side moments, FP64 before the FP32 store)
+    against the oracle's element matrices on a sphere with a voxel scale field."""
+    n = (8, 8, 8)
+    L = synth.sphere_levelset(n, (0.45, 0.5, 0.55), 0.3)
+    lm = synth.lame_from_E_nu(8.0, 0.2)
+    lp = synth.lame_from_E_nu(1.0, 0.3)
+    sc = synth.voxel_scale(n, 3).astype(np.float64)
+    o = XFEM(L, n, lame_minus=lm, lame_plus=lp, scale=sc)
+    vol = float(np.prod(o.h)) / 6.0
+    iu = np.triu_indices(24)
+    worst = 0.0
+    for idx in range(0, len(o.cut_list), 3):
+        v, t = o.cut_list[idx]
+        Lv = np.ascontiguousarray(o.L[o.tet_nodes[v, t]])
+        Mp = {}
+        for s in (+1, -1):
+            m = np.zeros(4)
+            Mp[s] = np.zeros(10)
+            geo.host_side_moments(_ptr(Lv), s, vol, _ptr(m), _ptr(Mp[s]))
+        dsc = np.ascontiguousarray(o.Dinvsqrt[o.enr_id[o.tet_nodes[v, t]]])
+        sv = sc.ravel()[v]
+        lame = np.array([lp[0] * sv, lp[1] * sv, lm[0] * sv, lm[1] * sv])
+        K = np.zeros(300)
+        geo.host_cut_element_matrix(_ptr(Lv), int(t), _ptr(np.ascontiguousarray(o.h)), _ptr(Mp[+1]),
+                                    _ptr(Mp[-1]), _ptr(dsc), _ptr(lame), _ptr(K))
+        _, Ko, _ = o.cut_element(idx)
+        worst = max(worst, np.abs(K - Ko[iu]).max() / np.abs(Ko).max())
+    assert worst < 1e-13, worst
