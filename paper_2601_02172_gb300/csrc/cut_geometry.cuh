@@ -233,4 +233,71 @@ XFFT_HD inline double cut_element_entry(int i, int j, const SideW w[2], const do
   return v;
 }
 
+// Contributions of one cut tet to the enriched scaling (eq. XFFT_diagonal, per DOF) and, if
+// want_off, to the off-diagonal entries of the per-node 3 x 3 Gram blocks.  On side s,
+// grad N_X^a = sum_b N_b V_ab with V_ab = c_b g_a + delta_ab gamma, so
+//   D_{a,k} = 1/2 sum_bc M_bc (V_ab . V_ac + V_ab[k] V_ac[k])
+// and the (k, l) block entry is 1/2 sum_bc M_bc V_ab[k] V_ac[l] for k != l.  Mp[0] / Mp[1]: the
+// packed moments of the plus / minus side; off[a] = entries (0,1), (0,2), (1,2).
+XFFT_HD inline void cut_scaling_terms(const double L[4], const double gr[4][3], const double Mp[2][10],
+                                      double acc[4][3], double off[4][3], bool want_off) {
+  for (int a = 0; a < 4; ++a)
+    for (int x = 0; x < 3; ++x) acc[a][x] = off[a][x] = 0.0;
+  for (int si = 0; si < 2; ++si) {
+    const double s = si == 0 ? 1.0 : -1.0;
+    double c[4], gam[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < 4; ++b) {
+      c[b] = fabs(L[b]) - s * L[b];
+      for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
+    }
+    const double* M = Mp[si];
+    for (int a = 0; a < 4; ++a) {
+      double V[4][3];
+      for (int b = 0; b < 4; ++b)
+        for (int x = 0; x < 3; ++x) V[b][x] = c[b] * gr[a][x] + (a == b ? gam[x] : 0.0);
+      for (int b = 0; b < 4; ++b)
+        for (int cc = 0; cc < 4; ++cc) {
+          const double w = M[midx(b, cc)];
+          const double dot = V[b][0] * V[cc][0] + V[b][1] * V[cc][1] + V[b][2] * V[cc][2];
+          for (int x = 0; x < 3; ++x) acc[a][x] += 0.5 * w * (dot + V[b][x] * V[cc][x]);
+          if (want_off) {
+            off[a][0] += 0.5 * w * V[b][0] * V[cc][1];
+            off[a][1] += 0.5 * w * V[b][0] * V[cc][2];
+            off[a][2] += 0.5 * w * V[b][1] * V[cc][2];
+          }
+        }
+    }
+  }
+}
+
+// Inverse of the symmetric positive definite 3 x 3 matrix (a00, a11, a22; a10, a20, a21) by its
+// Cholesky factor: v = (inv00, inv11, inv22, inv10, inv20, inv21); false (and v = identity) on a
+// non-positive pivot.
+XFFT_HD inline bool block_inverse3(double a00, double a11, double a22, double a10, double a20, double a21,
+                                   double v[6]) {
+  v[0] = v[1] = v[2] = 1.0;
+  v[3] = v[4] = v[5] = 0.0;
+  if (!(a00 > 0.0)) return false;
+  const double l00 = sqrt(a00);
+  const double l10 = a10 / l00, l20 = a20 / l00;
+  const double p11 = a11 - l10 * l10;
+  if (!(p11 > 0.0)) return false;
+  const double l11 = sqrt(p11);
+  const double l21 = (a21 - l20 * l10) / l11;
+  const double p22 = a22 - l20 * l20 - l21 * l21;
+  if (!(p22 > 0.0)) return false;
+  const double l22 = sqrt(p22);
+  const double m00 = 1.0 / l00, m11 = 1.0 / l11, m22 = 1.0 / l22;
+  const double m10 = -l10 * m00 * m11;
+  const double m21 = -l21 * m11 * m22;
+  const double m20 = -(l20 * m00 + l21 * m10) * m22;
+  v[0] = m00 * m00 + m10 * m10 + m20 * m20;
+  v[1] = m11 * m11 + m21 * m21;
+  v[2] = m22 * m22;
+  v[3] = m10 * m11 + m20 * m21;
+  v[4] = m20 * m22;
+  v[5] = m21 * m22;
+  return true;
+}
+
 }  // namespace xfft

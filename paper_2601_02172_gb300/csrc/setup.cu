@@ -301,36 +301,12 @@ __global__ void k_cut_scaling(const int* __restrict__ ip, const double* __restri
     double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
     double gr[4][3];
     tet_grads<double>(t, ih, gr);
-    double L[4];
+    double L[4], Mp[2][10];
     for (int b = 0; b < 4; ++b) L[b] = dp[cut_f_L(b) * (long long)ncut + e];
-    double acc[4][3] = {};
-    double off[4][3] = {};
-    for (int si = 0; si < 2; ++si) {
-      const double s = si == 0 ? 1.0 : -1.0;
-      double c[4], gam[3] = {0.0, 0.0, 0.0};
-      for (int b = 0; b < 4; ++b) {
-        c[b] = fabs(L[b]) - s * L[b];
-        for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
-      }
-      double M[10];
-      for (int k = 0; k < 10; ++k) M[k] = dp[cut_f_M(si, k) * (long long)ncut + e];
-      for (int a = 0; a < 4; ++a) {
-        double V[4][3];
-        for (int b = 0; b < 4; ++b)
-          for (int x = 0; x < 3; ++x) V[b][x] = c[b] * gr[a][x] + (a == b ? gam[x] : 0.0);
-        for (int b = 0; b < 4; ++b)
-          for (int cc = 0; cc < 4; ++cc) {
-            const double w = M[midx(b, cc)];
-            const double dot = V[b][0] * V[cc][0] + V[b][1] * V[cc][1] + V[b][2] * V[cc][2];
-            for (int x = 0; x < 3; ++x) acc[a][x] += 0.5 * w * (dot + V[b][x] * V[cc][x]);
-            if (Doff) {
-              off[a][0] += 0.5 * w * V[b][0] * V[cc][1];
-              off[a][1] += 0.5 * w * V[b][0] * V[cc][2];
-              off[a][2] += 0.5 * w * V[b][1] * V[cc][2];
-            }
-          }
-      }
-    }
+    for (int si = 0; si < 2; ++si)
+      for (int k = 0; k < 10; ++k) Mp[si][k] = dp[cut_f_M(si, k) * (long long)ncut + e];
+    double acc[4][3], off[4][3];
+    cut_scaling_terms(L, gr, Mp, acc, off, Doff != nullptr);
     for (int a = 0; a < 4; ++a) {
       const int j = ip[(4 + a) * ncut + e];
       for (int x = 0; x < 3; ++x) atomicAdd(&D[(long long)x * nX + j], acc[a][x]);
@@ -396,33 +372,8 @@ __global__ void k_block_inverse(const double* __restrict__ D, const double* __re
     const double s0 = isd[j], s1 = isd[nX + j], s2 = isd[2 * (long long)nX + j];
     const double a00 = D[j] * s0 * s0, a11 = D[nX + j] * s1 * s1, a22 = D[2 * (long long)nX + j] * s2 * s2;
     const double a10 = Doff[j] * s0 * s1, a20 = Doff[nX + j] * s0 * s2, a21 = Doff[2 * (long long)nX + j] * s1 * s2;
-    double v[6] = {1.0, 1.0, 1.0, 0.0, 0.0, 0.0};
-    bool ok = a00 > 0.0;
-    if (ok) {
-      const double l00 = sqrt(a00);
-      const double l10 = a10 / l00, l20 = a20 / l00;
-      const double p11 = a11 - l10 * l10;
-      ok = p11 > 0.0;
-      if (ok) {
-        const double l11 = sqrt(p11);
-        const double l21 = (a21 - l20 * l10) / l11;
-        const double p22 = a22 - l20 * l20 - l21 * l21;
-        ok = p22 > 0.0;
-        if (ok) {
-          const double l22 = sqrt(p22);
-          const double m00 = 1.0 / l00, m11 = 1.0 / l11, m22 = 1.0 / l22;
-          const double m10 = -l10 * m00 * m11;
-          const double m21 = -l21 * m11 * m22;
-          const double m20 = -(l20 * m00 + l21 * m10) * m22;
-          v[0] = m00 * m00 + m10 * m10 + m20 * m20;
-          v[1] = m11 * m11 + m21 * m21;
-          v[2] = m22 * m22;
-          v[3] = m10 * m11 + m20 * m21;
-          v[4] = m20 * m22;
-          v[5] = m21 * m22;
-        }
-      }
-    }
+    double v[6];
+    const bool ok = block_inverse3(a00, a11, a22, a10, a20, a21, v);
     if (!ok) atomicExch(bad, 1);
     for (int k = 0; k < 6; ++k) {
       b64[(long long)k * nX + j] = v[k];

@@ -44,4 +44,28 @@ void host_cut_element_matrix(const double* L, int t, const double* h, const doub
     for (int j = i; j < 24; ++j) K[k++] = xfft::cut_element_entry(i, j, w, gr, d);
 }
 
+// One cut tet's contributions to D0 (acc, 4 x 3) and to the off-diagonal Gram entries (off,
+// 4 x 3: (0,1), (0,2), (1,2)); Mplus / Mminus: packed side moments
+void host_cut_scaling(const double* L, int t, const double* h, const double* Mplus, const double* Mminus,
+                      double* acc, double* off) {
+  const double ih[3] = {1.0 / h[0], 1.0 / h[1], 1.0 / h[2]};
+  double gr[4][3], Mp[2][10], A[4][3], O[4][3];
+  xfft::tet_grads<double>(t, ih, gr);
+  for (int k = 0; k < 10; ++k) {
+    Mp[0][k] = Mplus[k];
+    Mp[1][k] = Mminus[k];
+  }
+  xfft::cut_scaling_terms(L, gr, Mp, A, O, true);
+  for (int a = 0; a < 4; ++a)
+    for (int x = 0; x < 3; ++x) {
+      acc[3 * a + x] = A[a][x];
+      off[3 * a + x] = O[a][x];
+    }
+}
+
+// a = (a00, a11, a22, a10, a20, a21) -> v = the inverse in the same order; returns 1 if SPD
+int host_block_inverse(const double* a, double* v) {
+  return xfft::block_inverse3(a[0], a[1], a[2], a[3], a[4], a[5], v) ? 1 : 0;
+}
+
 }  // extern "C"

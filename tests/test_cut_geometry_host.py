@@ -38,6 +38,9 @@ def geo(tmp_path_factory):
     lib.host_classify_tet.argtypes = [dp, C.c_int, ip, ip, ip]
     lib.host_classify_tet.restype = C.c_uint
     lib.host_cut_element_matrix.argtypes = [dp, C.c_int, dp, dp, dp, dp, dp, dp]
+    lib.host_cut_scaling.argtypes = [dp, C.c_int, dp, dp, dp, dp, dp]
+    lib.host_block_inverse.argtypes = [dp, dp]
+    lib.host_block_inverse.restype = C.c_int
     return lib
 
 
@@ -144,3 +147,47 @@ def test_cut_element_matrix_matches_the_oracle(geo):
         _, Ko, _ = o.cut_element(idx)
         worst = max(worst, np.abs(K - Ko[iu]).max() / np.abs(Ko).max())
     assert worst < 1e-13, worst
+
+
+def test_scaling_and_block_inverse_match_the_oracle(geo):
+    """D0 per enriched DOF (eq. XFFT_diagonal) and the off-diagonal entries of the per-node
+    enriched Gram blocks, summed from the per-tet terms of the CUDA path, against the oracle's
+    quadrature; the 3 x 3 inverse of each scaled block against numpy's inverse."""
+    n = (8, 10, 6)
+    ell = (1.1, 0.9, 1.0)
+    L = synth.sphere_levelset(n, (0.5, 0.45, 0.55), 0.3, ell)
+    o = XFEM(L, n, ell)
+    vol = float(np.prod(o.h)) / 6.0
+    D = np.zeros((o.nX, 3))
+    off = np.zeros((o.nX, 3))
+    for v, t in o.cut_list:
+        Lv = np.ascontiguousarray(o.L[o.tet_nodes[v, t]])
+        Mp = {}
+        for s in (+1, -1):
+            m = np.zeros(4)
+            Mp[s] = np.zeros(10)
+            geo.host_side_moments(_ptr(Lv), s, vol, _ptr(m), _ptr(Mp[s]))
+        acc = np.zeros(12)
+        of = np.zeros(12)
+        geo.host_cut_scaling(_ptr(Lv), int(t), _ptr(np.ascontiguousarray(o.h)), _ptr(Mp[+1]), _ptr(Mp[-1]),
+                             _ptr(acc), _ptr(of))
+        eids = o.enr_id[o.tet_nodes[v, t]]
+        np.add.at(D, eids, acc.reshape(4, 3))
+        np.add.at(off, eids, of.reshape(4, 3))
+    assert np.abs(D - o.D).max() < 1e-12 * np.abs(o.D).max()
+    ref_off = np.stack([o.Dblk[:, 0, 1], o.Dblk[:, 0, 2], o.Dblk[:, 1, 2]], axis=1)
+    assert np.abs(off - ref_off).max() < 1e-12 * np.abs(o.D).max()
+    worst = 0.0
+    for j in range(o.nX):
+        B = o.Bblk[j]
+        a = np.array([B[0, 0], B[1, 1], B[2, 2], B[1, 0], B[2, 0], B[2, 1]])
+        inv = np.zeros(6)
+        assert geo.host_block_inverse(_ptr(a), _ptr(inv)) == 1
+        R = np.linalg.inv(B)
+        worst = max(worst, np.abs(inv - [R[0, 0], R[1, 1], R[2, 2], R[1, 0], R[2, 0], R[2, 1]]).max()
+                    / np.abs(R).max())
+    assert worst < 1e-12, worst
+    # a non-positive-definite block is refused and leaves the identity
+    inv = np.zeros(6)
+    assert geo.host_block_inverse(_ptr(np.array([1.0, 1.0, 1.0, 2.0, 0.0, 0.0])), _ptr(inv)) == 0
+    assert np.array_equal(inv, [1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
