@@ -44,6 +44,8 @@ def algorithmic_bytes(kind, N, nX, ncut, has_scale, cut_cache=False):
         # enriched ids (32 B); per RHS the DOFs of the enriched nodes (all nodes of cut tets):
         # std and enr d read (24 B) and std and enr q atomically updated (48 B)
         return 1232 * ncut, 72 * nX
+    if kind in ("apply_cut_f32", "apply_cut_f64"):
+        return cut_bytes(kind[-3:], nX, ncut)
     per = _per_rhs_bytes(kind, N, nX, ncut, geo)
     return (0, per) if per is not None else None
 
@@ -57,11 +59,17 @@ def _per_rhs_bytes(kind, N, nX, ncut, geo):
         return 48 * (N + nX)
     if kind == "prec_f64":
         return 48 * (N + nX)
-    if kind == "apply_cut_f32":  # per RHS: geometry (168 B per tet, once per 6 RHS) + 24 gathers
-        return (28 + 240) * ncut   # (incl. 1/sqrt(D0)) + 24 atomic adds
-    if kind == "apply_cut_f64":
-        return 776 * ncut
     return None
+
+
+def cut_bytes(prec, nX, ncut):
+    """Unique bytes of one cut-tet apply as (per launch, per right-hand side): each cut tet's
+    geometry once per launch (11 ints and 32 reals, FP32 copy 172 B, FP64 300 B) and 1/sqrt(D0)
+    of the enriched nodes (3 reals); per right-hand side, at every enriched node (the nodes of
+    the cut tets), the standard and enriched d read (6 reals) and q updated (6 reals read and
+    written): 72 B in FP32, 144 B in FP64."""
+    r = 4 if prec == "f32" else 8
+    return (44 + 32 * r) * ncut + 3 * r * nX, 18 * r * nX
 
 
 def parse():
@@ -140,75 +148,111 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _oracle_sample(n_cpu, tol):
-    """One bounded run of the CPU oracle (FP64, as it stands) on the workload's ellipsoids
-    resampled at n_cpu^3: setup + assembly, then PCG (FFT Green operator) for one load case."""
+def _oracle_case(job):
+    """One load case of the CPU oracle's PCG (FFT Green operator), run in a worker process."""
+    o, k, tol = job
+    e = np.eye(6)[k]
+    t0 = time.perf_counter()
+    u, info = o.pcg(e, tol=tol, green="fft")
+    return k, time.perf_counter() - t0, int(info["iters"]), o.mean_stress(u, e)
+
+
+def resampled_workload(n_cpu):
+    """The bench workload's ellipsoids (and scale field, subsampled) on an n_cpu^3 grid."""
     import synth
-    from oracle import XFEM
     w = synth.make_workload("ellipsoids40")
     n = (n_cpu,) * 3
     L = synth.ellipsoids_levelset(n, w["info"]["inclusions"])
     step = 128 // n_cpu if 128 % n_cpu == 0 else 1
-    sc = np.ascontiguousarray(w["scale"][::step, ::step, ::step][:n_cpu, :n_cpu, :n_cpu])
+    sc = np.ascontiguousarray(w["scale"][::step, ::step, ::step][:n_cpu, :n_cpu, :n_cpu]).astype(np.float32)
+    return L, sc, w["lame_minus"], w["lame_plus"]
+
+
+def oracle_pool(workers):
+    """Worker processes for the oracle's six load cases (spawned: safe after CUDA is initialised)."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(workers)
+
+
+def oracle_solve(n_cpu, tol, pool):
+    """The CPU oracle as it stands, one whole six-case solve of the resampled workload: setup and
+    assembly in this process, then the six load cases' PCG spread over the worker pool (they
+    are independent).  Returns times, iteration counts and C_eff."""
+    from oracle import XFEM
+    L, sc, lm, lp = resampled_workload(n_cpu)
     t0 = time.perf_counter()
-    o = XFEM(L, n, lame_minus=w["lame_minus"], lame_plus=w["lame_plus"], scale=sc)
+    o = XFEM(L, (n_cpu,) * 3, lame_minus=lm, lame_plus=lp, scale=sc)
     o.assemble()
     t1 = time.perf_counter()
-    u, info = o.pcg(np.eye(6)[0], tol=tol, green="fft")
+    res = pool.map(_oracle_case, [(o, k, tol) for k in range(6)])
     t2 = time.perf_counter()
-    return {"n": n_cpu, "ncut": len(o.cut_list), "t_setup": t1 - t0, "t_pcg": t2 - t1,
-            "iters": info["iters"], "dofit": o.ndof * info["iters"] / (t2 - t1)}
+    C = np.zeros((6, 6))
+    for k, _, _, sig in res:
+        C[:, k] = sig
+    iters = [r[2] for r in res]
+    return {"n": n_cpu, "ncut": len(o.cut_list), "ndof": o.ndof, "t_setup": t1 - t0,
+            "t_pcg": t2 - t1, "t": t2 - t0, "iters": iters, "C": C,
+            "dofit": o.ndof * sum(iters) / (t2 - t1)}
 
 
-_FULL = {}
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
 
 
-def _full_size_counts():
-    """Cut tets and DOFs of the 128^3 workload (host classification, computed once)."""
-    if not _FULL:
-        import synth
-        from oracle import classify
-        w = synth.make_workload("ellipsoids40")
-        cut, J = classify(w["L"], (128,) * 3, 1e-6 / 128)
-        _FULL.update(ncut=int(cut.sum()), ndof=3 * (128 ** 3 + J.size))
-    return _FULL
+def _sample_text(r, tol, workers):
+    return ("ellipsoids40 resampled at %d^3 (%d cut tets, %d DOF): the oracle's whole six-case "
+            "solve, tol %g, measured (not scaled): setup + assembly %.1f s on 1 core, six PCGs "
+            "(%s iterations) %.1f s on %d worker processes" % (
+                r["n"], r["ncut"], r["ndof"], tol, r["t_setup"],
+                "/".join(str(i) for i in r["iters"]), r["t_pcg"], workers))
 
 
-def _scaled(sample):
-    """Seconds for one 128^3 six-case solve: setup scales with the cut tets, each PCG with
-    DOF-iterations (iteration counts are mesh independent, Sec. 4)."""
-    full = _full_size_counts()
-    t_setup = sample["t_setup"] * full["ncut"] / max(sample["ncut"], 1)
-    t_pcg = 6.0 * sample["iters"] * full["ndof"] / sample["dofit"]
-    return t_setup + t_pcg
-
-
-def _sample_text(sample, tol):
-    full = _full_size_counts()
-    return ("ellipsoids40 resampled at %d^3 (%d cut tets), one load case, tol %g: setup %.1f s, PCG "
-            "%d it in %.2f s (%.3g DOF-it/s); scaled to 128^3 x 6 cases by cut tets (%d) and "
-            "DOF-iterations (6 x %d it x %d DOF)" % (sample["n"], sample["ncut"], tol, sample["t_setup"],
-                                                    sample["iters"], sample["t_pcg"], sample["dofit"],
-                                                    full["ncut"], sample["iters"], full["ndof"]))
-
-
-def cpu_baseline(n_cpu, tol):
-    sample = _oracle_sample(n_cpu, tol)
-    t = _scaled(sample)
-    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": _sample_text(sample, tol), "dof_iters_per_s": sample["dofit"],
-            "os_cpu_count": os.cpu_count()}
+def cpu_baseline(n_cpu, tol, dev=None):
+    """The oracle timed on this host on the resampled workload, and the GPU on the same input."""
+    workers = min(6, _cores())
+    with oracle_pool(workers) as pool:
+        r = oracle_solve(n_cpu, tol, pool)
+    out = {"value": 1.0 / r["t"], "unit": UNIT, "cores": workers, "kind": "oracle",
+           "sample": _sample_text(r, tol, workers), "dof_iters_per_s": r["dofit"],
+           "os_cpu_count": os.cpu_count(), "affinity_cores": _cores()}
+    if dev is not None:
+        import torch
+        from paper_2601_02172_gb300 import Solver
+        L, sc, lm, lp = resampled_workload(n_cpu)
+        same = {}
+        for prec in ("fp64", "fp32"):
+            sv = Solver((n_cpu,) * 3, precision=prec, tol=tol)
+            sv.set_microstructure(L, lm, lp, sc)
+            sv.effective_stiffness()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps = 5
+            for _ in range(reps):
+                sv.set_microstructure(L, lm, lp, sc)
+                Cg, _ = sv.effective_stiffness()
+            torch.cuda.synchronize()
+            same[prec] = {"solves_per_s": reps / (time.perf_counter() - t0),
+                          "ceff_rel_diff_vs_oracle": float(np.abs(Cg - r["C"]).max() / np.abs(r["C"]).max())}
+            sv.close()
+        out["gpu_same_input"] = dict(same, note="the GPU's setup + six-case solve of the identical "
+                                                "%d^3 input (host level set), same tolerance" % n_cpu)
+    return out
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle as it stands, each step a bounded sample of the workload."""
-    _full_size_counts()
-    ts, samples = [], []
-    for k in range(args.warmup + args.steps):
-        sample = _oracle_sample(args.cpu_n, args.tol)
-        if k >= args.warmup:
-            samples.append(sample)
-            ts.append(_scaled(sample))
+    """Reference arm: the CPU oracle as it stands; each step is one measured six-case solve of the
+    workload resampled at --cpu-n^3 (a bounded sample of the 128^3 workload)."""
+    workers = min(6, _cores())
+    ts, rs = [], []
+    with oracle_pool(workers) as pool:
+        for k in range(args.warmup + args.steps):
+            r = oracle_solve(args.cpu_n, args.tol, pool)
+            if k >= args.warmup:
+                rs.append(r)
+                ts.append(r["t"])
     t = statistics.mean(ts)
     value = 1.0 / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -216,11 +260,11 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "tol": args.tol,
-                       "sample": "each step: the oracle on the workload resampled at %d^3, one load "
-                                 "case, scaled to the 128^3 six-case solve" % args.cpu_n},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
-                             "sample": _sample_text(samples[-1], args.tol),
-                             "dof_iters_per_s": statistics.mean(s["dofit"] for s in samples)},
+                       "sample": "each step: the oracle's whole six-case solve of the workload "
+                                 "resampled at %d^3, measured" % args.cpu_n},
+            "cpu_baseline": {"kind": "oracle", "cores": workers, "value": value, "unit": UNIT,
+                             "sample": _sample_text(rs[-1], args.tol, workers),
+                             "dof_iters_per_s": statistics.mean(r["dofit"] for r in rs)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -322,7 +366,8 @@ def main():
     if dist:
         dist.barrier()
     info.update(iters=0, dofit=0.0)
-    solver.profile(True)
+    # the timed region runs the production path: tracing off, so the CG iterations between two
+    # convergence polls replay as captured CUDA graphs
     sampler = ClockSampler(local)
     sampler.start()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -334,8 +379,6 @@ def main():
     ev1.record()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    prof = solver.profile_read()
-    solver.profile(False)
     ms = ev0.elapsed_time(ev1)
     if dist:
         ms = max_over_ranks(ms, dist, dev)
@@ -343,6 +386,15 @@ def main():
     steps_iters = info["iters"]
     dofit_rate = info["dofit"] / (ms / 1000.0)
     value = job_value(world, args.steps, ms)
+    # per-kernel-group device times (roofline): a separate, untimed pass of the same steps with
+    # the library's event tracing on (each group bracketed by events on the solver's stream)
+    prof_steps = max(1, min(args.steps, 3))
+    solver.profile(True)
+    for _ in range(prof_steps):
+        step()
+    prof = solver.profile_read()
+    solver.profile(False)
+    torch.cuda.synchronize()
 
     # live roofline of the dominant kernel group
     peak, peak_kind = load_peaks()
@@ -358,15 +410,17 @@ def main():
             "bytes_per_rhs": bpu,
             "launches": klaunch, "rhs_units": kunits, "avg_launch_ms": kms / max(klaunch, 1),
             "traffic": (tr["dram_bytes_per_rhs"] * kunits / max(klaunch, 1)) if tr else None,
-            "groups_ms": {k: round(v[0], 3) for k, v in prof.items()}}
-    gpu_launches = int(sum(v[1] for v in prof.values()))
+            "groups_ms_per_step": {k: round(v[0] / prof_steps, 3) for k, v in prof.items()},
+            "profiled_steps": prof_steps}
+    # the library's kernels per step (counted by the traced pass) times the timed steps
+    gpu_launches = int(sum(v[1] for v in prof.values()) * args.steps // prof_steps)
 
     line = None
     if rank == 0:
         # end to end: host buffers in, host results out, copies inside the timed region
         torch.cuda.synchronize()
         te = []
-        for _ in range(max(1, min(args.steps, 2))):
+        for _ in range(args.steps):
             t0 = time.perf_counter()
             C_e, dl_e, ds_e = step(device_inputs=False)
             torch.cuda.synchronize()
@@ -428,7 +482,7 @@ def main():
             batch_effective_stiffness(bsolvers)  # warm-up (graph capture)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, bst = batch_effective_stiffness(bsolvers)
+            Cbat, bst = batch_effective_stiffness(bsolvers)
             torch.cuda.synchronize()
             t_bat = time.perf_counter() - t0
             t0 = time.perf_counter()
@@ -436,7 +490,16 @@ def main():
                 sv.effective_stiffness()
             torch.cuda.synchronize()
             t_seq = time.perf_counter() - t0
+            # accuracy of the FP32-refined batch against plain FP64 solves of the same members
+            errs = []
+            for wb, Cb in zip(bw, Cbat):
+                s64 = Solver(wb["n"], precision="fp64", tol=1e-8)
+                s64.set_microstructure(wb["L"], wb["lame_minus"], wb["lame_plus"])
+                C64, _s = s64.effective_stiffness()
+                errs.append(float(np.abs(Cb - C64).max() / np.abs(C64).max()))
+                s64.close()
             extra["batch16"] = {"microstructures": len(bw), "rhs": 6 * len(bw),
+                                "ceff_max_rel_err_vs_fp64": max(errs),
                                 "grids": [int(wb["n"][0]) for wb in bw], "tol": 1e-8,
                                 "solves_per_s_batched": len(bw) / t_bat,
                                 "solves_per_s_sequential": len(bw) / t_seq,
@@ -465,18 +528,23 @@ def main():
             Lh, phh, ellh = synth.hashin_neutral_inclusion(128)
             eh = np.array([[1.0, 1.0, 1.0, 0.0, 0.0, 0.0]])
             hashin = {"N": 128, "tol": 1e-7}
-            for prec, scheme in (("fp64", "cg"), ("fp64", "nlcg"), ("fp64", "bb"), ("fp64", "basic"),
-                                 ("fp32", "cg")):
-                sv = Solver((128, 128, 128), ellh, precision=prec, tol=1e-7, scheme=scheme, maxit=5000)
+            runs = [("fp64", "cg", {}), ("fp64", "nlcg", {}), ("fp64", "bb", {}), ("fp64", "basic", {}),
+                    ("fp32", "cg", {})]
+            # every Barzilai-Borwein step rule (the paper prints no formula; 115 iterations)
+            runs += [("fp64", "bb", {"bb_rule": r}) for r in ("bb2", "alt", "bb1e", "bb2e")]
+            runs += [("fp64", "bb", {"bb_cycle": m}) for m in (2, 3, 4)]
+            for prec, scheme, kw in runs:
+                sv = Solver((128, 128, 128), ellh, precision=prec, tol=1e-7, scheme=scheme, maxit=5000, **kw)
                 sv.set_microstructure_phases(Lh, phh)
                 sv.solve(eh, u=False)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 oh = sv.solve(eh, u=False)
                 torch.cuda.synchronize()
-                hashin[prec + "_" + scheme] = {"iters": int(oh["stats"]["iters"][0]),
-                                               "K_eff_minus_K_matrix": float(oh["mean_stress"][0, :3].sum() / 9.0 - 1.0),
-                                               "ms": 1e3 * (time.perf_counter() - t0)}
+                key = prec + "_" + scheme + "".join("_%s%s" % (k.replace("bb_", ""), v) for k, v in kw.items())
+                hashin[key] = {"iters": int(oh["stats"]["iters"][0]), "converged": bool(oh["converged"]),
+                               "K_eff_minus_K_matrix": float(oh["mean_stress"][0, :3].sum() / 9.0 - 1.0),
+                               "ms": 1e3 * (time.perf_counter() - t0)}
                 hashin["enriched_node_share"] = sv.num_enriched / 128 ** 3
                 sv.close()
             extra["hashin_neutral_inclusion"] = hashin
@@ -524,7 +592,7 @@ def main():
         cpu = None
         if not args.no_cpu and world == 1:
             try:
-                cpu = cpu_baseline(args.cpu_n, args.tol)
+                cpu = cpu_baseline(args.cpu_n, args.tol, dev)
             except Exception as exc:  # report, never fail the GPU line
                 cpu = {"error": repr(exc)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

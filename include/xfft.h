@@ -86,6 +86,18 @@ typedef struct {
  * XFFT_SCHEME_NLCG the nonlinear CG the paper compares (Sec. 2.3): the fixed step s0 without a
  * line search and the Fletcher-Reeves momentum beta = f_k^T P^-1 f_k / f_{k-1}^T P^-1 f_{k-1}. */
 enum { XFFT_SCHEME_CG = 0, XFFT_SCHEME_BASIC = 1, XFFT_SCHEME_BB = 2, XFFT_SCHEME_NLCG = 3 };
+/* Step rule of XFFT_SCHEME_BB.  The paper cites the Barzilai-Borwein scheme (Sec. 2.3) without
+ * its formula, so every classical rule is offered; du = s d and dg = A du are the previous
+ * iteration's changes of the iterate and of the gradient (d = P^-1 f, steepest descent):
+ *   XFFT_BB1        <du, P du> / <du, dg>       (metric of P; equals the previous exact
+ *                                                 line-search step; default)
+ *   XFFT_BB2        <du, dg> / <dg, P^-1 dg>    (metric of P; from scalars already reduced)
+ *   XFFT_BB_ALT     BB1 and BB2 in turn (BB2 first)
+ *   XFFT_BB1_EUCLID <du, du> / <du, dg>         (Euclidean metric of the scaled DOFs)
+ *   XFFT_BB2_EUCLID <du, dg> / <dg, dg>
+ * The Euclidean rules are not invariant under a change of length unit (A scales like length,
+ * P^-1 A does not); they need one more reduction pass per iteration. */
+enum { XFFT_BB1 = 0, XFFT_BB2 = 1, XFFT_BB_ALT = 2, XFFT_BB1_EUCLID = 3, XFFT_BB2_EUCLID = 4 };
 
 typedef struct {
   int precision;       /* XFFT_FP64 (all FP64) or XFFT_FP32_REFINED (FP32 CG; residuals of the
@@ -108,6 +120,16 @@ typedef struct {
                           action from the 32 per-side moments at every apply, which is about three
                           times faster on GB300 (the cached matrices make the kernel wait on
                           memory) */
+  int bb_rule;         /* XFFT_SCHEME_BB: the step rule (XFFT_BB1 default) */
+  int bb_cycle;        /* XFFT_SCHEME_BB: the step is renewed every bb_cycle iterations and kept
+                          in between (cyclic BB; 1 = every iteration, the default) */
+  int enrichment;      /* 1 (default): the X-FEM space of eq. X-FEM_space.  0: the P1 baseline of
+                          the paper's discretization table (Sec. 4.1), voxel-segmented P1 elements
+                          without enrichment: each voxel takes the phase of its centre, where the
+                          level set is the mean of its eight corner values (several level sets:
+                          the first one negative there), and nX = 0 */
+  long long max_device_bytes; /* cap on the context's own device allocations (0 = none); a
+                          request above it fails with XFFT_ENOMEM as a failed cudaMalloc would */
 } xfft_options;
 
 typedef struct {
@@ -120,7 +142,8 @@ typedef struct {
 } xfft_stats;
 
 /* Fill *opt with the defaults: FP64, tol 1e-10, maxit 10000, snap_tau 0 (=> 1e-6 min h),
- * identity enriched block, inner_tol 1e-5, max_refine 20, poll_every 8, linear CG, cut_cache 0. */
+ * identity enriched block, inner_tol 1e-5, max_refine 20, poll_every 8, linear CG, cut_cache 0,
+ * bb_rule XFFT_BB1, bb_cycle 1, enrichment 1, max_device_bytes 0. */
 xfft_status xfft_default_options(xfft_options* opt);
 
 /* Create a context for one grid.  stream: a cudaStream_t (or NULL for the legacy stream).
@@ -248,10 +271,14 @@ xfft_status xfft_profile_read(xfft_ctx* ctx, double ms[16], long long launches[1
  *            int_Y C grad^s d (Mandel 6) per RHS.
  * Its reduction scratch is a fixed array in the library's device memory (about 1.8 MB,
  * present on every GPU that loads the library until the process exits), so it serves at most
- * XFFT_NOALLOC_MAX_RHS right-hand sides and grids whose apply needs at most
- * XFFT_NOALLOC_MAX_PARTS partial sums per value (128^3 grids fit, 256^3 grids do not);
- * larger requests return XFFT_EINVAL and touch nothing.  The first call on each device looks
- * up the scratch address (a one-time set-up): make that first call before any stream capture.
+ * XFFT_NOALLOC_MAX_RHS right-hand sides and grids whose apply launches at most
+ * XFFT_NOALLOC_MAX_PARTS blocks, each writing one partial sum per value: the stencil's
+ * ceil(n2 / 15) ceil(n1 / 15) ceil(n0 / 32) blocks plus the cut-tet kernel's blocks (at most
+ * a few waves of the GPU's SMs).  With the default tiling 256^3 grids fit and 384^3 grids do
+ * not; larger requests return XFFT_EINVAL and touch nothing.  The scratch address of a device
+ * is looked up once, by the first xfft_set_microstructure (or xfft_apply_noalloc) on that
+ * device; a first lookup attempted while the context's stream is being captured returns
+ * XFFT_ESTATE instead.
  * Every call shares the one scratch array: calls that overlap on the GPU (other streams,
  * other threads, other contexts on the same device) race and must be serialised by the
  * caller.  The context must exist with its microstructure set (those calls do allocate). */

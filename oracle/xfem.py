@@ -223,7 +223,7 @@ class XFEM:
     """
 
     def __init__(self, L, n, length=(1.0, 1.0, 1.0), lame_minus=(1.0, 1.0),
-                 lame_plus=(1.0, 1.0), scale=None, tau=None, phases=None):
+                 lame_plus=(1.0, 1.0), scale=None, tau=None, phases=None, enrichment=True):
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
         self.h = np.array([self.length[a] / self.n[a] for a in range(3)])
@@ -244,6 +244,7 @@ class XFEM:
         self.phases = [tuple(map(float, p)) for p in phases]
         self.scale = (np.ones(self.nvox) if scale is None
                       else np.asarray(scale, dtype=np.float64).ravel().copy())
+        self.enrichment = bool(enrichment)
         self._geometry()
         self._classify()
         self._cut_quadrature()
@@ -284,6 +285,8 @@ class XFEM:
         self.B_std = [symgrad_operator(G) for G in self.tet_grads]  # 6 x 12 per tet type
 
     def _classify(self):
+        if not self.enrichment:
+            return self._classify_p1()
         K = self.nL
         Lt = self.Ls[:, self.tet_nodes]  # (K, nvox, 6, 4)
         neg = Lt.min(axis=3) < 0.0
@@ -313,6 +316,26 @@ class XFEM:
         pp = np.where(lneg.any(axis=0), lneg.argmax(axis=0), K)
         self.cut_iface = ki
         self.cut_phase = {-1: ki, +1: pp}
+
+    def _classify_p1(self):
+        """The P1 baseline of the discretization table (Sec. 4.1): voxel-segmented P1 elements
+        without enrichment.  Each voxel takes one phase, that of its centre, where the level set
+        is the trilinear interpolant of the corner values, i.e. their mean; with several level
+        sets the first one negative at the centre decides (phase K if none is).  Nothing is cut
+        and nothing is enriched."""
+        K = self.nL
+        corners = self.node_index(self.vox_ijk[:, None, :] + VOXEL_CORNERS[None, :, :])  # (nvox, 8)
+        centre = self.Ls[:, corners].mean(axis=2)  # (K, nvox)
+        neg = centre < 0.0
+        first = np.where(neg.any(axis=0), neg.argmax(axis=0), K)
+        self.tet_phase = np.repeat(first[:, None], 6, axis=1)
+        self.cut = np.zeros((self.nvox, 6), bool)
+        self.enr_nodes = np.zeros(0, dtype=np.int64)
+        self.nX = 0
+        self.enr_id = -np.ones(self.nFE, dtype=np.int64)
+        self.cut_list = np.zeros((0, 2), np.int64)
+        self.cut_iface = np.zeros(0, dtype=np.int64)
+        self.cut_phase = {-1: np.zeros(0, dtype=np.int64), +1: np.zeros(0, dtype=np.int64)}
 
     # ------------------------------------------------------------------ cut elements
     def _cut_tet_points(self, v, t, k):
@@ -638,7 +661,7 @@ class XFEM:
         return 2.0 / (min(ev) * float(self.scale.min()) + max(ev) * float(self.scale.max()))
 
     def pcg(self, eps, tol=1e-10, maxit=10000, green="sparse", u0=None, enr="identity",
-            scheme="cg", step=None):
+            scheme="cg", step=None, bb_rule="bb1", bb_cycle=1):
         """Linear CG of Algorithm 1 on A u = -b with the X-FFT preconditioner.
 
         Reading of Algorithm 1: f is the negative residual -b - A u, z = A d is the linear part
@@ -648,9 +671,15 @@ class XFEM:
         iterations.  Returns (u, info) with iteration count and residual history.
 
         The other schemes of Sec. 2.3 on the same system and preconditioner: "basic" (fixed
-        step s0 of eq. stepsize, beta = 0), "bb" (Barzilai-Borwein: the previous exact
-        line-search step, s0 first, beta = 0) and "nlcg" (nonlinear CG: fixed step s0, no line
-        search, Fletcher-Reeves beta = res^2 / res_old^2).
+        step s0 of eq. stepsize, beta = 0), "bb" (Barzilai-Borwein, beta = 0, s0 first) and
+        "nlcg" (nonlinear CG: fixed step s0, no line search, Fletcher-Reeves beta = res^2 /
+        res_old^2).  The paper cites the Barzilai-Borwein scheme without its formula; with
+        du = u_k - u_{k-1} and dg = A du (the change of the energy gradient) the classical
+        steps are ``bb_rule`` "bb1" = <du, P du> / <du, dg> and "bb2" = <du, dg> /
+        <dg, P^{-1} dg> in the metric of the preconditioner, "alt" (bb2 and bb1 in turn, bb2
+        on odd iterations), "bb1e" = <du, du> / <du, dg> and "bb2e" = <du, dg> / <dg, dg> in
+        the Euclidean metric of the scaled DOFs; ``bb_cycle`` m renews the step every m
+        iterations and keeps it in between (cyclic Barzilai-Borwein).
         """
         if not hasattr(self, "A"):
             self.assemble()
@@ -658,8 +687,11 @@ class XFEM:
         n3 = 3 * self.nFE
         if scheme not in ("cg", "basic", "bb", "nlcg"):
             raise ValueError(scheme)
+        if bb_rule not in ("bb1", "bb2", "alt", "bb1e", "bb2e") or int(bb_cycle) < 1:
+            raise ValueError(bb_rule)
         s0 = self.basic_step() if step is None else float(step)
-        prev_cauchy = s0
+        alpha = s0
+        du = dg = None
 
         def P(f):
             z = np.empty_like(f)
@@ -685,14 +717,24 @@ class XFEM:
             if k >= maxit:
                 break
             z = self.A @ d
-            cauchy = rr / float(z @ d)  # exact line search step along d
             if scheme == "cg":
-                alpha = cauchy
+                alpha = rr / float(z @ d)  # exact line search along d
             elif scheme in ("basic", "nlcg"):  # fixed step s0 (no line search)
                 alpha = s0
-            else:  # Barzilai-Borwein (BB1 in the P metric): the previous Cauchy step, s0 first
-                alpha = s0 if k == 0 else prev_cauchy
-            prev_cauchy = cauchy
+            elif k == 0:
+                alpha = s0
+            elif (k - 1) % int(bb_cycle) == 0:  # Barzilai-Borwein step from du, dg
+                rule = bb_rule if bb_rule != "alt" else ("bb2" if k % 2 == 1 else "bb1")
+                if rule == "bb1":
+                    alpha = float(du @ self._precond_metric(du, enr)) / float(du @ dg)
+                elif rule == "bb2":
+                    alpha = float(du @ dg) / float(dg @ P(dg))
+                elif rule == "bb1e":
+                    alpha = float(du @ du) / float(du @ dg)
+                else:
+                    alpha = float(du @ dg) / float(dg @ dg)
+            du = alpha * d
+            dg = alpha * z
             u += alpha * d
             f -= alpha * z
             zz = P(f)
@@ -703,6 +745,21 @@ class XFEM:
             rr = rr_new
             k += 1
         return u, {"iters": k, "converged": converged, "history": hist}
+
+    def _precond_metric(self, du, enr="identity"):
+        """P du for the metric of the preconditioner, P itself (not its inverse):
+        P = diag(A0_11, I) (eq. scaledPreconditioner) with the assembled A0_11 on the standard
+        part and the identity (or, for enr="block3", the enriched node blocks) on the scaled
+        enriched part."""
+        if not hasattr(self, "A0"):
+            self.assemble_reference()
+        n3 = 3 * self.nFE
+        out = du.copy()
+        out[:n3] = self.A0 @ du[:n3]
+        if enr == "block3":
+            F = du[n3:].reshape(3, self.nX).T
+            out[n3:] = np.einsum("jkl,jl->jk", self.Bblk, F).T.ravel()
+        return out
 
     # ------------------------------------------------------------------ post-processing
     def effective_stiffness(self, solver="direct", tol=1e-12, green="sparse"):

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libxfft.so")
 XFFT_OK, XFFT_EINVAL, XFFT_ENOMEM, XFFT_ECUDA, XFFT_ENOTCONV, XFFT_EBREAKDOWN, XFFT_ETIMEOUT, \
     XFFT_EUNSUPPORTED, XFFT_ESTATE = range(9)
 XFFT_FP64, XFFT_FP32_REFINED, XFFT_DW = 0, 1, 2
+BB_RULES = {"bb1": 0, "bb2": 1, "alt": 2, "bb1e": 3, "bb2e": 4}
 _PREC = {"fp64": XFFT_FP64, "fp32": XFFT_FP32_REFINED, "dw": XFFT_DW}
 
 EXPORTED = (
@@ -41,7 +42,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
                 ("snap_tau", C.c_double), ("enr_precond", C.c_int), ("inner_tol", C.c_double),
                 ("max_refine", C.c_int), ("poll_every", C.c_int), ("scheme", C.c_int),
-                ("step", C.c_double), ("cut_cache", C.c_int)]
+                ("step", C.c_double), ("cut_cache", C.c_int), ("bb_rule", C.c_int),
+                ("bb_cycle", C.c_int), ("enrichment", C.c_int), ("max_device_bytes", C.c_longlong)]
 
 
 class Stats(C.Structure):
@@ -155,6 +157,28 @@ def _ordered(method):
     return wrapper
 
 
+def check_noalloc_args(stride, device_index, d, q, dAd_sig=None):
+    """Shapes and devices of the tensors of ``Solver.apply_noalloc``, checked before anything is
+    launched: the library reads d and writes q and dAd_sig through raw pointers sized by the
+    number of rows k and the DOF stride, so a short or misplaced tensor would be accessed out of
+    bounds on the GPU."""
+    ts = (d, q) + (() if dAd_sig is None else (dAd_sig,))
+    if not all(_is_torch(x) for x in ts):
+        raise TypeError("apply_noalloc takes torch CUDA tensors only")
+    if d.dim() != 2 or int(d.shape[1]) != int(stride) or int(d.shape[0]) < 1:
+        raise ValueError("d must be (k, %d) with k >= 1" % stride)
+    if tuple(q.shape) != tuple(d.shape):
+        raise ValueError("q must have the shape of d")
+    if dAd_sig is not None and tuple(dAd_sig.shape) != (int(d.shape[0]), 7):
+        raise ValueError("dAd_sig must be (k, 7)")
+    import torch
+    for x in ts:
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("apply_noalloc takes contiguous float64 tensors")
+        if not x.is_cuda or x.device.index != device_index:
+            raise ValueError("tensors must be on the solver's device cuda:%d" % device_index)
+
+
 class Solver:
     """One grid on the current CUDA device (thin wrapper of ``xfft_ctx``).
 
@@ -165,7 +189,8 @@ class Solver:
 
     def __init__(self, n, length=(1.0, 1.0, 1.0), precision="fp64", tol=1e-10, maxit=10000,
                  snap_tau=0.0, inner_tol=1e-5, max_refine=20, poll_every=8, stream=None,
-                 enr_precond="identity", scheme="cg", step=0.0, cut_cache=False):
+                 enr_precond="identity", scheme="cg", step=0.0, cut_cache=False, bb_rule="bb1",
+                 bb_cycle=1, enrichment=True, max_device_bytes=0):
         L = lib()
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
@@ -187,8 +212,17 @@ class Solver:
         o.scheme = {"cg": 0, "basic": 1, "bb": 2, "nlcg": 3}[scheme]
         o.step = step
         o.cut_cache = int(bool(cut_cache))
+        o.bb_rule = BB_RULES[bb_rule]
+        o.bb_cycle = int(bb_cycle)
+        o.enrichment = int(bool(enrichment))
+        o.max_device_bytes = int(max_device_bytes)
         self.precision = precision
         self.num_phases = 0
+        try:
+            import torch
+            self.device_index = torch.cuda.current_device() if torch.cuda.is_available() else -1
+        except ImportError:
+            self.device_index = -1
         self._ctx = C.c_void_p()
         self._tstream = None
         handle = None
@@ -337,13 +371,13 @@ class Solver:
         """Allocation-free FP64 apply on caller-owned CUDA tensors (k x stride): q = A d; if
         given, dAd_sig (k x 7) receives <d, A d> and int_Y C grad^s d.  The library allocates
         nothing in this call."""
+        check_noalloc_args(self.stride, self.device_index, d, q, dAd_sig)
         k = int(d.shape[0])
-        dp, dev1 = _ptr(d, np.float64)
-        qp, dev2 = _ptr(q, np.float64)
-        sp_, dev3 = _ptr(dAd_sig, np.float64)
-        if not (dev1 and dev2 and (dAd_sig is None or dev3)):
-            raise TypeError("apply_noalloc takes CUDA tensors only")
+        dp, _ = _ptr(d, np.float64)
+        qp, _ = _ptr(q, np.float64)
+        sp_, _ = _ptr(dAd_sig, np.float64)
         check(lib().xfft_apply_noalloc(self._ctx, k, dp, qp, sp_))
+
 
     @_ordered
     def precondition(self, f, precision="fp64"):

@@ -20,6 +20,7 @@
 #include <string>
 #include <thread>
 #include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/xfft.h"
@@ -42,16 +43,22 @@ static xfft_status fail(xfft_status s, const std::string& msg) {
                   std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));              \
   } while (0)
 
+struct xfft_ctx;
+static cudaError_t dalloc_bytes(xfft_ctx* c, void** p, size_t bytes);
+static void dfree_bytes(xfft_ctx* c, void* p);
+
+// Device allocations of a context go through these two: they keep the context's byte count
+// (option max_device_bytes) and the size of every live block.
 template <typename T>
-static cudaError_t dalloc(T** p, size_t count) {
+static cudaError_t dalloc(xfft_ctx* c, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  return cudaMalloc((void**)p, count * sizeof(T));
+  return dalloc_bytes(c, (void**)p, count * sizeof(T));
 }
 
 template <typename T>
-static void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
+static void dfree(xfft_ctx* c, T*& p) {
+  if (p) dfree_bytes(c, (void*)p);
   p = nullptr;
 }
 
@@ -132,7 +139,37 @@ struct xfft_ctx {
   double pms[16] = {};
   long long plaunch[16] = {};
   unsigned long long* punits = nullptr;  // device, 16 counters
+  // device memory owned by the context (option max_device_bytes)
+  std::unordered_map<void*, size_t> blocks;
+  size_t bytes = 0;
+  // Euclidean Barzilai-Borwein steps: <d, d>, <A d, A d> partial sums
+  double* bbpart = nullptr;
 };
+
+static cudaError_t dalloc_bytes(xfft_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (c->opt.max_device_bytes > 0 && c->bytes + bytes > (size_t)c->opt.max_device_bytes)
+    return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  c->blocks[*p] = bytes;
+  c->bytes += bytes;
+  return cudaSuccess;
+}
+
+static void dfree_bytes(xfft_ctx* c, void* p) {
+  auto it = c->blocks.find(p);
+  if (it != c->blocks.end()) {
+    c->bytes -= it->second;
+    c->blocks.erase(it);
+  }
+  cudaFree(p);
+}
+
+static xfft_status noalloc_prepare(cudaStream_t stream);
 
 static cudaEvent_t prof_event(xfft_ctx* c) {
   if (!c->evpool.empty()) {
@@ -233,6 +270,10 @@ extern "C" xfft_status xfft_default_options(xfft_options* opt) {
   opt->scheme = XFFT_SCHEME_CG;
   opt->step = 0.0;
   opt->cut_cache = 0;
+  opt->bb_rule = XFFT_BB1;
+  opt->bb_cycle = 1;
+  opt->enrichment = 1;
+  opt->max_device_bytes = 0;
   return XFFT_OK;
 }
 
@@ -258,6 +299,10 @@ extern "C" xfft_status xfft_create(xfft_ctx** out, const xfft_grid* grid, const 
       o.scheme != XFFT_SCHEME_NLCG)
     return fail(XFFT_EINVAL, "unknown iteration scheme");
   if (o.cut_cache != 0 && o.cut_cache != 1) return fail(XFFT_EINVAL, "cut_cache must be 0 or 1");
+  if (o.bb_rule < XFFT_BB1 || o.bb_rule > XFFT_BB2_EUCLID || o.bb_cycle < 1)
+    return fail(XFFT_EINVAL, "unknown Barzilai-Borwein rule or bb_cycle < 1");
+  if (o.enrichment != 0 && o.enrichment != 1) return fail(XFFT_EINVAL, "enrichment must be 0 or 1");
+  if (o.max_device_bytes < 0) return fail(XFFT_EINVAL, "max_device_bytes must be >= 0");
   if (!(o.tol > 0.0) || o.maxit < 1 || o.poll_every < 1 || o.max_refine < 1 || !(o.inner_tol > 0.0))
     return fail(XFFT_EINVAL, "invalid options");
   xfft_ctx* c = new xfft_ctx();
@@ -298,29 +343,29 @@ static void drop_graphs(xfft_ctx* c) {
 
 static void free_micro(xfft_ctx* c) {
   drop_graphs(c);
-  dfree(c->Ls);
-  dfree(c->Lin);
-  dfree(c->kcache);
-  dfree(c->code);
-  dfree(c->cutcount);
-  dfree(c->enr_flag);
-  dfree(c->enr_id);
-  dfree(c->enr_nodes);
-  dfree(c->scan_tmp);
-  dfree(c->d_tot);
-  dfree(c->scale);
-  dfree(c->cut_ip);
-  dfree(c->cut_dp);
-  dfree(c->cut_fp);
-  dfree(c->D);
-  dfree(c->isD);
-  dfree(c->isF);
-  dfree(c->Doff);
-  dfree(c->eb64);
-  dfree(c->eb32);
-  dfree(c->U6);
-  dfree(c->dscale);
-  dfree(c->dscale_f);
+  dfree(c, c->Ls);
+  dfree(c, c->Lin);
+  dfree(c, c->kcache);
+  dfree(c, c->code);
+  dfree(c, c->cutcount);
+  dfree(c, c->enr_flag);
+  dfree(c, c->enr_id);
+  dfree(c, c->enr_nodes);
+  dfree(c, c->scan_tmp);
+  dfree(c, c->d_tot);
+  dfree(c, c->scale);
+  dfree(c, c->cut_ip);
+  dfree(c, c->cut_dp);
+  dfree(c, c->cut_fp);
+  dfree(c, c->D);
+  dfree(c, c->isD);
+  dfree(c, c->isF);
+  dfree(c, c->Doff);
+  dfree(c, c->eb64);
+  dfree(c, c->eb32);
+  dfree(c, c->U6);
+  dfree(c, c->dscale);
+  dfree(c, c->dscale_f);
   c->have_micro = false;
   c->have6 = false;
   c->nX = c->ncut = -1;
@@ -329,17 +374,18 @@ static void free_micro(xfft_ctx* c) {
 static void free_work(xfft_ctx* c) {
   drop_graphs(c);
   for (int k = 0; k < 6; ++k) {
-    dfree(c->v64[k]);
-    dfree(c->v32[k]);
+    dfree(c, c->v64[k]);
+    dfree(c, c->v32[k]);
   }
-  if (c->spec) cudaFree(c->spec);
+  if (c->spec) dfree_bytes(c, c->spec);
   c->spec = nullptr;
-  dfree(c->st);
-  dfree(c->act);
-  dfree(c->outer_mask);
-  dfree(c->eps_d);
-  dfree(c->partials);
-  dfree(c->red_out);
+  dfree(c, c->st);
+  dfree(c, c->act);
+  dfree(c, c->outer_mask);
+  dfree(c, c->eps_d);
+  dfree(c, c->partials);
+  dfree(c, c->red_out);
+  dfree(c, c->bbpart);
   c->cap_rhs = 0;
   c->cap_stride = 0;
   c->cap_prec = -1;
@@ -361,6 +407,7 @@ extern "C" void xfft_destroy(xfft_ctx* c) {
   }
   for (auto e : c->evpool) cudaEventDestroy(e);
   if (c->punits) cudaFree(c->punits);
+  for (auto& kv : c->blocks) cudaFree(kv.first);  // anything a failed call left behind
   delete c;
 }
 
@@ -397,21 +444,21 @@ extern "C" xfft_status xfft_set_microstructure_phases(xfft_ctx* c, int n_levelse
   }
   c->ph.nph = nph;
   c->tau = c->opt.snap_tau > 0.0 ? c->opt.snap_tau : 1e-6 * std::min(g.h[0], std::min(g.h[1], g.h[2]));
-  CU(dalloc(&c->Ls, (size_t)n_levelsets * N));
-  CU(dalloc(&c->code, N));
-  CU(dalloc(&c->cutcount, N));
-  CU(dalloc(&c->enr_flag, N));
-  CU(dalloc(&c->enr_id, N));
-  CU(dalloc(&c->scan_tmp, scan_tmp_ints(N)));
-  CU(dalloc(&c->d_tot, 4));
+  CU(dalloc(c, &c->Ls, (size_t)n_levelsets * N));
+  CU(dalloc(c, &c->code, N));
+  CU(dalloc(c, &c->cutcount, N));
+  CU(dalloc(c, &c->enr_flag, N));
+  CU(dalloc(c, &c->enr_id, N));
+  CU(dalloc(c, &c->scan_tmp, scan_tmp_ints(N)));
+  CU(dalloc(c, &c->d_tot, 8));
   const double* Ldev = L;
   if (!ptrs_on_device) {
-    CU(dalloc(&c->Lin, (size_t)n_levelsets * N));
+    CU(dalloc(c, &c->Lin, (size_t)n_levelsets * N));
     CU(cudaMemcpyAsync(c->Lin, L, n_levelsets * N * sizeof(double), cudaMemcpyHostToDevice, s));
     Ldev = c->Lin;
   }
   if (voxel_scale) {
-    CU(dalloc(&c->scale, N));
+    CU(dalloc(c, &c->scale, N));
     CU(cudaMemcpyAsync(c->scale, voxel_scale, N * sizeof(float),
                        ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     c->has_scale = true;
@@ -442,35 +489,39 @@ extern "C" xfft_status xfft_set_microstructure_phases(xfft_ctx* c, int n_levelse
     const double cmax = *std::max_element(ev, ev + 2 * nph) * smax;
     c->step0 = 2.0 / (cmin + cmax);
   }
-  ProfScope ps_setup(c, XFFT_PROF_SETUP, 14);
+  ProfScope ps_setup(c, XFFT_PROF_SETUP, 15);
+  CU(launch_count_nonfinite(Ldev, (long long)n_levelsets * N, c->has_scale ? c->scale : nullptr, N,
+                            c->d_tot + 4, s));
   CU(launch_snap_classify(Ldev, c->Ls, n_levelsets, c->code, c->cutcount, c->enr_flag, c->d_tot + 3,
-                          g, c->tau, s));
+                          g, c->tau, c->opt.enrichment ? 0 : 1, s));
   // enriched ids (scan of node flags) and cut-tet offsets (scan of per-voxel counts)
   CU(launch_scan(c->enr_flag, c->enr_id, N, c->d_tot + 0, c->scan_tmp, s));
   CU(launch_scan(c->cutcount, c->cutcount, N, c->d_tot + 1, c->scan_tmp, s));
-  int tot[4];
-  CU(cudaMemcpyAsync(tot, c->d_tot, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  int tot[8];
+  CU(cudaMemcpyAsync(tot, c->d_tot, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
+  if (tot[4] > 0) return fail(XFFT_EINVAL, "the level set holds NaN or Inf values");
+  if (tot[5] > 0) return fail(XFFT_EINVAL, "the voxel scale holds NaN or Inf values");
   if (tot[3] > 0) return fail(XFFT_EINVAL, "a tet is cut by two interfaces (one interface per element)");
   c->nX = tot[0];
   c->ncut = tot[1];
-  CU(dalloc(&c->enr_nodes, c->nX));
-  CU(dalloc(&c->cut_ip, (size_t)kCutInts * c->ncut));
-  CU(dalloc(&c->cut_dp, (size_t)kCutReals * c->ncut));
-  CU(dalloc(&c->cut_fp, (size_t)kCutReals * c->ncut));
+  CU(dalloc(c, &c->enr_nodes, c->nX));
+  CU(dalloc(c, &c->cut_ip, (size_t)kCutInts * c->ncut));
+  CU(dalloc(c, &c->cut_dp, (size_t)kCutReals * c->ncut));
+  CU(dalloc(c, &c->cut_fp, (size_t)kCutReals * c->ncut));
   CU(launch_build_lists(c->code, c->cutcount, c->enr_flag, c->enr_id, c->enr_nodes, c->cut_ip,
                         c->ncut, g, s));
   CutData cd = cutdata(c);
   CU(launch_cut_geometry(c->Ls, n_levelsets, cd, c->cut_dp, c->cut_ip, g, s));
   CU(launch_cut_eids(c->cut_ip, c->enr_id, c->ncut, s));
-  CU(dalloc(&c->D, 3 * (size_t)c->nX));
-  CU(dalloc(&c->isD, 3 * (size_t)c->nX));
-  CU(dalloc(&c->isF, 3 * (size_t)c->nX));
+  CU(dalloc(c, &c->D, 3 * (size_t)c->nX));
+  CU(dalloc(c, &c->isD, 3 * (size_t)c->nX));
+  CU(dalloc(c, &c->isF, 3 * (size_t)c->nX));
   const bool blk = c->opt.enr_precond == XFFT_ENR_BLOCK3;
   if (blk) {
-    CU(dalloc(&c->Doff, 3 * (size_t)c->nX));
-    CU(dalloc(&c->eb64, 6 * (size_t)c->nX));
-    CU(dalloc(&c->eb32, 6 * (size_t)c->nX));
+    CU(dalloc(c, &c->Doff, 3 * (size_t)c->nX));
+    CU(dalloc(c, &c->eb64, 6 * (size_t)c->nX));
+    CU(dalloc(c, &c->eb32, 6 * (size_t)c->nX));
   }
   CU(launch_cut_scaling(cd, c->D, blk ? c->Doff : nullptr, c->nX, g, s));
   CU(launch_finish_scaling(c->D, c->isD, c->isF, c->nX, s));
@@ -485,43 +536,74 @@ extern "C" xfft_status xfft_set_microstructure_phases(xfft_ctx* c, int n_levelse
   }
   CU(launch_cut_to_float(c->cut_dp, c->cut_fp, (long long)kCutReals * c->ncut, s));
   if (c->opt.precision == XFFT_FP32_REFINED && c->opt.cut_cache && c->ncut > 0) {
-    CU(dalloc(&c->kcache, (size_t)kCutPacked * c->ncut));
+    CU(dalloc(c, &c->kcache, (size_t)kCutPacked * c->ncut));
     CU(launch_cut_matrix(cd, c->isD, c->nX, g, c->ph, c->has_scale ? c->scale : nullptr, c->kcache, s));
   }
   CU(cudaEventRecord(c->ev1, s));
   CU(cudaStreamSynchronize(s));
+  {
+    const xfft_status ps = noalloc_prepare(s);
+    if (ps != XFFT_OK) return ps;
+  }
   c->have_micro = true;
   c->have6 = false;
   return XFFT_OK;
 }
 
 // ---------------------------------------------------------------- workspace
+static bool bb_euclid(const xfft_ctx* c) {
+  return c->opt.scheme == XFFT_SCHEME_BB &&
+         (c->opt.bb_rule == XFFT_BB1_EUCLID || c->opt.bb_rule == XFFT_BB2_EUCLID);
+}
+
+static FinArgs fin_args(const xfft_ctx* c, int mode, int crit, double tol, int maxit, int nparts,
+                        int nparts_used, int parity) {
+  FinArgs fa;
+  fa.scheme = c->opt.scheme;
+  fa.step0 = c->step0;
+  fa.mode = mode;
+  fa.crit = crit;
+  fa.tol = tol;
+  fa.volY = c->g.volY;
+  fa.maxit = maxit;
+  fa.nparts = nparts;
+  fa.nparts_used = nparts_used;
+  fa.set_rel = 0;
+  fa.inner_floor = 0.0;
+  fa.parity = parity;
+  fa.bb_rule = c->opt.bb_rule;
+  fa.bb_cycle = c->opt.bb_cycle;
+  fa.bbpart = nullptr;
+  return fa;
+}
+
 static xfft_status ensure_work(xfft_ctx* c, int n_rhs, int prec) {
   const long long stride = stride_of(c);
   if (c->cap_rhs >= n_rhs && c->cap_stride == stride && c->cap_prec == prec) return XFFT_OK;
   free_work(c);
   const size_t tot = (size_t)n_rhs * stride;
   if (prec == XFFT_FP64) {
-    for (int k = 0; k < 6; ++k) CU(dalloc(&c->v64[k], tot));
+    for (int k = 0; k < 6; ++k) CU(dalloc(c, &c->v64[k], tot));
   } else {
-    CU(dalloc(&c->v64[0], tot));  // u (FP64 iterate)
-    CU(dalloc(&c->v64[4], tot));  // FP64 residual
-    for (int k = 0; k < 6; ++k) CU(dalloc(&c->v32[k], tot));
+    CU(dalloc(c, &c->v64[0], tot));  // u (FP64 iterate)
+    CU(dalloc(c, &c->v64[4], tot));  // FP64 residual
+    for (int k = 0; k < 6; ++k) CU(dalloc(c, &c->v32[k], tot));
   }
   c->spec_bytes = (size_t)n_rhs * fft_spectrum_elems(c->fft) * (prec == XFFT_FP64 ? 16 : 8);
-  CU(cudaMalloc(&c->spec, c->spec_bytes));
-  CU(dalloc(&c->st, 64));
-  CU(dalloc(&c->act, 64));
-  CU(dalloc(&c->outer_mask, 64));
-  CU(dalloc(&c->eps_d, 6 * 64));
+  CU(dalloc_bytes(c, &c->spec, c->spec_bytes));
+  CU(dalloc(c, &c->st, 64));
+  CU(dalloc(c, &c->act, 64));
+  CU(dalloc(c, &c->outer_mask, 64));
+  CU(dalloc(c, &c->eps_d, 6 * 64));
   const int na = apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut);
   const int np =
       std::max(precondition_blocks(c->fft, c->nX, true), precondition_blocks(c->fft, c->nX, false));
   const int ng = grad_blocks_uncut(c->g) + grad_blocks_cut(c->ncut);
   const int nparts = std::max(na, np);
   c->partials_count = std::max((size_t)n_rhs * 7 * nparts, (size_t)kGradValues * ng);
-  CU(dalloc(&c->partials, c->partials_count));
-  CU(dalloc(&c->red_out, 64));
+  CU(dalloc(c, &c->partials, c->partials_count));
+  CU(dalloc(c, &c->red_out, 64));
+  if (bb_euclid(c)) CU(dalloc(c, &c->bbpart, (size_t)n_rhs * 2 * kBBParts));
   c->cap_rhs = n_rhs;
   c->cap_stride = stride;
   c->cap_prec = prec;
@@ -610,20 +692,14 @@ static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev
     CU(launch_apply_cut<A>(fz ? fdnew : d, q, isd_of<T>(c), cutdata(c), a, n_rhs, c->stream));
   }
   if (fin_mode >= 0) {
+    FinArgs fa = fin_args(c, fin_mode, crit, tol, maxit, a.nparts,
+                          apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut), parity);
+    if (fin_mode == 1 && bb_euclid(c) && c->bbpart) {
+      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+      CU(launch_bb_dots<T>(fz ? fdnew : d, q, active, stride_of(c), n_rhs, c->bbpart, c->stream));
+      fa.bbpart = c->bbpart;
+    }
     ProfScope ps(c, XFFT_PROF_FINALIZE, 1);
-    FinArgs fa;
-    fa.scheme = c->opt.scheme;
-    fa.step0 = c->step0;
-    fa.mode = fin_mode;
-    fa.crit = crit;
-    fa.tol = tol;
-    fa.volY = c->g.volY;
-    fa.maxit = maxit;
-    fa.nparts = a.nparts;
-    fa.nparts_used = apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut);
-    fa.set_rel = 0;
-    fa.inner_floor = 0.0;
-    fa.parity = parity;
     CU(launch_finalize(c->st, c->partials, fa, n_rhs, c->act, c->stream));
   }
   return XFFT_OK;
@@ -643,19 +719,10 @@ static xfft_status do_prec(xfft_ctx* c, T* f, T* z, int n_rhs, const int* active
   }
   if (fin_mode >= 0) {
     ProfScope ps(c, XFFT_PROF_FINALIZE, 1);
-    FinArgs fa;
-    fa.scheme = c->opt.scheme;
-    fa.step0 = c->step0;
-    fa.mode = fin_mode;
-    fa.crit = crit;
-    fa.tol = tol;
-    fa.volY = c->g.volY;
-    fa.maxit = maxit;
-    fa.nparts = nparts;
-    fa.nparts_used = precondition_blocks(c->fft, c->nX, sizeof(T) == 8);
+    FinArgs fa = fin_args(c, fin_mode, crit, tol, maxit, nparts,
+                          precondition_blocks(c->fft, c->nX, sizeof(T) == 8), parity);
     fa.set_rel = set_rel;
     fa.inner_floor = c->opt.inner_tol;
-    fa.parity = parity;
     CU(launch_finalize(c->st, c->partials, fa, n_rhs, c->act, c->stream));
   }
   return XFFT_OK;
@@ -913,8 +980,13 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
     }
     TRY(cg_loop<float>(c, du, f, d, d2, z, q, n_rhs, 0.5, 1, c->opt.maxit));
     TRY(read_states(c, n_rhs));
-    for (int r = 0; r < n_rhs; ++r)
+    for (int r = 0; r < n_rhs; ++r) {
       if (hmask[r]) R->iters[r] += c->h_st[r].iters;
+      if (hmask[r] && c->h_st[r].status == 5) {  // breakdown inside the inner solve
+        pending[r] = 0;
+        R->status[r] = 5;
+      }
+    }
     {
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
       CU(launch_add_to_double<float>(u, du, stride, n_rhs, c->outer_mask, s));
@@ -1011,7 +1083,7 @@ extern "C" xfft_status xfft_solve(xfft_ctx* c, int n_rhs, const double* eps_bar,
     double* out = voxel_stress;
     double* tmp = nullptr;
     if (!ptrs_on_device) {
-      CU(dalloc(&tmp, (size_t)n_rhs * 6 * g.N));
+      CU(dalloc(c, &tmp, (size_t)n_rhs * 6 * g.N));
       out = tmp;
     }
     ApplyArgs a = apply_args(c, c->eps_d, nullptr);
@@ -1023,7 +1095,7 @@ extern "C" xfft_status xfft_solve(xfft_ctx* c, int n_rhs, const double* eps_bar,
       CU(cudaMemcpyAsync(voxel_stress, tmp, (size_t)n_rhs * 6 * g.N * sizeof(double),
                          cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
-      cudaFree(tmp);
+      dfree(c, tmp);
     }
   }
   CU(cudaStreamSynchronize(s));
@@ -1060,7 +1132,7 @@ extern "C" xfft_status xfft_effective_stiffness(xfft_ctx* c, double C_eff[36], x
     return rs;
   }
   const long long stride = stride_of(c);
-  if (!c->U6) CU(dalloc(&c->U6, 6 * (size_t)stride));
+  if (!c->U6) CU(dalloc(c, &c->U6, 6 * (size_t)stride));
   CU(cudaMemcpyAsync(c->U6, c->v64[0], 6 * (size_t)stride * sizeof(double), cudaMemcpyDeviceToDevice,
                      c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -1140,7 +1212,7 @@ extern "C" xfft_status xfft_grad_phases(xfft_ctx* c, const double dL_dCeff[36], 
   a.partials = c->partials;
   a.nparts = grad_blocks_uncut(g) + grad_blocks_cut(c->ncut);
   a.part_offset_cut = grad_blocks_uncut(g);
-  if (!c->dscale) CU(dalloc(&c->dscale, g.N));
+  if (!c->dscale) CU(dalloc(c, &c->dscale, g.N));
   {
     ProfScope ps(c, XFFT_PROF_GRAD, 3);
     CU(launch_grad(c->U6, c->isD, cutdata(c), a, c->dscale, c->opt.precision == XFFT_FP32_REFINED, s));
@@ -1153,7 +1225,7 @@ extern "C" xfft_status xfft_grad_phases(xfft_ctx* c, const double dL_dCeff[36], 
     if (ptrs_on_device) {
       CU(launch_scale_copy<double, float>(c->dscale, dL_dscale, 1.0, g.N, 1, nullptr, s));
     } else {
-      if (!c->dscale_f) CU(dalloc(&c->dscale_f, g.N));
+      if (!c->dscale_f) CU(dalloc(c, &c->dscale_f, g.N));
       CU(launch_scale_copy<double, float>(c->dscale, c->dscale_f, 1.0, g.N, 1, nullptr, s));
       CU(cudaMemcpyAsync(dL_dscale, c->dscale_f, g.N * sizeof(float), cudaMemcpyDeviceToHost, s));
     }
@@ -1206,10 +1278,13 @@ static xfft_status apply_entry(xfft_ctx* c, int n_rhs, const double* d, const do
   double* scratch = nullptr;
   T* dd = nullptr;
   T* qq = nullptr;
-  CU(dalloc(&scratch, tot));
-  CU(dalloc(&dd, tot));
-  CU(dalloc(&qq, tot));
-  xfft_status st = stage_in<T>(c, d, dd, tot, on_dev, scratch);
+  cudaError_t ea = dalloc(c, &scratch, tot);
+  if (ea == cudaSuccess) ea = dalloc(c, &dd, tot);
+  if (ea == cudaSuccess) ea = dalloc(c, &qq, tot);
+  xfft_status st = XFFT_OK;
+  if (ea != cudaSuccess)
+    st = fail(ea == cudaErrorMemoryAllocation ? XFFT_ENOMEM : XFFT_ECUDA, cudaGetErrorString(ea));
+  if (st == XFFT_OK) st = stage_in<T>(c, d, dd, tot, on_dev, scratch);
   if (st == XFFT_OK && eps_bar) st = upload_eps(c, n_rhs, eps_bar);
   if (st == XFFT_OK)
     st = do_apply<T, A>(c, dd, qq, eps_bar ? c->eps_d : nullptr, n_rhs, nullptr, -1, 0, 0, 0, nullptr,
@@ -1228,9 +1303,9 @@ static xfft_status apply_entry(xfft_ctx* c, int n_rhs, const double* d, const do
       for (int k = 0; k < 6; ++k) sigma_int[6 * r + k] = red[7 * r + 1 + k];
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
-  cudaFree(scratch);
-  cudaFree(dd);
-  cudaFree(qq);
+  dfree(c, scratch);
+  dfree(c, dd);
+  dfree(c, qq);
   if (st == XFFT_OK && e != cudaSuccess) st = fail(XFFT_ECUDA, cudaGetErrorString(e));
   return st;
 }
@@ -1258,12 +1333,16 @@ static xfft_status prec_entry(xfft_ctx* c, int n_rhs, const double* f, double* z
   T* zz = nullptr;
   void* spec_save = c->spec;
   void* spec = nullptr;
-  CU(dalloc(&scratch, tot));
-  CU(dalloc(&ff, tot));
-  CU(dalloc(&zz, tot));
-  CU(cudaMalloc(&spec, (size_t)n_rhs * fft_spectrum_elems(c->fft) * sizeof(T) * 2));
-  c->spec = spec;
-  xfft_status st = stage_in<T>(c, f, ff, tot, on_dev, scratch);
+  cudaError_t ea = dalloc(c, &scratch, tot);
+  if (ea == cudaSuccess) ea = dalloc(c, &ff, tot);
+  if (ea == cudaSuccess) ea = dalloc(c, &zz, tot);
+  if (ea == cudaSuccess) ea = dalloc_bytes(c, &spec, (size_t)n_rhs * fft_spectrum_elems(c->fft) * sizeof(T) * 2);
+  xfft_status st = XFFT_OK;
+  if (ea != cudaSuccess)
+    st = fail(ea == cudaErrorMemoryAllocation ? XFFT_ENOMEM : XFFT_ECUDA, cudaGetErrorString(ea));
+  else
+    c->spec = spec;
+  if (st == XFFT_OK) st = stage_in<T>(c, f, ff, tot, on_dev, scratch);
   if (st == XFFT_OK) st = do_prec<T>(c, ff, zz, n_rhs, nullptr, -1, 0, 0, 0);
   if (st == XFFT_OK) st = stage_out<T>(c, zz, z, tot, on_dev, scratch);
   if (st == XFFT_OK && rr) {
@@ -1278,10 +1357,10 @@ static xfft_status prec_entry(xfft_ctx* c, int n_rhs, const double* f, double* z
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
   c->spec = spec_save;
-  cudaFree(spec);
-  cudaFree(scratch);
-  cudaFree(ff);
-  cudaFree(zz);
+  if (spec) dfree_bytes(c, spec);
+  dfree(c, scratch);
+  dfree(c, ff);
+  dfree(c, zz);
   if (st == XFFT_OK && e != cudaSuccess) st = fail(XFFT_ECUDA, cudaGetErrorString(e));
   return st;
 }
@@ -1355,18 +1434,33 @@ static __device__ __align__(256) double g_noalloc_scratch[XFFT_NOALLOC_MAX_RHS *
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_ptr[64] = {};
 
-static xfft_status noalloc_scratch(double** out) {
+// Device address of the scratch array on the current device, looked up once per device.
+// stream: when the address is not cached yet and this stream is being captured, the lookup
+// (which may initialise the module on the device) is refused with XFFT_ESTATE.
+static xfft_status noalloc_scratch(double** out, cudaStream_t stream) {
   int dev = 0;
   CU(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(XFFT_EUNSUPPORTED, "device index above 63");
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (stream && cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      return fail(XFFT_ESTATE,
+                  "xfft_apply_noalloc: the scratch address of this device is not known yet; make "
+                  "one call (or xfft_set_microstructure) before capturing the stream");
     void* p = nullptr;
     CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     g_noalloc_ptr[dev] = static_cast<double*>(p);
   }
   *out = g_noalloc_ptr[dev];
   return XFFT_OK;
+}
+
+// called by xfft_set_microstructure (which runs outside any capture): resolves the scratch
+// address of the current device so that xfft_apply_noalloc needs no set-up of its own
+static xfft_status noalloc_prepare(cudaStream_t stream) {
+  double* p = nullptr;
+  return noalloc_scratch(&p, stream);
 }
 
 extern "C" xfft_status xfft_apply_noalloc(xfft_ctx* c, int n_rhs, const double* d, double* q,
@@ -1379,7 +1473,7 @@ extern "C" xfft_status xfft_apply_noalloc(xfft_ctx* c, int n_rhs, const double* 
   if (nparts > XFFT_NOALLOC_MAX_PARTS)
     return fail(XFFT_EINVAL, "grid too large for the fixed scratch of xfft_apply_noalloc");
   double* scratch = nullptr;
-  TRY(noalloc_scratch(&scratch));
+  TRY(noalloc_scratch(&scratch, c->stream));
   ApplyArgs a;
   a.g = c->g;
   a.ph = c->ph;

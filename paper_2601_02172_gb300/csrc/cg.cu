@@ -177,6 +177,42 @@ template cudaError_t launch_add_to_double<float>(double*, const float*, long lon
 template cudaError_t launch_add_to_double<double>(double*, const double*, long long, int,
                                                   const int*, cudaStream_t);
 
+// <d, d> and <q, q> per right-hand side (Euclidean Barzilai-Borwein steps): kBBParts blocks
+// per right-hand side write their partial sums, the finalisation adds them in a fixed order
+template <typename T>
+__global__ void k_bb_dots(const T* __restrict__ d, const T* __restrict__ q, const int* __restrict__ active,
+                          long long stride, double* __restrict__ part) {
+  __shared__ double red[2 * 32];
+  const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;  // uniform per block
+  const T* dr = d + rhs * stride;
+  const T* qr = q + rhs * stride;
+  double v[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < stride;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double x = (double)dr[i], y = (double)qr[i];
+    v[0] += x * x;
+    v[1] += y * y;
+  }
+  double tot[2];
+  block_sum<2>(v, red, tot);
+  if (threadIdx.x == 0) {
+    part[((long long)rhs * 2 + 0) * kBBParts + blockIdx.x] = tot[0];
+    part[((long long)rhs * 2 + 1) * kBBParts + blockIdx.x] = tot[1];
+  }
+}
+
+template <typename T>
+cudaError_t launch_bb_dots(const T* d, const T* q, const int* active, long long stride, int n_rhs,
+                           double* part, cudaStream_t s) {
+  k_bb_dots<T><<<dim3(kBBParts, n_rhs), 256, 0, s>>>(d, q, active, stride, part);
+  return cudaGetLastError();
+}
+template cudaError_t launch_bb_dots<float>(const float*, const float*, const int*, long long, int,
+                                           double*, cudaStream_t);
+template cudaError_t launch_bb_dots<double>(const double*, const double*, const int*, long long, int,
+                                            double*, cudaStream_t);
+
 // ---------------------------------------------------------------- finalisation
 __device__ inline bool stop_rule(const RhsState& s, const FinArgs& fa) {
   if (!(s.rr > 0.0)) return true;
@@ -205,6 +241,7 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
   if (fa.mode == 0) {
     for (int k = 0; k < 6; ++k) s.sig[k] = tot[1 + k];
   } else if (fa.mode == 1) {
+    const double dq_prev = s.dq;
     s.dq = tot[0];
     for (int k = 0; k < 6; ++k) s.sd[k] = tot[1 + k];
     const double a = s.rr / s.dq;
@@ -214,9 +251,41 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
       s.alpha = 0.0;
       s.dpar = fa.parity;
     } else {
-      // 0 CG: exact line search; 1 basic and 3 nonlinear CG: fixed step s0; 2 BB: previous Cauchy
-      const double step = (fa.scheme == 1 || fa.scheme == 3) ? fa.step0
-                          : fa.scheme == 2 ? (s.iters == 0 ? fa.step0 : s.cauchy) : a;
+      // 0 CG: exact line search; 1 basic and 3 nonlinear CG: fixed step s0; 2 BB: a step from
+      // the previous iteration's differences du = s d, dg = s A d (steepest-descent directions
+      // d = P^-1 f), s0 first
+      double step = a;
+      if (fa.scheme == 1 || fa.scheme == 3) {
+        step = fa.step0;
+      } else if (fa.scheme == 2) {
+        double dd = 0.0, qq = 0.0;
+        if (fa.bbpart) {  // (thread 0 only from here on) fixed-order sum of the block partials
+          for (int i = 0; i < kBBParts; ++i) {
+            dd += fa.bbpart[((long long)rhs * 2 + 0) * kBBParts + i];
+            qq += fa.bbpart[((long long)rhs * 2 + 1) * kBBParts + i];
+          }
+        }
+        if (s.iters == 0) {
+          step = fa.step0;
+        } else if (fa.bb_cycle > 1 && (s.iters - 1) % fa.bb_cycle != 0) {
+          step = s.bb_step;  // cyclic rule: keep the step of the cycle
+        } else {
+          const double sp = s.alpha;  // previous step
+          // BB1 in the P metric: <du, P du> / <du, dg> = rr_prev / <d, A d>_prev (the previous
+          // exact line-search step); BB2 in the P metric: <du, dg> / <dg, P^-1 dg> with
+          // <dg, P^-1 dg> = rr - rr_prev + 2 s <d, A d>_prev (d = P^-1 f_prev)
+          const double bb1 = s.cauchy;
+          const double den2 = s.rr - s.rr_prev + 2.0 * sp * dq_prev;
+          const double bb2 = sp * sp * dq_prev / den2;
+          const double bb1e = s.dd / dq_prev, bb2e = dq_prev / s.qq;
+          const int rule = fa.bb_rule == 2 ? ((s.iters & 1) ? 1 : 0) : fa.bb_rule;  // BB2 on odd
+          step = rule == 0 ? bb1 : rule == 1 ? bb2 : rule == 3 ? bb1e : bb2e;
+          if (!(step > 0.0) || !isfinite(step)) step = bb1;  // safeguard: BB1 is positive
+        }
+        s.bb_step = step;
+        s.dd = dd;
+        s.qq = qq;
+      }
       s.cauchy = a;
       s.alpha = step;
       for (int k = 0; k < 6; ++k) s.sig[k] += step * s.sd[k];
@@ -247,6 +316,7 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
     } else {
       // Fletcher-Reeves momentum for linear and nonlinear CG; basic and BB: steepest descent
       s.beta = ((fa.scheme == 0 || fa.scheme == 3) && s.rr > 0.0) ? rr / s.rr : 0.0;
+      s.rr_prev = s.rr;
       s.rr = rr;
       s.iters += 1;
       s.dpar = fa.parity;
@@ -273,6 +343,7 @@ __global__ void k_init_state(RhsState* st, int* act, int n_rhs, const int* mask)
   if (r >= n_rhs) return;
   RhsState s;
   s.rr = s.rr0 = s.dq = s.alpha = s.beta = s.rel = s.cauchy = 0.0;
+  s.rr_prev = s.dd = s.qq = s.bb_step = 0.0;
   for (int k = 0; k < 6; ++k) s.sig[k] = s.sd[k] = 0.0;
   s.active = mask ? mask[r] : 1;
   s.dpar = 0;

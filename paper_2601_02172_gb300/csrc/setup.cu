@@ -38,7 +38,8 @@ __global__ void k_snap(const double* __restrict__ L, double* __restrict__ Ls, lo
 }
 
 __global__ void k_classify(const double* __restrict__ Ls, int nL, GridDev g, uint16_t* __restrict__ code,
-                           int* __restrict__ cutcount, int* __restrict__ enr_flag, int* __restrict__ bad) {
+                           int* __restrict__ cutcount, int* __restrict__ enr_flag, int* __restrict__ bad,
+                           int p1) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.N;
        v += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(v % g.n2);
@@ -51,6 +52,25 @@ __global__ void k_classify(const double* __restrict__ Ls, int nL, GridDev g, uin
     for (int l = 0; l < nL; ++l)
 #pragma unroll
       for (int c = 0; c < 8; ++c) Lc[l][c] = Ls[l * g.N + nd[c]];
+    if (p1) {
+      // P1 baseline (voxel-segmented, no enrichment): the voxel takes the phase of its centre,
+      // where the trilinear interpolant of the corner values is their mean; the first level
+      // set negative there decides (phase nL if none is)
+      int ph = nL;
+      for (int l = nL - 1; l >= 0; --l) {
+        double m = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) m += Lc[l][c];
+        if (m * 0.125 < 0.0) ph = l;
+      }
+      const unsigned pc = phase_code(ph);
+      unsigned cd = 0;
+#pragma unroll
+      for (int t = 0; t < 6; ++t) cd |= pc << (2 * t);
+      code[v] = (uint16_t)cd;
+      cutcount[v] = 0;
+      continue;
+    }
     unsigned cd = 0;
     int cnt = 0;
     bool two = false;
@@ -82,8 +102,33 @@ __global__ void k_classify(const double* __restrict__ Ls, int nL, GridDev g, uin
   }
 }
 
+// number of non-finite level-set values and of non-finite scale values (host validation)
+__global__ void k_count_nonfinite(const double* __restrict__ L, long long nL, const float* __restrict__ sc,
+                                  long long ns, int* __restrict__ out) {
+  int bl = 0, bs = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nL;
+       i += (long long)gridDim.x * blockDim.x)
+    bl += isfinite(L[i]) ? 0 : 1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ns;
+       i += (long long)gridDim.x * blockDim.x)
+    bs += isfinite(sc[i]) ? 0 : 1;
+  if (bl) atomicAdd(out, bl);
+  if (bs) atomicAdd(out + 1, bs);
+}
+
+cudaError_t launch_count_nonfinite(const double* L, long long nL, const float* sc, long long ns,
+                                   int* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  long long nb = ((nL > ns ? nL : ns) + kThreads - 1) / kThreads;
+  if (nb > 152 * 16) nb = 152 * 16;
+  if (nb < 1) nb = 1;
+  k_count_nonfinite<<<(int)nb, kThreads, 0, s>>>(L, nL, sc, sc ? ns : 0, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_snap_classify(const double* L, double* Ls, int nL, uint16_t* code, int* cutcount,
-                                 int* enr_flag, int* bad, GridDev g, double tau, cudaStream_t s) {
+                                 int* enr_flag, int* bad, GridDev g, double tau, int p1, cudaStream_t s) {
   if (nL < 1 || nL > kMaxPhases - 1) return cudaErrorInvalidValue;
   const int nb = (int)((g.N + kThreads - 1) / kThreads);
   const int grid = nb < 65535 * 16 ? nb : 65535 * 16;
@@ -92,7 +137,7 @@ cudaError_t launch_snap_classify(const double* L, double* Ls, int nL, uint16_t* 
   e = cudaMemsetAsync(bad, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_snap<<<grid, kThreads, 0, s>>>(L, Ls, nL * g.N, tau);
-  k_classify<<<grid, kThreads, 0, s>>>(Ls, nL, g, code, cutcount, enr_flag, bad);
+  k_classify<<<grid, kThreads, 0, s>>>(Ls, nL, g, code, cutcount, enr_flag, bad, p1);
   return cudaGetLastError();
 }
 

@@ -130,6 +130,9 @@ struct RhsState {
   int converged;
   int dpar;         // which of the two direction buffers holds the last direction d
   double cauchy;    // rr / <d, A d> of the last iteration (Barzilai-Borwein step)
+  double rr_prev;   // f^T P^-1 f one iteration earlier (Barzilai-Borwein BB2 step)
+  double dd, qq;    // <d, d> and <A d, A d> of the last iteration (Euclidean BB steps)
+  double bb_step;   // step in use by the cyclic Barzilai-Borwein rule
 };
 
 }  // namespace xfft

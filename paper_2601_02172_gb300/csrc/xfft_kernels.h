@@ -37,8 +37,12 @@ __host__ __device__ constexpr int midx(int b, int c) {
 
 // ---- setup (setup.cu)
 // nL level sets (node order, nL x N); *bad (device int) counts tets cut by two interfaces
+// p1 = 1: the P1 baseline (no cut tets, each voxel in the phase of its centre)
 cudaError_t launch_snap_classify(const double* L, double* Ls, int nL, uint16_t* code, int* cutcount,
-                                 int* enr_flag, int* bad, GridDev g, double tau, cudaStream_t s);
+                                 int* enr_flag, int* bad, GridDev g, double tau, int p1, cudaStream_t s);
+// out[0] = non-finite values among L (nL doubles), out[1] among sc (ns floats; sc may be null)
+cudaError_t launch_count_nonfinite(const double* L, long long nL, const float* sc, long long ns,
+                                   int* out, cudaStream_t s);
 // exclusive scan of n ints into out (may alias in); writes the total to *d_total (device)
 cudaError_t launch_scan(const int* in, int* out, long long n, int* d_total, int* d_tmp,
                         cudaStream_t s);
@@ -168,7 +172,18 @@ struct FinArgs {
   // step rr / <d, A d>, step0 first), 3 nonlinear CG (fixed step step0, Fletcher-Reeves momentum)
   int scheme;
   double step0;
+  // Barzilai-Borwein step rule (scheme 2): 0 BB1 and 1 BB2 in the metric of P, 2 BB1 and BB2
+  // alternating, 3 BB1 and 4 BB2 in the Euclidean metric of the scaled DOFs (these read
+  // bbpart); the step is renewed every bb_cycle iterations and kept in between
+  int bb_rule;
+  int bb_cycle;
+  const double* bbpart;  // [rhs][2][kBBParts]: <d, d> and <A d, A d> partial sums, or nullptr
 };
+constexpr int kBBParts = 256;
+// <d, d> and <q, q> per right-hand side into part[rhs][2][kBBParts] (Euclidean BB steps)
+template <typename T>
+cudaError_t launch_bb_dots(const T* d, const T* q, const int* active, long long stride, int n_rhs,
+                           double* part, cudaStream_t s);
 // act[rhs] mirrors st[rhs].active for the kernels' early exit
 cudaError_t launch_finalize(RhsState* st, const double* partials, FinArgs fa, int n_rhs, int* act,
                             cudaStream_t s);

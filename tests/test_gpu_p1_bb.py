@@ -1,0 +1,110 @@
+"""GPU <-> oracle parity of the P1 baseline (enrichment off, the discretization table of
+Sec. 4.1) and of the Barzilai-Borwein step rules (Sec. 2.3), through the C-ABI.
+
+P1: the voxel phases (tet codes) are bit-exact, C_eff matches the oracle's P1 system to 1e-10
+(FP64) / 1e-6 (FP32-refined).  On Hashin's neutral inclusion (Sec. 4.2, K_eff = K_matrix = 1)
+X-FEM converges about quadratically in h and P1 about linearly (the accuracy study of Sec.
+4.2 with the table's P1 discretization).
+
+Barzilai-Borwein: for each step rule the GPU's FP64 iteration count equals the oracle's within
+two iterations and the solution is the direct one.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import XFEM
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2601_02172_gb300 as pkg
+    return pkg
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def _ragged():
+    n = (10, 12, 8)
+    L = np.minimum(synth.sphere_levelset(n, (0.3, 0.4, 0.5), 0.22),
+                   synth.sphere_levelset(n, (0.8, 0.85, 0.2), 0.15))
+    return n, L, synth.lame_from_E_nu(20.0, 0.2), synth.lame_from_E_nu(1.0, 0.3), synth.voxel_scale(n, 3)
+
+
+def test_p1_setup_and_effective_stiffness_match_oracle(xf):
+    n, L, lm, lp, sc = _ragged()
+    o = XFEM(L, n, lame_minus=lm, lame_plus=lp, scale=sc, enrichment=False)
+    s = xf.Solver(n, tol=1e-12, enrichment=False)
+    s.set_microstructure(L, lm, lp, sc)
+    assert s.num_enriched == 0 and s.num_cut_tets == 0
+    _, _, code = s.setup_info()
+    exp = np.zeros(o.nvox, dtype=np.uint16)
+    for t in range(6):
+        exp |= o.tet_phase[:, t].astype(np.uint16) << (2 * t)
+    assert np.array_equal(code, exp)
+    C, st = s.effective_stiffness()
+    assert st["converged"]
+    o.assemble()
+    Cref = np.zeros((6, 6))
+    for k in range(6):
+        e = np.eye(6)[k]
+        Cref[:, k] = o.mean_stress(o.solve_direct(e), e)
+    assert np.abs(C - Cref).max() < 1e-10 * np.abs(Cref).max()
+    s32 = xf.Solver(n, precision="fp32", tol=1e-9, enrichment=False)
+    s32.set_microstructure(L, lm, lp, sc)
+    C32, st32 = s32.effective_stiffness()
+    assert st32["converged"] and np.abs(C32 - Cref).max() < 1e-6 * np.abs(Cref).max()
+    # the gradient runs on the P1 system too (no cut tets): Euler homogeneity in the moduli
+    G = np.random.default_rng(1).normal(size=(6, 6))
+    dl, _, Ce = s.grad(G, scale_grad=False)
+    lame = np.array([lm[0], lm[1], lp[0], lp[1]])
+    assert abs(dl @ lame - np.sum(G * Ce)) < 1e-9 * np.abs(G * Ce).sum()
+
+
+def _hashin_K(xf, N, enrichment):
+    Ls, ph, ell = synth.hashin_neutral_inclusion(N)
+    s = xf.Solver((N, N, N), ell, precision="fp32", tol=1e-8, enrichment=enrichment)
+    s.set_microstructure_phases(Ls, ph)
+    out = s.solve(np.array([[1.0, 1.0, 1.0, 0.0, 0.0, 0.0]]), u=False)
+    assert out["converged"]
+    return out["mean_stress"][0, :3].sum() / 9.0
+
+
+def test_hashin_convergence_xfem_against_p1(xf):
+    """K_eff - 1 on Hashin's neutral inclusion at N = 16 ... 128: X-FEM is far more accurate
+    than P1 at every N, its error falls faster (about h^2 against h for P1)."""
+    Ns = (16, 32, 64, 128)
+    ex = [abs(_hashin_K(xf, N, True) - 1.0) for N in Ns]
+    e1 = [abs(_hashin_K(xf, N, False) - 1.0) for N in Ns]
+    for a, b in zip(ex, e1):
+        assert a < 0.2 * b, (ex, e1)
+    # observed orders over N = 16 -> 64 (X-FEM reaches its floor near N = 128 at tol 1e-8)
+    px = np.log2(ex[0] / ex[2]) / 2
+    p1 = np.log2(e1[0] / e1[2]) / 2
+    assert px > 1.5 and 0.5 < p1 < 1.5, (px, p1, ex, e1)
+
+
+@pytest.mark.parametrize("rule,cycle", [("bb1", 1), ("bb2", 1), ("alt", 1), ("bb2e", 1), ("bb1", 3)])
+def test_bb_rules_match_oracle(xf, rule, cycle):
+    n = (16, 16, 16)
+    L = synth.sphere_levelset(n, (0.5, 0.5, 0.5), 0.3)
+    lm, lp = synth.lame_from_E_nu(10.0, 0.3), synth.lame_from_E_nu(1.0, 0.3)
+    o = XFEM(L, n, lame_minus=lm, lame_plus=lp)
+    eps = np.array([[0.2, -0.1, 0.3, 0.4, -0.2, 0.1]])
+    u_ref = o.solve_direct(eps[0])
+    _, info = o.pcg(eps[0], tol=1e-10, maxit=5000, scheme="bb", green="fft", bb_rule=rule, bb_cycle=cycle)
+    s = xf.Solver(n, tol=1e-10, maxit=5000, scheme="bb", bb_rule=rule, bb_cycle=cycle)
+    s.set_microstructure(L, lm, lp)
+    out = s.solve(eps, u=True)
+    assert out["converged"], out["stats"]
+    assert abs(out["stats"]["iters"][0] - info["iters"]) <= 2, (out["stats"]["iters"], info["iters"])
+    assert _rel(out["u_std"][0], u_ref[: 3 * o.nFE].reshape(3, -1)) < 1e-8
