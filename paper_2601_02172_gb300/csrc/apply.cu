@@ -2,6 +2,7 @@
 // apply_kernels.cuh.  This unit instantiates the one-interface kernels (two phases);
 // apply_multi.cu instantiates those of two interfaces (three phases).
 #include "apply_kernels.cuh"
+#include "apply_cut.cuh"
 
 namespace xfft {
 
@@ -145,8 +146,35 @@ cudaError_t launch_apply_cut(const typename Store<T>::type* d, typename Store<T>
   if constexpr (std::is_same<T, float>::value) {
     if (a.kcache && !a.eps && !a.want_sig && cd.ncut > 0) return launch_cut_cached(d, q, cd, a, n_rhs, s);
   }
-  return a.ph.nph > 2 ? launch_cut_nph<T, 3>(d, q, isD, cd, a, n_rhs, s)
-                      : launch_cut_nph<T, 2>(d, q, isD, cd, a, n_rhs, s);
+  // launched even without cut tets: its blocks write the (zero) partial sums of their slots
+  const int nb = apply_cut_blocks(cd.ncut);
+  const bool sig = a.want_sig || a.eps;
+  constexpr size_t smem = cut_smem_bytes<T>();
+  // opt in to the staged records' shared memory, once per variant and device
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess) return ed;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_apply_cut<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_apply_cut<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_apply_cut<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  for (int r0 = 0; r0 < n_rhs; r0 += kCutMaxR) {
+    const int nr = n_rhs - r0 < kCutMaxR ? n_rhs - r0 : kCutMaxR;
+    if (a.eps)
+      k_apply_cut<T, true, true><<<nb, kCutThreads, smem, s>>>(d, q, cd, a, r0, nr);
+    else if (sig)
+      k_apply_cut<T, false, true><<<nb, kCutThreads, smem, s>>>(d, q, cd, a, r0, nr);
+    else
+      k_apply_cut<T, false, false><<<nb, kCutThreads, smem, s>>>(d, q, cd, a, r0, nr);
+  }
+  return cudaGetLastError();
 }
 
 template <typename T>

@@ -2,20 +2,13 @@
 //   q = sum_e Lambda_e^T int_e B~^T C (eps_bar + B~ d_e)        (eps_bar only in TOTAL mode)
 // with fused reductions <d, A d> = sum_e int eps(d) : C : eps(d) and int_Y C (eps_bar + grad^s d).
 //
-// Uncut tets (constant strain, one phase): a 2.5-D marching kernel.  A block of 32 x 8 threads
-// owns one voxel column each (y, z) and walks along x; node planes of d are staged in shared
-// memory, each voxel's six Kuhn tets are evaluated once, the 8 corner forces are combined
-// along z by warp shuffles and along y through shared memory, and the x direction is carried
-// in registers, so every node force is written exactly once with a plain store.
+// Uncut tets (constant strain, one phase): a 2.5-D marching kernel.  A block of kTZ x kTY
+// (16 x 16) threads owns one voxel column each (y, z) and walks along x; node planes of d are
+// staged in shared memory, each voxel's six Kuhn tets are evaluated once, the 8 corner forces are
+// combined along z by warp shuffles and along y through shared memory, and the x direction is
+// carried in registers, so every node force is written exactly once with a plain store.
 //
-// Cut tets: one thread per cut tet.  On each side s the strain is linear in the parent P1
-// functions, eps(x) = sum_b N_b E_b with E_b = eps_std + c_b sym(W) + sym(w_b (x) gamma),
-// where c_b = |L_b| - s L_b, gamma = sum_b c_b grad N_b (modified abs enrichment restricted to
-// the side), w the unscaled enriched coefficients and W = sum_a w_a (x) grad N_a.  With the
-// side moments m_b = int N_b and M_bc = int N_b N_c every integral is exact:
-//   std force  q_a   = (sum_b m_b S_b) g_a
-//   enr force  q~_a  = D_a^{-1/2} [ (sum_b (sum_c M_bc c_c) S_b) g_a + (sum_b M_ab S_b) gamma ]
-// with S_b = C_s E_b.  Contributions are scatter-added with atomics after the uncut kernel.
+// Cut tets: apply_cut.cuh (one thread per cut tet, atomics after the uncut kernel).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -560,267 +553,7 @@ __global__ void __launch_bounds__(kTZ* kTY, std::is_same<T, dw>::value     ? XFF
   }
 }
 
-// Stress of the strain sum_b alpha_b E_b on one side, E_b = es + c_b ew + sym(w_b (x) gamma):
-//   sum_b alpha_b E_b = A0 es + A1 ew + sym(W (x) gamma),  A0 = sum alpha_b, A1 = sum alpha_b c_b,
-//   W = sum alpha_b w_b.
-template <typename T>
-__device__ __forceinline__ void side_stress(const T (&al)[4], const T (&c)[4], const T (&es)[6],
-                                            const T (&ew)[6], const T (&ws)[4][3], const T (&gam)[3],
-                                            T lam, T mu, T (&st)[6]) {
-  const T A0 = al[0] + al[1] + al[2] + al[3];
-  const T A1 = al[0] * c[0] + al[1] * c[1] + al[2] * c[2] + al[3] * c[3];
-  T W[3];
-#pragma unroll
-  for (int x = 0; x < 3; ++x) W[x] = al[0] * ws[0][x] + al[1] * ws[1][x] + al[2] * ws[2][x] + al[3] * ws[3][x];
-  T e[6];
-  e[0] = A0 * es[0] + A1 * ew[0] + W[0] * gam[0];
-  e[1] = A0 * es[1] + A1 * ew[1] + W[1] * gam[1];
-  e[2] = A0 * es[2] + A1 * ew[2] + W[2] * gam[2];
-  e[3] = A0 * es[3] + A1 * ew[3] + T(0.5) * (W[1] * gam[2] + W[2] * gam[1]);
-  e[4] = A0 * es[4] + A1 * ew[4] + T(0.5) * (W[0] * gam[2] + W[2] * gam[0]);
-  e[5] = A0 * es[5] + A1 * ew[5] + T(0.5) * (W[0] * gam[1] + W[1] * gam[0]);
-  iso_stress(e, lam, mu, st);
-}
-
-// (sym 3x3 stored as 00,11,22,12,02,01) times vector
-template <typename T>
-__device__ __forceinline__ void sym_mv(const T (&s)[6], const T* v, T (&out)[3]) {
-  out[0] = s[0] * v[0] + s[5] * v[1] + s[4] * v[2];
-  out[1] = s[5] * v[0] + s[1] * v[1] + s[3] * v[2];
-  out[2] = s[4] * v[0] + s[3] * v[1] + s[2] * v[2];
-}
-
-// One thread per cut tet; the right-hand sides r0 .. r0+nr-1 are processed one after another
-// inside the thread, so the tet's geometry comes from HBM once per apply and from L1 for the
-// further right-hand sides.  Per-RHS sums are reduced per warp each tet and kept in shared
-// memory.
-// Loads that the compiler must not hoist out of the per-RHS loop (they hit L1 after the first
-// right-hand side; keeping them live in registers across the loop would spill).
-__device__ __forceinline__ int ld_keep(const int* p) {
-  int v;
-  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ float ld_keep(const float* p) {
-  float v;
-  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ double ld_keep(const double* p) {
-  double v;
-  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
-  return v;
-}
-template <typename T>
-__device__ __forceinline__ T cut_real_keep(const CutData& cd, int f, int e);
-template <>
-__device__ __forceinline__ double cut_real_keep<double>(const CutData& cd, int f, int e) {
-  return ld_keep(cd.dp + (long long)f * cd.ncut + e);
-}
-template <>
-__device__ __forceinline__ float cut_real_keep<float>(const CutData& cd, int f, int e) {
-  return ld_keep(cd.fp + (long long)f * cd.ncut + e);
-}
-template <>
-__device__ __forceinline__ dw cut_real_keep<dw>(const CutData& cd, int f, int e) {
-  return dw(ld_keep(cd.dp + (long long)f * cd.ncut + e));
-}
-
-constexpr int kCutThreads = 128;
-constexpr int kCutMaxR = 8;  // right-hand sides per launch (more are split over launches)
-
-#ifndef XFFT_CUT_MINB
-#define XFFT_CUT_MINB 4  // resident blocks per SM asked of the FP32 cut kernel
-#endif
-template <typename T, bool TOTAL, int NPH>
-__global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1
-                                               : sizeof(T) == 8       ? 2
-                                                                      : XFFT_CUT_MINB)
-    k_apply_cut(const typename Store<T>::type* __restrict__ d, typename Store<T>::type* __restrict__ q,
-                const typename Store<T>::type* __restrict__ isD, const CutData cd, const ApplyArgs a,
-                int r0, int nr) {
-  typedef typename Store<T>::type S;
-  constexpr int NW = kCutThreads / 32;
-  __shared__ double acc[kCutMaxR][7][NW];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kCutMaxR * 7 * NW; i += kCutThreads) (&acc[0][0][0])[i] = 0.0;
-  if (a.units_cut && threadIdx.x == 0 && blockIdx.x == 0) {
-    unsigned long long n = 0;
-    for (int rr = 0; rr < nr; ++rr) n += (!a.active || a.active[r0 + rr]) ? 1 : 0;
-    atomicAdd(a.units_cut, n);
-  }
-  __syncthreads();
-  const GridDev& g = a.g;
-  const long long N = g.N;
-  const int nX = a.nX;
-  const int ncut = cd.ncut;
-  const bool want_sig = a.want_sig != 0;
-  T ih[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) ih[k] = (T)(1.0 / g.h[k]);
-  T lam_ph[NPH], mu_ph[NPH];
-#pragma unroll
-  for (int p = 0; p < NPH; ++p) {
-    lam_ph[p] = (T)a.ph.lam[p];
-    mu_ph[p] = (T)a.ph.mu[p];
-  }
-  for (int base = blockIdx.x * kCutThreads; base < ncut; base += gridDim.x * kCutThreads) {
-    const int e = base + threadIdx.x;
-    const bool ok = e < ncut;
-    const T sv = (ok && a.scale) ? from_store<T>(a.scale[cd.ip[8 * ncut + e]]) : T(1);
-    for (int rr = 0; rr < nr; ++rr) {
-      const int rhs = r0 + rr;
-      if (a.active && !a.active[rhs]) continue;  // uniform over the block
-      T en = T(0);
-      T sg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-      if (ok) {
-        const S* dr = d + rhs * a.stride;
-        S* qr = q + rhs * a.stride;
-        int nd[4], ei[4];
-        T L[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          nd[k] = ld_keep(cd.ip + k * ncut + e);
-          ei[k] = ld_keep(cd.ip + (4 + k) * ncut + e);
-          L[k] = cut_real_keep<T>(cd, cut_f_L(k), e);
-        }
-        const int t = ld_keep(cd.ip + 9 * ncut + e);
-        // phases of the two sides: minus / plus with one interface, else per tet
-        const int sph = NPH == 2 ? (0 | (1 << 8)) : ld_keep(cd.ip + kCutFieldPhases * ncut + e);
-        T gr[4][3];
-        tet_grads<T>(t, ih, gr);
-        T us[4][3], ws[4][3];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            us[k][c] = from_store<T>(dr[c * N + nd[k]]);
-            ws[k][c] = from_store<T>(dr[3 * N + (long long)c * nX + ei[k]]) *
-                       from_store<T>(ld_keep(isD + (long long)c * nX + ei[k]));
-          }
-        // standard and enriched symmetric gradients (constant on the tet)
-        T es[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, ew[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          es[0] += us[k][0] * gr[k][0];
-          es[1] += us[k][1] * gr[k][1];
-          es[2] += us[k][2] * gr[k][2];
-          es[3] += T(0.5) * (us[k][1] * gr[k][2] + us[k][2] * gr[k][1]);
-          es[4] += T(0.5) * (us[k][0] * gr[k][2] + us[k][2] * gr[k][0]);
-          es[5] += T(0.5) * (us[k][0] * gr[k][1] + us[k][1] * gr[k][0]);
-          ew[0] += ws[k][0] * gr[k][0];
-          ew[1] += ws[k][1] * gr[k][1];
-          ew[2] += ws[k][2] * gr[k][2];
-          ew[3] += T(0.5) * (ws[k][1] * gr[k][2] + ws[k][2] * gr[k][1]);
-          ew[4] += T(0.5) * (ws[k][0] * gr[k][2] + ws[k][2] * gr[k][0]);
-          ew[5] += T(0.5) * (ws[k][0] * gr[k][1] + ws[k][1] * gr[k][0]);
-        }
-        if (TOTAL) {
-          T E[6];
-          mandel_to_tensor(a.eps + 6 * rhs, E);
-#pragma unroll
-          for (int k = 0; k < 6; ++k) es[k] += E[k];
-        }
-        T qs[4][3], qe[4][3];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) qs[k][c] = qe[k][c] = T(0);
-        // double-word sides run one after the other (register pressure)
-        constexpr int kSides = std::is_same<T, dw>::value ? 1 : 2;
-#pragma unroll kSides
-        for (int si = 0; si < 2; ++si) {
-          const T s = si == 0 ? T(1) : T(-1);
-          const int ph = si == 0 ? cut_phase_plus(sph) : cut_phase_minus(sph);
-          T lam, mu;
-          if (NPH == 2) {
-            lam = lam_ph[ph] * sv;
-            mu = mu_ph[ph] * sv;
-          } else {  // selects, not a local-memory array
-            lam = (ph == 0 ? lam_ph[0] : ph == 1 ? lam_ph[1] : lam_ph[NPH - 1]) * sv;
-            mu = (ph == 0 ? mu_ph[0] : ph == 1 ? mu_ph[1] : mu_ph[NPH - 1]) * sv;
-          }
-          T c[4], gam[3] = {T(0), T(0), T(0)};
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            c[b] = absval(L[b]) - s * L[b];
-#pragma unroll
-            for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
-          }
-          T MM[10];
-#pragma unroll
-          for (int k = 0; k < 10; ++k) MM[k] = cut_real_keep<T>(cd, cut_f_M(si, k), e);
-          // weights: m_b = sum_c M_bc; P_b = sum_c M_bc c_c; rows of M
-          T mw[4], pw[4];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            mw[b] = MM[midx(b, 0)] + MM[midx(b, 1)] + MM[midx(b, 2)] + MM[midx(b, 3)];
-            pw[b] = MM[midx(b, 0)] * c[0] + MM[midx(b, 1)] * c[1] + MM[midx(b, 2)] * c[2] +
-                    MM[midx(b, 3)] * c[3];
-          }
-          T sbar[6], Tt[6];
-          side_stress(mw, c, es, ew, ws, gam, lam, mu, sbar);
-          side_stress(pw, c, es, ew, ws, gam, lam, mu, Tt);
-          if (want_sig) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) sg[k] += sbar[k];
-          }
-#pragma unroll
-          for (int aa = 0; aa < 4; ++aa) {
-            const T row[4] = {MM[midx(aa, 0)], MM[midx(aa, 1)], MM[midx(aa, 2)], MM[midx(aa, 3)]};
-            T Ra[6];
-            side_stress(row, c, es, ew, ws, gam, lam, mu, Ra);
-            T v1[3], v2[3], v3[3];
-            sym_mv(sbar, gr[aa], v1);
-            sym_mv(Tt, gr[aa], v2);
-            sym_mv(Ra, gam, v3);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-              qs[aa][i] += v1[i];
-              qe[aa][i] += v2[i] + v3[i];
-            }
-          }
-        }
-        // <d, q> of this element (d~ q~ = w q_raw on the enriched DOFs); equals int sigma : eps
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) en += us[k][c] * qs[k][c] + ws[k][c] * qe[k][c];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            atomicAdd(&qr[c * N + nd[k]], to_store(qs[k][c]));
-            atomicAdd(&qr[3 * N + (long long)c * nX + ei[k]],
-                      to_store(qe[k][c] * from_store<T>(ld_keep(isD + (long long)c * nX + ei[k]))));
-          }
-      }
-      const double ew_sum = (double)warp_sum(red_val(en));
-      if (lane == 0) acc[rr][0][wid] += ew_sum;
-      if (want_sig) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          const double v = (double)warp_sum(red_val(sg[k]));
-          if (lane == 0) acc[rr][1 + k][wid] += v;
-        }
-      }
-    }
-  }
-  __syncthreads();
-  const double r2 = 1.41421356237309504880;
-  for (int i = threadIdx.x; i < nr * 7; i += kCutThreads) {
-    const int rr = i / 7, k = i - rr * 7;
-    const int rhs = r0 + rr;
-    if (a.active && !a.active[rhs]) continue;
-    double v = 0.0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) v += acc[rr][k][w];
-    if (k >= 4) v *= r2;
-    a.partials[((long long)rhs * 7 + k) * a.nparts + a.part_offset_cut + blockIdx.x] = v;
-  }
-}
-
-// Kernel launches of one phase count NPH (2: one interface; 3: two interfaces).  The phase
+// Stencil launches of one phase count NPH (2: one interface; 3: two interfaces).  The phase
 // counts are instantiated in separate translation units (apply.cu, apply_multi.cu).
 template <typename T, int NPH>
 cudaError_t launch_uncut_nph(const typename Store<T>::type* d, typename Store<T>::type* q,
@@ -863,26 +596,8 @@ cudaError_t launch_uncut_nph(const typename Store<T>::type* d, typename Store<T>
   return cudaGetLastError();
 }
 
-template <typename T, int NPH>
-cudaError_t launch_cut_nph(const typename Store<T>::type* d, typename Store<T>::type* q,
-                           const typename Store<T>::type* isD, CutData cd, const ApplyArgs& a,
-                           int n_rhs, cudaStream_t s) {
-  const int nb = apply_cut_blocks(cd.ncut);
-  for (int r0 = 0; r0 < n_rhs; r0 += kCutMaxR) {
-    const int nr = n_rhs - r0 < kCutMaxR ? n_rhs - r0 : kCutMaxR;
-    if (a.eps)
-      k_apply_cut<T, true, NPH><<<nb, kCutThreads, 0, s>>>(d, q, isD, cd, a, r0, nr);
-    else
-      k_apply_cut<T, false, NPH><<<nb, kCutThreads, 0, s>>>(d, q, isD, cd, a, r0, nr);
-  }
-  return cudaGetLastError();
-}
-
 #define XFFT_APPLY_INST_NPH(EXT, T, NPH)                                                         \
   EXT template cudaError_t launch_uncut_nph<T, NPH>(const Store<T>::type*, Store<T>::type*,      \
-                                                    const ApplyArgs&, int, cudaStream_t);        \
-  EXT template cudaError_t launch_cut_nph<T, NPH>(const Store<T>::type*, Store<T>::type*,        \
-                                                  const Store<T>::type*, CutData, const ApplyArgs&, \
-                                                  int, cudaStream_t);
+                                                    const ApplyArgs&, int, cudaStream_t);
 
 }  // namespace xfft

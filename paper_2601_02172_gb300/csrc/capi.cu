@@ -86,6 +86,10 @@ struct xfft_ctx {
   int* cut_ip = nullptr;
   double* cut_dp = nullptr;
   float* cut_fp = nullptr;
+  int4* cut_n4 = nullptr;
+  int4* cut_e4 = nullptr;
+  double* cut_r64 = nullptr;
+  float* cut_r32 = nullptr;
   double* D = nullptr;
   double* isD = nullptr;
   float* isF = nullptr;
@@ -227,6 +231,10 @@ static CutData cutdata(const xfft_ctx* c) {
   cd.dp = c->cut_dp;
   cd.fp = c->cut_fp;
   cd.ncut = c->ncut;
+  cd.n4 = c->cut_n4;
+  cd.e4 = c->cut_e4;
+  cd.r64 = c->cut_r64;
+  cd.r32 = c->cut_r32;
   return cd;
 }
 
@@ -357,6 +365,10 @@ static void free_micro(xfft_ctx* c) {
   dfree(c, c->cut_ip);
   dfree(c, c->cut_dp);
   dfree(c, c->cut_fp);
+  dfree(c, c->cut_n4);
+  dfree(c, c->cut_e4);
+  dfree(c, c->cut_r64);
+  dfree(c, c->cut_r32);
   dfree(c, c->D);
   dfree(c, c->isD);
   dfree(c, c->isF);
@@ -450,7 +462,7 @@ extern "C" xfft_status xfft_set_microstructure_phases(xfft_ctx* c, int n_levelse
   CU(dalloc(c, &c->enr_flag, N));
   CU(dalloc(c, &c->enr_id, N));
   CU(dalloc(c, &c->scan_tmp, scan_tmp_ints(N)));
-  CU(dalloc(c, &c->d_tot, 8));
+  CU(dalloc(c, &c->d_tot, 16));
   const double* Ldev = L;
   if (!ptrs_on_device) {
     CU(dalloc(c, &c->Lin, (size_t)n_levelsets * N));
@@ -509,8 +521,16 @@ extern "C" xfft_status xfft_set_microstructure_phases(xfft_ctx* c, int n_levelse
   CU(dalloc(c, &c->cut_ip, (size_t)kCutInts * c->ncut));
   CU(dalloc(c, &c->cut_dp, (size_t)kCutReals * c->ncut));
   CU(dalloc(c, &c->cut_fp, (size_t)kCutReals * c->ncut));
-  CU(launch_build_lists(c->code, c->cutcount, c->enr_flag, c->enr_id, c->enr_nodes, c->cut_ip,
-                        c->ncut, g, s));
+  {
+    int* chunk_tmp = nullptr;
+    CU(dalloc(c, &chunk_tmp, 2 * (size_t)chunk_ints(c->ncut)));
+    const cudaError_t eb = launch_build_lists(c->code, c->cutcount, c->enr_flag, c->enr_id, c->enr_nodes,
+                                              c->cut_ip, c->ncut, g, c->d_tot + 8, c->scan_tmp, chunk_tmp,
+                                              chunk_tmp + chunk_ints(c->ncut), s);
+    CU(cudaStreamSynchronize(s));
+    dfree(c, chunk_tmp);
+    CU(eb);
+  }
   CutData cd = cutdata(c);
   CU(launch_cut_geometry(c->Ls, n_levelsets, cd, c->cut_dp, c->cut_ip, g, s));
   CU(launch_cut_eids(c->cut_ip, c->enr_id, c->ncut, s));
@@ -535,6 +555,12 @@ extern "C" xfft_status xfft_set_microstructure_phases(xfft_ctx* c, int n_levelse
     if (hbad) return fail(XFFT_EBREAKDOWN, "an enriched 3x3 block is not positive definite");
   }
   CU(launch_cut_to_float(c->cut_dp, c->cut_fp, (long long)kCutReals * c->ncut, s));
+  CU(dalloc(c, &c->cut_n4, c->ncut));
+  CU(dalloc(c, &c->cut_e4, c->ncut));
+  CU(dalloc(c, &c->cut_r64, (size_t)kRec * c->ncut));
+  CU(dalloc(c, &c->cut_r32, (size_t)kRec * c->ncut));
+  CU(launch_cut_records(cd, c->isD, c->nX, g, c->ph, c->has_scale ? c->scale : nullptr, c->cut_n4,
+                        c->cut_e4, c->cut_r64, c->cut_r32, s));
   if (c->opt.precision == XFFT_FP32_REFINED && c->opt.cut_cache && c->ncut > 0) {
     CU(dalloc(c, &c->kcache, (size_t)kCutPacked * c->ncut));
     CU(launch_cut_matrix(cd, c->isD, c->nX, g, c->ph, c->has_scale ? c->scale : nullptr, c->kcache, s));

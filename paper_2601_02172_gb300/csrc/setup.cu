@@ -239,10 +239,8 @@ cudaError_t launch_scan(const int* in, int* out, long long n, int* d_total, int*
 }
 
 // ---------------------------------------------------------------- lists
-__global__ void k_build_lists(const uint16_t* __restrict__ code, const int* __restrict__ cutoff,
-                              const int* __restrict__ enr_flag, int* __restrict__ enr_id,
-                              int* __restrict__ enr_nodes, int* __restrict__ cut_ints, int ncut,
-                              GridDev g) {
+__global__ void k_enr_lists(const int* __restrict__ enr_flag, int* __restrict__ enr_id,
+                            int* __restrict__ enr_nodes, GridDev g) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.N;
        v += (long long)gridDim.x * blockDim.x) {
     // enr_id holds the exclusive scan of enr_flag on entry
@@ -251,26 +249,120 @@ __global__ void k_build_lists(const uint16_t* __restrict__ code, const int* __re
     } else {
       enr_id[v] = -1;
     }
-    const unsigned cd = code[v];
-    int off = cutoff[v];
-    for (int t = 0; t < 6; ++t) {
-      if (((cd >> (2 * t)) & 3u) == 2u) {
-        cut_ints[8 * ncut + off] = (int)v;  // voxel
-        cut_ints[9 * ncut + off] = t;       // tet
-        ++off;
-      }
-    }
   }
 }
 
-cudaError_t launch_build_lists(const uint16_t* code, const int* cutoff, const int* enr_flag,
-                               int* enr_id, int* enr_nodes, int* cut_ints, int ncut, GridDev g,
-                               cudaStream_t s) {
+// cut flags of Kuhn tet t per voxel (t < 0: the voxel has some cut tet)
+__global__ void k_tet_flags(const uint16_t* __restrict__ code, int t, int* __restrict__ flags, long long N) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    const unsigned cd = code[v];
+    int f = 0;
+    if (t >= 0) {
+      f = ((cd >> (2 * t)) & 3u) == kCodeCut;
+    } else {
+      for (int k = 0; k < 6; ++k) f |= ((cd >> (2 * k)) & 3u) == kCodeCut;
+    }
+    flags[v] = f;
+  }
+}
+
+// first voxel of each chunk of kChunkVoxels consecutive cut voxels (rank = exclusive scan of the
+// cut-voxel flags); first[nchunks] = N
+constexpr int kChunkVoxels = 2048;
+__global__ void k_chunk_first(const uint16_t* __restrict__ code, const int* __restrict__ rank,
+                              const int* __restrict__ ncv, int* __restrict__ first, long long N) {
+  const int nchunks = (*ncv + kChunkVoxels - 1) / kChunkVoxels;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    const unsigned cd = code[v];
+    bool cut = false;
+    for (int k = 0; k < 6; ++k) cut |= ((cd >> (2 * k)) & 3u) == kCodeCut;
+    if (cut && rank[v] % kChunkVoxels == 0) first[rank[v] / kChunkVoxels] = (int)v;
+    if (v == 0) first[nchunks] = (int)N;
+  }
+}
+
+// acc[k] = position of chunk k's first cut tet (voxel order, cutoff = scan of per-voxel counts)
+__global__ void k_chunk_init(const int* __restrict__ first, const int* __restrict__ cutoff,
+                             const int* __restrict__ ncv, int* __restrict__ acc) {
+  const int nchunks = (*ncv + kChunkVoxels - 1) / kChunkVoxels;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nchunks; k += gridDim.x * blockDim.x)
+    acc[k] = cutoff[first[k]];
+}
+
+__device__ inline int chunk_of(const int* __restrict__ first, int nchunks, long long v) {
+  int lo = 0, hi = nchunks - 1;  // largest k with first[k] <= v
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// cut tets of type t: position acc[chunk] + (their rank among the chunk's voxels cut there);
+// P = exclusive scan of the type-t flags
+__global__ void k_place_tets(const uint16_t* __restrict__ code, const int* __restrict__ P, int t,
+                             const int* __restrict__ first, const int* __restrict__ acc,
+                             const int* __restrict__ ncv, int* __restrict__ cut_ints, int ncut, long long N) {
+  const int nchunks = (*ncv + kChunkVoxels - 1) / kChunkVoxels;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+       v += (long long)gridDim.x * blockDim.x) {
+    if (((code[v] >> (2 * t)) & 3u) != kCodeCut) continue;
+    const int k = chunk_of(first, nchunks, v);
+    const int e = acc[k] + P[v] - P[first[k]];
+    cut_ints[8 * ncut + e] = (int)v;  // voxel
+    cut_ints[9 * ncut + e] = t;       // tet
+  }
+}
+
+// acc[k] += number of type-t cut tets in chunk k
+__global__ void k_chunk_advance(const int* __restrict__ P, const int* __restrict__ total_t,
+                                const int* __restrict__ first, const int* __restrict__ ncv,
+                                int* __restrict__ acc, long long N) {
+  const int nchunks = (*ncv + kChunkVoxels - 1) / kChunkVoxels;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nchunks; k += gridDim.x * blockDim.x) {
+    const int hi = first[k + 1] >= N ? *total_t : P[first[k + 1]];
+    acc[k] += hi - P[first[k]];
+  }
+}
+
+int chunk_ints(int ncut) { return ncut / kChunkVoxels + 2; }
+
+// Enriched numbering, then the cut-tet list in chunks of kChunkVoxels consecutive cut voxels,
+// inside a chunk grouped by Kuhn tet type (voxel order within a type): the apply kernels then run
+// one compile-time tet type per warp (except at the few group boundaries) while a chunk's node
+// data stays in cache.  work: N ints (enr_flag's storage, free once the enriched ids exist);
+// cutoff: exclusive scan of the per-voxel cut-tet counts; tot: 7 device ints; first, acc:
+// chunk_ints(ncut) ints each.
+cudaError_t launch_build_lists(const uint16_t* code, const int* cutoff, int* enr_flag, int* enr_id,
+                               int* enr_nodes, int* cut_ints, int ncut, GridDev g, int* tot,
+                               int* scan_tmp, int* first, int* acc, cudaStream_t s) {
   const int nb = (int)((g.N + kThreads - 1) / kThreads);
   const int grid = nb < 65535 * 16 ? nb : 65535 * 16;
-  k_build_lists<<<grid, kThreads, 0, s>>>(code, cutoff, enr_flag, enr_id, enr_nodes, cut_ints,
-                                           ncut, g);
-  return cudaGetLastError();
+  k_enr_lists<<<grid, kThreads, 0, s>>>(enr_flag, enr_id, enr_nodes, g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || ncut == 0) return e;
+  int* work = enr_flag;
+  int* ncv = tot + 6;
+  k_tet_flags<<<grid, kThreads, 0, s>>>(code, -1, work, g.N);
+  e = launch_scan(work, work, g.N, ncv, scan_tmp, s);
+  if (e != cudaSuccess) return e;
+  k_chunk_first<<<grid, kThreads, 0, s>>>(code, work, ncv, first, g.N);
+  const int cb = (chunk_ints(ncut) + kThreads - 1) / kThreads;
+  k_chunk_init<<<cb, kThreads, 0, s>>>(first, cutoff, ncv, acc);
+  e = cudaGetLastError();
+  for (int t = 0; t < 6 && e == cudaSuccess; ++t) {
+    k_tet_flags<<<grid, kThreads, 0, s>>>(code, t, work, g.N);
+    e = launch_scan(work, work, g.N, tot + t, scan_tmp, s);
+    if (e == cudaSuccess) {
+      k_place_tets<<<grid, kThreads, 0, s>>>(code, work, t, first, acc, ncv, cut_ints, ncut, g.N);
+      k_chunk_advance<<<cb, kThreads, 0, s>>>(work, tot + t, first, ncv, acc, g.N);
+      e = cudaGetLastError();
+    }
+  }
+  return e;
 }
 
 __global__ void k_cut_geometry(const double* __restrict__ Ls, int nL, int* __restrict__ ip,
@@ -390,6 +482,77 @@ __global__ void k_cut_matrix(const int* __restrict__ ip, const double* __restric
     for (int i = 0; i < 24; ++i)
       for (int j = i; j < 24; ++j, ++k) kc[(long long)k * ncut + e] = (float)cut_element_entry(i, j, w, gr, dsc);
   }
+}
+
+__global__ void k_cut_records(const int* __restrict__ ip, const double* __restrict__ dp,
+                              const double* __restrict__ isD, int nX, int ncut, GridDev g, PhaseDev ph,
+                              const float* __restrict__ scale, int4* __restrict__ n4,
+                              int4* __restrict__ e4, double* __restrict__ r64, float* __restrict__ r32) {
+  double ih[3];
+  for (int k = 0; k < 3; ++k) ih[k] = 1.0 / g.h[k];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncut; e += gridDim.x * blockDim.x) {
+    const int vox = ip[8 * ncut + e];
+    const int t = ip[9 * ncut + e];
+    const int sph = ip[kCutFieldPhases * ncut + e];
+    int nd[4], ej[4];
+    for (int a = 0; a < 4; ++a) {
+      nd[a] = ip[a * ncut + e];
+      ej[a] = ip[(4 + a) * ncut + e];
+    }
+    n4[e] = make_int4(nd[0], nd[1], nd[2], nd[3]);
+    e4[e] = make_int4(ej[0], ej[1], ej[2], ej[3]);
+    double gr[4][3];
+    tet_grads<double>(t, ih, gr);
+    const double sv = scale ? (double)scale[vox] : 1.0;
+    double R[kRec];
+    for (int k = 0; k < kRec; ++k) R[k] = 0.0;
+    for (int a = 0; a < 4; ++a)
+      for (int x = 0; x < 3; ++x) R[3 * a + x] = isD[(long long)x * nX + ej[a]];
+    double L[4];
+    for (int b = 0; b < 4; ++b) L[b] = dp[(long long)cut_f_L(b) * ncut + e];
+    for (int si = 0; si < 2; ++si) {
+      double* S = R + kRecSide + kRecSideLen * si;
+      const double sg = si == 0 ? 1.0 : -1.0;
+      double M[10], m[4], c[4];
+      for (int k = 0; k < 10; ++k) M[k] = dp[(long long)cut_f_M(si, k) * ncut + e];
+      for (int b = 0; b < 4; ++b) {
+        m[b] = dp[(long long)cut_f_m(si, b) * ncut + e];
+        c[b] = fabs(L[b]) - sg * L[b];
+      }
+      double V = 0.0, mc = 0.0, cMc = 0.0, gam[3] = {0.0, 0.0, 0.0};
+      for (int b = 0; b < 4; ++b) {
+        double P = 0.0;
+        for (int cc = 0; cc < 4; ++cc) P += M[midx(b, cc)] * c[cc];
+        S[14 + b] = P;
+        S[10 + b] = m[b];
+        V += m[b];
+        mc += m[b] * c[b];
+        cMc += P * c[b];
+        for (int x = 0; x < 3; ++x) gam[x] += c[b] * gr[b][x];
+      }
+      for (int k = 0; k < 10; ++k) S[k] = M[k];
+      for (int x = 0; x < 3; ++x) S[18 + x] = gam[x];
+      const int p = si == 0 ? cut_phase_plus(sph) : cut_phase_minus(sph);
+      S[21] = ph.lam[p] * sv;
+      S[22] = ph.mu[p] * sv;
+      S[23] = V;
+      S[24] = mc;
+      S[25] = cMc;
+    }
+    for (int k = 0; k < kRec; ++k) {
+      r64[(long long)e * kRec + k] = R[k];
+      r32[(long long)e * kRec + k] = (float)R[k];
+    }
+  }
+}
+
+cudaError_t launch_cut_records(CutData cd, const double* isD, int nX, GridDev g, PhaseDev ph,
+                               const float* scale, int4* n4, int4* e4, double* r64, float* r32,
+                               cudaStream_t s) {
+  if (cd.ncut == 0) return cudaSuccess;
+  k_cut_records<<<(cd.ncut + 127) / 128, 128, 0, s>>>(cd.ip, cd.dp, isD, nX, cd.ncut, g, ph, scale, n4,
+                                                        e4, r64, r32);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cut_matrix(CutData cd, const double* isD, int nX, GridDev g, PhaseDev ph,

@@ -20,7 +20,25 @@ struct CutData {
   const double* dp;
   const float* fp;
   int ncut;
+  // per cut tet, for the apply kernels: the four node ids and enriched ids (int4 each) and a
+  // record of kRec reals (FP32 and FP64 copies; layout below)
+  const int4* n4 = nullptr;
+  const int4* e4 = nullptr;
+  const float* r32 = nullptr;
+  const double* r64 = nullptr;
 };
+// Apply record of a cut tet (tet-major, kRec reals, 16-byte aligned groups):
+//   [3a + c]            D0^-1/2 of the enriched DOF (vertex a, component c)
+//   kRecSide + 28 s +   side s = 0 (plus, L > 0) or 1 (minus):
+//     0..9   M_bc = int_side N_b N_c (packed as midx)
+//     10..13 m_b = int_side N_b
+//     14..17 P_b = sum_c M_bc c_c with c_c = |L_c| - s L_c (s = +1 plus, -1 minus)
+//     18..20 gamma = grad rho on the side = sum_b c_b grad N_b
+//     21, 22 lambda, mu of the side's phase times the voxel's modulus scale
+//     23..25 V = sum_b m_b, m.c = sum_b m_b c_b (= sum_b P_b), c^T M c; 26, 27 zero
+constexpr int kRec = 68;
+constexpr int kRecSide = 12;
+constexpr int kRecSideLen = 28;
 constexpr int kCutInts = 11;
 constexpr int kCutFieldPhases = 10;
 __host__ __device__ constexpr int cut_phase_minus(int f) { return f & 0xff; }
@@ -47,9 +65,14 @@ cudaError_t launch_count_nonfinite(const double* L, long long nL, const float* s
 cudaError_t launch_scan(const int* in, int* out, long long n, int* d_total, int* d_tmp,
                         cudaStream_t s);
 size_t scan_tmp_ints(long long n);
-cudaError_t launch_build_lists(const uint16_t* code, const int* cutoff, const int* enr_flag,
-                               int* enr_id, int* enr_nodes, int* cut_ints, int ncut, GridDev g,
-                               cudaStream_t s);
+// enriched ids and nodes, and the cut-tet list (voxel, tet) in chunks of consecutive cut voxels,
+// grouped by Kuhn tet type inside a chunk.  enr_flag is used as scratch afterwards; cutoff: the
+// exclusive scan of the per-voxel cut-tet counts; tot: 7 device ints; scan_tmp: scan_tmp_ints(N);
+// first, acc: chunk_ints(ncut) device ints each
+cudaError_t launch_build_lists(const uint16_t* code, const int* cutoff, int* enr_flag, int* enr_id,
+                               int* enr_nodes, int* cut_ints, int ncut, GridDev g, int* tot,
+                               int* scan_tmp, int* first, int* acc, cudaStream_t s);
+int chunk_ints(int ncut);
 cudaError_t launch_cut_geometry(const double* Ls, int nL, CutData cd, double* dp_mut, int* ip_mut,
                                 GridDev g, cudaStream_t s);
 cudaError_t launch_cut_eids(int* ip_mut, const int* enr_id, int ncut, cudaStream_t s);
@@ -59,6 +82,10 @@ cudaError_t launch_block_inverse(const double* D, const double* Doff, const doub
 cudaError_t launch_finish_scaling(const double* D, double* isd, float* isf, int nX,
                                   cudaStream_t s);
 cudaError_t launch_cut_to_float(const double* dp, float* fp, long long count, cudaStream_t s);
+// apply records and node / enriched id quadruples of the cut tets (needs isD, phases, scale)
+cudaError_t launch_cut_records(CutData cd, const double* isD, int nX, GridDev g, PhaseDev ph,
+                               const float* scale, int4* n4, int4* e4, double* r64, float* r32,
+                               cudaStream_t s);
 // cached scaled element matrices of the cut tets (packed upper triangle, FP32; isD: D0^-1/2)
 constexpr int kCutPacked = 24 * 25 / 2;
 cudaError_t launch_cut_matrix(CutData cd, const double* isD, int nX, GridDev g, PhaseDev ph,

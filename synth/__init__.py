@@ -9,7 +9,9 @@ from .geometry import (  # noqa: F401
     node_coords,
     sphere_levelset,
     coated_sphere_levelsets,
+    hashin_contrast,
     hashin_neutral_inclusion,
+    hashin_neutral_moduli,
     HASHIN,
     spheres_levelset,
     rsa_spheres,

@@ -78,6 +78,27 @@ def hashin_neutral_inclusion(N):
     return Ls, phases, ell
 
 
+def hashin_neutral_moduli(ratio, K_matrix=1.0, poisson=0.25):
+    """Bulk moduli (inclusion, coating, matrix) of a neutral coated sphere with K_i / K_c =
+    ``ratio`` (the contrast study of Sec. 4.2): the composite sphere's bulk modulus
+    K* = K_c + c (K_i - K_c) / (1 + (1 - c)(K_i - K_c) / (K_c + 4 mu_c / 3)), c = (r_i / r_c)^3
+    (Hashin 1962), equals K_matrix.  With a common Poisson ratio mu_c = a K_c,
+    a = 3 (1 - 2 nu) / (2 (1 + nu)), and K* is K_c times a function of the ratio alone."""
+    c = (HASHIN["r_inclusion_um"] / HASHIN["r_coating_um"]) ** 3
+    a = 3.0 * (1.0 - 2.0 * poisson) / (2.0 * (1.0 + poisson))
+    q = ratio - 1.0
+    Kc = K_matrix / (1.0 + c * q / (1.0 + (1.0 - c) * q / (1.0 + 4.0 * a / 3.0)))
+    return (ratio * Kc, Kc, K_matrix)
+
+
+def hashin_contrast(N, ratio):
+    """Hashin's neutral inclusion on an N^3 grid with the inclusion/coating bulk-modulus ratio
+    ``ratio`` (matrix K = 1, all Poisson ratios 0.25): level sets, phases, cell lengths."""
+    Ls, _, ell = hashin_neutral_inclusion(N)
+    phases = [lame_from_K_nu(K, HASHIN["poisson"]) for K in hashin_neutral_moduli(ratio)]
+    return Ls, phases, ell
+
+
 def spheres_levelset(n, centers, radii, length=(1.0, 1.0, 1.0)):
     """Minimum over spheres of the periodic signed distances."""
     L = np.full(tuple(n), np.inf)

@@ -13,10 +13,10 @@ def test_algorithmic_bytes():
     geo = N * 6  # phase code (2 B) and voxel scale (4 B)
     assert bench.algorithmic_bytes("apply_uncut_f32", N, nX, ncut, True) == (0, 72 * N + geo)
     assert bench.algorithmic_bytes("prec_f32", N, nX, ncut, True) == (0, 48 * (N + nX))
-    # on-the-fly cut tets (the default): per launch the geometry (11 ints + 32 floats per cut
-    # tet) and 1/sqrt(D0); per right-hand side 72 B per enriched node (d read, q updated)
-    assert bench.algorithmic_bytes("apply_cut_f32", N, nX, ncut, True) == (172 * ncut + 12 * nX, 72 * nX)
-    assert bench.algorithmic_bytes("apply_cut_f64", N, nX, ncut, True) == (300 * ncut + 24 * nX, 144 * nX)
+    # on-the-fly cut tets (the default): per launch each cut tet's record (68 reals) and 9 ints;
+    # per right-hand side 72 B per enriched node (d read, q updated)
+    assert bench.algorithmic_bytes("apply_cut_f32", N, nX, ncut, True) == (308 * ncut, 72 * nX)
+    assert bench.algorithmic_bytes("apply_cut_f64", N, nX, ncut, True) == (580 * ncut, 144 * nX)
     # cached matrices: 1232 B per cut tet and launch, 72 B per enriched node and right-hand side
     assert bench.algorithmic_bytes("apply_cut_f32", N, nX, ncut, True, cut_cache=True) == (1232 * ncut, 72 * nX)
     assert bench.algorithmic_bytes("no_such_group", N, nX, ncut, True) is None

@@ -58,3 +58,14 @@ def test_hashin_inputs():
         assert abs(lam / (2.0 * (lam + mu)) - 0.25) < 1e-12
     # innermost first: negative inside the inclusion, and inside the coating's outer sphere
     assert Ls[0].min() < 0 and np.all(Ls[0] >= Ls[1])
+
+
+def test_hashin_contrast_moduli_reproduce_the_paper_table():
+    """The neutrality condition of the coated sphere (composite-sphere bulk modulus = matrix
+    modulus 1) gives, at K_i / K_c = 10, the paper's printed coating and inclusion moduli
+    (0.808024 and 8.080240 MPa, Sec. 4.2 table); K_i / K_c is the ratio asked for."""
+    Ki, Kc, Km = synth.hashin_neutral_moduli(10.0)
+    assert round(Kc, 6) == 0.808024 and round(Ki, 6) == 8.080240 and Km == 1.0
+    for ratio in (1e-5, 1e-1, 1e3, 1e5):
+        Ki, Kc, Km = synth.hashin_neutral_moduli(ratio)
+        assert abs(Ki / Kc - ratio) < 1e-12 * ratio and Kc > 0
