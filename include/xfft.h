@@ -54,7 +54,7 @@ typedef enum {
   XFFT_ECUDA = 3,        /* a CUDA runtime call failed; see xfft_last_error() */
   XFFT_ENOTCONV = 4,     /* maxit reached before the stopping rule held */
   XFFT_EBREAKDOWN = 5,   /* CG breakdown: <A d, d> <= 0 or a NaN/Inf scalar */
-  XFFT_ETIMEOUT = 6,     /* reserved: a bounded device wait gave up */
+  XFFT_ETIMEOUT = 6,     /* a device-driven iteration loop reached spin_limit_ns */
   XFFT_EUNSUPPORTED = 7, /* valid request that the library does not implement */
   XFFT_ESTATE = 8        /* call order violated (e.g. solve before set_microstructure) */
 } xfft_status;
@@ -130,6 +130,15 @@ typedef struct {
                           the first one negative there), and nX = 0 */
   long long max_device_bytes; /* cap on the context's own device allocations (0 = none); a
                           request above it fails with XFFT_ENOMEM as a failed cudaMalloc would */
+  long long spin_limit_ns; /* limit on the device time of one device-driven iteration loop (the
+                          CG iterations between two residual checks run as one CUDA graph whose
+                          while node repeats poll_every iterations until no right-hand side is
+                          active); past it the loop stops, the outputs hold the last iterate and
+                          the call returns XFFT_ETIMEOUT.  < 0 (default): no limit */
+  int autotune;        /* FP32_REFINED: 1 (default) times candidate launch shapes of the cut-tet
+                          kernel (grid size, right-hand sides per launch) on the microstructure at
+                          its first solve and keeps the fastest (cached per grid and cut-tet
+                          count for the process; see xfft_get_tuning); 0 keeps the defaults */
 } xfft_options;
 
 typedef struct {
@@ -143,7 +152,7 @@ typedef struct {
 
 /* Fill *opt with the defaults: FP64, tol 1e-10, maxit 10000, snap_tau 0 (=> 1e-6 min h),
  * identity enriched block, inner_tol 1e-5, max_refine 20, poll_every 8, linear CG, cut_cache 0,
- * bb_rule XFFT_BB1, bb_cycle 1, enrichment 1, max_device_bytes 0. */
+ * bb_rule XFFT_BB1, bb_cycle 1, enrichment 1, max_device_bytes 0, spin_limit_ns -1, autotune 1. */
 xfft_status xfft_default_options(xfft_options* opt);
 
 /* Create a context for one grid.  stream: a cudaStream_t (or NULL for the legacy stream).
@@ -191,13 +200,18 @@ xfft_status xfft_solve(xfft_ctx* ctx, int n_rhs, const double* eps_bar, double* 
  * The six converged fields stay in the context as the checkpoint for xfft_grad. */
 xfft_status xfft_effective_stiffness(xfft_ctx* ctx, double C_eff[36], xfft_stats* stats);
 
-/* Batch of microstructures (uneven grids allowed): xfft_effective_stiffness on each of the n
- * contexts, all at once.  Each context's solve runs from its own host thread on its own stream,
- * so kernels of different microstructures overlap on the GPU; within a context the iterations
- * between two convergence polls replay as one captured CUDA graph.  Give every context its own
- * non-legacy stream at xfft_create (contexts on the legacy stream serialise and run without
- * graphs).  C_eff: n x 36 (host), stats: n entries or NULL.  The first error (or ENOTCONV) is
- * returned with the context's index in the message; every context is solved regardless. */
+/* Batch of microstructures (uneven grids allowed, at most 64): xfft_effective_stiffness on each of
+ * the n contexts, all at once (the benchmark spec's batching of many microstructures; the paper
+ * solves one at a time).  The contexts advance in lockstep: the residual phases of all contexts
+ * run on their own streams, then every inner CG solve of every context still iterating runs as
+ * ONE device-driven graph launch (a conditional while node whose body holds poll_every
+ * iterations of each context, forked onto the contexts' streams, and a kernel that ends the
+ * loop once no right-hand side of any context is active), so the host does not poll between
+ * iterations.  Contexts need their own non-legacy streams and tracing off; otherwise (or where
+ * conditional graphs are unavailable) each context runs from its own host thread.  spin_limit_ns:
+ * the smallest limit of the contexts applies to the shared loop.  C_eff: n x 36 (host), stats: n
+ * entries or NULL (ms_solve is the whole batch's device time).  The first error (or ENOTCONV /
+ * ETIMEOUT) is returned with the context's index in the message; every context is solved. */
 xfft_status xfft_batch_effective_stiffness(int n, xfft_ctx* const* ctxs, double* C_eff,
                                            xfft_stats* stats);
 
@@ -286,6 +300,11 @@ xfft_status xfft_profile_read(xfft_ctx* ctx, double ms[16], long long launches[1
 #define XFFT_NOALLOC_MAX_PARTS 4096
 xfft_status xfft_apply_noalloc(xfft_ctx* ctx, int n_rhs, const double* d, double* q,
                                double* dAd_sig);
+
+/* Launch shape of the FP32 cut-tet kernel in use (not in the paper): its grid in blocks and the
+ * right-hand sides per launch, as picked by the tuner (option autotune) or the defaults.
+ * Errors: EINVAL (NULL), ESTATE (no microstructure). */
+xfft_status xfft_get_tuning(const xfft_ctx* ctx, int* cut_blocks, int* cut_rhs_per_launch);
 
 int xfft_num_enriched(const xfft_ctx* ctx);   /* nX, or -1 before set_microstructure */
 int xfft_num_cut_tets(const xfft_ctx* ctx);   /* number of cut tetrahedra, or -1 */

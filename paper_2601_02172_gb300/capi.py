@@ -26,7 +26,7 @@ EXPORTED = (
     "xfft_effective_stiffness", "xfft_grad", "xfft_grad_phases", "xfft_apply", "xfft_precondition", "xfft_get_setup",
     "xfft_num_enriched", "xfft_num_cut_tets", "xfft_status_string", "xfft_last_error",
     "xfft_destroy", "xfft_profile", "xfft_profile_read", "xfft_apply_noalloc",
-    "xfft_batch_effective_stiffness",
+    "xfft_batch_effective_stiffness", "xfft_get_tuning",
 )
 NOALLOC_MAX_RHS = 8
 PROF_KINDS = ("apply_uncut_f32", "apply_cut_f32", "apply_uncut_f64", "apply_cut_f64", "prec_f32",
@@ -43,7 +43,8 @@ class Options(C.Structure):
                 ("snap_tau", C.c_double), ("enr_precond", C.c_int), ("inner_tol", C.c_double),
                 ("max_refine", C.c_int), ("poll_every", C.c_int), ("scheme", C.c_int),
                 ("step", C.c_double), ("cut_cache", C.c_int), ("bb_rule", C.c_int),
-                ("bb_cycle", C.c_int), ("enrichment", C.c_int), ("max_device_bytes", C.c_longlong)]
+                ("bb_cycle", C.c_int), ("enrichment", C.c_int), ("max_device_bytes", C.c_longlong),
+                ("spin_limit_ns", C.c_longlong), ("autotune", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -92,11 +93,13 @@ def lib():
     L.xfft_profile_read.argtypes = [vp, vp, vp, vp]
     L.xfft_apply_noalloc.argtypes = [vp, i, vp, vp, vp]
     L.xfft_batch_effective_stiffness.argtypes = [i, vp, C.POINTER(d), C.POINTER(Stats)]
+    L.xfft_get_tuning.argtypes = [vp, C.POINTER(i), C.POINTER(i)]
     for name in ("xfft_default_options", "xfft_create", "xfft_set_microstructure",
                  "xfft_set_microstructure_phases", "xfft_solve",
                  "xfft_effective_stiffness", "xfft_grad", "xfft_grad_phases", "xfft_apply", "xfft_precondition",
                  "xfft_get_setup", "xfft_num_enriched", "xfft_num_cut_tets", "xfft_profile",
-                 "xfft_profile_read", "xfft_apply_noalloc", "xfft_batch_effective_stiffness"):
+                 "xfft_profile_read", "xfft_apply_noalloc", "xfft_batch_effective_stiffness",
+                 "xfft_get_tuning"):
         getattr(L, name).restype = i
     _lib = L
     return L
@@ -190,7 +193,7 @@ class Solver:
     def __init__(self, n, length=(1.0, 1.0, 1.0), precision="fp64", tol=1e-10, maxit=10000,
                  snap_tau=0.0, inner_tol=1e-5, max_refine=20, poll_every=8, stream=None,
                  enr_precond="identity", scheme="cg", step=0.0, cut_cache=False, bb_rule="bb1",
-                 bb_cycle=1, enrichment=True, max_device_bytes=0):
+                 bb_cycle=1, enrichment=True, max_device_bytes=0, spin_limit_ns=-1, autotune=True):
         L = lib()
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
@@ -216,6 +219,8 @@ class Solver:
         o.bb_cycle = int(bb_cycle)
         o.enrichment = int(bool(enrichment))
         o.max_device_bytes = int(max_device_bytes)
+        o.spin_limit_ns = int(spin_limit_ns)
+        o.autotune = int(bool(autotune))
         self.precision = precision
         self.num_phases = 0
         try:
@@ -251,6 +256,13 @@ class Solver:
     @property
     def num_cut_tets(self):
         return lib().xfft_num_cut_tets(self._ctx)
+
+    @property
+    def tuning(self):
+        """(cut-tet kernel grid in blocks, right-hand sides per launch) in use."""
+        b, r = C.c_int(), C.c_int()
+        check(lib().xfft_get_tuning(self._ctx, C.byref(b), C.byref(r)))
+        return b.value, r.value
 
     @property
     def stride(self):
@@ -417,7 +429,8 @@ class Solver:
 
 def batch_effective_stiffness(solvers):
     """C_eff (list of 6x6) and stats of several solvers at once (``xfft_batch_effective_stiffness``:
-    one host thread and stream per solver, graph-replayed CG iterations)."""
+    the solvers advance in lockstep and every inner CG solve of all of them runs as one
+    device-driven graph launch)."""
     import torch
     n = len(solvers)
     arr = (C.c_void_p * n)(*[sv._ctx for sv in solvers])

@@ -26,6 +26,14 @@ int apply_cut_blocks(int ncut) {
   return nb < 1 ? 1 : (nb > kCutBlocksMax ? kCutBlocksMax : nb);
 }
 
+constexpr int kCutBlocksTuneMax = 4 * 4 * 152;  // four waves of four resident blocks per SM
+int apply_cut_blocks_max(int ncut) {
+  const int nb = (ncut + kCutThreads - 1) / kCutThreads;
+  const int cap = nb < kCutBlocksTuneMax ? nb : kCutBlocksTuneMax;
+  const int def = apply_cut_blocks(ncut);
+  return cap > def ? cap : def;
+}
+
 template <typename T>
 cudaError_t launch_apply_uncut(const typename Store<T>::type* d, typename Store<T>::type* q,
                                const ApplyArgs& a, int n_rhs, cudaStream_t s) {
@@ -147,7 +155,8 @@ cudaError_t launch_apply_cut(const typename Store<T>::type* d, typename Store<T>
     if (a.kcache && !a.eps && !a.want_sig && cd.ncut > 0) return launch_cut_cached(d, q, cd, a, n_rhs, s);
   }
   // launched even without cut tets: its blocks write the (zero) partial sums of their slots
-  const int nb = apply_cut_blocks(cd.ncut);
+  const int nb = a.cut_blocks > 0 ? a.cut_blocks : apply_cut_blocks(cd.ncut);
+  const int rpl = a.cut_rpl > 0 && a.cut_rpl < kCutMaxR ? a.cut_rpl : kCutMaxR;
   const bool sig = a.want_sig || a.eps;
   constexpr size_t smem = cut_smem_bytes<T>();
   // opt in to the staged records' shared memory, once per variant and device
@@ -165,8 +174,8 @@ cudaError_t launch_apply_cut(const typename Store<T>::type* d, typename Store<T>
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  for (int r0 = 0; r0 < n_rhs; r0 += kCutMaxR) {
-    const int nr = n_rhs - r0 < kCutMaxR ? n_rhs - r0 : kCutMaxR;
+  for (int r0 = 0; r0 < n_rhs; r0 += rpl) {
+    const int nr = n_rhs - r0 < rpl ? n_rhs - r0 : rpl;
     if (a.eps)
       k_apply_cut<T, true, true><<<nb, kCutThreads, smem, s>>>(d, q, cd, a, r0, nr);
     else if (sig)

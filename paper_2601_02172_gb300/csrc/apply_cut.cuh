@@ -34,6 +34,14 @@ constexpr int kCutMaxR = 8;  // right-hand sides per launch (more are split over
 #define XFFT_CUT_MINB 4  // resident blocks per SM asked of the FP32 cut kernel
 #endif
 
+// Staging: the FP32 and FP64 kernels stage; the double-word kernel (one or two resident blocks
+// per SM, long per-thread work) reads its records from global memory instead, where a block-wide
+// barrier per group of tets would idle the SM.
+template <typename T>
+constexpr bool cut_staged() {
+  return !std::is_same<T, dw>::value;
+}
+
 // Records are staged per block in shared memory, RecStride<S> reals apart: 68 floats (272 B)
 // or 70 doubles (560 B), so that the 16-byte loads of 8 consecutive lanes hit distinct banks.
 template <typename S>
@@ -49,10 +57,10 @@ struct RecStride<double> {
 template <typename T>
 constexpr size_t cut_smem_bytes() {
   typedef typename Store<T>::type S;
-  return (size_t)kCutThreads * RecStride<S>::v * sizeof(S);
+  return cut_staged<T>() ? (size_t)kCutThreads * RecStride<S>::v * sizeof(S) : 0;
 }
 
-// record loads from shared memory: 4 consecutive reals (16-byte aligned groups of the record)
+// record loads from shared or global memory: 4 consecutive reals (16-byte aligned groups)
 __device__ __forceinline__ void ld_rec4(const float* p, float (&o)[4]) {
   const float4 v = *reinterpret_cast<const float4*>(p);
   o[0] = v.x;
@@ -349,7 +357,8 @@ __global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1
       nd = __ldg(cd.n4 + e);
       ej = __ldg(cd.e4 + e);
     }
-    {
+    const S* rec;
+    if (cut_staged<T>()) {
       const int nval = ncut - base < kCutThreads ? ncut - base : kCutThreads;
       const float4* src = reinterpret_cast<const float4*>(recs + (long long)base * kRec);
       __syncthreads();  // the previous group's records are no longer read
@@ -358,8 +367,10 @@ __global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1
         *reinterpret_cast<float4*>(srec + te * RS + ch * (16 / (int)sizeof(S))) = __ldg(src + i);
       }
       __syncthreads();
+      rec = srec + threadIdx.x * RS;
+    } else {
+      rec = recs + (long long)(ok ? e : 0) * kRec;
     }
-    const S* rec = srec + threadIdx.x * RS;
     for (int rr = 0; rr < nr; ++rr) {
       const int rhs = r0 + rr;
       if (a.active && !a.active[rhs]) continue;  // uniform over the block

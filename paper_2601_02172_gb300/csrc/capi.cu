@@ -43,6 +43,11 @@ static xfft_status fail(xfft_status s, const std::string& msg) {
                   std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));              \
   } while (0)
 
+// device loop memory: LoopState (padded), then kMaxBatch act pointers and kMaxBatch RHS counts
+constexpr int kMaxBatch = 64;
+constexpr size_t kLoopHead = 64;
+constexpr size_t kLoopBytes = kLoopHead + (sizeof(void*) + sizeof(int)) * kMaxBatch;
+
 struct xfft_ctx;
 static cudaError_t dalloc_bytes(xfft_ctx* c, void** p, size_t bytes);
 static void dfree_bytes(xfft_ctx* c, void* p);
@@ -93,15 +98,22 @@ struct xfft_ctx {
   double* D = nullptr;
   double* isD = nullptr;
   float* isF = nullptr;
-  // captured CG iteration chunks (poll_every iterations each), keyed by their arguments
+  // device-driven CG loops (a conditional while graph per inner solve), keyed by their arguments
   struct CgGraph {
     bool valid = false;
-    int tsz = 0, n_rhs = 0, crit = 0, maxit = 0, pe = 0;
+    bool dbl = false;
+    int n_rhs = 0, crit = 0, maxit = 0, pe = 0;
     double tol = 0.0;
+    long long limit = -1;
     const void* p[6] = {};
     cudaGraphExec_t exec = nullptr;
   } cg_graphs[4];
   int cg_next = 0;
+  bool devloop_ok = true;            // false once a conditional graph could not be built
+  unsigned char* loopmem = nullptr;  // device: LoopState, act pointers, RHS counts
+  unsigned char* h_loop = nullptr;   // pinned host staging of loopmem
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
   double step0 = 0.0;  // step of the basic / Barzilai-Borwein schemes
   // block enriched preconditioner: off-diagonal block entries and the inverse blocks
   double* Doff = nullptr;
@@ -148,6 +160,9 @@ struct xfft_ctx {
   size_t bytes = 0;
   // Euclidean Barzilai-Borwein steps: <d, d>, <A d, A d> partial sums
   double* bbpart = nullptr;
+  // launch shape of the FP32 cut-tet kernel picked by the tuner (0: defaults)
+  int cut_blocks = 0, cut_rpl = 0;
+  bool tuned = false;
 };
 
 static cudaError_t dalloc_bytes(xfft_ctx* c, void** p, size_t bytes) {
@@ -282,6 +297,8 @@ extern "C" xfft_status xfft_default_options(xfft_options* opt) {
   opt->bb_cycle = 1;
   opt->enrichment = 1;
   opt->max_device_bytes = 0;
+  opt->spin_limit_ns = -1;
+  opt->autotune = 1;
   return XFFT_OK;
 }
 
@@ -311,6 +328,7 @@ extern "C" xfft_status xfft_create(xfft_ctx** out, const xfft_grid* grid, const 
     return fail(XFFT_EINVAL, "unknown Barzilai-Borwein rule or bb_cycle < 1");
   if (o.enrichment != 0 && o.enrichment != 1) return fail(XFFT_EINVAL, "enrichment must be 0 or 1");
   if (o.max_device_bytes < 0) return fail(XFFT_EINVAL, "max_device_bytes must be >= 0");
+  if (o.autotune != 0 && o.autotune != 1) return fail(XFFT_EINVAL, "autotune must be 0 or 1");
   if (!(o.tol > 0.0) || o.maxit < 1 || o.poll_every < 1 || o.max_refine < 1 || !(o.inner_tol > 0.0))
     return fail(XFFT_EINVAL, "invalid options");
   xfft_ctx* c = new xfft_ctx();
@@ -334,7 +352,15 @@ extern "C" xfft_status xfft_create(xfft_ctx** out, const xfft_grid* grid, const 
       (e = cudaMallocHost((void**)&c->h_act, 64 * sizeof(int))) != cudaSuccess ||
       (e = cudaMallocHost((void**)&c->h_st, 64 * sizeof(RhsState))) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->punits, 16 * sizeof(unsigned long long))) != cudaSuccess ||
-      (e = cudaMemset(c->punits, 0, 16 * sizeof(unsigned long long))) != cudaSuccess) {
+      (e = cudaMemset(c->punits, 0, 16 * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->loopmem, kLoopBytes)) != cudaSuccess ||
+      (e = cudaMallocHost((void**)&c->h_loop, kLoopBytes)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess) {
+    xfft_destroy(c);
+    return fail(XFFT_ECUDA, cudaGetErrorString(e));
+  }
+  c->ev_join.assign(1, nullptr);
+  if ((e = cudaEventCreateWithFlags(&c->ev_join[0], cudaEventDisableTiming)) != cudaSuccess) {
     xfft_destroy(c);
     return fail(XFFT_ECUDA, cudaGetErrorString(e));
   }
@@ -351,6 +377,8 @@ static void drop_graphs(xfft_ctx* c) {
 
 static void free_micro(xfft_ctx* c) {
   drop_graphs(c);
+  c->tuned = false;
+  c->cut_blocks = c->cut_rpl = 0;
   dfree(c, c->Ls);
   dfree(c, c->Lin);
   dfree(c, c->kcache);
@@ -419,8 +447,21 @@ extern "C" void xfft_destroy(xfft_ctx* c) {
   }
   for (auto e : c->evpool) cudaEventDestroy(e);
   if (c->punits) cudaFree(c->punits);
+  if (c->loopmem) cudaFree(c->loopmem);
+  if (c->h_loop) cudaFreeHost(c->h_loop);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  for (auto e : c->ev_join)
+    if (e) cudaEventDestroy(e);
   for (auto& kv : c->blocks) cudaFree(kv.first);  // anything a failed call left behind
   delete c;
+}
+
+extern "C" xfft_status xfft_get_tuning(const xfft_ctx* c, int* cut_blocks, int* cut_rhs_per_launch) {
+  if (!c || !cut_blocks || !cut_rhs_per_launch) return fail(XFFT_EINVAL, "NULL argument");
+  if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
+  *cut_blocks = c->cut_blocks > 0 ? c->cut_blocks : apply_cut_blocks(c->ncut);
+  *cut_rhs_per_launch = c->cut_rpl > 0 ? c->cut_rpl : 8;
+  return XFFT_OK;
 }
 
 extern "C" int xfft_num_enriched(const xfft_ctx* c) { return c && c->have_micro ? c->nX : -1; }
@@ -621,7 +662,7 @@ static xfft_status ensure_work(xfft_ctx* c, int n_rhs, int prec) {
   CU(dalloc(c, &c->act, 64));
   CU(dalloc(c, &c->outer_mask, 64));
   CU(dalloc(c, &c->eps_d, 6 * 64));
-  const int na = apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut);
+  const int na = apply_uncut_blocks(c->g) + apply_cut_blocks_max(c->ncut);
   const int np =
       std::max(precondition_blocks(c->fft, c->nX, true), precondition_blocks(c->fft, c->nX, false));
   const int ng = grad_blocks_uncut(c->g) + grad_blocks_cut(c->ncut);
@@ -636,8 +677,13 @@ static xfft_status ensure_work(xfft_ctx* c, int n_rhs, int prec) {
   return XFFT_OK;
 }
 
+// the cut-tet kernel's grid in use; its partial slots are reserved for the largest tuned grid
+static int cut_blocks_of(const xfft_ctx* c) {
+  return c->cut_blocks > 0 ? c->cut_blocks : apply_cut_blocks(c->ncut);
+}
+
 static int nparts_of(const xfft_ctx* c) {
-  return std::max(apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut),
+  return std::max(apply_uncut_blocks(c->g) + apply_cut_blocks_max(c->ncut),
                   std::max(precondition_blocks(c->fft, c->nX, true), precondition_blocks(c->fft, c->nX, false)));
 }
 
@@ -662,6 +708,8 @@ static ApplyArgs apply_args(const xfft_ctx* c, const double* eps, const int* act
   a.fdnew = nullptr;
   a.fu = nullptr;
   a.st = nullptr;
+  a.cut_blocks = c->cut_blocks;
+  a.cut_rpl = c->cut_rpl;
   return a;
 }
 
@@ -719,7 +767,7 @@ static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev
   }
   if (fin_mode >= 0) {
     FinArgs fa = fin_args(c, fin_mode, crit, tol, maxit, a.nparts,
-                          apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut), parity);
+                          apply_uncut_blocks(c->g) + cut_blocks_of(c), parity);
     if (fin_mode == 1 && bb_euclid(c) && c->bbpart) {
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
       CU(launch_bb_dots<T>(fz ? fdnew : d, q, active, stride_of(c), n_rhs, c->bbpart, c->stream));
@@ -751,6 +799,81 @@ static xfft_status do_prec(xfft_ctx* c, T* f, T* z, int n_rhs, const int* active
     fa.inner_floor = c->opt.inner_tol;
     CU(launch_finalize(c->st, c->partials, fa, n_rhs, c->act, c->stream));
   }
+  return XFFT_OK;
+}
+
+// ---------------------------------------------------------------- launch-shape tuner
+// The FP32 cut-tet kernel's grid (its blocks loop over the cut list) and the right-hand sides
+// per launch (all six in one launch, or three per launch) are picked by timing each candidate
+// on the context's own microstructure: a warm-up and three timed launches of the FP32 apply of
+// the inner CG iterations, CUDA events on the context's stream.  The choice is cached per grid
+// and cut-tet / enriched-node counts for the process, so a repeated microstructure is not
+// timed again.  The partial-sum rows keep room for the largest candidate grid
+// (apply_cut_blocks_max), so the finalisation reads the slots the chosen grid writes.
+struct TuneEntry {
+  int n0, n1, n2, ncut, nX, blocks, rpl;
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tune_cache;
+
+static xfft_status autotune(xfft_ctx* c) {
+  if (c->tuned || !c->opt.autotune || c->opt.precision != XFFT_FP32_REFINED || c->opt.cut_cache ||
+      c->ncut < 4 * kThreads || c->prof || c->cap_rhs < 6)
+    return XFFT_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& t : g_tune_cache)
+      if (t.n0 == c->g.n0 && t.n1 == c->g.n1 && t.n2 == c->g.n2 && t.ncut == c->ncut && t.nX == c->nX) {
+        c->cut_blocks = t.blocks;
+        c->cut_rpl = t.rpl;
+        c->tuned = true;
+        return XFFT_OK;
+      }
+  }
+  const int n_rhs = 6;
+  float* d = c->v32[2];
+  float* q = c->v32[4];
+  CU(cudaMemsetAsync(d, 0, (size_t)n_rhs * stride_of(c) * sizeof(float), c->stream));
+  const int bmax = apply_cut_blocks_max(c->ncut);
+  std::vector<int> blocks;
+  for (int w : {152, 304, 608, 912, 1216, 1824, 2432})
+    if (w <= bmax) blocks.push_back(w);
+  if (std::find(blocks.begin(), blocks.end(), bmax) == blocks.end()) blocks.push_back(bmax);
+  struct Ev {
+    cudaEvent_t e = nullptr;
+    ~Ev() {
+      if (e) cudaEventDestroy(e);
+    }
+  } t0, t1;
+  CU(cudaEventCreate(&t0.e));
+  CU(cudaEventCreate(&t1.e));
+  double best = 1e30;
+  int bb = 0, br = 0;
+  for (int rpl : {6, 3}) {
+    for (int nb : blocks) {
+      c->cut_blocks = nb;
+      c->cut_rpl = rpl;
+      ApplyArgs a = apply_args(c, nullptr, nullptr);
+      a.want_sig = 0;
+      CU(launch_apply_cut<float>(d, q, c->isF, cutdata(c), a, n_rhs, c->stream));
+      CU(cudaEventRecord(t0.e, c->stream));
+      for (int k = 0; k < 3; ++k) CU(launch_apply_cut<float>(d, q, c->isF, cutdata(c), a, n_rhs, c->stream));
+      CU(cudaEventRecord(t1.e, c->stream));
+      CU(cudaEventSynchronize(t1.e));
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, t0.e, t1.e));
+      if (ms < best) {
+        best = ms;
+        bb = nb;
+        br = rpl;
+      }
+    }
+  }
+  c->cut_blocks = bb;
+  c->cut_rpl = br;
+  c->tuned = true;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.push_back({c->g.n0, c->g.n1, c->g.n2, c->ncut, c->nX, bb, br});
   return XFFT_OK;
 }
 
@@ -801,83 +924,182 @@ static xfft_status cg_iter(xfft_ctx* c, int it, T* u, T* f, T* const* dbuf, T* z
   return XFFT_OK;
 }
 
-// Executable graph of poll_every iterations (captured once per argument set, then replayed:
-// the iterations between two convergence polls are fixed launch sequences whose scalars live
-// on the device).  Needs a non-legacy stream, an even poll_every and tracing off.
+// One inner CG solve of a context (the FP64 solver's whole solve, or one FP32 inner solve of the
+// refinement) as a loop argument set.
+struct LoopArgs {
+  xfft_ctx* c = nullptr;
+  bool dbl = false;
+  void *u = nullptr, *f = nullptr, *dA = nullptr, *dB = nullptr, *z = nullptr, *q = nullptr;
+  int n_rhs = 0;
+  double tol = 0.0;
+  int crit = 0, maxit = 0;
+};
+
+// iterations per round of a device-driven loop: poll_every rounded up to an even count, so that
+// the two direction buffers are in the same roles at the start of every round
+static int loop_pe(const xfft_ctx* c) { return c->opt.poll_every + (c->opt.poll_every & 1); }
+
 template <typename T>
-static xfft_status cg_graph(xfft_ctx* c, T* u, T* f, T* const* dbuf, T* z, T* q, int n_rhs, double tol,
-                            int crit, int maxit, cudaGraphExec_t* out) {
-  const int pe = c->opt.poll_every;
-  const void* key[6] = {u, f, dbuf[0], dbuf[1], z, q};
-  for (auto& g : c->cg_graphs) {
-    if (g.valid && g.tsz == (int)sizeof(T) && g.n_rhs == n_rhs && g.crit == crit && g.maxit == maxit &&
-        g.pe == pe && g.tol == tol && std::equal(key, key + 6, g.p)) {
-      *out = g.exec;
-      return XFFT_OK;
-    }
-  }
-  cudaGraph_t graph = nullptr;
-  CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
-  xfft_status st = XFFT_OK;
-  for (int j = 0; j < pe && st == XFFT_OK; ++j) st = cg_iter<T>(c, j, u, f, dbuf, z, q, n_rhs, tol, crit, maxit);
-  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
-  if (st != XFFT_OK) {
-    if (graph) cudaGraphDestroy(graph);
-    return st;
-  }
-  if (e != cudaSuccess) return fail(XFFT_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return fail(XFFT_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-  auto& g = c->cg_graphs[c->cg_next];
-  c->cg_next = (c->cg_next + 1) % 4;
-  if (g.exec) cudaGraphExecDestroy(g.exec);
-  g.valid = true;
-  g.tsz = (int)sizeof(T);
-  g.n_rhs = n_rhs;
-  g.crit = crit;
-  g.maxit = maxit;
-  g.pe = pe;
-  g.tol = tol;
-  std::copy(key, key + 6, g.p);
-  g.exec = exec;
-  *out = exec;
+static xfft_status loop_round(const LoopArgs& L, int pe) {
+  T* dbuf[2] = {(T*)L.dA, (T*)L.dB};
+  for (int j = 0; j < pe; ++j)
+    TRY(cg_iter<T>(L.c, j, (T*)L.u, (T*)L.f, dbuf, (T*)L.z, (T*)L.q, L.n_rhs, L.tol, L.crit, L.maxit));
   return XFFT_OK;
 }
 
-template <typename T>
-static xfft_status cg_loop(xfft_ctx* c, T* u, T* f, T* dA, T* dB, T* z, T* q, int n_rhs, double tol,
-                           int crit, int maxit) {
-  const long long stride = stride_of(c);
-  T* dbuf[2] = {dA, dB};
-  const int pe = c->opt.poll_every;
-  const bool graphs = !c->prof && c->stream != nullptr && c->stream != cudaStreamLegacy &&
-                      c->stream != cudaStreamPerThread && pe % 2 == 0;
-  if (graphs) {
-    cudaGraphExec_t exec = nullptr;
-    TRY(cg_graph<T>(c, u, f, dbuf, z, q, n_rhs, tol, crit, maxit, &exec));
-    for (int it = 0; it <= maxit; it += pe) {
-      int na = 0;
-      TRY(poll_active(c, n_rhs, &na));
-      if (na == 0) break;
-      CU(cudaGraphLaunch(exec, c->stream));
-    }
-  } else {
-    for (int it = 0; it <= maxit; ++it) {
-      if (it % pe == 0) {
-        int na = 0;
-        TRY(poll_active(c, n_rhs, &na));
-        if (na == 0) break;
-      }
-      TRY(cg_iter<T>(c, it, u, f, dbuf, z, q, n_rhs, tol, crit, maxit));
-    }
+static xfft_status loop_finish(const LoopArgs& L) {
+  ProfScope ps(L.c, XFFT_PROF_VECTOR, 1);
+  const long long stride = stride_of(L.c);
+  if (L.dbl)
+    CU(launch_cg_finish<double>((double*)L.u, (double*)L.dA, (double*)L.dB, L.c->st, stride, L.n_rhs,
+                                L.c->stream));
+  else
+    CU(launch_cg_finish<float>((float*)L.u, (float*)L.dA, (float*)L.dB, L.c->st, stride, L.n_rhs,
+                               L.c->stream));
+  return XFFT_OK;
+}
+
+static bool graph_stream(const xfft_ctx* c) {
+  return !c->prof && c->stream != nullptr && c->stream != cudaStreamLegacy && c->stream != cudaStreamPerThread;
+}
+
+// The device-driven loop over the inner solves `items` (one or several contexts): one graph with
+// a conditional while node, each round loop_pe(c) iterations of every item on its context's
+// stream, forked from and joined to `master`.  lm: device LoopState followed by the act pointers
+// and RHS counts of the items (filled here).  Returns XFFT_EUNSUPPORTED when the graph cannot be
+// built (the caller then polls on the host).
+static xfft_status build_device_loop(const std::vector<LoopArgs>& items, cudaStream_t master,
+                                     unsigned char* lm, unsigned char* lm_host, cudaEvent_t fork,
+                                     const std::vector<cudaEvent_t>& joins, long long limit_ns,
+                                     cudaGraphExec_t* exec) {
+  const int n = (int)items.size();
+  LoopState* st = reinterpret_cast<LoopState*>(lm);
+  const int** acts = reinterpret_cast<const int**>(lm + kLoopHead);
+  int* nr = reinterpret_cast<int*>(lm + kLoopHead + sizeof(void*) * kMaxBatch);
+  // the act pointers and counts: staged in pinned host memory, copied on the master stream
+  const int** hacts = reinterpret_cast<const int**>(lm_host + kLoopHead);
+  int* hnr = reinterpret_cast<int*>(lm_host + kLoopHead + sizeof(void*) * kMaxBatch);
+  unsigned max_rounds = 1;
+  for (int i = 0; i < n; ++i) {
+    hacts[i] = items[i].c->act;
+    hnr[i] = items[i].n_rhs;
+    max_rounds = std::max(max_rounds, (unsigned)(items[i].maxit / loop_pe(items[i].c) + 2));
   }
-  {
-    ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-    CU(launch_cg_finish<T>(u, dA, dB, c->st, stride, n_rhs, c->stream));
+  CU(cudaMemcpyAsync(lm + kLoopHead, lm_host + kLoopHead, kLoopBytes - kLoopHead, cudaMemcpyHostToDevice,
+                     master));
+  xfft_status body_status = XFFT_OK;
+  const LoopBody body = [&](cudaStream_t m) -> cudaError_t {
+    cudaError_t e = cudaEventRecord(fork, m);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+      xfft_ctx* c = items[i].c;
+      if (c->stream != m) e = cudaStreamWaitEvent(c->stream, fork, 0);
+      if (e != cudaSuccess) break;
+      const xfft_status s = items[i].dbl ? loop_round<double>(items[i], loop_pe(c))
+                                         : loop_round<float>(items[i], loop_pe(c));
+      if (s != XFFT_OK) {
+        body_status = s;
+        e = cudaErrorUnknown;
+        break;
+      }
+      if (c->stream != m) {
+        e = cudaEventRecord(joins[i], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m, joins[i], 0);
+      }
+    }
+    return e;
+  };
+  const cudaError_t e = build_loop_graph(master, body, acts, nr, n, st, max_rounds, limit_ns, exec);
+  if (body_status != XFFT_OK) return body_status;
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear a sticky launch-configuration error of the failed build
+    return fail(XFFT_EUNSUPPORTED, std::string("device-driven loop: ") + cudaGetErrorString(e));
   }
   return XFFT_OK;
+}
+
+// Launch a built device loop: master after every item's earlier work, every item after the loop.
+static xfft_status run_device_loop(const std::vector<LoopArgs>& items, cudaStream_t master,
+                                   cudaGraphExec_t exec, cudaEvent_t fork, const std::vector<cudaEvent_t>& joins) {
+  for (size_t i = 0; i < items.size(); ++i) {
+    xfft_ctx* c = items[i].c;
+    if (c->stream == master) continue;
+    CU(cudaEventRecord(joins[i], c->stream));
+    CU(cudaStreamWaitEvent(master, joins[i], 0));
+  }
+  CU(cudaGraphLaunch(exec, master));
+  CU(cudaEventRecord(fork, master));
+  for (const auto& L : items)
+    if (L.c->stream != master) CU(cudaStreamWaitEvent(L.c->stream, fork, 0));
+  for (const auto& L : items) TRY(loop_finish(L));
+  return XFFT_OK;
+}
+
+// One context's inner solve: the device-driven loop (cached per argument set) when the stream
+// allows graphs, else convergence polls on the host every poll_every iterations.  *timed_out is
+// set when the loop's device-time limit (option spin_limit_ns) ended it.
+static xfft_status cg_loop(const LoopArgs& L, bool* timed_out) {
+  xfft_ctx* c = L.c;
+  *timed_out = false;
+  if (graph_stream(c) && c->devloop_ok) {
+    const void* key[6] = {L.u, L.f, L.dA, L.dB, L.z, L.q};
+    xfft_ctx::CgGraph* hit = nullptr;
+    for (auto& g : c->cg_graphs)
+      if (g.valid && g.dbl == L.dbl && g.n_rhs == L.n_rhs && g.crit == L.crit && g.maxit == L.maxit &&
+          g.pe == loop_pe(c) && g.tol == L.tol && g.limit == c->opt.spin_limit_ns &&
+          std::equal(key, key + 6, g.p))
+        hit = &g;
+    if (!hit) {
+      cudaGraphExec_t exec = nullptr;
+      const std::vector<LoopArgs> items{L};
+      const xfft_status s = build_device_loop(items, c->stream, c->loopmem, c->h_loop, c->ev_fork,
+                                              c->ev_join, c->opt.spin_limit_ns, &exec);
+      if (s == XFFT_EUNSUPPORTED) {
+        c->devloop_ok = false;
+      } else {
+        TRY(s);
+        hit = &c->cg_graphs[c->cg_next];
+        c->cg_next = (c->cg_next + 1) % 4;
+        if (hit->exec) cudaGraphExecDestroy(hit->exec);
+        *hit = xfft_ctx::CgGraph();
+        hit->valid = true;
+        hit->dbl = L.dbl;
+        hit->n_rhs = L.n_rhs;
+        hit->crit = L.crit;
+        hit->maxit = L.maxit;
+        hit->pe = loop_pe(c);
+        hit->tol = L.tol;
+        hit->limit = c->opt.spin_limit_ns;
+        std::copy(key, key + 6, hit->p);
+        hit->exec = exec;
+      }
+    }
+    if (hit) {
+      TRY(run_device_loop({L}, c->stream, hit->exec, c->ev_fork, c->ev_join));
+      CU(cudaMemcpyAsync(c->h_loop, c->loopmem, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+      *timed_out = reinterpret_cast<LoopState*>(c->h_loop)->timed_out != 0;
+      return XFFT_OK;
+    }
+  }
+  // host-polled loop (tracing on, legacy streams, or no conditional graphs)
+  const int pe = c->opt.poll_every;
+  for (int it = 0; it <= L.maxit; ++it) {
+    if (it % pe == 0) {
+      int na = 0;
+      TRY(poll_active(c, L.n_rhs, &na));
+      if (na == 0) break;
+    }
+    if (L.dbl) {
+      double* dbuf[2] = {(double*)L.dA, (double*)L.dB};
+      TRY(cg_iter<double>(c, it, (double*)L.u, (double*)L.f, dbuf, (double*)L.z, (double*)L.q, L.n_rhs,
+                          L.tol, L.crit, L.maxit));
+    } else {
+      float* dbuf[2] = {(float*)L.dA, (float*)L.dB};
+      TRY(cg_iter<float>(c, it, (float*)L.u, (float*)L.f, dbuf, (float*)L.z, (float*)L.q, L.n_rhs, L.tol,
+                         L.crit, L.maxit));
+    }
+  }
+  return loop_finish(L);
 }
 
 __global__ void k_copy_act_to_mask(const int* act, int* mask, int n) {
@@ -893,13 +1115,30 @@ struct SolveResult {
   int refine_steps;
 };
 
-// Solve for n_rhs strains (device eps_d already filled); the FP64 solution (scaled enriched
-// DOFs) ends in c->v64[0].
-static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
-  const long long stride = stride_of(c);
-  const size_t tot = (size_t)n_rhs * stride;
-  const double tol = c->opt.tol;
-  cudaStream_t s = c->stream;
+// The phases of a solve for n_rhs strains (device eps_d filled), shared by the single-context
+// solve and the lockstep batch: the FP64 solver is one residual phase and one inner solve; the
+// FP32-refined solver repeats (residual of the FP64 iterate, check, inner FP32 solve of the
+// correction).  The FP64 solution (scaled enriched DOFs) ends in c->v64[0].
+struct SolveRun {
+  xfft_ctx* c = nullptr;
+  int n_rhs = 0;
+  SolveResult* R = nullptr;
+  int ref = 0;
+  bool done = false;
+  int pending[64];
+  int hmask[64];
+};
+
+static xfft_status run_begin(SolveRun& s, xfft_ctx* c, int n_rhs, SolveResult* R) {
+  s.c = c;
+  s.n_rhs = n_rhs;
+  s.R = R;
+  s.ref = 0;
+  s.done = false;
+  for (int r = 0; r < 64; ++r) {
+    s.pending[r] = r < n_rhs ? 1 : 0;
+    s.hmask[r] = 0;
+  }
   for (int r = 0; r < n_rhs; ++r) {
     R->iters[r] = 0;
     R->res[r] = 0.0;
@@ -907,116 +1146,208 @@ static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
     for (int k = 0; k < 6; ++k) R->sig[r][k] = 0.0;
   }
   R->refine_steps = 0;
+  CU(cudaMemsetAsync(c->v64[0], 0, (size_t)n_rhs * stride_of(c) * sizeof(double), c->stream));
+  return XFFT_OK;
+}
+
+// enqueue the residual phase: the residual f of the current iterate, z = P^-1 f and the stopping
+// rule (finalisation mode 3)
+static xfft_status run_residual(SolveRun& s) {
+  xfft_ctx* c = s.c;
+  cudaStream_t st = c->stream;
+  const long long stride = stride_of(c);
+  const size_t tot = (size_t)s.n_rhs * stride;
+  const double tol = c->opt.tol;
   if (c->opt.precision == XFFT_FP64) {
-    double *u = c->v64[0], *f = c->v64[1], *d = c->v64[2], *z = c->v64[3], *q = c->v64[4],
-           *d2 = c->v64[5];
-    CU(cudaMemsetAsync(u, 0, tot * sizeof(double), s));
+    double *u = c->v64[0], *f = c->v64[1], *d = c->v64[2], *z = c->v64[3], *q = c->v64[4];
     {
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-      CU(launch_init_state(c->st, c->act, n_rhs, nullptr, s));
+      CU(launch_init_state(c->st, c->act, s.n_rhs, nullptr, st));
     }
-    TRY(do_apply<double>(c, u, q, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit));
+    TRY(do_apply<double>(c, u, q, c->eps_d, s.n_rhs, c->act, 0, tol, 0, c->opt.maxit));
     {
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-      CU(launch_scale_copy<double, double>(q, f, -1.0, stride, n_rhs, c->act, s));
+      CU(launch_scale_copy<double, double>(q, f, -1.0, stride, s.n_rhs, c->act, st));
     }
-    TRY(do_prec<double>(c, f, z, n_rhs, c->act, 3, tol, 0, c->opt.maxit));
-    CU(cudaMemsetAsync(d, 0, tot * sizeof(double), s));
-    TRY(cg_loop<double>(c, u, f, d, d2, z, q, n_rhs, tol, 0, c->opt.maxit));
-    TRY(read_states(c, n_rhs));
-    for (int r = 0; r < n_rhs; ++r) {
-      const RhsState& st = c->h_st[r];
-      R->iters[r] = st.iters;
-      double sn = 0.0;
-      for (int k = 0; k < 6; ++k) {
-        R->sig[r][k] = st.sig[k];
-        sn += st.sig[k] * st.sig[k];
+    TRY(do_prec<double>(c, f, z, s.n_rhs, c->act, 3, tol, 0, c->opt.maxit));
+    CU(cudaMemsetAsync(d, 0, tot * sizeof(double), st));
+    return XFFT_OK;
+  }
+  double* u = c->v64[0];
+  double* r64 = c->v64[4];
+  float *f = c->v32[1], *d = c->v32[2], *z = c->v32[3], *q = c->v32[4];
+  for (int r = 0; r < 64; ++r) s.hmask[r] = r < s.n_rhs ? s.pending[r] : 0;
+  CU(cudaMemcpyAsync(c->outer_mask, s.hmask, 64 * sizeof(int), cudaMemcpyHostToDevice, st));
+  {
+    ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+    CU(launch_init_state(c->st, c->act, s.n_rhs, c->outer_mask, st));
+  }
+  if (s.ref == 0) {
+    // u = 0: the residual is -b; FP32 suffices for the first inner solve because every later
+    // check recomputes the residual of the accumulated iterate in FP64
+    CU(cudaMemsetAsync(d, 0, tot * sizeof(float), st));
+    TRY(do_apply<float>(c, d, q, c->eps_d, s.n_rhs, c->act, 0, tol, 0, c->opt.maxit));
+    ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+    CU(launch_scale_copy<float, float>(q, f, -1.0, stride, s.n_rhs, c->act, st));
+  } else {
+    // residual of the accumulated FP64 iterate in double-word arithmetic (about 48 bits, far
+    // below the FP32 rounding it corrects) and the stopping rule
+    TRY((do_apply<double, dw>(c, u, r64, c->eps_d, s.n_rhs, c->act, 0, tol, 0, c->opt.maxit)));
+    ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+    CU(launch_scale_copy<double, float>(r64, f, -1.0, stride, s.n_rhs, c->act, st));
+  }
+  TRY(do_prec<float>(c, f, z, s.n_rhs, c->act, 3, tol, 0, c->opt.maxit, 1));
+  return XFFT_OK;
+}
+
+static void fill_result(SolveRun& s, int r, const RhsState& st) {
+  double sn = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    s.R->sig[r][k] = st.sig[k];
+    sn += st.sig[k] * st.sig[k];
+  }
+  const double vol = s.c->g.volY;
+  s.R->res[r] = sn > 0 ? sqrt(std::max(st.rr, 0.0) / vol) / (sqrt(sn) / vol) : 0.0;
+}
+
+// read the residual phase's states: done, or an inner solve is needed
+static xfft_status run_check(SolveRun& s, bool* need_inner) {
+  xfft_ctx* c = s.c;
+  TRY(read_states(c, s.n_rhs));
+  *need_inner = false;
+  if (c->opt.precision == XFFT_FP64) {
+    for (int r = 0; r < s.n_rhs; ++r) *need_inner |= c->h_st[r].active != 0;
+    if (!*need_inner) {  // converged (or broke down) at the start
+      for (int r = 0; r < s.n_rhs; ++r) {
+        fill_result(s, r, c->h_st[r]);
+        s.R->status[r] = c->h_st[r].converged ? 0 : (c->h_st[r].status ? c->h_st[r].status : 4);
       }
-      R->res[r] = sn > 0 ? sqrt(std::max(st.rr, 0.0) / c->g.volY) / (sqrt(sn) / c->g.volY) : 0.0;
-      R->status[r] = st.converged ? 0 : (st.status ? st.status : 4);
+      s.done = true;
     }
     return XFFT_OK;
   }
-  // FP32 inner solves with FP64 residual refinement
-  double* u = c->v64[0];
-  double* r64 = c->v64[4];
-  float *du = c->v32[0], *f = c->v32[1], *d = c->v32[2], *z = c->v32[3], *q = c->v32[4],
-        *d2 = c->v32[5];
-  CU(cudaMemsetAsync(u, 0, tot * sizeof(double), s));
-  std::vector<int> pending(n_rhs, 1);
-  std::vector<int> hmask(64, 0);
-  for (int ref = 0; ref <= c->opt.max_refine; ++ref) {
-    for (int r = 0; r < n_rhs; ++r) hmask[r] = pending[r];
-    CU(cudaMemcpyAsync(c->outer_mask, hmask.data(), 64 * sizeof(int), cudaMemcpyHostToDevice, s));
-    {
-      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-      CU(launch_init_state(c->st, c->act, n_rhs, c->outer_mask, s));
-    }
-    if (ref == 0) {
-      // u = 0: the residual is -b; FP32 suffices for the first inner solve because every later
-      // check recomputes the residual of the accumulated iterate in FP64
-      CU(cudaMemsetAsync(d, 0, tot * sizeof(float), s));
-      TRY(do_apply<float>(c, d, q, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit));
-      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-      CU(launch_scale_copy<float, float>(q, f, -1.0, stride, n_rhs, c->act, s));
+  int still = 0;
+  for (int r = 0; r < s.n_rhs; ++r) {
+    if (!s.pending[r]) continue;
+    const RhsState& st = c->h_st[r];
+    fill_result(s, r, st);
+    if (st.converged) {
+      s.pending[r] = 0;
+      s.R->status[r] = 0;
+    } else if (st.status == 5) {
+      s.pending[r] = 0;
+      s.R->status[r] = 5;
     } else {
-      // residual of the accumulated FP64 iterate in double-word arithmetic (about 48 bits, far
-      // below the FP32 rounding it corrects) and the stopping rule
-      TRY((do_apply<double, dw>(c, u, r64, c->eps_d, n_rhs, c->act, 0, tol, 0, c->opt.maxit)));
-      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-      CU(launch_scale_copy<double, float>(r64, f, -1.0, stride, n_rhs, c->act, s));
+      ++still;
     }
-    TRY(do_prec<float>(c, f, z, n_rhs, c->act, 3, tol, 0, c->opt.maxit, 1));
-    TRY(read_states(c, n_rhs));
-    int still = 0;
-    for (int r = 0; r < n_rhs; ++r) {
-      if (!pending[r]) continue;
+  }
+  if (still == 0) {
+    s.done = true;
+  } else if (s.ref == c->opt.max_refine) {
+    for (int r = 0; r < s.n_rhs; ++r)
+      if (s.pending[r]) s.R->status[r] = 4;
+    s.done = true;
+  } else {
+    if (s.ref > 0) s.R->refine_steps++;
+    *need_inner = true;
+  }
+  return XFFT_OK;
+}
+
+// enqueue what precedes the inner solve and return its loop arguments
+static xfft_status run_inner_pre(SolveRun& s, LoopArgs* L) {
+  xfft_ctx* c = s.c;
+  L->c = c;
+  L->n_rhs = s.n_rhs;
+  L->maxit = c->opt.maxit;
+  if (c->opt.precision == XFFT_FP64) {
+    L->dbl = true;
+    L->u = c->v64[0];
+    L->f = c->v64[1];
+    L->dA = c->v64[2];
+    L->dB = c->v64[5];
+    L->z = c->v64[3];
+    L->q = c->v64[4];
+    L->tol = c->opt.tol;
+    L->crit = 0;
+    return XFFT_OK;
+  }
+  const size_t tot = (size_t)s.n_rhs * stride_of(c);
+  // inner FP32 PCG on A delta = r (relative reduction inner_tol); the act flags of the refining
+  // RHS were set by the mode-3 finalisation
+  {
+    ProfScope ps(c, XFFT_PROF_VECTOR, 2);
+    k_copy_act_to_mask<<<1, 64, 0, c->stream>>>(c->act, c->outer_mask, s.n_rhs);
+    CU(cudaGetLastError());
+    CU(cudaMemsetAsync(c->v32[0], 0, tot * sizeof(float), c->stream));
+    CU(cudaMemsetAsync(c->v32[2], 0, tot * sizeof(float), c->stream));
+  }
+  L->dbl = false;
+  L->u = c->v32[0];
+  L->f = c->v32[1];
+  L->dA = c->v32[2];
+  L->dB = c->v32[5];
+  L->z = c->v32[3];
+  L->q = c->v32[4];
+  L->tol = 0.5;
+  L->crit = 1;
+  return XFFT_OK;
+}
+
+// after the inner solve (its last u += alpha d applied): results or the next refinement round
+static xfft_status run_inner_post(SolveRun& s, bool timed_out) {
+  xfft_ctx* c = s.c;
+  TRY(read_states(c, s.n_rhs));
+  if (c->opt.precision == XFFT_FP64) {
+    for (int r = 0; r < s.n_rhs; ++r) {
       const RhsState& st = c->h_st[r];
-      double sn = 0.0;
-      for (int k = 0; k < 6; ++k) {
-        R->sig[r][k] = st.sig[k];
-        sn += st.sig[k] * st.sig[k];
+      s.R->iters[r] = st.iters;
+      fill_result(s, r, st);
+      s.R->status[r] = st.converged ? 0 : (st.status ? st.status : (timed_out && st.active ? 6 : 4));
+    }
+    s.done = true;
+    return XFFT_OK;
+  }
+  for (int r = 0; r < s.n_rhs; ++r) {
+    if (s.hmask[r]) s.R->iters[r] += c->h_st[r].iters;
+    if (s.hmask[r] && c->h_st[r].status == 5) {  // breakdown inside the inner solve
+      s.pending[r] = 0;
+      s.R->status[r] = 5;
+    }
+  }
+  {
+    ProfScope ps(c, XFFT_PROF_VECTOR, 1);
+    CU(launch_add_to_double<float>(c->v64[0], c->v32[0], stride_of(c), s.n_rhs, c->outer_mask, c->stream));
+  }
+  if (timed_out) {
+    for (int r = 0; r < s.n_rhs; ++r)
+      if (s.pending[r] && c->h_st[r].active) {
+        s.pending[r] = 0;
+        s.R->status[r] = 6;
       }
-      R->res[r] = sn > 0 ? sqrt(std::max(st.rr, 0.0) / c->g.volY) / (sqrt(sn) / c->g.volY) : 0.0;
-      if (st.converged) {
-        pending[r] = 0;
-        R->status[r] = 0;
-      } else if (st.status == 5) {
-        pending[r] = 0;
-        R->status[r] = 5;
-      } else {
-        ++still;
-      }
-    }
-    if (still == 0) break;
-    if (ref == c->opt.max_refine) {
-      for (int r = 0; r < n_rhs; ++r)
-        if (pending[r]) R->status[r] = 4;
-      break;
-    }
-    if (ref > 0) R->refine_steps++;
-    // inner FP32 PCG on A delta = r (relative reduction inner_tol); the act flags of the
-    // refining RHS were set by the mode-3 finalisation
-    {
-      ProfScope ps(c, XFFT_PROF_VECTOR, 2);
-      k_copy_act_to_mask<<<1, 64, 0, s>>>(c->act, c->outer_mask, n_rhs);
-      CU(cudaGetLastError());
-      CU(cudaMemsetAsync(du, 0, tot * sizeof(float), s));
-      CU(cudaMemsetAsync(d, 0, tot * sizeof(float), s));
-    }
-    TRY(cg_loop<float>(c, du, f, d, d2, z, q, n_rhs, 0.5, 1, c->opt.maxit));
-    TRY(read_states(c, n_rhs));
-    for (int r = 0; r < n_rhs; ++r) {
-      if (hmask[r]) R->iters[r] += c->h_st[r].iters;
-      if (hmask[r] && c->h_st[r].status == 5) {  // breakdown inside the inner solve
-        pending[r] = 0;
-        R->status[r] = 5;
-      }
-    }
-    {
-      ProfScope ps(c, XFFT_PROF_VECTOR, 1);
-      CU(launch_add_to_double<float>(u, du, stride, n_rhs, c->outer_mask, s));
-    }
+  }
+  s.ref += 1;
+  for (int r = 0; r < s.n_rhs; ++r)
+    if (s.pending[r]) return XFFT_OK;
+  s.done = true;
+  return XFFT_OK;
+}
+
+// Solve for n_rhs strains (device eps_d already filled); the FP64 solution (scaled enriched
+// DOFs) ends in c->v64[0].
+static xfft_status solve_core(xfft_ctx* c, int n_rhs, SolveResult* R) {
+  SolveRun s;
+  TRY(run_begin(s, c, n_rhs, R));
+  while (!s.done) {
+    TRY(run_residual(s));
+    bool need = false;
+    TRY(run_check(s, &need));
+    if (!need) break;
+    LoopArgs L;
+    TRY(run_inner_pre(s, &L));
+    bool timed_out = false;
+    TRY(cg_loop(L, &timed_out));
+    TRY(run_inner_post(s, timed_out));
   }
   return XFFT_OK;
 }
@@ -1059,9 +1390,11 @@ static xfft_status status_of(const SolveResult& R, int n_rhs) {
   xfft_status st = XFFT_OK;
   for (int r = 0; r < n_rhs; ++r) {
     if (R.status[r] == 5) return fail(XFFT_EBREAKDOWN, "CG breakdown");
-    if (R.status[r] == 4) st = XFFT_ENOTCONV;
+    if (R.status[r] == 6) st = XFFT_ETIMEOUT;
+    if (R.status[r] == 4 && st == XFFT_OK) st = XFFT_ENOTCONV;
   }
   if (st == XFFT_ENOTCONV) g_err = "maximum number of iterations reached";
+  if (st == XFFT_ETIMEOUT) g_err = "the device-driven iteration loop reached its time limit (spin_limit_ns)";
   return st;
 }
 
@@ -1072,6 +1405,7 @@ extern "C" xfft_status xfft_solve(xfft_ctx* c, int n_rhs, const double* eps_bar,
   if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
   if (n_rhs < 1 || n_rhs > 64) return fail(XFFT_EINVAL, "n_rhs must be in [1, 64]");
   TRY(ensure_work(c, n_rhs, c->opt.precision));
+  TRY(autotune(c));
   cudaStream_t s = c->stream;
   TRY(upload_eps(c, n_rhs, eps_bar));
   cudaEvent_t e0, e1;
@@ -1136,14 +1470,32 @@ extern "C" xfft_status xfft_solve(xfft_ctx* c, int n_rhs, const double* eps_bar,
   return status_of(R, n_rhs);
 }
 
+// C_eff, the six-case checkpoint and the stats of a finished six-case solve
+static xfft_status finish_six(xfft_ctx* c, const SolveResult& R, double C_eff[36], xfft_stats* stats,
+                              float msolve) {
+  const long long stride = stride_of(c);
+  if (!c->U6) CU(dalloc(c, &c->U6, 6 * (size_t)stride));
+  CU(cudaMemcpyAsync(c->U6, c->v64[0], 6 * (size_t)stride * sizeof(double), cudaMemcpyDeviceToDevice,
+                     c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  // C_eff[i][k] = <sigma_i>(E_k)
+  for (int i = 0; i < 6; ++i)
+    for (int k = 0; k < 6; ++k) C_eff[i * 6 + k] = R.sig[k][i] / c->g.volY;
+  memcpy(c->C6, C_eff, sizeof(c->C6));
+  finish_stats(c, R, 6, msolve, stats);
+  xfft_status st = status_of(R, 6);
+  if (st == XFFT_OK) c->have6 = true;
+  return st;
+}
+
 extern "C" xfft_status xfft_effective_stiffness(xfft_ctx* c, double C_eff[36], xfft_stats* stats) {
   if (!c || !C_eff) return fail(XFFT_EINVAL, "NULL argument");
   if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
   double eps[36];
   for (int k = 0; k < 36; ++k) eps[k] = (k % 7 == 0) ? 1.0 : 0.0;
-  double ms[36];
   c->have6 = false;
   TRY(ensure_work(c, 6, c->opt.precision));
+  TRY(autotune(c));
   TRY(upload_eps(c, 6, eps));
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
@@ -1157,38 +1509,17 @@ extern "C" xfft_status xfft_effective_stiffness(xfft_ctx* c, double C_eff[36], x
     cudaEventDestroy(e1);
     return rs;
   }
-  const long long stride = stride_of(c);
-  if (!c->U6) CU(dalloc(c, &c->U6, 6 * (size_t)stride));
-  CU(cudaMemcpyAsync(c->U6, c->v64[0], 6 * (size_t)stride * sizeof(double), cudaMemcpyDeviceToDevice,
-                     c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  for (int r = 0; r < 6; ++r)
-    for (int k = 0; k < 6; ++k) ms[6 * r + k] = R.sig[r][k] / c->g.volY;
-  // C_eff[i][k] = <sigma_i>(E_k)
-  for (int i = 0; i < 6; ++i)
-    for (int k = 0; k < 6; ++k) C_eff[i * 6 + k] = ms[6 * k + i];
-  memcpy(c->C6, C_eff, sizeof(c->C6));
+  CU(cudaEventSynchronize(e1));
   float msolve = 0.f;
   cudaEventElapsedTime(&msolve, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  finish_stats(c, R, 6, msolve, stats);
-  xfft_status st = status_of(R, 6);
-  if (st == XFFT_OK) c->have6 = true;
-  return st;
+  return finish_six(c, R, C_eff, stats, msolve);
 }
 
-extern "C" xfft_status xfft_batch_effective_stiffness(int n, xfft_ctx* const* ctxs, double* C_eff,
-                                                      xfft_stats* stats) {
-  if (n < 1 || !ctxs || !C_eff) return fail(XFFT_EINVAL, "n >= 1 contexts and C_eff required");
-  for (int i = 0; i < n; ++i) {
-    if (!ctxs[i]) return fail(XFFT_EINVAL, "NULL context");
-    if (!ctxs[i]->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
-    for (int k = 0; k < i; ++k)
-      if (ctxs[k] == ctxs[i]) return fail(XFFT_EINVAL, "a context appears twice in the batch");
-  }
-  int dev = 0;
-  CU(cudaGetDevice(&dev));
+// The threaded form of the batch (contexts on the legacy stream, or tracing on): each context's
+// xfft_effective_stiffness from its own host thread.
+static xfft_status batch_threaded(int n, xfft_ctx* const* ctxs, double* C_eff, xfft_stats* stats, int dev) {
   std::vector<xfft_status> st(n, XFFT_OK);
   std::vector<std::string> msg(n);
   std::vector<std::thread> th;
@@ -1210,6 +1541,130 @@ extern "C" xfft_status xfft_batch_effective_stiffness(int n, xfft_ctx* const* ct
       return fail(st[i], "context " + std::to_string(i) + ": " + msg[i]);
   for (int i = 0; i < n; ++i)
     if (st[i] != XFFT_OK) return fail(st[i], "context " + std::to_string(i) + ": " + msg[i]);
+  return XFFT_OK;
+}
+
+// Resources of one lockstep batch call: a master stream, fork / join events, loop memory.
+struct BatchRes {
+  cudaStream_t master = nullptr;
+  cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+  std::vector<cudaEvent_t> joins;
+  unsigned char* lm = nullptr;
+  unsigned char* lm_host = nullptr;
+  ~BatchRes() {
+    if (master) cudaStreamSynchronize(master);
+    for (auto e : joins)
+      if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (lm) cudaFree(lm);
+    if (lm_host) cudaFreeHost(lm_host);
+    if (master) cudaStreamDestroy(master);
+  }
+};
+
+extern "C" xfft_status xfft_batch_effective_stiffness(int n, xfft_ctx* const* ctxs, double* C_eff,
+                                                      xfft_stats* stats) {
+  if (n < 1 || !ctxs || !C_eff) return fail(XFFT_EINVAL, "n >= 1 contexts and C_eff required");
+  if (n > kMaxBatch) return fail(XFFT_EINVAL, "at most 64 contexts per batch");
+  bool lockstep = true;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(XFFT_EINVAL, "NULL context");
+    if (!ctxs[i]->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return fail(XFFT_EINVAL, "a context appears twice in the batch");
+    lockstep = lockstep && graph_stream(ctxs[i]) && ctxs[i]->devloop_ok;
+  }
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (!lockstep) return batch_threaded(n, ctxs, C_eff, stats, dev);
+  // Lockstep: the residual phases of all contexts on their own streams, then ONE device-driven
+  // loop graph over every context still iterating, until every context is done.
+  BatchRes B;
+  CU(cudaStreamCreateWithFlags(&B.master, cudaStreamNonBlocking));
+  CU(cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming));
+  CU(cudaEventCreate(&B.t0));
+  CU(cudaEventCreate(&B.t1));
+  B.joins.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) CU(cudaEventCreateWithFlags(&B.joins[i], cudaEventDisableTiming));
+  CU(cudaMalloc((void**)&B.lm, kLoopBytes));
+  CU(cudaMallocHost((void**)&B.lm_host, kLoopBytes));
+  double eps[36];
+  for (int k = 0; k < 36; ++k) eps[k] = (k % 7 == 0) ? 1.0 : 0.0;
+  std::vector<SolveRun> runs(n);
+  std::vector<SolveResult> Rs(n);
+  long long limit = -1;
+  for (int i = 0; i < n; ++i) {
+    xfft_ctx* c = ctxs[i];
+    c->have6 = false;
+    TRY(ensure_work(c, 6, c->opt.precision));
+    TRY(autotune(c));
+    TRY(upload_eps(c, 6, eps));
+    if (c->opt.spin_limit_ns >= 0 && (limit < 0 || c->opt.spin_limit_ns < limit)) limit = c->opt.spin_limit_ns;
+  }
+  CU(cudaEventRecord(B.t0, B.master));
+  for (int i = 0; i < n; ++i) {
+    CU(cudaStreamWaitEvent(ctxs[i]->stream, B.t0, 0));
+    TRY(run_begin(runs[i], ctxs[i], 6, &Rs[i]));
+  }
+  for (;;) {
+    for (auto& r : runs)
+      if (!r.done) TRY(run_residual(r));
+    std::vector<LoopArgs> items;
+    std::vector<SolveRun*> inner;
+    for (auto& r : runs) {
+      if (r.done) continue;
+      bool need = false;
+      TRY(run_check(r, &need));
+      if (!need) continue;
+      LoopArgs L;
+      TRY(run_inner_pre(r, &L));
+      items.push_back(L);
+      inner.push_back(&r);
+    }
+    if (items.empty()) break;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> joins(B.joins.begin(), B.joins.begin() + items.size());
+    const xfft_status bs = build_device_loop(items, B.master, B.lm, B.lm_host, B.fork, joins, limit, &exec);
+    bool timed_out = false;
+    if (bs == XFFT_OK) {
+      const xfft_status rs = run_device_loop(items, B.master, exec, B.fork, joins);
+      cudaGraphExecDestroy(exec);
+      TRY(rs);
+      CU(cudaMemcpyAsync(B.lm_host, B.lm, sizeof(LoopState), cudaMemcpyDeviceToHost, B.master));
+      CU(cudaStreamSynchronize(B.master));
+      timed_out = reinterpret_cast<LoopState*>(B.lm_host)->timed_out != 0;
+    } else if (bs == XFFT_EUNSUPPORTED) {
+      for (const auto& L : items) {  // no conditional graphs: each context's own loop
+        L.c->devloop_ok = false;
+        bool to = false;
+        TRY(cg_loop(L, &to));
+        timed_out = timed_out || to;
+      }
+    } else {
+      return bs;
+    }
+    for (auto* r : inner) TRY(run_inner_post(*r, timed_out));
+  }
+  for (int i = 0; i < n; ++i) {
+    CU(cudaEventRecord(B.joins[i], ctxs[i]->stream));
+    CU(cudaStreamWaitEvent(B.master, B.joins[i], 0));
+  }
+  CU(cudaEventRecord(B.t1, B.master));
+  CU(cudaEventSynchronize(B.t1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, B.t0, B.t1);
+  xfft_status first = XFFT_OK;
+  std::string msg;
+  for (int i = 0; i < n; ++i) {
+    const xfft_status st = finish_six(ctxs[i], Rs[i], C_eff + 36 * (size_t)i, stats ? stats + i : nullptr, ms);
+    if (st != XFFT_OK && (first == XFFT_OK || (first == XFFT_ENOTCONV && st != XFFT_ENOTCONV))) {
+      first = st;
+      msg = "context " + std::to_string(i) + ": " + g_err;
+    }
+  }
+  if (first != XFFT_OK) return fail(first, msg);
   return XFFT_OK;
 }
 
@@ -1318,7 +1773,7 @@ static xfft_status apply_entry(xfft_ctx* c, int n_rhs, const double* d, const do
   if (st == XFFT_OK) st = stage_out<T>(c, qq, q, tot, on_dev, scratch);
   if (st == XFFT_OK && sigma_int) {
     const int nparts = nparts_of(c);
-    const int used = apply_uncut_blocks(c->g) + apply_cut_blocks(c->ncut);
+    const int used = apply_uncut_blocks(c->g) + cut_blocks_of(c);
     cudaError_t e = launch_reduce_partials(c->partials, 7 * n_rhs, nparts, used, c->red_out, c->stream);
     double red[7 * 64];
     if (e == cudaSuccess)

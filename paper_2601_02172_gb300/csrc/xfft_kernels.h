@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 #include "dw.cuh"
 #include "xfft_common.cuh"
 
@@ -118,6 +120,10 @@ struct ApplyArgs {
   // FP32 cached cut-tet matrices (kCutPacked x ncut) or nullptr; used by the FP32 cut apply of
   // linear applies without stress integrals (the inner CG iterations)
   const float* kcache = nullptr;
+  // launch shape of the cut-tet kernel (0: the defaults, apply_cut_blocks(ncut) blocks and up
+  // to kCutMaxR right-hand sides per launch); the partial slots must hold cut_blocks
+  int cut_blocks = 0;
+  int cut_rpl = 0;
 };
 // T is the arithmetic type (float, double or dw = double-word on FP64 data); the vectors are
 // stored as Store<T>::type
@@ -133,7 +139,8 @@ cudaError_t launch_apply_cut(const typename Store<T>::type* d, typename Store<T>
                              const typename Store<T>::type* isD, CutData cd, const ApplyArgs& a,
                              int n_rhs, cudaStream_t s);
 int apply_uncut_blocks(const GridDev& g);
-int apply_cut_blocks(int ncut);
+int apply_cut_blocks(int ncut);      // the default grid of the cut-tet kernel
+int apply_cut_blocks_max(int ncut);  // the largest grid a tuned launch shape may use
 
 // per-voxel average stress of the (scaled) solution u, double
 cudaError_t launch_voxel_stress(const double* u, const double* isD, CutData cd,
@@ -215,6 +222,23 @@ cudaError_t launch_bb_dots(const T* d, const T* q, const int* active, long long 
 cudaError_t launch_finalize(RhsState* st, const double* partials, FinArgs fa, int n_rhs, int* act,
                             cudaStream_t s);
 cudaError_t launch_init_state(RhsState* st, int* act, int n_rhs, const int* mask, cudaStream_t s);
+
+// ---- device-driven loops (loop.cu)
+struct LoopState {
+  unsigned long long t0;  // globaltimer at the graph's start
+  unsigned rounds;        // body rounds run
+  int timed_out;          // 1: the device-time limit ended the loop
+};
+// captures one round of the loop body: called while `master` is capturing; work on other
+// streams must fork from and join back to master
+using LoopBody = std::function<cudaError_t(cudaStream_t master)>;
+// An executable graph: a start kernel, then a conditional while node whose body is one round
+// followed by the condition kernel (continue while some act[i][r], r < nr[i], of the n contexts is
+// set, fewer than max_rounds rounds ran and less than limit_ns device time passed; limit_ns < 0:
+// no limit).  acts (n device pointers), nr (n ints) and st live in device memory.
+cudaError_t build_loop_graph(cudaStream_t master, const LoopBody& body, const int* const* acts,
+                             const int* nr, int n, LoopState* st, unsigned max_rounds, long long limit_ns,
+                             cudaGraphExec_t* exec);
 
 // ---- gradient (grad.cu)
 // values reduced per gradient call: dLoss/dlambda_p (p < kMaxPhases), dLoss/dmu_p, then the 21

@@ -112,3 +112,30 @@ def test_allocation_cap_returns_enomem_and_leaks_nothing(xf):
     s.set_microstructure(L, lm, lp)
     assert s.effective_stiffness()[1]["converged"]
     s.close()
+
+
+def test_device_loop_time_limit_returns_etimeout(xf):
+    """spin_limit_ns = 0: the device-driven iteration loop stops after its first round and the
+    call returns XFFT_ETIMEOUT with the last iterate; nothing is left running on the GPU (the
+    stream drains) and the same microstructure then converges without the limit, in a single
+    solve and in a lockstep batch."""
+    import torch
+    n, L, lm, lp = _case()
+    for prec in ("fp64", "fp32"):
+        s = xf.Solver(n, precision=prec, tol=1e-10, spin_limit_ns=0)
+        s.set_microstructure(L, lm, lp)
+        with pytest.raises(xf.XfftError) as ei:
+            s.solve(np.eye(6)[:2], u=False)
+        assert ei.value.status == xf.capi.XFFT_ETIMEOUT
+        torch.cuda.synchronize()
+        s2 = xf.Solver(n, precision=prec, tol=1e-10)
+        s2.set_microstructure(L, lm, lp)
+        assert s2.solve(np.eye(6)[:2], u=False)["converged"]
+        with pytest.raises(xf.XfftError) as ei:
+            xf.batch_effective_stiffness([s, s2])
+        assert ei.value.status == xf.capi.XFFT_ETIMEOUT
+        torch.cuda.synchronize()
+        C, st = xf.batch_effective_stiffness([s2])
+        assert st[0]["iters"][0] > 0
+        s.close()
+        s2.close()

@@ -402,9 +402,9 @@ def test_autograd_effective_stiffness(xf):
 
 
 def test_batch_uneven_microstructures(xf):
-    """Batch of microstructures on uneven grids solved at once (one host thread and stream per
-    context, graph-replayed iterations), FP32-refined to 1e-8: each C_eff against its own FP64
-    solve, against the same solver run alone, and (16^3 member) against the oracle."""
+    """Batch of microstructures on uneven grids solved at once (lockstep; every inner solve of
+    all contexts one device-driven graph launch), FP32-refined to 1e-8: each C_eff against its
+    own FP64 solve, against the same solver run alone, and (16^3 member) against the oracle."""
     ws = synth.batch_uneven(count=6, seed=5, sizes=(16, 32, 48))
     ws[0] = dict(ws[0], n=(16, 16, 16), L=synth.sphere_levelset((16, 16, 16), (0.5, 0.5, 0.5), 0.3))
     solvers = []
@@ -425,6 +425,28 @@ def test_batch_uneven_microstructures(xf):
     o = XFEM(ws[0]["L"], ws[0]["n"], lame_minus=ws[0]["lame_minus"], lame_plus=ws[0]["lame_plus"])
     Co, _, _ = o.effective_stiffness()
     assert np.abs(Cs[0] - Co).max() < 1e-6 * np.abs(Co).max()
+
+
+def test_batch_mixed_precisions_and_schemes(xf):
+    """One lockstep batch holding an FP64 context, an FP32-refined context and a nonlinear-CG
+    context (their inner solves share one device-driven graph): each C_eff and iteration count
+    equals that of the same context solved alone."""
+    n = (16, 16, 16)
+    L = synth.sphere_levelset(n, (0.45, 0.5, 0.55), 0.3)
+    lm, lp = synth.lame_from_E_nu(10.0, 0.3), synth.lame_from_E_nu(1.0, 0.3)
+    kws = [dict(precision="fp64", tol=1e-10), dict(precision="fp32", tol=1e-8),
+           dict(precision="fp64", tol=1e-9, scheme="nlcg")]
+    solvers = []
+    for kw in kws:
+        sv = xf.Solver(n, **kw)
+        sv.set_microstructure(L, lm, lp)
+        solvers.append(sv)
+    Cs, sts = xf.batch_effective_stiffness(solvers)
+    for sv, C, st in zip(solvers, Cs, sts):
+        C1, st1 = sv.effective_stiffness()
+        assert st1["converged"] and st["iters"] == st1["iters"], (st["iters"], st1["iters"])
+        assert np.abs(C1 - C).max() < 1e-9 * np.abs(C).max()
+        sv.close()
 
 
 def test_legacy_stream_matches_own_stream(xf):
