@@ -63,6 +63,9 @@ def _per_rhs_bytes(kind, N, nX, ncut, geo):
 
 
 REC_REALS = 68  # reals of a cut tet's apply record (geometry, moduli, 1/sqrt(D0) of its DOFs)
+# algorithmic flops of the stencil per voxel and right-hand side: six Kuhn tets of about 35 each
+# (gradient columns, trace, stress, edge tensions) and the corner forces
+STENCIL_FLOPS = 250
 
 
 def cut_bytes(prec, nX, ncut):
@@ -455,23 +458,50 @@ def main():
             extra["fp64"] = {"solves_per_s_batched6": 1.0 / t_b, "solves_per_s_single_rhs": 1.0 / t_1,
                              "iters_batched6": sum(st64["iters"]), "iters_single_rhs": its1,
                              "tol": args.tol}
+            # the FP64 path against the measured FMA peaks (GB300's FP64 rate is far below FP32's):
+            # the FP64 stencil at STENCIL_FLOPS per voxel and right-hand side, traced separately
+            from paper_2601_02172_gb300.capi import fma_rate
+            peak64, peak32 = fma_rate("fp64"), fma_rate("fp32")
+            s64.profile(True)
+            s64.effective_stiffness()
+            p64 = s64.profile_read()
+            s64.profile(False)
+            ms_u, la_u, un_u = p64["apply_uncut_f64"]
+            fl = STENCIL_FLOPS * N * un_u / (ms_u / 1e3) if ms_u > 0 else 0.0
+            by = (48 * N + 6 * N) * un_u / (ms_u / 1e3) if ms_u > 0 else 0.0
+            extra["fp64"].update({
+                "fma_peak_fp64_tflops_measured": peak64 / 1e12, "fma_peak_fp32_tflops_measured": peak32 / 1e12,
+                "stencil_fp64": {"ms_per_launch": ms_u / max(la_u, 1), "achieved_tflops": fl / 1e12,
+                                 "frac_of_measured_fp64_fma_peak": fl / peak64,
+                                 "achieved_gbs": by / 1e9, "frac_of_measured_hbm": by / 1e9 / load_peaks()[0],
+                                 "flops_per_voxel_rhs": STENCIL_FLOPS}})
             extra["accuracy"] = {
                 "ceff_rel_err_fp32_refined_vs_fp64_tol1e-10": float(np.abs(C - Cref).max() / np.abs(Cref).max()),
                 "ceff_rel_err_fp64_vs_fp64_tol1e-10": float(np.abs(C64 - Cref).max() / np.abs(Cref).max())}
             s64.close()
             sref.close()
         if not args.no_extras:
-            # variant enriched preconditioner (3x3 node blocks): same system, iteration count and rate
+            # variant enriched preconditioner (3x3 node blocks, the north star's "block preconditioner
+            # to the enriched DOFs"): the same whole step (set-up, six-case solve, gradient), timed
+            # like the headline
             sb = Solver(n, precision="fp32", tol=args.tol, enr_precond="block3")
             sb.set_microstructure(L_d, lm, lp, s_d)
             sb.effective_stiffness()
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            Cb, stb = sb.effective_stiffness()
+            e0b, e1b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0b.record()
+            its_b = 0
+            for _ in range(args.steps):
+                sb.set_microstructure(L_d, lm, lp, s_d)
+                Cb, stb = sb.effective_stiffness()
+                sb.grad(2.0 * (Cb - Ct), device=dev)
+                its_b += sum(stb["iters"])
+            e1b.record()
             torch.cuda.synchronize()
-            extra["enr_block3"] = {"solves_per_s": 1.0 / (time.perf_counter() - t0),
-                                   "cg_iters": int(sum(stb["iters"])),
-                                   "identity_cg_iters": steps_iters / args.steps,
+            extra["enr_block3"] = {"solves_per_s": args.steps / (e0b.elapsed_time(e1b) / 1e3),
+                                   "cg_iters_per_step": its_b / args.steps,
+                                   "identity_cg_iters_per_step": steps_iters / args.steps,
+                                   "identity_solves_per_s": value,
                                    "ceff_rel_diff_vs_identity": float(np.abs(Cb - C).max() / np.abs(C).max())}
             sb.close()
             # many microstructures at once (16 uneven grids x 6 load cases, FP32-refined to 1e-8):
@@ -494,6 +524,16 @@ def main():
                 sv.effective_stiffness()
             torch.cuda.synchronize()
             t_seq = time.perf_counter() - t0
+            # per-context concurrency: one host thread per solver (ctypes releases the GIL), each
+            # with its own stream and device-driven loops
+            import concurrent.futures as cf
+            with cf.ThreadPoolExecutor(len(bsolvers)) as ex:
+                list(ex.map(lambda sv: sv.effective_stiffness(), bsolvers))  # warm
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                list(ex.map(lambda sv: sv.effective_stiffness(), bsolvers))
+                torch.cuda.synchronize()
+                t_thr = time.perf_counter() - t0
             # accuracy of the FP32-refined batch against plain FP64 solves of the same members
             errs = []
             for wb, Cb in zip(bw, Cbat):
@@ -506,7 +546,10 @@ def main():
                                 "ceff_max_rel_err_vs_fp64": max(errs),
                                 "grids": [int(wb["n"][0]) for wb in bw], "tol": 1e-8,
                                 "solves_per_s_batched": len(bw) / t_bat,
+                                "solves_per_s_threads": len(bw) / t_thr,
                                 "solves_per_s_sequential": len(bw) / t_seq,
+                                "batched": "lockstep: every inner solve of all 16 one device-driven graph launch",
+                                "launch_shapes": [list(sv.tuning) for sv in bsolvers],
                                 "dof_iters_per_s_batched": sum(3.0 * (sb["n_fe"] + sb["n_x"]) * sum(sb["iters"])
                                                                for sb in bst) / t_bat}
             for sv in bsolvers:
@@ -563,6 +606,37 @@ def main():
                 hashin["enriched_node_share"] = sv.num_enriched / 128 ** 3
                 sv.close()
             extra["hashin_neutral_inclusion"] = hashin
+            # precision at scale (config 5): the 256^3 fibres and the 384^3 tilted laminate, one
+            # FP32-refined six-case solve each (set-up excluded), and their preconditioner's device
+            # time per right-hand side and HBM fraction from a traced repeat
+            scale5 = {}
+            for name in ("fibers60", "laminate"):
+                w5 = synth.make_workload(name)
+                n5 = tuple(w5["n"])
+                N5 = int(np.prod(n5))
+                sv = Solver(n5, precision="fp32", tol=1e-8)
+                sv.set_microstructure(w5["L"], w5["lame_minus"], w5["lame_plus"])
+                sv.effective_stiffness()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                C5, st5 = sv.effective_stiffness()
+                torch.cuda.synchronize()
+                t5 = time.perf_counter() - t0
+                sv.profile(True)
+                sv.effective_stiffness()
+                p5 = sv.profile_read()
+                sv.profile(False)
+                pm, _, pu = p5["prec_f32"]
+                nX5 = sv.num_enriched
+                bps = 48.0 * (N5 + nX5) * pu / (pm / 1e3) if pm > 0 else 0.0
+                scale5[name] = {"grid": list(n5), "n_enriched": nX5, "solves_per_s": 1.0 / t5,
+                                "cg_iters": int(sum(st5["iters"])), "converged": bool(st5["converged"]),
+                                "prec_ms_per_rhs": pm / max(pu, 1),
+                                "prec_frac_of_measured_hbm": bps / 1e9 / load_peaks()[0],
+                                "prec_path": "five-pass (the fused y-z slab passes cover 128 x 128 planes)"}
+                sv.close()
+                del w5
+            extra["precision_at_scale"] = scale5
             # the paper's caching trade-off: cut-tet element matrices cached (option cut_cache)
             # against their action recomputed from the per-side moments at every apply (default)
             cc = {"cache_bytes": 1200 * info["ncut"]}
@@ -617,6 +691,8 @@ def main():
                            "precision": "FP32 PCG; residuals of the FP64 iterate in double-word arithmetic; "
                                          "FP64 CG scalars",
                            "tol": args.tol, "n_enriched": nX, "n_cut_tets": info["ncut"],
+                           "launch_shapes": dict(zip(("cut_blocks", "cut_rhs_per_launch", "prec_rhs_per_group"),
+                                                     solver.tuning)),
                            "l2": "inputs larger than L2 (about 1.3 GB of fields per step)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "dof_iters_per_s": dofit_rate, "cg_iters_per_step": steps_iters / args.steps,

@@ -136,9 +136,11 @@ typedef struct {
                           active); past it the loop stops, the outputs hold the last iterate and
                           the call returns XFFT_ETIMEOUT.  < 0 (default): no limit */
   int autotune;        /* FP32_REFINED: 1 (default) times candidate launch shapes of the cut-tet
-                          kernel (grid size, right-hand sides per launch) on the microstructure at
-                          its first solve and keeps the fastest (cached per grid and cut-tet
-                          count for the process; see xfft_get_tuning); 0 keeps the defaults */
+                          kernel (grid size, right-hand sides per launch) and of the
+                          preconditioner (right-hand sides per group of FFT passes) on the
+                          microstructure at its first solve and keeps the fastest (cached per
+                          grid and cut-tet count for the process; see xfft_get_tuning); 0 keeps
+                          the defaults */
 } xfft_options;
 
 typedef struct {
@@ -301,10 +303,20 @@ xfft_status xfft_profile_read(xfft_ctx* ctx, double ms[16], long long launches[1
 xfft_status xfft_apply_noalloc(xfft_ctx* ctx, int n_rhs, const double* d, double* q,
                                double* dAd_sig);
 
-/* Launch shape of the FP32 cut-tet kernel in use (not in the paper): its grid in blocks and the
- * right-hand sides per launch, as picked by the tuner (option autotune) or the defaults.
- * Errors: EINVAL (NULL), ESTATE (no microstructure). */
-xfft_status xfft_get_tuning(const xfft_ctx* ctx, int* cut_blocks, int* cut_rhs_per_launch);
+/* Launch shapes in use (not in the paper), as picked by the tuner (option autotune) or the
+ * defaults: the FP32 cut-tet kernel's grid in blocks and right-hand sides per launch (default 8,
+ * i.e. all of a six-case solve), and the FP32 preconditioner's right-hand sides per group of FFT
+ * passes (default 64, i.e. all at once; smaller groups keep a group's spectrum in L2 between the
+ * passes).  Errors: EINVAL (NULL), ESTATE (no microstructure). */
+xfft_status xfft_get_tuning(const xfft_ctx* ctx, int* cut_blocks, int* cut_rhs_per_launch,
+                            int* prec_rhs_per_group);
+
+/* Measured FMA throughput of the current GPU in FLOP/s (2 per FMA; not in the paper: the
+ * denominator of the ALU roofline reported for the FP64 kernels, precision XFFT_FP64, and for the
+ * double-word kernels on the FP32 pipes, XFFT_FP32_REFINED).  A probe kernel of independent FMA
+ * chains over 8 blocks per SM, timed with CUDA events on `stream` (a cudaStream_t or NULL);
+ * about a millisecond.  Errors: EINVAL, ECUDA. */
+xfft_status xfft_fma_rate(int precision, double* flops_per_s, void* stream);
 
 int xfft_num_enriched(const xfft_ctx* ctx);   /* nX, or -1 before set_microstructure */
 int xfft_num_cut_tets(const xfft_ctx* ctx);   /* number of cut tetrahedra, or -1 */

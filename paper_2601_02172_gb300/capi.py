@@ -26,7 +26,7 @@ EXPORTED = (
     "xfft_effective_stiffness", "xfft_grad", "xfft_grad_phases", "xfft_apply", "xfft_precondition", "xfft_get_setup",
     "xfft_num_enriched", "xfft_num_cut_tets", "xfft_status_string", "xfft_last_error",
     "xfft_destroy", "xfft_profile", "xfft_profile_read", "xfft_apply_noalloc",
-    "xfft_batch_effective_stiffness", "xfft_get_tuning",
+    "xfft_batch_effective_stiffness", "xfft_get_tuning", "xfft_fma_rate",
 )
 NOALLOC_MAX_RHS = 8
 PROF_KINDS = ("apply_uncut_f32", "apply_cut_f32", "apply_uncut_f64", "apply_cut_f64", "prec_f32",
@@ -93,13 +93,14 @@ def lib():
     L.xfft_profile_read.argtypes = [vp, vp, vp, vp]
     L.xfft_apply_noalloc.argtypes = [vp, i, vp, vp, vp]
     L.xfft_batch_effective_stiffness.argtypes = [i, vp, C.POINTER(d), C.POINTER(Stats)]
-    L.xfft_get_tuning.argtypes = [vp, C.POINTER(i), C.POINTER(i)]
+    L.xfft_get_tuning.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
+    L.xfft_fma_rate.argtypes = [i, C.POINTER(d), vp]
     for name in ("xfft_default_options", "xfft_create", "xfft_set_microstructure",
                  "xfft_set_microstructure_phases", "xfft_solve",
                  "xfft_effective_stiffness", "xfft_grad", "xfft_grad_phases", "xfft_apply", "xfft_precondition",
                  "xfft_get_setup", "xfft_num_enriched", "xfft_num_cut_tets", "xfft_profile",
                  "xfft_profile_read", "xfft_apply_noalloc", "xfft_batch_effective_stiffness",
-                 "xfft_get_tuning"):
+                 "xfft_get_tuning", "xfft_fma_rate"):
         getattr(L, name).restype = i
     _lib = L
     return L
@@ -259,10 +260,11 @@ class Solver:
 
     @property
     def tuning(self):
-        """(cut-tet kernel grid in blocks, right-hand sides per launch) in use."""
-        b, r = C.c_int(), C.c_int()
-        check(lib().xfft_get_tuning(self._ctx, C.byref(b), C.byref(r)))
-        return b.value, r.value
+        """(cut-tet kernel grid in blocks, its right-hand sides per launch, the preconditioner's
+        right-hand sides per group of FFT passes) in use."""
+        b, r, g = C.c_int(), C.c_int(), C.c_int()
+        check(lib().xfft_get_tuning(self._ctx, C.byref(b), C.byref(r), C.byref(g)))
+        return b.value, r.value, g.value
 
     @property
     def stride(self):
@@ -425,6 +427,13 @@ class Solver:
         check(lib().xfft_get_setup(self._ctx, C.c_void_p(en.ctypes.data), C.c_void_p(D0.ctypes.data),
                                    C.c_void_p(code.ctypes.data)))
         return en[:nX], D0[:nX], code
+
+
+def fma_rate(precision="fp64"):
+    """Measured FMA throughput (FLOP/s) of the current GPU in FP64 ("fp64") or FP32 ("fp32")."""
+    r = C.c_double()
+    check(lib().xfft_fma_rate(XFFT_FP64 if precision == "fp64" else XFFT_FP32_REFINED, C.byref(r), None))
+    return r.value
 
 
 def batch_effective_stiffness(solvers):

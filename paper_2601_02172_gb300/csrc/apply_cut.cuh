@@ -149,6 +149,51 @@ __device__ __forceinline__ void sym_grad(const T (&v)[4][3], const T (&ih)[3], T
   e[5] = T(0.5) * (H[1][0] + H[0][1]);
 }
 
+// The same two operations with the gradients as data (Kuhn type known at run time only): the
+// double-word kernel runs this single body, whatever the order of the tet types in its warps.
+template <typename T>
+struct TetGrad {
+  T g[4][3];
+};
+template <typename T>
+__device__ __forceinline__ void add_forces_rt(const T (&S)[6], const TetGrad<T>& G, T (&F)[4][3]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    T v[3];
+    symv(S, G.g[a], v);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[a][i] += v[i];
+  }
+}
+template <typename T>
+__device__ __forceinline__ void sym_grad_rt(const T (&v)[4][3], const TetGrad<T>& G, T (&e)[6]) {
+  T H[3][3];  // H[k][i] = d v_i / d x_k
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      H[k][i] = v[0][i] * G.g[0][k] + v[1][i] * G.g[1][k] + v[2][i] * G.g[2][k] + v[3][i] * G.g[3][k];
+  e[0] = H[0][0];
+  e[1] = H[1][1];
+  e[2] = H[2][2];
+  e[3] = T(0.5) * (H[2][1] + H[1][2]);
+  e[4] = T(0.5) * (H[2][0] + H[0][2]);
+  e[5] = T(0.5) * (H[1][0] + H[0][1]);
+}
+
+// the gradient operations of a cut-tet body: compile-time Kuhn type t (sparse) or, with t < 0,
+// the run-time gradients G
+template <int t, typename T>
+__device__ __forceinline__ void forces_of(const T (&S)[6], const T (&ih)[3], const TetGrad<T>& G, T (&F)[4][3]) {
+  if constexpr (t >= 0) add_forces<t>(S, ih, F);
+  else add_forces_rt(S, G, F);
+}
+template <int t, typename T>
+__device__ __forceinline__ void strain_of(const T (&v)[4][3], const T (&ih)[3], const TetGrad<T>& G, T (&e)[6]) {
+  if constexpr (t >= 0) sym_grad<t>(v, ih, e);
+  else sym_grad_rt(v, G, e);
+}
+
 // a * e1 + b * e2 + sym(W (x) g)
 template <typename T>
 __device__ __forceinline__ void strain_comb(T a, const T (&e1)[6], T b, const T (&e2)[6], const T (&W)[3],
@@ -168,7 +213,8 @@ __device__ __forceinline__ void strain_comb(T a, const T (&e1)[6], T b, const T 
 template <int t, bool SIG, typename T, typename R>
 __device__ __forceinline__ void cut_side(const R* __restrict__ S, const T (&ws)[4][3], const T (&es)[6],
                                          const T (&ed)[6], const T (&ew)[6], const T (&ih)[3],
-                                         T (&qs)[4][3], T (&qe)[4][3], T& en, T (&sg)[6]) {
+                                         const TetGrad<T>& G, T (&qs)[4][3], T (&qe)[4][3], T& en,
+                                         T (&sg)[6]) {
   T M[10], m[4], P[4], gx[8], sc[4];
   {
     T buf[28];
@@ -206,7 +252,7 @@ __device__ __forceinline__ void cut_side(const R* __restrict__ S, const T (&ws)[
     T e[6], s[6];
     strain_comb(sc[0], es, sc[1], ew, Wm, gam, e);
     iso_C(e, lam, mu, s);
-    add_forces<t>(s, ih, qs);
+    forces_of<t>(s, ih, G, qs);
     en += ddot(s, ed);
     if (SIG) {
 #pragma unroll
@@ -218,7 +264,7 @@ __device__ __forceinline__ void cut_side(const R* __restrict__ S, const T (&ws)[
     T e[6], s[6];
     strain_comb(sc[1], es, sc[2], ew, Wp, gam, e);
     iso_C(e, lam, mu, s);
-    add_forces<t>(s, ih, qe);
+    forces_of<t>(s, ih, G, qe);
     en += ddot(s, ew);
   }
   // enriched forces, R_a gamma
@@ -245,12 +291,27 @@ __device__ __forceinline__ void cut_side(const R* __restrict__ S, const T (&ws)[
 }
 
 // One cut tet of Kuhn type t, one right-hand side: gathers, both sides, scatter-adds.
+// t >= 0: compile-time Kuhn type; t < 0: the type trt given at run time
 template <int t, bool TOTAL, bool SIG, typename T>
 __device__ __forceinline__ void cut_tet(const typename Store<T>::type* __restrict__ dr,
                                         typename Store<T>::type* __restrict__ qr,
                                         const typename Store<T>::type* __restrict__ rec, const int4 nd,
                                         const int4 ej, long long N, int nX, const T (&ih)[3],
-                                        const double* eps, T& en, T (&sg)[6]) {
+                                        const double* eps, T& en, T (&sg)[6], int trt = 0) {
+  TetGrad<T> G;
+  if constexpr (t < 0) {
+    // g0 = -e_p/h_p, g1 = e_p/h_p - e_q/h_q, g2 = e_q/h_q - e_r/h_r, g3 = e_r/h_r, formed with
+    // selects (no register array indexed at run time)
+    const int p = perm_p(trt), q = perm_q(trt), r = perm_r(trt);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T ip = c == p ? ih[c] : T(0), iq = c == q ? ih[c] : T(0), ir = c == r ? ih[c] : T(0);
+      G.g[0][c] = -ip;
+      G.g[1][c] = ip - iq;
+      G.g[2][c] = iq - ir;
+      G.g[3][c] = ir;
+    }
+  }
   const int ndk[4] = {nd.x, nd.y, nd.z, nd.w};
   const int ejk[4] = {ej.x, ej.y, ej.z, ej.w};
   T ws[4][3];
@@ -266,8 +327,8 @@ __device__ __forceinline__ void cut_tet(const typename Store<T>::type* __restric
         us[a][c] = from_store<T>(dr[c * N + ndk[a]]);
         ws[a][c] = from_store<T>(dr[3 * N + (long long)c * nX + ejk[a]]) * isd[3 * a + c];
       }
-    sym_grad<t>(us, ih, es);
-    sym_grad<t>(ws, ih, ew);
+    strain_of<t>(us, ih, G, es);
+    strain_of<t>(ws, ih, G, ew);
   }
   // ed: the strain of d alone (the energy term); es also carries eps_bar in TOTAL mode
   T ed[6];
@@ -288,7 +349,7 @@ __device__ __forceinline__ void cut_tet(const typename Store<T>::type* __restric
   constexpr int kSides = std::is_same<T, double>::value ? 2 : 1;
 #pragma unroll kSides
   for (int si = 0; si < 2; ++si)
-    cut_side<t, SIG>(rec + kRecSide + kRecSideLen * si, ws, es, ed, ew, ih, qs, qe, en, sg);
+    cut_side<t, SIG>(rec + kRecSide + kRecSideLen * si, ws, es, ed, ew, ih, G, qs, qe, en, sg);
   T isd[12];
   ld_rec<3, T>(rec, isd);
 #pragma unroll
@@ -380,7 +441,9 @@ __global__ void __launch_bounds__(kCutThreads, std::is_same<T, dw>::value ? 1
         const S* dr = d + rhs * a.stride;
         S* qr = q + rhs * a.stride;
         const double* eps = TOTAL ? a.eps + 6 * rhs : nullptr;
-        switch (t) {  // uniform over a warp except at the boundaries of the type groups
+        if constexpr (std::is_same<T, dw>::value) {
+          cut_tet<-1, TOTAL, SIG, T>(dr, qr, rec, nd, ej, N, nX, ih, eps, en, sg, t);
+        } else switch (t) {  // uniform over a warp except at the boundaries of the type groups
           case 0: cut_tet<0, TOTAL, SIG, T>(dr, qr, rec, nd, ej, N, nX, ih, eps, en, sg); break;
           case 1: cut_tet<1, TOTAL, SIG, T>(dr, qr, rec, nd, ej, N, nX, ih, eps, en, sg); break;
           case 2: cut_tet<2, TOTAL, SIG, T>(dr, qr, rec, nd, ej, N, nX, ih, eps, en, sg); break;

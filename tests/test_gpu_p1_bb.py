@@ -94,14 +94,19 @@ def test_hashin_convergence_xfem_against_p1(xf):
     assert px > 1.5 and 0.3 < p1 < 1.5 and p1 < px, (px, p1, ex, e1)
 
 
-@pytest.mark.parametrize("rule,cycle", [("bb1", 1), ("bb2", 1), ("alt", 1), ("bb2e", 1), ("bb1", 3)])
-def test_bb_rules_match_oracle(xf, rule, cycle):
+@pytest.fixture(scope="module")
+def sphere16():
     n = (16, 16, 16)
     L = synth.sphere_levelset(n, (0.5, 0.5, 0.5), 0.3)
     lm, lp = synth.lame_from_E_nu(10.0, 0.3), synth.lame_from_E_nu(1.0, 0.3)
     o = XFEM(L, n, lame_minus=lm, lame_plus=lp)
     eps = np.array([[0.2, -0.1, 0.3, 0.4, -0.2, 0.1]])
-    u_ref = o.solve_direct(eps[0])
+    return n, L, lm, lp, o, eps, o.solve_direct(eps[0])
+
+
+@pytest.mark.parametrize("rule,cycle", [("bb1", 1), ("bb2", 1), ("alt", 1), ("bb2e", 1), ("bb1", 3)])
+def test_bb_rules_match_oracle(xf, sphere16, rule, cycle):
+    n, L, lm, lp, o, eps, u_ref = sphere16
     _, info = o.pcg(eps[0], tol=1e-10, maxit=5000, scheme="bb", green="fft", bb_rule=rule, bb_cycle=cycle)
     s = xf.Solver(n, tol=1e-10, maxit=5000, scheme="bb", bb_rule=rule, bb_cycle=cycle)
     s.set_microstructure(L, lm, lp)

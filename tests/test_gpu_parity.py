@@ -655,6 +655,26 @@ def test_full_size_gradient_128(xf):
     assert _rel(ds32.astype(np.float64), ds.astype(np.float64)) < 1e-4
 
 
+def test_dw_residual_suffices_at_high_contrast_128(xf):
+    """The refinement's residual uses the plain double-word sum (no relative bound under
+    cancellation).  At 128^3 (the bench's ellipsoids) with contrast 1000 and tol 1e-10 the
+    FP32-refined solve still converges and its mean stress equals a plain FP64 solve's to 1e-9:
+    the residual's rounding stays below the tolerance there."""
+    w = synth.make_workload("ellipsoids40")
+    lm, lp = synth.lame_from_E_nu(1000.0, 0.2), synth.lame_from_E_nu(1.0, 0.3)
+    e = np.eye(6)[:1]
+    out = {}
+    for prec in ("fp32", "fp64"):
+        s = xf.Solver((128, 128, 128), precision=prec, tol=1e-10, maxit=20000)
+        s.set_microstructure(w["L"], lm, lp, w["scale"])
+        out[prec] = s.solve(e, u=False)
+        s.close()
+    assert out["fp32"]["converged"] and out["fp64"]["converged"]
+    assert out["fp32"]["stats"]["final_res"][0] <= 1e-10
+    a, b = out["fp32"]["mean_stress"][0], out["fp64"]["mean_stress"][0]
+    assert np.abs(a - b).max() < 1e-9 * np.abs(b).max(), np.abs(a - b).max() / np.abs(b).max()
+
+
 def test_homogeneous_and_equal_phase_edge_cases(xf):
     n = (4, 4, 4)
     lp = synth.lame_from_E_nu(2.0, 0.3)

@@ -37,10 +37,10 @@ def test_tuned_launch_shape_matches_defaults(xf):
         ncut = s.num_cut_tets
         s.close()
     nb_max = min(-(-ncut // 128), 2432)
-    blocks, rpl = shapes[1]
-    assert rpl in (3, 6) and 152 <= blocks <= max(nb_max, 1216), shapes
-    assert shapes[2] == shapes[1]  # the cached choice for the same microstructure
-    assert shapes[0][1] == 8       # untuned: all right-hand sides in one launch
+    blocks, rpl, group = shapes[1]
+    assert rpl in (3, 6) and 152 <= blocks <= max(nb_max, 1216) and group in (1, 2, 3, 64), shapes
+    assert shapes[2] == shapes[1]             # the cached choice for the same microstructure
+    assert shapes[0][1:] == (8, 64)           # untuned: all right-hand sides in one launch
     assert np.abs(Cs[1] - Cs[0]).max() < 1e-6 * np.abs(Cs[0]).max()
 
 
