@@ -94,6 +94,9 @@ def parse():
     ap.add_argument("--cpu-n", type=int, default=16)
     ap.add_argument("--cut-cache", action="store_true",
                     help="run the timed solves with the cached cut-tet element matrices")
+    ap.add_argument("--enr", choices=("block3", "identity"), default="block3",
+                    help="preconditioner on the enriched DOFs: the 3x3 node blocks (default) or the "
+                         "paper's identity; the other one is timed beside it")
     return ap.parse_args()
 
 
@@ -164,9 +167,13 @@ def _oracle_case(job):
     return k, time.perf_counter() - t0, int(info["iters"]), o.mean_stress(u, e)
 
 
-def resampled_workload(n_cpu):
-    """The bench workload's ellipsoids (and scale field, subsampled) on an n_cpu^3 grid."""
+def resampled_workload(n_cpu, name="ellipsoids40"):
+    """The bench workload's ellipsoids (and scale field, subsampled) on an n_cpu^3 grid; or, for
+    name "single_sphere", the 16^3 single-sphere case (no scale field)."""
     import synth
+    if name == "single_sphere":
+        w = synth.make_workload("single_sphere")
+        return w["L"], None, w["lame_minus"], w["lame_plus"]
     w = synth.make_workload("ellipsoids40")
     n = (n_cpu,) * 3
     L = synth.ellipsoids_levelset(n, w["info"]["inclusions"])
@@ -181,12 +188,12 @@ def oracle_pool(workers):
     return mp.get_context("spawn").Pool(workers)
 
 
-def oracle_solve(n_cpu, tol, pool):
+def oracle_solve(n_cpu, tol, pool, name="ellipsoids40"):
     """The CPU oracle as it stands, one whole six-case solve of the resampled workload: setup and
     assembly in this process, then the six load cases' PCG spread over the worker pool (they
     are independent).  Returns times, iteration counts and C_eff."""
     from oracle import XFEM
-    L, sc, lm, lp = resampled_workload(n_cpu)
+    L, sc, lm, lp = resampled_workload(n_cpu, name)
     t0 = time.perf_counter()
     o = XFEM(L, (n_cpu,) * 3, lame_minus=lm, lame_plus=lp, scale=sc)
     o.assemble()
@@ -217,35 +224,53 @@ def _sample_text(r, tol, workers):
                 "/".join(str(i) for i in r["iters"]), r["t_pcg"], workers))
 
 
-def cpu_baseline(n_cpu, tol, dev=None):
-    """The oracle timed on this host on the resampled workload, and the GPU on the same input."""
+def _gpu_same_input(n_cpu, tol, r, name="ellipsoids40"):
+    """The GPU's set-up + six-case solve of the oracle's input (host level set), same tolerance."""
+    import torch
+    from paper_2601_02172_gb300 import Solver
+    L, sc, lm, lp = resampled_workload(n_cpu, name)
+    same = {}
+    for prec in ("fp64", "fp32"):
+        sv = Solver((n_cpu,) * 3, precision=prec, tol=tol)
+        sv.set_microstructure(L, lm, lp, sc)
+        sv.effective_stiffness()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 5
+        for _ in range(reps):
+            sv.set_microstructure(L, lm, lp, sc)
+            Cg, _ = sv.effective_stiffness()
+        torch.cuda.synchronize()
+        same[prec] = {"solves_per_s": reps / (time.perf_counter() - t0),
+                      "ceff_rel_diff_vs_oracle": float(np.abs(Cg - r["C"]).max() / np.abs(r["C"]).max())}
+        sv.close()
+    return same
+
+
+def cpu_baseline(n_cpu, tol, dev=None, more=True):
+    """The oracle timed on this host on the resampled workload, and the GPU on the same input;
+    with more, also the 16^3 single sphere (config 1) and the workload resampled at 32^3."""
     workers = min(6, _cores())
     with oracle_pool(workers) as pool:
         r = oracle_solve(n_cpu, tol, pool)
+        others = []
+        if more:
+            for name, nn in (("single_sphere", 16), ("ellipsoids40", 32)):
+                others.append((name, nn, oracle_solve(nn, tol, pool, name)))
     out = {"value": 1.0 / r["t"], "unit": UNIT, "cores": workers, "kind": "oracle",
            "sample": _sample_text(r, tol, workers), "dof_iters_per_s": r["dofit"],
            "os_cpu_count": os.cpu_count(), "affinity_cores": _cores()}
     if dev is not None:
-        import torch
-        from paper_2601_02172_gb300 import Solver
-        L, sc, lm, lp = resampled_workload(n_cpu)
-        same = {}
-        for prec in ("fp64", "fp32"):
-            sv = Solver((n_cpu,) * 3, precision=prec, tol=tol)
-            sv.set_microstructure(L, lm, lp, sc)
-            sv.effective_stiffness()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            reps = 5
-            for _ in range(reps):
-                sv.set_microstructure(L, lm, lp, sc)
-                Cg, _ = sv.effective_stiffness()
-            torch.cuda.synchronize()
-            same[prec] = {"solves_per_s": reps / (time.perf_counter() - t0),
-                          "ceff_rel_diff_vs_oracle": float(np.abs(Cg - r["C"]).max() / np.abs(r["C"]).max())}
-            sv.close()
-        out["gpu_same_input"] = dict(same, note="the GPU's setup + six-case solve of the identical "
-                                                "%d^3 input (host level set), same tolerance" % n_cpu)
+        out["gpu_same_input"] = dict(_gpu_same_input(n_cpu, tol, r),
+                                     note="the GPU's setup + six-case solve of the identical %d^3 input "
+                                          "(host level set), same tolerance" % n_cpu)
+        more_out = []
+        for name, nn, ro in others:
+            more_out.append({"input": "%s at %d^3" % (name, nn), "ncut": ro["ncut"], "ndof": ro["ndof"],
+                             "oracle_solves_per_s": 1.0 / ro["t"], "oracle_setup_s": ro["t_setup"],
+                             "oracle_pcg_s": ro["t_pcg"], "oracle_iters": ro["iters"],
+                             "gpu": _gpu_same_input(nn, tol, ro, name)})
+        out["more_samples"] = more_out
     return out
 
 
@@ -338,7 +363,7 @@ def main():
     s_d = torch.from_numpy(s_h).to(dev)
     L_pin = torch.from_numpy(L_h).pin_memory()  # e2e inputs come from pinned host memory
     s_pin = torch.from_numpy(s_h).pin_memory()
-    solver = Solver(n, precision="fp32", tol=args.tol, cut_cache=args.cut_cache)
+    solver = Solver(n, precision="fp32", tol=args.tol, cut_cache=args.cut_cache, enr_precond=args.enr)
 
     # C_target: a random SPD perturbation of C_eff (seeded)
     solver.set_microstructure(L_d, lm, lp, s_d)
@@ -481,10 +506,10 @@ def main():
             s64.close()
             sref.close()
         if not args.no_extras:
-            # variant enriched preconditioner (3x3 node blocks, the north star's "block preconditioner
-            # to the enriched DOFs"): the same whole step (set-up, six-case solve, gradient), timed
-            # like the headline
-            sb = Solver(n, precision="fp32", tol=args.tol, enr_precond="block3")
+            # the other enriched preconditioner (3x3 node blocks or the paper's identity): the same
+            # whole step (set-up, six-case solve, gradient), timed like the headline
+            other = "identity" if args.enr == "block3" else "block3"
+            sb = Solver(n, precision="fp32", tol=args.tol, enr_precond=other)
             sb.set_microstructure(L_d, lm, lp, s_d)
             sb.effective_stiffness()
             torch.cuda.synchronize()
@@ -498,11 +523,11 @@ def main():
                 its_b += sum(stb["iters"])
             e1b.record()
             torch.cuda.synchronize()
-            extra["enr_block3"] = {"solves_per_s": args.steps / (e0b.elapsed_time(e1b) / 1e3),
-                                   "cg_iters_per_step": its_b / args.steps,
-                                   "identity_cg_iters_per_step": steps_iters / args.steps,
-                                   "identity_solves_per_s": value,
-                                   "ceff_rel_diff_vs_identity": float(np.abs(Cb - C).max() / np.abs(C).max())}
+            extra["enr_" + other] = {"solves_per_s": args.steps / (e0b.elapsed_time(e1b) / 1e3),
+                                     "cg_iters_per_step": its_b / args.steps,
+                                     args.enr + "_cg_iters_per_step": steps_iters / args.steps,
+                                     args.enr + "_solves_per_s": value,
+                                     "ceff_rel_diff": float(np.abs(Cb - C).max() / np.abs(C).max())}
             sb.close()
             # many microstructures at once (16 uneven grids x 6 load cases, FP32-refined to 1e-8):
             # one call, one host thread and stream per microstructure, against the same solvers in turn
@@ -690,6 +715,10 @@ def main():
                 "config": {"workload": WORKLOAD, "grid": list(n), "n_rhs": 6,
                            "precision": "FP32 PCG; residuals of the FP64 iterate in double-word arithmetic; "
                                          "FP64 CG scalars",
+                           "enriched_preconditioner": {"block3": "3x3 node blocks of the enriched reference "
+                                                                 "Gram matrix, inverted in FP64",
+                                                       "identity": "the paper's identity on the scaled "
+                                                                   "DOFs"}[args.enr],
                            "tol": args.tol, "n_enriched": nX, "n_cut_tets": info["ncut"],
                            "launch_shapes": dict(zip(("cut_blocks", "cut_rhs_per_launch", "prec_rhs_per_group"),
                                                      solver.tuning)),

@@ -43,10 +43,10 @@ static xfft_status fail(xfft_status s, const std::string& msg) {
                   std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));              \
   } while (0)
 
-// device loop memory: LoopState (padded), then kMaxBatch act pointers and kMaxBatch RHS counts
+// device loop memory: one LoopState (padded to kLoopStride bytes) per loop of a graph
 constexpr int kMaxBatch = 64;
-constexpr size_t kLoopHead = 64;
-constexpr size_t kLoopBytes = kLoopHead + (sizeof(void*) + sizeof(int)) * kMaxBatch;
+constexpr size_t kLoopStride = 64;
+constexpr size_t kLoopBytes = kLoopStride * kMaxBatch;
 
 struct xfft_ctx;
 static cudaError_t dalloc_bytes(xfft_ctx* c, void** p, size_t bytes);
@@ -996,52 +996,36 @@ static bool graph_stream(const xfft_ctx* c) {
   return !c->prof && c->stream != nullptr && c->stream != cudaStreamLegacy && c->stream != cudaStreamPerThread;
 }
 
-// The device-driven loop over the inner solves `items` (one or several contexts): one graph with
-// a conditional while node, each round loop_pe(c) iterations of every item on its context's
-// stream, forked from and joined to `master`.  lm: device LoopState followed by the act pointers
-// and RHS counts of the items (filled here).  Returns XFFT_EUNSUPPORTED when the graph cannot be
-// built (the caller then polls on the host).
-static xfft_status build_device_loop(const std::vector<LoopArgs>& items, cudaStream_t master,
-                                     unsigned char* lm, unsigned char* lm_host, cudaEvent_t fork,
-                                     const std::vector<cudaEvent_t>& joins, long long limit_ns,
-                                     cudaGraphExec_t* exec) {
+// The device-driven loops of the inner solves `items` (one or several contexts) as one graph:
+// for each item an independent conditional while loop whose body is loop_pe(c) iterations on its
+// context's stream.  lm: device LoopState per item (kLoopStride bytes apart).  Returns
+// XFFT_EUNSUPPORTED when the graph cannot be built (the caller then polls on the host).
+static xfft_status build_device_loop(const std::vector<LoopArgs>& items, unsigned char* lm,
+                                     long long limit_ns, cudaGraphExec_t* exec) {
   const int n = (int)items.size();
-  LoopState* st = reinterpret_cast<LoopState*>(lm);
-  const int** acts = reinterpret_cast<const int**>(lm + kLoopHead);
-  int* nr = reinterpret_cast<int*>(lm + kLoopHead + sizeof(void*) * kMaxBatch);
-  // the act pointers and counts: staged in pinned host memory, copied on the master stream
-  const int** hacts = reinterpret_cast<const int**>(lm_host + kLoopHead);
-  int* hnr = reinterpret_cast<int*>(lm_host + kLoopHead + sizeof(void*) * kMaxBatch);
-  unsigned max_rounds = 1;
-  for (int i = 0; i < n; ++i) {
-    hacts[i] = items[i].c->act;
-    hnr[i] = items[i].n_rhs;
-    max_rounds = std::max(max_rounds, (unsigned)(items[i].maxit / loop_pe(items[i].c) + 2));
-  }
-  CU(cudaMemcpyAsync(lm + kLoopHead, lm_host + kLoopHead, kLoopBytes - kLoopHead, cudaMemcpyHostToDevice,
-                     master));
   xfft_status body_status = XFFT_OK;
-  const LoopBody body = [&](cudaStream_t m) -> cudaError_t {
-    cudaError_t e = cudaEventRecord(fork, m);
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-      xfft_ctx* c = items[i].c;
-      if (c->stream != m) e = cudaStreamWaitEvent(c->stream, fork, 0);
-      if (e != cudaSuccess) break;
-      const xfft_status s = items[i].dbl ? loop_round<double>(items[i], loop_pe(c))
-                                         : loop_round<float>(items[i], loop_pe(c));
+  std::vector<LoopSpec> loops;
+  loops.reserve(n);
+  for (int i = 0; i < n; ++i) {
+    const LoopArgs L = items[i];
+    LoopSpec sp;
+    sp.stream = L.c->stream;
+    sp.body = [L, &body_status](cudaStream_t) -> cudaError_t {
+      const xfft_status s = L.dbl ? loop_round<double>(L, loop_pe(L.c)) : loop_round<float>(L, loop_pe(L.c));
       if (s != XFFT_OK) {
         body_status = s;
-        e = cudaErrorUnknown;
-        break;
+        return cudaErrorUnknown;
       }
-      if (c->stream != m) {
-        e = cudaEventRecord(joins[i], c->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(m, joins[i], 0);
-      }
-    }
-    return e;
-  };
-  const cudaError_t e = build_loop_graph(master, body, acts, nr, n, st, max_rounds, limit_ns, exec);
+      return cudaSuccess;
+    };
+    sp.act = L.c->act;
+    sp.nr = L.n_rhs;
+    sp.st = reinterpret_cast<LoopState*>(lm + kLoopStride * i);
+    sp.max_rounds = (unsigned)(L.maxit / loop_pe(L.c) + 2);
+    sp.limit_ns = limit_ns;
+    loops.push_back(std::move(sp));
+  }
+  const cudaError_t e = build_loop_graph(loops, exec);
   if (body_status != XFFT_OK) return body_status;
   if (e != cudaSuccess) {
     cudaGetLastError();  // clear a sticky launch-configuration error of the failed build
@@ -1050,7 +1034,15 @@ static xfft_status build_device_loop(const std::vector<LoopArgs>& items, cudaStr
   return XFFT_OK;
 }
 
-// Launch a built device loop: master after every item's earlier work, every item after the loop.
+// whether any of the n loop states in lm_host (copied back from the device) timed out
+static bool loops_timed_out(const unsigned char* lm_host, int n) {
+  for (int i = 0; i < n; ++i)
+    if (reinterpret_cast<const LoopState*>(lm_host + kLoopStride * i)->timed_out) return true;
+  return false;
+}
+
+// Launch a built device loop graph on master: master after every item's earlier work, every
+// item after the graph.
 static xfft_status run_device_loop(const std::vector<LoopArgs>& items, cudaStream_t master,
                                    cudaGraphExec_t exec, cudaEvent_t fork, const std::vector<cudaEvent_t>& joins) {
   for (size_t i = 0; i < items.size(); ++i) {
@@ -1084,8 +1076,7 @@ static xfft_status cg_loop(const LoopArgs& L, bool* timed_out) {
     if (!hit) {
       cudaGraphExec_t exec = nullptr;
       const std::vector<LoopArgs> items{L};
-      const xfft_status s = build_device_loop(items, c->stream, c->loopmem, c->h_loop, c->ev_fork,
-                                              c->ev_join, c->opt.spin_limit_ns, &exec);
+      const xfft_status s = build_device_loop(items, c->loopmem, c->opt.spin_limit_ns, &exec);
       if (s == XFFT_EUNSUPPORTED) {
         c->devloop_ok = false;
       } else {
@@ -1110,7 +1101,7 @@ static xfft_status cg_loop(const LoopArgs& L, bool* timed_out) {
       TRY(run_device_loop({L}, c->stream, hit->exec, c->ev_fork, c->ev_join));
       CU(cudaMemcpyAsync(c->h_loop, c->loopmem, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
       CU(cudaStreamSynchronize(c->stream));
-      *timed_out = reinterpret_cast<LoopState*>(c->h_loop)->timed_out != 0;
+      *timed_out = loops_timed_out(c->h_loop, 1);
       return XFFT_OK;
     }
   }
@@ -1659,15 +1650,15 @@ extern "C" xfft_status xfft_batch_effective_stiffness(int n, xfft_ctx* const* ct
     if (items.empty()) break;
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaEvent_t> joins(B.joins.begin(), B.joins.begin() + items.size());
-    const xfft_status bs = build_device_loop(items, B.master, B.lm, B.lm_host, B.fork, joins, limit, &exec);
+    const xfft_status bs = build_device_loop(items, B.lm, limit, &exec);
     bool timed_out = false;
     if (bs == XFFT_OK) {
       const xfft_status rs = run_device_loop(items, B.master, exec, B.fork, joins);
       cudaGraphExecDestroy(exec);
       TRY(rs);
-      CU(cudaMemcpyAsync(B.lm_host, B.lm, sizeof(LoopState), cudaMemcpyDeviceToHost, B.master));
+      CU(cudaMemcpyAsync(B.lm_host, B.lm, kLoopStride * items.size(), cudaMemcpyDeviceToHost, B.master));
       CU(cudaStreamSynchronize(B.master));
-      timed_out = reinterpret_cast<LoopState*>(B.lm_host)->timed_out != 0;
+      timed_out = loops_timed_out(B.lm_host, (int)items.size());
     } else if (bs == XFFT_EUNSUPPORTED) {
       for (const auto& L : items) {  // no conditional graphs: each context's own loop
         L.c->devloop_ok = false;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <functional>
+#include <vector>
 
 #include "dw.cuh"
 #include "xfft_common.cuh"
@@ -227,20 +228,27 @@ cudaError_t launch_init_state(RhsState* st, int* act, int n_rhs, const int* mask
 
 // ---- device-driven loops (loop.cu)
 struct LoopState {
-  unsigned long long t0;  // globaltimer at the graph's start
+  unsigned long long t0;  // globaltimer at the loop's start
   unsigned rounds;        // body rounds run
   int timed_out;          // 1: the device-time limit ended the loop
 };
-// captures one round of the loop body: called while `master` is capturing; work on other
-// streams must fork from and join back to master
-using LoopBody = std::function<cudaError_t(cudaStream_t master)>;
-// An executable graph: a start kernel, then a conditional while node whose body is one round
-// followed by the condition kernel (continue while some act[i][r], r < nr[i], of the n contexts is
-// set, fewer than max_rounds rounds ran and less than limit_ns device time passed; limit_ns < 0:
-// no limit).  acts (n device pointers), nr (n ints) and st live in device memory.
-cudaError_t build_loop_graph(cudaStream_t master, const LoopBody& body, const int* const* acts,
-                             const int* nr, int n, LoopState* st, unsigned max_rounds, long long limit_ns,
-                             cudaGraphExec_t* exec);
+// captures one round of a loop body on `stream` (called while the stream is capturing)
+using LoopBody = std::function<cudaError_t(cudaStream_t stream)>;
+// One device-driven loop of a graph: a start kernel, then a conditional while node whose body is
+// one round (captured on `stream`) followed by the condition kernel: continue while some act[r],
+// r < nr, is set, fewer than max_rounds rounds ran and less than limit_ns device time passed
+// (limit_ns < 0: no limit).  act and st live in device memory.
+struct LoopSpec {
+  cudaStream_t stream;
+  LoopBody body;
+  const int* act;
+  int nr;
+  LoopState* st;
+  unsigned max_rounds;
+  long long limit_ns;
+};
+// An executable graph of independent loops (one per context; no dependencies between them).
+cudaError_t build_loop_graph(const std::vector<LoopSpec>& loops, cudaGraphExec_t* exec);
 
 // ---- gradient (grad.cu)
 // values reduced per gradient call: dLoss/dlambda_p (p < kMaxPhases), dLoss/dmu_p, then the 21

@@ -55,6 +55,18 @@ def _case(name):
     raise KeyError(name)
 
 
+_ORACLES = {}
+
+
+def _oracle(name):
+    """The oracle of case `name`, built once per test module (its assembly and LU factorisation
+    are cached on the object, so later tests reuse them)."""
+    if name not in _ORACLES:
+        n, ell, L, lm, lp, sc = _case(name)
+        _ORACLES[name] = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    return _ORACLES[name]
+
+
 def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
@@ -64,7 +76,7 @@ def test_setup_matches_oracle(xf, name):
     n, ell, L, lm, lp, sc = _case(name)
     s = xf.Solver(n, ell)
     s.set_microstructure(L, lm, lp, sc)
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle(name)
     en, D0, code = s.setup_info()
     assert s.num_enriched == o.nX
     assert s.num_cut_tets == len(o.cut_list)
@@ -84,7 +96,7 @@ def test_apply_matches_oracle(xf, name, prec):
     n, ell, L, lm, lp, sc = _case(name)
     s = xf.Solver(n, ell)
     s.set_microstructure(L, lm, lp, sc)
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle(name)
     o.assemble()
     rng = np.random.default_rng(5)
     d = rng.normal(size=(2, o.ndof))
@@ -106,7 +118,7 @@ def test_cached_cut_apply_matches_oracle(xf, name):
     scaled element matrices (option cut_cache) and from the per-side moments (the default), both
     against the oracle's assembled operator."""
     n, ell, L, lm, lp, sc = _case(name)
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle(name)
     o.assemble()
     d = np.random.default_rng(21).normal(size=(3, o.ndof))
     for cache in (True, False):
@@ -150,7 +162,7 @@ def test_fp32_solve_with_cut_cache(xf):
     """FP32-refined C_eff with the cached cut-tet matrices in the CG iterations (graph-replayed)
     equals the default solve and the oracle's."""
     n, ell, L, lm, lp, sc = _case("ragged")
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle("ragged")
     Cs, _, _ = o.effective_stiffness()
     out = {}
     for cache in (True, False):
@@ -169,7 +181,7 @@ def test_dw_residual_at_the_solution(xf, name):
     n, ell, L, lm, lp, sc = _case(name)
     s = xf.Solver(n, ell)
     s.set_microstructure(L, lm, lp, sc)
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle(name)
     o.assemble()
     eps = np.eye(6)[[0, 3]]
     u = np.stack([o.solve_direct(e) for e in eps])
@@ -190,7 +202,7 @@ def test_precondition_matches_oracle(xf, name, prec):
     n, ell, L, lm, lp, sc = _case(name)
     s = xf.Solver(n, ell)
     s.set_microstructure(L, lm, lp, sc)
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle(name)
     rng = np.random.default_rng(9)
     f = rng.normal(size=(3, o.ndof))
     for r in range(3):  # the standard part must be mean-free per component
@@ -211,7 +223,7 @@ def test_block_enriched_preconditioner(xf, name, prec):
     """Variant enriched preconditioner (3x3 node blocks): P^-1 against the oracle, and a solve
     with it reaching the direct solution (the system does not depend on the preconditioner)."""
     n, ell, L, lm, lp, sc = _case(name)
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle(name)
     s = xf.Solver(n, ell, precision=prec, tol=1e-12 if prec == "fp64" else 1e-10, enr_precond="block3")
     s.set_microstructure(L, lm, lp, sc)
     rng = np.random.default_rng(13)
@@ -241,7 +253,7 @@ def test_basic_and_bb_schemes(xf, scheme):
     on the same system: FP64 iteration counts as the oracle's (up to rounding) and the direct
     solution; the FP32-refined form reaches the same mean stress to 1e-6."""
     n, ell, L, lm, lp, sc = _case("sphere16")
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle("sphere16")
     eps = np.array([[0.2, -0.1, 0.3, 0.4, -0.2, 0.1]])
     u_ref = o.solve_direct(eps[0])
     _, info = o.pcg(eps[0], tol=1e-10, maxit=5000, scheme=scheme, green="fft")
@@ -262,7 +274,7 @@ def test_basic_and_bb_schemes(xf, scheme):
 def test_one_call_solve(xf):
     """The one-call Python solve equals the oracle's direct solution (sphere16)."""
     n, ell, L, lm, lp, sc = _case("sphere16")
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle("sphere16")
     eps = np.array([[0.3, 0.1, -0.2, 0.0, 0.5, 0.0]])
     out = xf.solve(L, lm, lp, eps, precision="fp64", tol=1e-12)
     assert out["converged"]
@@ -275,7 +287,7 @@ def test_fp64_solve_matches_direct(xf, name):
     n, ell, L, lm, lp, sc = _case(name)
     s = xf.Solver(n, ell, tol=1e-12)
     s.set_microstructure(L, lm, lp, sc)
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle(name)
     eps = np.array([[1.0, 0, 0, 0, 0, 0], [0.2, -0.1, 0.3, 0.4, -0.2, 0.1]])
     out = s.solve(eps, u=True, voxel_stress=True)
     assert out["converged"], out["stats"]
@@ -296,7 +308,7 @@ def test_fp64_effective_stiffness_and_gradient(xf):
     n, ell, L, lm, lp, sc = _case("ragged")
     s = xf.Solver(n, ell, tol=1e-12)
     s.set_microstructure(L, lm, lp, sc)
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle("ragged")
     C, st = s.effective_stiffness()
     assert st["converged"]
     Cs, Ce, U = o.effective_stiffness()
@@ -316,7 +328,7 @@ def test_fp32_refined_effective_stiffness(xf):
     n, ell, L, lm, lp, sc = _case("ragged")
     s = xf.Solver(n, ell, precision="fp32", tol=1e-10)
     s.set_microstructure(L, lm, lp, sc)
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle("ragged")
     C, st = s.effective_stiffness()
     assert st["converged"], st
     Cs, Ce, U = o.effective_stiffness()
@@ -329,7 +341,7 @@ def test_fp32_refined_gradient(xf):
     n, ell, L, lm, lp, sc = _case("ragged")
     s = xf.Solver(n, ell, precision="fp32", tol=1e-10)
     s.set_microstructure(L, lm, lp, sc)
-    o = XFEM(L, n, ell, lame_minus=lm, lame_plus=lp, scale=sc)
+    o = _oracle("ragged")
     C, st = s.effective_stiffness()
     assert st["converged"], st
     Cs, Ce, U = o.effective_stiffness()

@@ -45,7 +45,7 @@ def test_tuned_launch_shape_matches_defaults(xf):
 
 
 def test_tuned_solve_matches_oracle(xf):
-    n = (24, 24, 24)
+    n = (16, 16, 16)
     L = synth.sphere_levelset(n, (0.45, 0.5, 0.55), 0.33)
     lm, lp = synth.lame_from_E_nu(20.0, 0.2), synth.lame_from_E_nu(1.0, 0.3)
     s = xf.Solver(n, precision="fp32", tol=1e-9)
