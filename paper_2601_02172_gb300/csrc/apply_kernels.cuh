@@ -181,9 +181,13 @@ __device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3]
                                             EdgeT<T>* te = nullptr) {
   constexpr int p = perm_p(t), q = perm_q(t), r = perm_r(t);
   constexpr int c1 = tet_c1(t), c2 = tet_c2(t);
+  // a cut tet (handled by the cut-tet kernel) contributes nothing here: its coefficients are
+  // selected as zero instead of branching, so the six tets of a voxel run without divergence
   const unsigned cd = (code >> (2 * t)) & 3u;
-  if (cd == kCodeCut) return;
-  const int ph = NPH == 2 ? (int)cd : code_phase(cd);
+  const bool cut = cd == kCodeCut;
+  const int ph = NPH == 2 ? (int)(cd & 1u) : code_phase(cut ? 0u : cd);
+  auto cl = [&](int k) { return cut ? T(0) : cf.l(ph, k); };
+  auto cm = [&](int k) { return cut ? T(0) : cf.m(ph, k); };
   T G[3][3];  // G[k][i]: column k (axis k) of the gradient, component i
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -217,16 +221,16 @@ __device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3]
   T Tn[3][3];  // Tn[k][i] = tension on the column-k edge, component i
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const T lw = cf.l(ph, k), mw = cf.m(ph, k);
+    const T lw = cl(k), mw = cm(k);
     Tn[k][k] = lw * tr + (mw + mw) * G[k][k];
   }
   {
-    Tn[0][1] = cf.m(ph, 0) * s01;
-    Tn[1][0] = cf.m(ph, 1) * s01;
-    Tn[0][2] = cf.m(ph, 0) * s02;
-    Tn[2][0] = cf.m(ph, 2) * s02;
-    Tn[1][2] = cf.m(ph, 1) * s12;
-    Tn[2][1] = cf.m(ph, 2) * s12;
+    Tn[0][1] = cm(0) * s01;
+    Tn[1][0] = cm(1) * s01;
+    Tn[0][2] = cm(0) * s02;
+    Tn[2][0] = cm(2) * s02;
+    Tn[1][2] = cm(1) * s12;
+    Tn[2][1] = cm(2) * s12;
   }
   if (EDGE) {
 #pragma unroll
@@ -445,9 +449,8 @@ __global__ void __launch_bounds__(kTZ* kTY, std::is_same<T, dw>::value     ? XFF
   const long long yz = (long long)yv * n2 + zv;
   unsigned nx_code = a.code[(long long)xfirst * plane + yz];
   float nx_scale = a.scale ? a.scale[(long long)xfirst * plane + yz] : 1.0f;
-  for (int s = 0; s <= x1 - x0; ++s) {
-    const int xv = x0 - 1 + s;
-    const int xw = (xv % n0 + n0) % n0;
+  int xw = xfirst;  // the wrapped voxel index x0 - 1 + s, advanced without a division per step
+  for (int s = 0; s <= x1 - x0; ++s, xw = xw + 1 >= n0 ? xw + 1 - n0 : xw + 1) {
     const unsigned code = nx_code;
     const T sv = from_store<T>(nx_scale);
     commit((s + 1) & 1);  // plane x0 + s

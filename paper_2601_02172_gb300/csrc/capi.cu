@@ -1044,7 +1044,8 @@ static bool loops_timed_out(const unsigned char* lm_host, int n) {
 // Launch a built device loop graph on master: master after every item's earlier work, every
 // item after the graph.
 static xfft_status run_device_loop(const std::vector<LoopArgs>& items, cudaStream_t master,
-                                   cudaGraphExec_t exec, cudaEvent_t fork, const std::vector<cudaEvent_t>& joins) {
+                                   cudaGraphExec_t exec, cudaEvent_t fork, const std::vector<cudaEvent_t>& joins,
+                                   const std::vector<char>* finish = nullptr) {
   for (size_t i = 0; i < items.size(); ++i) {
     xfft_ctx* c = items[i].c;
     if (c->stream == master) continue;
@@ -1055,7 +1056,8 @@ static xfft_status run_device_loop(const std::vector<LoopArgs>& items, cudaStrea
   CU(cudaEventRecord(fork, master));
   for (const auto& L : items)
     if (L.c->stream != master) CU(cudaStreamWaitEvent(L.c->stream, fork, 0));
-  for (const auto& L : items) TRY(loop_finish(L));
+  for (size_t i = 0; i < items.size(); ++i)
+    if (!finish || (*finish)[i]) TRY(loop_finish(items[i]));
   return XFFT_OK;
 }
 
@@ -1278,24 +1280,42 @@ static xfft_status run_check(SolveRun& s, bool* need_inner) {
   return XFFT_OK;
 }
 
+// the loop arguments of a run's inner solves (the same in every refinement round)
+static LoopArgs run_loop_args(const SolveRun& s) {
+  xfft_ctx* c = s.c;
+  LoopArgs L;
+  L.c = c;
+  L.n_rhs = s.n_rhs;
+  L.maxit = c->opt.maxit;
+  if (c->opt.precision == XFFT_FP64) {
+    L.dbl = true;
+    L.u = c->v64[0];
+    L.f = c->v64[1];
+    L.dA = c->v64[2];
+    L.dB = c->v64[5];
+    L.z = c->v64[3];
+    L.q = c->v64[4];
+    L.tol = c->opt.tol;
+    L.crit = 0;
+  } else {
+    L.dbl = false;
+    L.u = c->v32[0];
+    L.f = c->v32[1];
+    L.dA = c->v32[2];
+    L.dB = c->v32[5];
+    L.z = c->v32[3];
+    L.q = c->v32[4];
+    L.tol = 0.5;
+    L.crit = 1;
+  }
+  return L;
+}
+
 // enqueue what precedes the inner solve and return its loop arguments
 static xfft_status run_inner_pre(SolveRun& s, LoopArgs* L) {
   xfft_ctx* c = s.c;
-  L->c = c;
-  L->n_rhs = s.n_rhs;
-  L->maxit = c->opt.maxit;
-  if (c->opt.precision == XFFT_FP64) {
-    L->dbl = true;
-    L->u = c->v64[0];
-    L->f = c->v64[1];
-    L->dA = c->v64[2];
-    L->dB = c->v64[5];
-    L->z = c->v64[3];
-    L->q = c->v64[4];
-    L->tol = c->opt.tol;
-    L->crit = 0;
-    return XFFT_OK;
-  }
+  *L = run_loop_args(s);
+  if (c->opt.precision == XFFT_FP64) return XFFT_OK;
   const size_t tot = (size_t)s.n_rhs * stride_of(c);
   // inner FP32 PCG on A delta = r (relative reduction inner_tol); the act flags of the refining
   // RHS were set by the mode-3 finalisation
@@ -1306,15 +1326,6 @@ static xfft_status run_inner_pre(SolveRun& s, LoopArgs* L) {
     CU(cudaMemsetAsync(c->v32[0], 0, tot * sizeof(float), c->stream));
     CU(cudaMemsetAsync(c->v32[2], 0, tot * sizeof(float), c->stream));
   }
-  L->dbl = false;
-  L->u = c->v32[0];
-  L->f = c->v32[1];
-  L->dA = c->v32[2];
-  L->dB = c->v32[5];
-  L->z = c->v32[3];
-  L->q = c->v32[4];
-  L->tol = 0.5;
-  L->crit = 1;
   return XFFT_OK;
 }
 
@@ -1632,44 +1643,60 @@ extern "C" xfft_status xfft_batch_effective_stiffness(int n, xfft_ctx* const* ct
     CU(cudaStreamWaitEvent(ctxs[i]->stream, B.t0, 0));
     TRY(run_begin(runs[i], ctxs[i], 6, &Rs[i]));
   }
+  // one graph of n independent device loops, built at the first inner solve and launched in
+  // every round; a context without an inner solve in a round has its activity flags cleared, so
+  // its loop ends after one round of early-exiting kernels and its state stays as it was
+  std::vector<LoopArgs> all(n);
+  for (int i = 0; i < n; ++i) all[i] = run_loop_args(runs[i]);
+  struct ExecGuard {
+    cudaGraphExec_t e = nullptr;
+    ~ExecGuard() {
+      if (e) cudaGraphExecDestroy(e);
+    }
+  } G;
+  bool graph_ok = true;
   for (;;) {
     for (auto& r : runs)
       if (!r.done) TRY(run_residual(r));
-    std::vector<LoopArgs> items;
-    std::vector<SolveRun*> inner;
-    for (auto& r : runs) {
+    std::vector<char> part(n, 0);
+    int nin = 0;
+    for (int i = 0; i < n; ++i) {
+      SolveRun& r = runs[i];
       if (r.done) continue;
       bool need = false;
       TRY(run_check(r, &need));
       if (!need) continue;
       LoopArgs L;
       TRY(run_inner_pre(r, &L));
-      items.push_back(L);
-      inner.push_back(&r);
+      part[i] = 1;
+      ++nin;
     }
-    if (items.empty()) break;
-    cudaGraphExec_t exec = nullptr;
-    std::vector<cudaEvent_t> joins(B.joins.begin(), B.joins.begin() + items.size());
-    const xfft_status bs = build_device_loop(items, B.lm, limit, &exec);
+    if (nin == 0) break;
+    if (graph_ok && !G.e) {
+      const xfft_status bs = build_device_loop(all, B.lm, limit, &G.e);
+      if (bs == XFFT_EUNSUPPORTED) graph_ok = false;
+      else TRY(bs);
+    }
     bool timed_out = false;
-    if (bs == XFFT_OK) {
-      const xfft_status rs = run_device_loop(items, B.master, exec, B.fork, joins);
-      cudaGraphExecDestroy(exec);
-      TRY(rs);
-      CU(cudaMemcpyAsync(B.lm_host, B.lm, kLoopStride * items.size(), cudaMemcpyDeviceToHost, B.master));
+    if (graph_ok) {
+      for (int i = 0; i < n; ++i)
+        if (!part[i]) CU(cudaMemsetAsync(ctxs[i]->act, 0, 64 * sizeof(int), ctxs[i]->stream));
+      TRY(run_device_loop(all, B.master, G.e, B.fork, B.joins, &part));
+      CU(cudaMemcpyAsync(B.lm_host, B.lm, kLoopStride * n, cudaMemcpyDeviceToHost, B.master));
       CU(cudaStreamSynchronize(B.master));
-      timed_out = loops_timed_out(B.lm_host, (int)items.size());
-    } else if (bs == XFFT_EUNSUPPORTED) {
-      for (const auto& L : items) {  // no conditional graphs: each context's own loop
-        L.c->devloop_ok = false;
+      for (int i = 0; i < n; ++i)
+        if (part[i] && reinterpret_cast<const LoopState*>(B.lm_host + kLoopStride * i)->timed_out) timed_out = true;
+    } else {
+      for (int i = 0; i < n; ++i) {  // no conditional graphs: each context's own loop
+        if (!part[i]) continue;
+        ctxs[i]->devloop_ok = false;
         bool to = false;
-        TRY(cg_loop(L, &to));
+        TRY(cg_loop(all[i], &to));
         timed_out = timed_out || to;
       }
-    } else {
-      return bs;
     }
-    for (auto* r : inner) TRY(run_inner_post(*r, timed_out));
+    for (int i = 0; i < n; ++i)
+      if (part[i]) TRY(run_inner_post(runs[i], timed_out));
   }
   for (int i = 0; i < n; ++i) {
     CU(cudaEventRecord(B.joins[i], ctxs[i]->stream));
