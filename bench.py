@@ -658,7 +658,7 @@ def main():
                                 "cg_iters": int(sum(st5["iters"])), "converged": bool(st5["converged"]),
                                 "prec_ms_per_rhs": pm / max(pu, 1),
                                 "prec_frac_of_measured_hbm": bps / 1e9 / load_peaks()[0],
-                                "prec_path": "five-pass (the fused y-z slab passes cover 128 x 128 planes)"}
+                                "prec_path": "five-pass (the fused y-z plane passes cover square planes of 32 ... 128 nodes)"}
                 sv.close()
                 del w5
             extra["precision_at_scale"] = scale5

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxfft.so")
-SOURCES = ["setup.cu", "apply.cu", "apply_multi.cu", "fft.cu", "fft_fast.cu", "fft_slab.cu", "cg.cu", "grad.cu", "loop.cu", "peak.cu", "capi.cu"]
+SOURCES = ["setup.cu", "apply.cu", "apply_multi.cu", "fft.cu", "fft_fast.cu", "fft_slab.cu", "fft_slab_sq.cu", "cg.cu", "grad.cu", "loop.cu", "peak.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(HERE, "..", "include")]

@@ -59,11 +59,11 @@ struct FftPlan {
 
 // slab path (fft_slab.cu)
 bool slab_supported(int n0, int n1, int n2);
-size_t slab_table_floats(int n0);
+size_t slab_table_floats(int n0, int n1);
 int slab_z_blocks(int n0);
-cudaError_t slab_green_table(float* table, int n0, const void* const* ge, const void* const* gs,
+cudaError_t slab_green_table(float* table, int n0, int n1, const void* const* ge, const void* const* gs,
                              const double* ih, double halfvol, cudaStream_t s);
-cudaError_t slab_precondition(int n0, float* f, float* z, void* spec, long long stride, long long sstride,
+cudaError_t slab_precondition(int n0, int n1, float* f, float* z, void* spec, long long stride, long long sstride,
                               const int* active, const void* tw0, const void* tw1, const void* tw2,
                               const float* table, const void* const* ge, const void* const* gs,
                               const double* ih, double halfvol, unsigned long long* units, const float* q,
@@ -714,12 +714,12 @@ FftPlan* fft_plan_create(const GridDev& g, cudaError_t* err) {
   p->slab = false;
   p->gtab = nullptr;
   if (p->fast && slab_supported(g.n0, g.n1, g.n2)) {
-    *err = cudaMalloc(&p->gtab, slab_table_floats(g.n0) * sizeof(float));
+    *err = cudaMalloc(&p->gtab, slab_table_floats(g.n0, g.n1) * sizeof(float));
     if (*err == cudaSuccess) {
       const void* ge[3] = {p->gef[0], p->gef[1], p->gef[2]};
       const void* gs[3] = {p->gsf[0], p->gsf[1], p->gsf[2]};
       const double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
-      *err = slab_green_table(p->gtab, g.n0, ge, gs, ih, 0.5 * g.vol_tet, 0);
+      *err = slab_green_table(p->gtab, g.n0, g.n1, ge, gs, ih, 0.5 * g.vol_tet, 0);
       if (*err == cudaSuccess) *err = cudaDeviceSynchronize();
     }
     if (*err != cudaSuccess) {
@@ -811,7 +811,7 @@ cudaError_t launch_precondition(const FftPlan* p, T* f, T* z, void* spec_v, long
     const void* ge[3] = {p->gef[0], p->gef[1], p->gef[2]};
     const void* gs[3] = {p->gsf[0], p->gsf[1], p->gsf[2]};
     const double ih[3] = {1.0 / p->g.h[0], 1.0 / p->g.h[1], 1.0 / p->g.h[2]};
-    cudaError_t e = slab_precondition(p->n[0], (float*)f, (float*)z, spec, stride, sstride, active, p->twf[0],
+    cudaError_t e = slab_precondition(p->n[0], p->n[1], (float*)f, (float*)z, spec, stride, sstride, active, p->twf[0],
                                       p->twf[1], p->twf[2], p->gtab, ge, gs, ih, 0.5 * p->g.vol_tet, units,
                                       (const float*)q, st, partials, nparts, n_rhs, s);
     if (e != cudaSuccess) return e;

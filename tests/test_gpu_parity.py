@@ -493,14 +493,15 @@ def test_laminate_closed_form_gpu(xf):
         assert np.abs(C - Cref).max() < tol * np.abs(Cref).max(), (prec, np.abs(C - Cref).max())
 
 
-def _slab_modes(rng):
-    """Fourier modes for a 16 x 128 x 128 grid that reach every line type of the FP32 y-z plane
-    path: z frequencies 0 and 64 (real z lines) with y frequencies 0, 64 and others, x
-    frequencies 0 and 8 (Nyquist), odd and even y frequencies, and generic modes."""
-    ks = [(0, 0, 1), (1, 0, 0), (8, 0, 0), (3, 0, 64), (0, 64, 0), (8, 64, 64), (5, 64, 0),
-          (2, 7, 0), (6, 100, 0), (4, 9, 64), (7, 120, 64), (3, 64, 5), (1, 2, 3), (9, 33, 17),
-          (15, 127, 127), (8, 1, 63), (0, 77, 40), (11, 64, 64), (12, 0, 64), (0, 0, 64)]
-    ks += [tuple(int(v) for v in rng.integers(0, (16, 128, 128))) for _ in range(12)]
+def _slab_modes(rng, n=(16, 128, 128)):
+    """Fourier modes for an n0 x N x N grid that reach every line type of the FP32 y-z plane
+    path: z frequencies 0 and N/2 (real z lines) with y frequencies 0, N/2 and others, x
+    frequencies 0 and n0/2 (Nyquist), odd and even y frequencies, and generic modes."""
+    h0, h = n[0] // 2, n[1] // 2
+    ks = [(0, 0, 1), (1, 0, 0), (h0, 0, 0), (3, 0, h), (0, h, 0), (h0, h, h), (5, h, 0),
+          (2, 7, 0), (6, h + 36, 0), (4, 9, h), (7, n[1] - 8, h), (3, h, 5), (1, 2, 3), (9, 33, 17),
+          (n[0] - 1, n[1] - 1, n[2] - 1), (h0, 1, h - 1), (0, h + 13, h - 24), (11, h, h), (12, 0, h), (0, 0, h)]
+    ks += [tuple(int(v) for v in rng.integers(0, n)) for _ in range(12)]
     return [(k, rng.normal(size=3) + 1j * rng.normal(size=3)) for k in ks]
 
 
@@ -518,6 +519,24 @@ def test_precondition_plane_waves_yz128(xf, prec):
     assert _rel(z[0], zref) < tol
     assert np.abs(z[0] - zref).max() < 10 * tol * np.abs(zref).max()
     assert abs(rr[0] - f @ zref) <= 10 * tol * abs(f @ zref)
+
+
+@pytest.mark.parametrize("n", [(16, 32, 32), (32, 48, 48), (48, 64, 64), (16, 80, 80), (32, 96, 96),
+                               (96, 48, 48)])
+def test_precondition_plane_waves_square_planes(xf, n):
+    """The FP32 y-z plane path at every other square plane size it serves (32 ... 96 nodes, several
+    x lengths) against the oracle's exact single-mode preconditioner, element by element, with
+    three right-hand sides (one x-pass group of two and a partial one)."""
+    s = xf.Solver(n)
+    s.set_microstructure(np.ones(n), synth.lame_from_E_nu(2.0, 0.3), synth.lame_from_E_nu(1.0, 0.3))
+    o = XFEM(np.ones(n), n)
+    rng = np.random.default_rng(n[1] + n[0])
+    fs, zs = zip(*(o.precondition_modes(_slab_modes(rng, n)) for _ in range(3)))
+    z, rr = s.precondition(np.stack(fs), precision="fp32")
+    for k in range(3):
+        assert _rel(z[k], zs[k]) < 2e-5, (n, k)
+        assert np.abs(z[k] - zs[k]).max() < 2e-4 * np.abs(zs[k]).max()
+        assert abs(rr[k] - fs[k] @ zs[k]) <= 2e-4 * abs(fs[k] @ zs[k])
 
 
 def test_laminate_closed_form_yz128(xf):
