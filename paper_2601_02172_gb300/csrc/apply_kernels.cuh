@@ -181,13 +181,9 @@ __device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3]
                                             EdgeT<T>* te = nullptr) {
   constexpr int p = perm_p(t), q = perm_q(t), r = perm_r(t);
   constexpr int c1 = tet_c1(t), c2 = tet_c2(t);
-  // a cut tet (handled by the cut-tet kernel) contributes nothing here: its coefficients are
-  // selected as zero instead of branching, so the six tets of a voxel run without divergence
   const unsigned cd = (code >> (2 * t)) & 3u;
-  const bool cut = cd == kCodeCut;
-  const int ph = NPH == 2 ? (int)(cd & 1u) : code_phase(cut ? 0u : cd);
-  auto cl = [&](int k) { return cut ? T(0) : cf.l(ph, k); };
-  auto cm = [&](int k) { return cut ? T(0) : cf.m(ph, k); };
+  if (cd == kCodeCut) return;
+  const int ph = NPH == 2 ? (int)cd : code_phase(cd);
   T G[3][3];  // G[k][i]: column k (axis k) of the gradient, component i
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -221,16 +217,16 @@ __device__ __forceinline__ void tet_stencil(const Node4<T> (&u)[8], T (&F)[8][3]
   T Tn[3][3];  // Tn[k][i] = tension on the column-k edge, component i
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const T lw = cl(k), mw = cm(k);
+    const T lw = cf.l(ph, k), mw = cf.m(ph, k);
     Tn[k][k] = lw * tr + (mw + mw) * G[k][k];
   }
   {
-    Tn[0][1] = cm(0) * s01;
-    Tn[1][0] = cm(1) * s01;
-    Tn[0][2] = cm(0) * s02;
-    Tn[2][0] = cm(2) * s02;
-    Tn[1][2] = cm(1) * s12;
-    Tn[2][1] = cm(2) * s12;
+    Tn[0][1] = cf.m(ph, 0) * s01;
+    Tn[1][0] = cf.m(ph, 1) * s01;
+    Tn[0][2] = cf.m(ph, 0) * s02;
+    Tn[2][0] = cf.m(ph, 2) * s02;
+    Tn[1][2] = cf.m(ph, 1) * s12;
+    Tn[2][1] = cf.m(ph, 2) * s12;
   }
   if (EDGE) {
 #pragma unroll
