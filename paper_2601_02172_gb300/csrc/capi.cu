@@ -1747,7 +1747,11 @@ extern "C" xfft_status xfft_grad_phases(xfft_ctx* c, const double dL_dCeff[36], 
   if (!c->dscale) CU(dalloc(c, &c->dscale, g.N));
   {
     ProfScope ps(c, XFFT_PROF_GRAD, 3);
-    CU(launch_grad(c->U6, c->isD, cutdata(c), a, c->dscale, c->opt.precision == XFFT_FP32_REFINED, s));
+    // the mixed-precision gradient splits U into float pairs in the solve's float work vectors
+    // (free between solves; at least 6 * stride floats each)
+    const bool f32 = c->opt.precision == XFFT_FP32_REFINED && c->cap_prec == XFFT_FP32_REFINED && c->v32[0] &&
+                     c->v32[1] && c->cap_rhs >= 6;
+    CU(launch_grad(c->U6, c->isD, cutdata(c), a, c->dscale, f32 ? c->v32[0] : nullptr, f32 ? c->v32[1] : nullptr, s));
     CU(launch_reduce_partials(c->partials, kGradValues, a.nparts, a.nparts, c->red_out, s));
   }
   double red[kGradValues];

@@ -44,7 +44,9 @@ struct Sq {
   static_assert(N % 8 == 0 && N1 == N2, "square planes, 8-slot x tiles");
 };
 constexpr int kGF = 9;                     // floats per Green factor: il00, il11, il22, l10, l20, l21
-constexpr int ST = 8;                      // slots per x-pass block (one 64-byte segment)
+#ifndef XFFT_KXS_ST
+#define XFFT_KXS_ST 8
+#endif
 #ifndef XFFT_KXS_RG
 #define XFFT_KXS_RG 2
 #endif
@@ -53,6 +55,9 @@ constexpr int RG = XFFT_KXS_RG;            // right-hand sides per x-pass block
 template <int N0>
 struct XCfg {
   static constexpr int EX = N0 == 128 ? 16 : fast::Plan<N0>::E;
+  // slots per x-pass block (XFFT_KXS_ST complex values: 8 = one 64-byte segment per plane), fewer
+  // where the block would exceed 1024 threads
+  static constexpr int ST = 3 * RG * XFFT_KXS_ST * (N0 / EX) <= 1024 ? XFFT_KXS_ST : 8;
   static constexpr int THREADS = 3 * RG * ST * (N0 / EX);
   static constexpr int MINB = THREADS <= 384 ? 2 : 1;
 };
@@ -356,6 +361,7 @@ __global__ void __launch_bounds__(XCfg<N0>::THREADS, XCfg<N0>::MINB)
   constexpr int EX = XCfg<N0>::EX;
   constexpr int TL = N0 / EX;
   constexpr int LS = N0 + 1;
+  constexpr int ST = XCfg<N0>::ST;
   constexpr int LINES = 3 * RG * ST;
   constexpr int NTX = LINES * TL;
   constexpr int N2 = Sq<N>::N2, H2 = Sq<N>::H2, PL = Sq<N>::PL;
@@ -502,10 +508,10 @@ cudaError_t precondition_n(int n0, float* f, float* z, void* spec, long long str
   switch (n0) {
 #define X(n)                                                                                          \
   case n: {                                                                                           \
-    const size_t smx = sizeof(float2) * (n + (size_t)3 * RG * ST * (n + 1));                         \
+    const size_t smx = sizeof(float2) * (n + (size_t)3 * RG * XCfg<n>::ST * (n + 1));                \
     e = slab_smem((const void*)kx_slab<n, N>, smx);                                                   \
     if (e != cudaSuccess) return e;                                                                   \
-    kx_slab<n, N><<<(Q::N1 / 2) * (Q::N2 / ST) * ngroups, XCfg<n>::THREADS, smx, s>>>(                \
+    kx_slab<n, N><<<(Q::N1 / 2) * (Q::N2 / XCfg<n>::ST) * ngroups, XCfg<n>::THREADS, smx, s>>>(       \
         (float2*)spec, sstride, n_rhs, ngroups, active, (const float2*)tw0, table, (const float2*)ge[0], \
         (const float2*)ge[1], (const float2*)ge[2], (const float2*)gs[0], (const float2*)gs[1],        \
         (const float2*)gs[2], (float)ih[0], (float)ih[1], (float)ih[2], (float)halfvol);              \

@@ -11,15 +11,30 @@
 //   dL/ds_v      += sum_kl G_kl int eps_k : C_p : eps_l / |Y|
 // and the energy form C_kl = int eps_k : C : eps_l / |Y| as a by-product.
 //
-// Arithmetic type T: double for the FP64 solver; float for the mixed-precision solver, where the
-// displacement differences are still formed in FP64 (they cancel) and only the strains and
-// their products are FP32, each item's contribution being accumulated in FP64.
+// Arithmetic type T: double for the FP64 solver; float for the mixed-precision solver.  There the
+// standard displacements are first split into float pairs u = hi + lo (hi = u rounded to FP32,
+// lo = the rounded remainder); a node difference (hi_a - hi_b) + (lo_a - lo_b) then carries the
+// FP64 difference to FP32 precision without FP64 arithmetic (hi_a - hi_b is exact for neighbours
+// within a factor two of each other, and otherwise rounds relative to the difference itself).
+// The enriched strains are still formed in FP64 (products with 1/sqrt(D0), then differences);
+// strains and their products are FP32, each item's contribution accumulated in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include "xfft_kernels.h"
 
 namespace xfft {
+
+// u = hi + lo in float pairs (hi = fl32(u), lo = fl32(u - hi))
+__global__ void k_split_hilo(const double* __restrict__ u, float* __restrict__ hi, float* __restrict__ lo,
+                             long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = u[i];
+    const float h = (float)v;
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
+  }
+}
 
 // partial values: dlambda[p] (p < kMaxPhases), dmu[p], C_energy (21 upper entries)
 constexpr int kNG = kGradValues;
@@ -45,14 +60,12 @@ __device__ __forceinline__ T dd6(const T* a, const T* b) {
 // the phase sums and the energy-form entries (accumulated in T per thread; FP32 sums of a few
 // dozen items are exact to ~1e-7), and the voxel-scale contribution.
 template <typename T, int t>
-__device__ __forceinline__ void grad_uncut_tet(const double* __restrict__ U, const GradArgs& a,
-                                               const double* Gs, long long v, int ph, T (&acc)[kNG],
-                                               double& contrib) {
+__device__ __forceinline__ void grad_uncut_tet(const double* __restrict__ U, const float* __restrict__ Uh,
+                                               const float* __restrict__ Ul, const GradArgs& a,
+                                               const T* Gk, long long v, int i3, int j3, int k3, int ph,
+                                               T (&acc)[kNG], double& contrib) {
   const GridDev& g = a.g;
   constexpr int p = perm_p(t), q = perm_q(t), r = perm_r(t);
-  const int k3 = (int)(v % g.n2);
-  const int j3 = (int)((v / g.n2) % g.n1);
-  const int i3 = (int)(v / ((long long)g.n1 * g.n2));
   long long nd[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) nd[c] = corner_node(g, i3, j3, k3, tet_corner(t, c));
@@ -61,16 +74,28 @@ __device__ __forceinline__ void grad_uncut_tet(const double* __restrict__ U, con
   T eps[6][6], tr[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const double* uk = U + k * a.stride;
     T H[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const double u0 = uk[i * g.N + nd[0]], u1 = uk[i * g.N + nd[1]];
-      const double u2 = uk[i * g.N + nd[2]], u3 = uk[i * g.N + nd[3]];
-      // the differences cancel: formed in FP64, then scaled in T
-      H[i][p] = (T)(u1 - u0) * ih[p];
-      H[i][q] = (T)(u2 - u1) * ih[q];
-      H[i][r] = (T)(u3 - u2) * ih[r];
+      // the differences cancel: formed in FP64 (FP64 solver) or from the float pairs
+      T d01, d12, d23;
+      if constexpr (sizeof(T) == 8) {
+        const double* uk = U + k * a.stride + i * g.N;
+        const double u0 = uk[nd[0]], u1 = uk[nd[1]], u2 = uk[nd[2]], u3 = uk[nd[3]];
+        d01 = u1 - u0;
+        d12 = u2 - u1;
+        d23 = u3 - u2;
+      } else {
+        const long long o = k * a.stride + i * g.N;
+        const float h0 = Uh[o + nd[0]], h1 = Uh[o + nd[1]], h2 = Uh[o + nd[2]], h3 = Uh[o + nd[3]];
+        const float l0 = Ul[o + nd[0]], l1 = Ul[o + nd[1]], l2 = Ul[o + nd[2]], l3 = Ul[o + nd[3]];
+        d01 = (h1 - h0) + (l1 - l0);
+        d12 = (h2 - h1) + (l2 - l1);
+        d23 = (h3 - h2) + (l3 - l2);
+      }
+      H[i][p] = d01 * ih[p];
+      H[i][q] = d12 * ih[q];
+      H[i][r] = d23 * ih[r];
     }
     eps[k][0] = H[0][0];
     eps[k][1] = H[1][1];
@@ -92,7 +117,7 @@ __device__ __forceinline__ void grad_uncut_tet(const double* __restrict__ U, con
     for (int l = k; l < 6; ++l) {
       const T tt = tr[k] * tr[l];
       const T ee = T(2) * dd6(eps[k], eps[l]);
-      const T gk = (T)((k == l) ? Gs[k * 6 + l] : Gs[k * 6 + l] + Gs[l * 6 + k]);
+      const T gk = Gk[upper_idx(k, l)];
       ql += gk * tt;
       qm += gk * ee;
       acc[kNGC + upper_idx(k, l)] += wsv * (lam * tt + mu * ee);
@@ -113,14 +138,18 @@ __device__ __forceinline__ void grad_uncut_tet(const double* __restrict__ U, con
 
 // block: 32 voxels (x) by 6 tets (y); each warp handles one tet of 32 voxels
 template <typename T>
-__global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U, const GradArgs a,
+__global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U, const float* __restrict__ Uh,
+                                                     const float* __restrict__ Ul, const GradArgs a,
                                                      double* __restrict__ dscale) {
   __shared__ double sds[6][32];
   __shared__ double red[kNG * 32];
-  __shared__ double Gs[36];
+  __shared__ T Gk[21];  // G_kl + G_lk (k < l), G_kk: the weights of the upper-triangle pair sums
   const int lane = threadIdx.x, t = threadIdx.y;
   const int tid = lane + 32 * t;
-  if (tid < 36) Gs[tid] = a.G[tid];
+  if (tid < 36) {
+    const int k = tid / 6, l = tid - 6 * (tid / 6);
+    if (k <= l) Gk[upper_idx(k, l)] = (T)(k == l ? a.G[k * 6 + l] : a.G[k * 6 + l] + a.G[l * 6 + k]);
+  }
   __syncthreads();
   const GridDev& g = a.g;
   T acc[kNG];
@@ -134,13 +163,25 @@ __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U
       const unsigned cd = (a.code[v] >> (2 * t)) & 3u;
       if (cd != kCodeCut) {
         const int ph = code_phase(cd);
+        // voxel coordinates (32-bit division where the grid allows it)
+        int i3, j3, k3;
+        if (g.N <= 0xffffffffLL) {
+          const unsigned vu = (unsigned)v, r2 = vu / (unsigned)g.n2;
+          k3 = (int)(vu - r2 * (unsigned)g.n2);
+          i3 = (int)(r2 / (unsigned)g.n1);
+          j3 = (int)(r2 - (unsigned)i3 * (unsigned)g.n1);
+        } else {
+          k3 = (int)(v % g.n2);
+          j3 = (int)((v / g.n2) % g.n1);
+          i3 = (int)(v / ((long long)g.n1 * g.n2));
+        }
         switch (t) {  // uniform per warp
-          case 0: grad_uncut_tet<T, 0>(U, a, Gs, v, ph, acc, contrib); break;
-          case 1: grad_uncut_tet<T, 1>(U, a, Gs, v, ph, acc, contrib); break;
-          case 2: grad_uncut_tet<T, 2>(U, a, Gs, v, ph, acc, contrib); break;
-          case 3: grad_uncut_tet<T, 3>(U, a, Gs, v, ph, acc, contrib); break;
-          case 4: grad_uncut_tet<T, 4>(U, a, Gs, v, ph, acc, contrib); break;
-          default: grad_uncut_tet<T, 5>(U, a, Gs, v, ph, acc, contrib); break;
+          case 0: grad_uncut_tet<T, 0>(U, Uh, Ul, a, Gk, v, i3, j3, k3, ph, acc, contrib); break;
+          case 1: grad_uncut_tet<T, 1>(U, Uh, Ul, a, Gk, v, i3, j3, k3, ph, acc, contrib); break;
+          case 2: grad_uncut_tet<T, 2>(U, Uh, Ul, a, Gk, v, i3, j3, k3, ph, acc, contrib); break;
+          case 3: grad_uncut_tet<T, 3>(U, Uh, Ul, a, Gk, v, i3, j3, k3, ph, acc, contrib); break;
+          case 4: grad_uncut_tet<T, 4>(U, Uh, Ul, a, Gk, v, i3, j3, k3, ph, acc, contrib); break;
+          default: grad_uncut_tet<T, 5>(U, Uh, Ul, a, Gk, v, i3, j3, k3, ph, acc, contrib); break;
         }
       }
     }
@@ -159,10 +200,17 @@ __global__ void __launch_bounds__(192) k_grad_uncut(const double* __restrict__ U
 }
 
 template <typename T>
-__global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
+__global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U, const float* __restrict__ Uh,
+                                                  const float* __restrict__ Ul,
                                                   const double* __restrict__ isD, const CutData cd,
                                                   const GradArgs a, double* __restrict__ dscale) {
   __shared__ double red[kNG * 32];
+  __shared__ T Gk[21];  // G_kl + G_lk (k < l), G_kk
+  if (threadIdx.x < 36) {
+    const int k = threadIdx.x / 6, l = threadIdx.x - 6 * (threadIdx.x / 6);
+    if (k <= l) Gk[upper_idx(k, l)] = (T)(k == l ? a.G[k * 6 + l] : a.G[k * 6 + l] + a.G[l * 6 + k]);
+  }
+  __syncthreads();
   const GridDev& g = a.g;
   const long long N = g.N;
   const int nX = a.nX, ncut = cd.ncut;
@@ -200,6 +248,51 @@ __global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
       for (int k = 0; k < 10; ++k) M[k] = (T)cd.dp[(long long)cut_f_M(si, k) * ncut + e];
       T Eb[6][4][6];  // [load case][b][component]
       T trb[6][4];
+      if constexpr (sizeof(T) == 4) {
+        // standard strain from the float pairs along the tet's path 0 -> e_p -> e_p+e_q -> (1,1,1);
+        // enriched strain from FP64 differences of the physical enriched coefficients
+        const int p = perm_p(t), q = perm_q(t), r = perm_r(t);
+        const float ihf[3] = {(float)ih[0], (float)ih[1], (float)ih[2]};
+        float cf[4], gamf[3];
+        for (int b = 0; b < 4; ++b) cf[b] = (float)c[b];
+        for (int x = 0; x < 3; ++x) gamf[x] = (float)gam[x];
+        for (int k = 0; k < 6; ++k) {
+          float Hs[3][3], Hw[3][3], wsf[4][3];
+          for (int i = 0; i < 3; ++i) {
+            const long long o = k * a.stride + i * N;
+            float hv[4], lv[4];
+            double wv[4];
+            for (int aa = 0; aa < 4; ++aa) {
+              hv[aa] = Uh[o + nd[aa]];
+              lv[aa] = Ul[o + nd[aa]];
+              const long long oe = (long long)i * nX + ei[aa];
+              wv[aa] = U[k * a.stride + 3 * N + oe] * isD[oe];
+              wsf[aa][i] = (float)wv[aa];
+            }
+            Hs[i][p] = ((hv[1] - hv[0]) + (lv[1] - lv[0])) * ihf[p];
+            Hs[i][q] = ((hv[2] - hv[1]) + (lv[2] - lv[1])) * ihf[q];
+            Hs[i][r] = ((hv[3] - hv[2]) + (lv[3] - lv[2])) * ihf[r];
+            Hw[i][p] = (float)(wv[1] - wv[0]) * ihf[p];
+            Hw[i][q] = (float)(wv[2] - wv[1]) * ihf[q];
+            Hw[i][r] = (float)(wv[3] - wv[2]) * ihf[r];
+          }
+          const float rs = 0.70710678118654752440f;
+          float es[6] = {Hs[0][0], Hs[1][1], Hs[2][2], 0.5f * (Hs[1][2] + Hs[2][1]),
+                         0.5f * (Hs[0][2] + Hs[2][0]), 0.5f * (Hs[0][1] + Hs[1][0])};
+          es[k] += k < 3 ? 1.0f : rs;  // unit Mandel strain E_k
+          const float ew[6] = {Hw[0][0], Hw[1][1], Hw[2][2], 0.5f * (Hw[1][2] + Hw[2][1]),
+                               0.5f * (Hw[0][2] + Hw[2][0]), 0.5f * (Hw[0][1] + Hw[1][0])};
+          for (int b = 0; b < 4; ++b) {
+            const float* wb = wsf[b];
+            const float sw[6] = {wb[0] * gamf[0], wb[1] * gamf[1], wb[2] * gamf[2],
+                                 0.5f * (wb[1] * gamf[2] + wb[2] * gamf[1]),
+                                 0.5f * (wb[0] * gamf[2] + wb[2] * gamf[0]),
+                                 0.5f * (wb[0] * gamf[1] + wb[1] * gamf[0])};
+            for (int x = 0; x < 6; ++x) Eb[k][b][x] = es[x] + cf[b] * ew[x] + sw[x];
+            trb[k][b] = Eb[k][b][0] + Eb[k][b][1] + Eb[k][b][2];
+          }
+        }
+      } else
       for (int k = 0; k < 6; ++k) {
         const double* uk = U + k * a.stride;
         double us[4][3], ws[4][3];
@@ -237,20 +330,33 @@ __global__ void __launch_bounds__(64) k_grad_cut(const double* __restrict__ U,
       }
       T ql = T(0), qm = T(0);
       const T lamT = (T)lam, muT = (T)mu;
-      for (int k = 0; k < 6; ++k)
-        for (int l = k; l < 6; ++l) {
+#pragma unroll 1
+      for (int l = 0; l < 6; ++l) {
+        // the side's moment matrix applied to load case l's corner strains and traces, so that
+        // each pair (k, l) costs one pass over load case k's corners
+        T ME[4][6], mt[4];
+        for (int b = 0; b < 4; ++b) {
+          mt[b] = T(0);
+          for (int x = 0; x < 6; ++x) ME[b][x] = T(0);
+          for (int cc = 0; cc < 4; ++cc) {
+            const T m = M[midx(b, cc)];
+            mt[b] += m * trb[l][cc];
+            for (int x = 0; x < 6; ++x) ME[b][x] += m * Eb[l][cc][x];
+          }
+        }
+        for (int k = 0; k <= l; ++k) {
           T tt = T(0), ee = T(0);
-          for (int b = 0; b < 4; ++b)
-            for (int cc = 0; cc < 4; ++cc) {
-              const T m = M[midx(b, cc)];
-              tt += m * trb[k][b] * trb[l][cc];
-              ee += m * T(2) * dd6(Eb[k][b], Eb[l][cc]);
-            }
-          const T gk = (T)((k == l) ? a.G[k * 6 + l] : a.G[k * 6 + l] + a.G[l * 6 + k]);
+          for (int b = 0; b < 4; ++b) {
+            tt += trb[k][b] * mt[b];
+            ee += dd6(Eb[k][b], ME[b]);
+          }
+          ee *= T(2);
+          const T gk = Gk[upper_idx(k, l)];
           ql += gk * tt;
           qm += gk * ee;
           acc[kNGC + upper_idx(k, l)] += inv * sv * (double)(lamT * tt + muT * ee);
         }
+      }
       acc[ph] += inv * sv * (double)ql;
       acc[kMaxPhases + ph] += inv * sv * (double)qm;
       contrib += inv * (double)(lamT * ql + muT * qm);
@@ -274,17 +380,24 @@ int grad_blocks_cut(int ncut) {
 }
 
 cudaError_t launch_grad(const double* U, const double* isD, CutData cd, const GradArgs& a,
-                        double* dscale, bool fp32, cudaStream_t s) {
-  if (fp32)
-    k_grad_uncut<float><<<grad_blocks_uncut(a.g), dim3(32, 6), 0, s>>>(U, a, dscale);
-  else
-    k_grad_uncut<double><<<grad_blocks_uncut(a.g), dim3(32, 6), 0, s>>>(U, a, dscale);
+                        double* dscale, float* hi, float* lo, cudaStream_t s) {
+  const bool fp32 = hi != nullptr;
+  if (fp32) {
+    const long long n = 6 * a.stride;
+    const long long nb = (n + 255) / 256;
+    k_split_hilo<<<(int)(nb < 8192 ? nb : 8192), 256, 0, s>>>(U, hi, lo, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_grad_uncut<float><<<grad_blocks_uncut(a.g), dim3(32, 6), 0, s>>>(U, hi, lo, a, dscale);
+  } else {
+    k_grad_uncut<double><<<grad_blocks_uncut(a.g), dim3(32, 6), 0, s>>>(U, nullptr, nullptr, a, dscale);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (fp32)
-    k_grad_cut<float><<<grad_blocks_cut(cd.ncut), 64, 0, s>>>(U, isD, cd, a, dscale);
+    k_grad_cut<float><<<grad_blocks_cut(cd.ncut), 64, 0, s>>>(U, hi, lo, isD, cd, a, dscale);
   else
-    k_grad_cut<double><<<grad_blocks_cut(cd.ncut), 64, 0, s>>>(U, isD, cd, a, dscale);
+    k_grad_cut<double><<<grad_blocks_cut(cd.ncut), 64, 0, s>>>(U, nullptr, nullptr, isD, cd, a, dscale);
   return cudaGetLastError();
 }
 

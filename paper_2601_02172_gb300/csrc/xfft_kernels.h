@@ -266,9 +266,10 @@ struct GradArgs {
   int nparts;
   int part_offset_cut;
 };
-// fp32: strain products in FP32 (mixed-precision solver), else all FP64
+// hi, lo (6 * stride floats each, scratch): the mixed-precision solver's gradient (float pairs of U,
+// strain products in FP32); nullptr: all FP64
 cudaError_t launch_grad(const double* U, const double* isD, CutData cd, const GradArgs& a,
-                        double* dscale, bool fp32, cudaStream_t s);
+                        double* dscale, float* hi, float* lo, cudaStream_t s);
 int grad_blocks_uncut(const GridDev& g);
 int grad_blocks_cut(int ncut);
 cudaError_t launch_reduce_partials(const double* partials, int nvals, int nparts, int ncount,

@@ -336,8 +336,9 @@ def test_fp32_refined_effective_stiffness(xf):
 
 
 def test_fp32_refined_gradient(xf):
-    """Mixed-precision solver: FP32 strain products (FP64 differences and sums) stay within the
-    accuracy of the tol-limited solution."""
+    """Mixed-precision solver: standard strains from float-pair node differences, enriched strains
+    from FP64 differences, FP32 strain products and FP64 sums stay within the accuracy of the
+    tol-limited solution."""
     n, ell, L, lm, lp, sc = _case("ragged")
     s = xf.Solver(n, ell, precision="fp32", tol=1e-10)
     s.set_microstructure(L, lm, lp, sc)
