@@ -311,8 +311,14 @@ def traffic_for(kind):
     ent = d.get(kind)
     if not ent:
         return None
-    src = os.path.join(ROOT, "paper_2601_02172_gb300", "csrc", ent["source"])
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    srcs = ent["source"] if isinstance(ent["source"], list) else [ent["source"]]
+    h = hashlib.sha256()
+    for f in srcs:
+        p = os.path.join(ROOT, "paper_2601_02172_gb300", "csrc", f)
+        if not os.path.exists(p):
+            return None
+        h.update(open(p, "rb").read())
+    sha = h.hexdigest()[:16]
     if sha != ent.get("source_sha"):
         return None
     return ent

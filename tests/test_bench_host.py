@@ -35,6 +35,14 @@ def test_traffic_is_used_only_for_the_captured_source(tmp_path, monkeypatch):
     assert bench.traffic_for("other") is None
     (src_dir / "k.cu").write_text("kernel v2")  # the kernel changed since the capture
     assert bench.traffic_for("grp") is None
+    # several source files: the sha covers them in order
+    (src_dir / "h.cuh").write_text("header v1")
+    sha2 = hashlib.sha256(b"kernel v2" + b"header v1").hexdigest()[:16]
+    entry2 = {"kernels": ["k"], "source": ["k.cu", "h.cuh"], "source_sha": sha2, "dram_bytes_per_rhs": 7.0}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"grp": entry2}))
+    assert bench.traffic_for("grp")["dram_bytes_per_rhs"] == 7.0
+    (src_dir / "h.cuh").write_text("header v2")
+    assert bench.traffic_for("grp") is None
 
 
 def test_committed_traffic_entries_name_existing_sources():
@@ -42,4 +50,6 @@ def test_committed_traffic_entries_name_existing_sources():
     for k, ent in d.items():
         if k.startswith("_"):
             continue
-        assert os.path.exists(os.path.join(bench.ROOT, "paper_2601_02172_gb300", "csrc", ent["source"])), k
+        srcs = ent["source"] if isinstance(ent["source"], list) else [ent["source"]]
+        for f in srcs:
+            assert os.path.exists(os.path.join(bench.ROOT, "paper_2601_02172_gb300", "csrc", f)), k
