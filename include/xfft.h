@@ -141,6 +141,14 @@ typedef struct {
                           microstructure at its first solve and keeps the fastest (cached per
                           grid and cut-tet count for the process; see xfft_get_tuning); 0 keeps
                           the defaults */
+  int residual_update; /* FP32_REFINED (iterative refinement with a residual update, not in the
+                          paper): 1 (default) recomputes the residual of the FP64 iterate in
+                          double-word arithmetic until it is below 100 * tol (stopping-rule
+                          measure), and from then on updates it, r_k = r_{k-1} - A delta_k and
+                          <sigma>_k = <sigma>_{k-1} + <C grad^s delta_k>, with the FP32 operator
+                          applied to the last inner solve's correction delta_k: the FP32 rounding
+                          of A delta_k is far below the tolerance once delta_k is that small.
+                          0: every residual recomputed in double-word arithmetic */
 } xfft_options;
 
 typedef struct {
@@ -154,7 +162,8 @@ typedef struct {
 
 /* Fill *opt with the defaults: FP64, tol 1e-10, maxit 10000, snap_tau 0 (=> 1e-6 min h),
  * identity enriched block, inner_tol 1e-5, max_refine 20, poll_every 8, linear CG, cut_cache 0,
- * bb_rule XFFT_BB1, bb_cycle 1, enrichment 1, max_device_bytes 0, spin_limit_ns -1, autotune 1. */
+ * bb_rule XFFT_BB1, bb_cycle 1, enrichment 1, max_device_bytes 0, spin_limit_ns -1, autotune 1,
+ * residual_update 1. */
 xfft_status xfft_default_options(xfft_options* opt);
 
 /* Create a context for one grid.  stream: a cudaStream_t (or NULL for the legacy stream).

@@ -44,7 +44,7 @@ class Options(C.Structure):
                 ("max_refine", C.c_int), ("poll_every", C.c_int), ("scheme", C.c_int),
                 ("step", C.c_double), ("cut_cache", C.c_int), ("bb_rule", C.c_int),
                 ("bb_cycle", C.c_int), ("enrichment", C.c_int), ("max_device_bytes", C.c_longlong),
-                ("spin_limit_ns", C.c_longlong), ("autotune", C.c_int)]
+                ("spin_limit_ns", C.c_longlong), ("autotune", C.c_int), ("residual_update", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -194,7 +194,8 @@ class Solver:
     def __init__(self, n, length=(1.0, 1.0, 1.0), precision="fp64", tol=1e-10, maxit=10000,
                  snap_tau=0.0, inner_tol=1e-5, max_refine=20, poll_every=8, stream=None,
                  enr_precond="identity", scheme="cg", step=0.0, cut_cache=False, bb_rule="bb1",
-                 bb_cycle=1, enrichment=True, max_device_bytes=0, spin_limit_ns=-1, autotune=True):
+                 bb_cycle=1, enrichment=True, max_device_bytes=0, spin_limit_ns=-1, autotune=True,
+                 residual_update=True):
         L = lib()
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
@@ -222,6 +223,7 @@ class Solver:
         o.max_device_bytes = int(max_device_bytes)
         o.spin_limit_ns = int(spin_limit_ns)
         o.autotune = int(bool(autotune))
+        o.residual_update = int(bool(residual_update))
         self.precision = precision
         self.num_phases = 0
         try:

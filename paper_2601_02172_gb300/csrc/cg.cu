@@ -239,7 +239,9 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
   block_sum<7>(v, red, tot);
   if (threadIdx.x != 0) return;
   if (fa.mode == 0) {
-    for (int k = 0; k < 6; ++k) s.sig[k] = tot[1 + k];
+    for (int k = 0; k < 6; ++k) s.sig[k] = (fa.sig_base ? fa.sig_base[6 * rhs + k] : 0.0) + tot[1 + k];
+    if (fa.sig_keep)
+      for (int k = 0; k < 6; ++k) fa.sig_keep[6 * rhs + k] = s.sig[k];
   } else if (fa.mode == 1) {
     const double dq_prev = s.dq;
     s.dq = tot[0];

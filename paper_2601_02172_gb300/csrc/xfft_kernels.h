@@ -215,6 +215,10 @@ struct FinArgs {
   int bb_rule;
   int bb_cycle;
   const double* bbpart;  // [rhs][2][kBBParts]: <d, d> and <A d, A d> partial sums, or nullptr
+  // mode 0: the stress integrals are sig_base[rhs] (a residual update) plus this apply's, or this
+  // apply's alone (sig_base nullptr); they are also recorded in sig_keep[rhs] when given
+  const double* sig_base;
+  double* sig_keep;
 };
 constexpr int kBBParts = 256;
 // <d, d> and <q, q> per right-hand side into part[rhs][2][kBBParts] (Euclidean BB steps)
