@@ -81,7 +81,10 @@ __global__ void __launch_bounds__(256) kz_r2c(T* __restrict__ f, typename Cplx<T
     dst[rl & 1] = v;
   }
   __syncthreads();
-  const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
+  // threads line-minor (consecutive threads on consecutive lines, odd line stride LS): the
+  // Stockham stages then touch distinct shared-memory banks
+  const int nl = blockDim.x / TL;
+  const int line = threadIdx.x % nl, t = threadIdx.x / nl;
   line_fft<C, N, false>(buf + line * LS, tws, t);
   C* sp = spec + rhs * sstride + (long long)c * K2 * n1 * n0 + (long long)j * n0 + i0;
   for (int idx = threadIdx.x; idx < 2 * LPB * K2; idx += blockDim.x) {
@@ -139,7 +142,10 @@ __global__ void __launch_bounds__(256) ky(typename Cplx<T>::type* __restrict__ s
     buf[kk * LS + j] = v[e];
   }
   __syncthreads();
-  const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
+  // threads line-minor (consecutive threads on consecutive lines, odd line stride LS): the
+  // Stockham stages then touch distinct shared-memory banks
+  const int nl = blockDim.x / TL;
+  const int line = threadIdx.x % nl, t = threadIdx.x / nl;
   line_fft<C, N, INV>(buf + line * LS, tws, t);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -204,7 +210,10 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : XFFT_KX_MAXT, sizeof(T)
     }
   }
   __syncthreads();
-  const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
+  // threads line-minor (consecutive threads on consecutive lines, odd line stride LS): the
+  // Stockham stages then touch distinct shared-memory banks
+  const int nl = blockDim.x / TL;
+  const int line = threadIdx.x % nl, t = threadIdx.x / nl;
   line_fft<C, N, false>(buf + line * LS, tws, t);
   const C e1 = ge1[j], s1 = gs1[j], e2 = ge2[k2], s2 = gs2[k2];
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -319,7 +328,10 @@ __global__ void __launch_bounds__(256) kz_c2r(const typename Cplx<T>::type* __re
     }
   }
   __syncthreads();
-  const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
+  // threads line-minor (consecutive threads on consecutive lines, odd line stride LS): the
+  // Stockham stages then touch distinct shared-memory banks
+  const int nl = blockDim.x / TL;
+  const int line = threadIdx.x % nl, t = threadIdx.x / nl;
   line_fft<C, N, true>(buf + line * LS, tws, t);
   const long long N3 = (long long)n0 * n1 * N;
   const T* fr = f + rhs * stride + c * N3;
