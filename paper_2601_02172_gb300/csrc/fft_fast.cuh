@@ -36,7 +36,7 @@ XFFT_PLAN(96, 12, 4, 4, 2, 3)
 XFFT_PLAN(128, 8, 8, 8, 2, 1)
 XFFT_PLAN(192, 24, 8, 8, 3, 1)
 XFFT_PLAN(256, 8, 8, 8, 4, 1)
-XFFT_PLAN(384, 24, 8, 8, 2, 3)
+XFFT_PLAN(384, 12, 4, 4, 4, 6)
 #undef XFFT_PLAN
 // radix sequence for E elements per thread (the default plan, or fewer passes where E allows)
 template <int N, int E>
@@ -161,6 +161,31 @@ struct Dft<C, 5, INV> {
     v[4] = csub(a1, ib1);
     v[2] = cadd(a2, ib2);
     v[3] = csub(a2, ib2);
+  }
+};
+
+// radix 6 = two radix-3 DFTs on even / odd inputs combined with W6^k: X_k = E_k + W6^k O_k,
+// X_{k+3} = E_k - W6^k O_k (k < 3), W6 = exp(-+2 pi i / 6) = 1/2 -+ i sqrt(3)/2
+template <typename C, bool INV>
+struct Dft<C, 6, INV> {
+  __host__ __device__ __forceinline__ static void run(C* v) {
+    typedef decltype(v[0].x) T;
+    const T h = (T)0.5, s = INV ? (T)0.86602540378443864676 : (T)-0.86602540378443864676;
+    C e[3] = {v[0], v[2], v[4]};
+    C o[3] = {v[1], v[3], v[5]};
+    Dft<C, 3, INV>::run(e);
+    Dft<C, 3, INV>::run(o);
+    C w1, w2;  // W6^1 o_1 = (h + i s) o_1, W6^2 o_2 = (-h + i s) o_2
+    w1.x = h * o[1].x - s * o[1].y;
+    w1.y = h * o[1].y + s * o[1].x;
+    w2.x = -h * o[2].x - s * o[2].y;
+    w2.y = -h * o[2].y + s * o[2].x;
+    v[0] = cadd(e[0], o[0]);
+    v[3] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], w1);
+    v[4] = csub(e[1], w1);
+    v[2] = cadd(e[2], w2);
+    v[5] = csub(e[2], w2);
   }
 };
 

@@ -54,7 +54,9 @@ constexpr int RG = XFFT_KXS_RG;            // right-hand sides per x-pass block
 // x pass: elements per thread and block size for x length N0
 template <int N0>
 struct XCfg {
-  static constexpr int EX = N0 == 128 ? 16 : fast::Plan<N0>::E;
+  // elements per thread of an x line (a multiple of every radix of the length's plan), so that
+  // the block stays within 1024 threads
+  static constexpr int EX = N0 == 128 || N0 == 256 ? 16 : N0 == 384 ? 24 : fast::Plan<N0>::E;
   // slots per x-pass block (XFFT_KXS_ST complex values: 8 = one 64-byte segment per plane), fewer
   // where the block would exceed 1024 threads
   static constexpr int ST = 3 * RG * XFFT_KXS_ST * (N0 / EX) <= 1024 ? XFFT_KXS_ST : 8;

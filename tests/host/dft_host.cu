@@ -22,6 +22,7 @@ extern "C" int host_dft(int R, int inv, double* v) {
     case 3: inv ? run<3, true>(v) : run<3, false>(v); return 1;
     case 4: inv ? run<4, true>(v) : run<4, false>(v); return 1;
     case 5: inv ? run<5, true>(v) : run<5, false>(v); return 1;
+    case 6: inv ? run<6, true>(v) : run<6, false>(v); return 1;
     case 8: inv ? run<8, true>(v) : run<8, false>(v); return 1;
     case 16: inv ? run<16, true>(v) : run<16, false>(v); return 1;
     default: return 0;

@@ -764,3 +764,30 @@ def test_residual_update_equals_recomputed_residuals(xf, tol):
     assert stu["refine_steps"] >= 1 and str_["refine_steps"] >= 1, (stu, str_)
     assert np.abs(Cu - Cr).max() < 10 * tol * sc, np.abs(Cu - Cr).max() / sc
     assert np.abs(Cu - C64).max() < 10 * tol * sc + 1e-10 * sc, np.abs(Cu - C64).max() / sc
+
+
+def _axis_modes(rng, n):
+    """Fourier modes of an n0 x n1 x n2 grid: zero and Nyquist frequencies on each axis and in
+    combination, odd frequencies, and random ones."""
+    h = [m // 2 for m in n]
+    ks = [(0, 0, 1), (1, 0, 0), (0, 1, 0), (h[0], 0, 0), (0, h[1], 0), (0, 0, h[2]), (h[0], h[1], h[2]),
+          (3, 5, 7), (h[0] - 1, 1, h[2]), (1, h[1] + 3, 2), (n[0] - 1, n[1] - 1, n[2] - 1), (5, 0, h[2] + 1)]
+    ks += [tuple(int(v) for v in rng.integers(0, n)) for _ in range(12)]
+    return [(k, rng.normal(size=3) + 1j * rng.normal(size=3)) for k in ks]
+
+
+@pytest.mark.parametrize("n", [(384, 16, 16), (16, 384, 16), (16, 16, 384)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_precondition_plane_waves_384(xf, n, prec):
+    """Lines of 384 points (the plan 4 x 4 x 4 x 6 with the radix-6 butterfly) along each axis:
+    the preconditioner against the oracle's exact single-mode values, element by element (x:
+    the y-z plane path's x pass; y, z: the five-pass kernels)."""
+    s = xf.Solver(n)
+    s.set_microstructure(np.ones(n), synth.lame_from_E_nu(2.0, 0.3), synth.lame_from_E_nu(1.0, 0.3))
+    o = XFEM(np.ones(n), n)
+    f, zref = o.precondition_modes(_axis_modes(np.random.default_rng(sum(n)), n))
+    z, rr = s.precondition(f[None, :], precision=prec)
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    assert _rel(z[0], zref) < tol
+    assert np.abs(z[0] - zref).max() < 10 * tol * np.abs(zref).max()
+    assert abs(rr[0] - f @ zref) <= 10 * tol * abs(f @ zref)

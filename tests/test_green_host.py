@@ -86,7 +86,7 @@ def dft(tmp_path_factory):
     return lib
 
 
-@pytest.mark.parametrize("R", [2, 3, 4, 5, 8, 16])
+@pytest.mark.parametrize("R", [2, 3, 4, 5, 6, 8, 16])
 @pytest.mark.parametrize("inv", [0, 1])
 def test_radix_butterflies_are_dfts(dft, R, inv):
     """Each radix-R butterfly of the FFT stages is the length-R DFT, exp(-2 pi i jk/R)
