@@ -231,10 +231,13 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
   const int rhs = blockIdx.x;
   RhsState& s = st[rhs];
   if (!s.active) return;  // uniform per block
-  const int nv = (fa.mode <= 1) ? 7 : 1;
+  const int nv = (fa.mode <= 1) ? 7 : 1;  // values per RHS in the partial rows
+  // an iteration under the relative stopping rule (crit 1) needs <d, A d> alone: the stress
+  // increments (zero there) are not read
+  const int nread = (fa.mode == 1 && fa.crit == 1) ? 1 : nv;
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < ncount; i += blockDim.x)
-    for (int k = 0; k < nv; ++k) v[k] += partials[((long long)rhs * nv + k) * fa.nparts + i];
+    for (int k = 0; k < nread; ++k) v[k] += partials[((long long)rhs * nv + k) * fa.nparts + i];
   double tot[7];
   block_sum<7>(v, red, tot);
   if (threadIdx.x != 0) return;
@@ -336,7 +339,7 @@ __global__ void k_finalize(RhsState* __restrict__ st, int* __restrict__ act,
 
 cudaError_t launch_finalize(RhsState* st, const double* partials, FinArgs fa, int n_rhs, int* act,
                             cudaStream_t s) {
-  k_finalize<<<n_rhs, 256, 0, s>>>(st, act, partials, fa, fa.nparts_used);
+  k_finalize<<<n_rhs, 512, 0, s>>>(st, act, partials, fa, fa.nparts_used);
   return cudaGetLastError();
 }
 

@@ -81,13 +81,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && N == 384) ? 2 : 1) kz_
     dst[rl & 1] = v;
   }
   __syncthreads();
-  // with 8 or more lines per block the threads run line-minor (consecutive threads on
-  // consecutive lines, odd line stride LS: fewer shared-memory bank conflicts in the Stockham
-  // stages); with fewer lines (an x pass of one or two right-hand sides) line-major (measured)
-  const int nl = blockDim.x / TL;
-  const bool lm = nl >= 8;
-  const int line = lm ? threadIdx.x % nl : threadIdx.x / TL;
-  const int t = lm ? threadIdx.x / nl : threadIdx.x - line * TL;
+  const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
   line_fft<C, N, false>(buf + line * LS, tws, t);
   C* sp = spec + rhs * sstride + (long long)c * K2 * n1 * n0 + (long long)j * n0 + i0;
   for (int idx = threadIdx.x; idx < 2 * LPB * K2; idx += blockDim.x) {
@@ -145,13 +139,7 @@ __global__ void __launch_bounds__(256) ky(typename Cplx<T>::type* __restrict__ s
     buf[kk * LS + j] = v[e];
   }
   __syncthreads();
-  // with 8 or more lines per block the threads run line-minor (consecutive threads on
-  // consecutive lines, odd line stride LS: fewer shared-memory bank conflicts in the Stockham
-  // stages); with fewer lines (an x pass of one or two right-hand sides) line-major (measured)
-  const int nl = blockDim.x / TL;
-  const bool lm = nl >= 8;
-  const int line = lm ? threadIdx.x % nl : threadIdx.x / TL;
-  const int t = lm ? threadIdx.x / nl : threadIdx.x - line * TL;
+  const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
   line_fft<C, N, INV>(buf + line * LS, tws, t);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -216,13 +204,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : XFFT_KX_MAXT, sizeof(T)
     }
   }
   __syncthreads();
-  // with 8 or more lines per block the threads run line-minor (consecutive threads on
-  // consecutive lines, odd line stride LS: fewer shared-memory bank conflicts in the Stockham
-  // stages); with fewer lines (an x pass of one or two right-hand sides) line-major (measured)
-  const int nl = blockDim.x / TL;
-  const bool lm = nl >= 8;
-  const int line = lm ? threadIdx.x % nl : threadIdx.x / TL;
-  const int t = lm ? threadIdx.x / nl : threadIdx.x - line * TL;
+  const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
   line_fft<C, N, false>(buf + line * LS, tws, t);
   const C e1 = ge1[j], s1 = gs1[j], e2 = ge2[k2], s2 = gs2[k2];
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -337,13 +319,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && N == 384) ? 2 : 1) kz_
     }
   }
   __syncthreads();
-  // with 8 or more lines per block the threads run line-minor (consecutive threads on
-  // consecutive lines, odd line stride LS: fewer shared-memory bank conflicts in the Stockham
-  // stages); with fewer lines (an x pass of one or two right-hand sides) line-major (measured)
-  const int nl = blockDim.x / TL;
-  const bool lm = nl >= 8;
-  const int line = lm ? threadIdx.x % nl : threadIdx.x / TL;
-  const int t = lm ? threadIdx.x / nl : threadIdx.x - line * TL;
+  const int line = threadIdx.x / TL, t = threadIdx.x - line * TL;
   line_fft<C, N, true>(buf + line * LS, tws, t);
   const long long N3 = (long long)n0 * n1 * N;
   const T* fr = f + rhs * stride + c * N3;
