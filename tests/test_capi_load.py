@@ -40,3 +40,29 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(capi, "_lib", None)
     with pytest.raises(RuntimeError):
         capi.lib()
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc not available")
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structures of the binding have the C header's size and field offsets (a field
+    appended on one side only would shift every later argument)."""
+    import ctypes as C
+    import subprocess
+    from paper_2601_02172_gb300 import capi
+    cases = {"xfft_grid": capi.Grid, "xfft_options": capi.Options, "xfft_stats": capi.Stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "xfft.h"', "int main(void) {"]
+    for cname, cls in cases.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in cases.items():
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
